@@ -1,0 +1,195 @@
+"""FP64 CPU oracle for the CLVisc hydro step -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``clv_oracle.c`` (plain C,
+FP64, ``-ffp-contract=off``), which shares no code with the CUDA library.
+
+The method it follows and every reading of the paper it takes are listed in
+the header of ``clv_oracle.c``.
+
+Parity status per function (what pins it, in ``tests/test_oracle_*.py``):
+  eos (conformal)       closed form and thermodynamic identity
+  eos (table)           numpy.interp on the same nodes
+  prim solve            conformal closed form; brute-force bisection
+  S_T, S_pi             generic Christoffel-symbol evaluation of the covariant
+                        equations (sympy) at random cell states
+  Heun + S_T            ideal Bjorken power law, second-order convergence
+  Heun + S_pi           viscous Bjorken ODE (scipy DOP853 at 1e-12)
+  KT in Milne + Heun    ideal Gubser flow closed form, convergence
+  KT (Cartesian)        Riemann rarefaction closed form, convergence
+  KT conservation       periodic Cartesian box, sum T^{t mu} constant
+  I^{mu nu}, full step  transversality / trace drift shrinking under refinement
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "clv_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libclv_oracle.so")
+_lock = threading.Lock()
+_libs = {}
+
+
+def build(force: bool = False, plant: int = 0) -> str:
+    """Compile the oracle with gcc (OpenMP, strict FP64 evaluation order).
+
+    ``plant`` > 0 builds a separate copy with one deliberate mistake compiled
+    in; only the pin meta-test uses it."""
+    os.makedirs(_BUILD, exist_ok=True)
+    lib = _LIB if plant == 0 else os.path.join(_BUILD, f"libclv_oracle_plant{plant}.so")
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+               "-fopenmp", "-fPIC", "-shared", f"-DPLANT={int(plant)}", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, lib)
+    return lib
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("neta", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("deta", ctypes.c_double),
+        ("tau0", ctypes.c_double), ("dtau", ctypes.c_double),
+        ("eta_over_s", ctypes.c_double),
+        ("eos_kind", ctypes.c_int), ("eos_n", ctypes.c_int),
+        ("eos_lne0", ctypes.c_double), ("eos_dlne", ctypes.c_double),
+        ("eos_P", ctypes.POINTER(ctypes.c_double)),
+        ("eos_T", ctypes.POINTER(ctypes.c_double)),
+        ("eos_cs2", ctypes.POINTER(ctypes.c_double)),
+        ("cartesian", ctypes.c_int), ("periodic", ctypes.c_int),
+        ("eps_cut", ctypes.c_double), ("nthreads", ctypes.c_int),
+    ]
+
+
+def _load(plant: int = 0):
+    with _lock:
+        if plant not in _libs:
+            lib = ctypes.CDLL(build(plant=plant))
+            P = ctypes.c_void_p
+            D = ctypes.POINTER(ctypes.c_double)
+            lib.orc_create.restype = P
+            lib.orc_create.argtypes = [ctypes.POINTER(_Config)]
+            lib.orc_destroy.argtypes = [P]
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
+            lib.orc_set_threads.restype = ctypes.c_int
+            lib.orc_set_initial.argtypes = [P, D, D, D, D, D]
+            lib.orc_step.argtypes = [P, ctypes.c_int]
+            lib.orc_get.argtypes = [P, ctypes.c_int, D]
+            lib.orc_stats.argtypes = [P, D]
+            lib.orc_eos.argtypes = [P, ctypes.c_double, D]
+            lib.orc_prim.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, D]
+            lib.orc_source_pi.argtypes = [P, ctypes.c_double, D, D, D, ctypes.c_double, D]
+            lib.orc_source_T.argtypes = [P, ctypes.c_double, D, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, D]
+            _libs[plant] = lib
+    return _libs[plant]
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+FIELD_INDEX = {"eps": 0, "ux": 1, "uy": 2, "ueta": 3,
+               "Ttt": 4, "Ttx": 5, "Tty": 6, "Tte": 7,
+               **{f"pi{k}": 8 + i for i, k in enumerate(
+                   ["tt", "tx", "ty", "te", "xx", "xy", "xe", "yy", "ye", "ee"])},
+               "upx": 18, "upy": 19, "upe": 20}
+
+
+class Oracle:
+    """One event on the CPU.  ``eos`` is None (conformal) or a dict with keys
+    ``lne0, dlne, P, T, cs2`` (nodes uniform in ln eps)."""
+
+    def __init__(self, nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
+                 cartesian=False, periodic=False, eps_cut=1e-7, nthreads=0, plant=0):
+        self._lib = _load(plant)
+        c = _Config()
+        c.nx, c.ny, c.neta = int(nx), int(ny), int(neta)
+        c.dx, c.dy, c.deta = float(dx), float(dy), float(deta)
+        c.tau0, c.dtau = float(tau0), float(dtau)
+        c.eta_over_s = float(eta_over_s)
+        self._keep = []
+        if eos is None:
+            c.eos_kind = 0
+        else:
+            c.eos_kind = 1
+            arrs = [np.ascontiguousarray(eos[k], dtype=np.float64) for k in ("P", "T", "cs2")]
+            self._keep += arrs
+            c.eos_n = len(arrs[0])
+            c.eos_lne0, c.eos_dlne = float(eos["lne0"]), float(eos["dlne"])
+            c.eos_P, c.eos_T, c.eos_cs2 = (_dp(a) for a in arrs)
+        c.cartesian, c.periodic = int(bool(cartesian)), int(bool(periodic))
+        c.eps_cut, c.nthreads = float(eps_cut), int(nthreads)
+        self.shape = (int(nx), int(ny), int(neta))
+        self._h = self._lib.orc_create(ctypes.byref(c))
+        if not self._h:
+            raise ValueError("oracle rejected the configuration")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.orc_destroy(h)
+            self._h = None
+
+    def set_initial(self, eps, ux, uy, ueta, pi=None):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(self.shape) for a in (eps, ux, uy, ueta)]
+        pi_arr = None
+        if pi is not None:
+            pi_arr = np.ascontiguousarray(pi, dtype=np.float64).reshape((10,) + self.shape)
+        self._lib.orc_set_initial(self._h, *(_dp(a) for a in arrs),
+                                  _dp(pi_arr) if pi_arr is not None else None)
+
+    def step(self, n=1):
+        return self._lib.orc_step(self._h, int(n))
+
+    def get(self, name):
+        out = np.empty(self.shape, dtype=np.float64)
+        if self._lib.orc_get(self._h, FIELD_INDEX[name], _dp(out)) != 0:
+            raise KeyError(name)
+        return out
+
+    def fields(self):
+        return {k: self.get(k) for k in FIELD_INDEX}
+
+    def stats(self):
+        out = np.zeros(8)
+        self._lib.orc_stats(self._h, _dp(out))
+        keys = ["tau", "step", "eps_max", "T_max", "E_tot", "n_rescaled", "n_rootfail", "_"]
+        return dict(zip(keys, out.tolist()))
+
+    def eos(self, e):
+        out = np.zeros(3)
+        self._lib.orc_eos(self._h, float(e), _dp(out))
+        return tuple(out)
+
+    def prim(self, E, Mx, My, Me):
+        out = np.zeros(6)
+        self._lib.orc_prim(self._h, float(E), float(Mx), float(My), float(Me), _dp(out))
+        return out
+
+    def source_pi(self, tau, u, du, pi, e):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        du = np.ascontiguousarray(du, dtype=np.float64).reshape(16)
+        pi = np.ascontiguousarray(pi, dtype=np.float64)
+        out = np.zeros(10)
+        self._lib.orc_source_pi(self._h, float(tau), _dp(u), _dp(du), _dp(pi), float(e), _dp(out))
+        return out
+
+    def source_T(self, tau, u, e, piee, Tte):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        out = np.zeros(4)
+        self._lib.orc_source_T(self._h, float(tau), _dp(u), float(e), float(piee), float(Tte), _dp(out))
+        return out
+
+
+def set_threads(n: int) -> int:
+    return _load().orc_set_threads(int(n))

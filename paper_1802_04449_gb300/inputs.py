@@ -1,0 +1,285 @@
+"""Seeded synthetic inputs shared by the oracle and the CUDA path.
+
+Nothing here is part of the hydro method: these functions only build initial
+conditions and the equation-of-state table that both implementations receive
+as inputs.  The paper's workloads (Trento / AMPT events, lattice and HRG EOS
+tables) are not available; the generators below stand in for them with the
+same shapes, scales and structure.
+
+Units: lengths in fm, energy density in GeV/fm^3, temperature in GeV.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+HBARC = 0.1973269804  # GeV fm
+DOF_CONF = 47.5       # degeneracy of the conformal u, d, s + gluon gas
+
+
+def cell_coords(n: int, d: float) -> np.ndarray:
+    """Cell centres x_i = (i - (n-1)/2) d."""
+    return (np.arange(n) - (n - 1) / 2.0) * d
+
+
+# --------------------------------------------------------------------------
+# equation of state tables
+# --------------------------------------------------------------------------
+def conformal_T(eps):
+    """Temperature of the conformal gas with eps = 3 g pi^2 T^4 / (90 (hbar c)^3)."""
+    eps = np.asarray(eps, dtype=np.float64)
+    return np.where(eps > 0, (30.0 * HBARC ** 3 * np.maximum(eps, 0) / (DOF_CONF * math.pi ** 2)) ** 0.25, 0.0)
+
+
+def crossover_cs2(eps):
+    """Synthetic crossover: c_s^2(eps) = 1/3 - 0.2 exp(-ln^2(eps/0.5)/2)."""
+    eps = np.asarray(eps, dtype=np.float64)
+    return 1.0 / 3.0 - 0.2 * np.exp(-0.5 * np.log(eps / 0.5) ** 2)
+
+
+def crossover_eos_table(n: int = 4096, eps_lo: float = 1e-7, eps_hi: float = 1e4, oversample: int = 64):
+    """Thermodynamically consistent stand-in for a lattice/HRG crossover EOS.
+
+    P = int_0^eps c_s^2, ln s = int d eps/(eps + P) + const, T = (eps + P)/s,
+    with the constant fixed so that T matches the conformal gas at eps = 1e3.
+    Returns nodes uniform in ln(eps): dict(lne0, dlne, P, T, cs2, eps).
+    """
+    lne0, lne1 = math.log(eps_lo), math.log(eps_hi)
+    m = (n - 1) * oversample + 1
+    x = np.linspace(lne0, lne1, m)
+    e = np.exp(x)
+    cs2 = crossover_cs2(e)
+    # P(eps_lo) from c_s^2 = 1/3 below the first node (the Gaussian term is
+    # ~exp(-118) there), then cumulative Simpson-like trapezoid in ln(eps).
+    integrand = cs2 * e
+    P = np.empty(m)
+    P[0] = eps_lo / 3.0
+    P[1:] = P[0] + np.cumsum(0.5 * (integrand[1:] + integrand[:-1]) * np.diff(x))
+    g = e / (e + P)
+    lns = np.empty(m)
+    lns[0] = 0.0
+    lns[1:] = np.cumsum(0.5 * (g[1:] + g[:-1]) * np.diff(x))
+    Tref = float(conformal_T(1e3))
+    lns_ref = np.interp(math.log(1e3), x, lns)
+    P_ref = np.interp(math.log(1e3), x, P)
+    # T = (eps + P)/s  ->  s_ref = (1e3 + P_ref)/Tref at eps = 1e3
+    s = np.exp(lns - lns_ref) * (1e3 + P_ref) / Tref
+    T = (e + P) / s
+    sel = slice(0, m, oversample)
+    dlne = (lne1 - lne0) / (n - 1)
+    return {"lne0": lne0, "dlne": dlne, "P": P[sel].copy(), "T": T[sel].copy(),
+            "cs2": cs2[sel].copy(), "eps": e[sel].copy()}
+
+
+# --------------------------------------------------------------------------
+# analytic-solution initial conditions
+# --------------------------------------------------------------------------
+def gubser_ideal(tau, x, y, q=1.0, eps_norm=10.0):
+    """Ideal conformal Gubser flow (Sec. 5, Eqs. conformal, visc_gubser with
+    lambda_1 -> infinity): eps = C (2q)^{8/3} tau^{-4/3} /
+    [1 + 2 q^2 (tau^2 + r^2) + q^4 (tau^2 - r^2)^2]^{4/3}, outward
+    v_perp = 2 q^2 tau r / (1 + q^2 tau^2 + q^2 r^2).  C is fixed so that
+    eps(tau=1 fm, r=0) = eps_norm.  Returns eps, u~^x, u~^y."""
+    def raw(t, r2):
+        return (2 * q) ** (8.0 / 3.0) * t ** (-4.0 / 3.0) / (
+            1 + 2 * q * q * (t * t + r2) + q ** 4 * (t * t - r2) ** 2) ** (4.0 / 3.0)
+    C = eps_norm / raw(1.0, 0.0)
+    X, Y = np.meshgrid(x, y, indexing="ij")
+    r2 = X * X + Y * Y
+    r = np.sqrt(r2)
+    eps = C * raw(tau, r2)
+    vr = 2 * q * q * tau * r / (1 + q * q * tau * tau + q * q * r2)
+    gam = 1.0 / np.sqrt(1 - vr * vr)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        cx = np.where(r > 0, X / r, 0.0)
+        cy = np.where(r > 0, Y / r, 0.0)
+    return eps, gam * vr * cx, gam * vr * cy
+
+
+def riemann_1d(nx, dx, eps0=10.0, t0=0.0):
+    """Step initial condition along x (Sec. 5, Eq. riemann): eps0 for x <= 0,
+    vacuum for x > 0, fluid at rest."""
+    x = cell_coords(nx, dx)
+    eps = np.where(x <= 1e-12, eps0, 0.0)
+    return x, eps
+
+
+def riemann_exact(zeta, eps0, cs):
+    """Rarefaction solution of Eq. (riemann) as a function of zeta = x/t."""
+    zeta = np.asarray(zeta, dtype=np.float64)
+    out = np.zeros_like(zeta)
+    left = zeta <= -cs
+    mid = (zeta > -cs) & (zeta < 1.0)
+    out[left] = eps0
+    z = zeta[mid]
+    out[mid] = eps0 * (((1 - cs) / (1 + cs)) * (1 - z) / (1 + z)) ** ((1 + cs * cs) / (2 * cs))
+    return out
+
+
+# --------------------------------------------------------------------------
+# hot-spot event initial conditions (stand-in for Trento / AMPT events)
+# --------------------------------------------------------------------------
+WS_R, WS_A, WS_RHO0 = 6.62, 0.546, 0.17  # Pb Woods-Saxon
+
+
+def _thickness_table(R=WS_R, a=WS_A, rho0=WS_RHO0, rmax=20.0, nr=801, nz=1601):
+    r = np.linspace(0.0, rmax, nr)
+    z = np.linspace(-rmax, rmax, nz)
+    rr = np.sqrt(r[:, None] ** 2 + z[None, :] ** 2)
+    rho = rho0 / (1.0 + np.exp((rr - R) / a))
+    Tz = np.trapezoid(rho, z, axis=1)
+    return r, Tz
+
+
+_TTAB = None
+
+
+def thickness(x, y):
+    global _TTAB
+    if _TTAB is None:
+        _TTAB = _thickness_table()
+    r, T = _TTAB
+    return np.interp(np.sqrt(x * x + y * y), r, T, right=0.0)
+
+
+def h_eta(eta, eta_w=2.0, sigma_eta=1.8):
+    """Longitudinal envelope of Eq. (h_eta)."""
+    eta = np.abs(np.asarray(eta, dtype=np.float64))
+    d = np.maximum(eta - eta_w, 0.0)
+    return np.exp(-d * d / (2 * sigma_eta ** 2))
+
+
+def n_binary_weight(b):
+    """Integral of T_A(x+b/2, y) T_B(x-b/2, y): relative binary-collision count."""
+    g = np.linspace(-15, 15, 301)
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    return float(np.sum(thickness(X + b / 2, Y) * thickness(X - b / 2, Y)) * (g[1] - g[0]) ** 2)
+
+
+def sample_spots(rng, n_spots, b, eta_max, eta_w=2.0, sigma_eta=1.8):
+    """Spot centres: transverse by rejection from T_A(x+b/2,y) T_B(x-b/2,y),
+    eta_s from H(|eta|), clipped to the grid."""
+    fmax = float(thickness(np.array(0.0), np.array(0.0))) ** 2 * 1.0001
+    xs, ys = [], []
+    lim = WS_R + 4 * WS_A
+    while len(xs) < n_spots:
+        m = max(4 * (n_spots - len(xs)), 256)
+        x = rng.uniform(-lim, lim, m)
+        y = rng.uniform(-lim, lim, m)
+        f = thickness(x + b / 2, y) * thickness(x - b / 2, y)
+        acc = rng.uniform(0, fmax, m) < f
+        xs.extend(x[acc].tolist())
+        ys.extend(y[acc].tolist())
+    xs = np.array(xs[:n_spots])
+    ys = np.array(ys[:n_spots])
+    etas = []
+    while len(etas) < n_spots:
+        m = max(4 * (n_spots - len(etas)), 256)
+        e = rng.uniform(0, eta_max, m)
+        acc = rng.uniform(0, 1, m) < h_eta(e, eta_w, sigma_eta)
+        etas.extend(e[acc].tolist())
+    etas = np.array(etas[:n_spots]) * np.where(rng.uniform(size=n_spots) < 0.5, -1.0, 1.0)
+    return xs, ys, etas
+
+
+def deposit_spots(nx, ny, neta, dx, dy, deta, xs, ys, etas, amp, sigma_r=0.6, sigma_eta=0.6,
+                  weights=None):
+    """Sum of Gaussians sum_s w_s amp exp(-r^2/2 sigma_r^2 - (eta-eta_s)^2/2 sigma_eta^2)."""
+    x = cell_coords(nx, dx)
+    y = cell_coords(ny, dy)
+    eta = cell_coords(neta, deta)
+    out = np.zeros((nx, ny, neta))
+    w = np.ones(len(xs)) if weights is None else np.asarray(weights)
+    cut = 5.0
+    for s in range(len(xs)):
+        ix = np.nonzero(np.abs(x - xs[s]) < cut * sigma_r)[0]
+        iy = np.nonzero(np.abs(y - ys[s]) < cut * sigma_r)[0]
+        ie = np.nonzero(np.abs(eta - etas[s]) < cut * sigma_eta)[0]
+        if len(ix) == 0 or len(iy) == 0 or len(ie) == 0:
+            continue
+        gx = np.exp(-(x[ix] - xs[s]) ** 2 / (2 * sigma_r ** 2))
+        gy = np.exp(-(y[iy] - ys[s]) ** 2 / (2 * sigma_r ** 2))
+        ge = np.exp(-(eta[ie] - etas[s]) ** 2 / (2 * sigma_eta ** 2))
+        out[np.ix_(ix, iy, ie)] += w[s] * amp * gx[:, None, None] * gy[None, :, None] * ge[None, None, :]
+    return out
+
+
+@dataclass
+class HydroCase:
+    """A complete seeded event: grid, run parameters, EOS and initial fields."""
+    name: str
+    nx: int
+    ny: int
+    neta: int
+    dx: float
+    dy: float
+    deta: float
+    tau0: float
+    dtau: float
+    eta_over_s: float
+    eos: dict | None
+    eps: np.ndarray
+    ux: np.ndarray
+    uy: np.ndarray
+    ueta: np.ndarray
+    nsteps: int
+    cartesian: bool = False
+    periodic: bool = False
+
+    @property
+    def ncells(self):
+        return self.nx * self.ny * self.neta
+
+
+_EOS_CACHE = {}
+
+
+def crossover_eos():
+    if "x" not in _EOS_CACHE:
+        _EOS_CACHE["x"] = crossover_eos_table()
+    return _EOS_CACHE["x"]
+
+
+def hotspot_event(nx=97, ny=97, neta=41, dx=0.2, deta=0.2, b=7.0, n_spots=2048, eps_max=55.0,
+                  seed=12345, tau0=0.4, dtau=0.01, eta_over_s=0.08, nsteps=400, eos="crossover",
+                  name="viscous hot-spot event"):
+    """Gaussian hot spots placed from Woods-Saxon thickness at impact parameter
+    b; zero initial velocity and pi; amplitude such that max eps = eps_max."""
+    rng = np.random.default_rng(seed)
+    eta_half = (neta - 1) / 2.0 * deta
+    xs, ys, etas = sample_spots(rng, n_spots, b, eta_half)
+    eps = deposit_spots(nx, ny, neta, dx, dx, deta, xs, ys, etas, 1.0)
+    eps *= eps_max / eps.max()
+    z = np.zeros_like(eps)
+    return HydroCase(name, nx, ny, neta, dx, dx, deta, tau0, dtau, eta_over_s,
+                     crossover_eos() if eos == "crossover" else None,
+                     eps, z.copy(), z.copy(), z.copy(), nsteps)
+
+
+def gubser_case(dx=0.3, nx=33, neta=9, deta=0.3, dtau=0.02, tau0=1.0, tau1=3.0, q=1.0):
+    """Ideal Gubser flow, conformal EOS, eta/s = 0 (the 33x33x9 check)."""
+    x = cell_coords(nx, dx)
+    eps2, ux2, uy2 = gubser_ideal(tau0, x, x, q)
+    rep = lambda a: np.repeat(a[:, :, None], neta, axis=2)
+    nsteps = int(round((tau1 - tau0) / dtau))
+    return HydroCase("ideal Gubser flow", nx, nx, neta, dx, dx, deta, tau0, dtau, 0.0, None,
+                     rep(eps2), rep(ux2), rep(uy2), np.zeros((nx, nx, neta)), nsteps)
+
+
+def random_smooth_box(rng, nx, ny, neta, eps_mean=5.0, amp=0.3, vamp=0.2, modes=3):
+    """Smooth periodic random fields for closed-box runs (Cartesian mode)."""
+    def field(a0, a):
+        X, Y, Z = np.meshgrid(np.arange(nx) / nx, np.arange(ny) / ny, np.arange(neta) / neta, indexing="ij")
+        f = np.full((nx, ny, neta), a0, dtype=np.float64)
+        for _ in range(modes):
+            kx, ky, kz = rng.integers(0, 2, 3)
+            ph = rng.uniform(0, 2 * np.pi)
+            f += a * rng.uniform(-1, 1) * np.cos(2 * np.pi * (kx * X + ky * Y + kz * Z) + ph)
+        return f
+    eps = field(eps_mean, amp * eps_mean)
+    ux = field(0.0, vamp)
+    uy = field(0.0, vamp)
+    ue = field(0.0, vamp)
+    return eps, ux, uy, ue

@@ -1,0 +1,36 @@
+"""Meta-test: each pin must catch a plausible mistake.
+
+The oracle is rebuilt with one deliberate mistake (compile-time PLANT=n, on
+the CPU only) and at least one pin must then fail:
+  1 I^{mu nu} sign flipped               -> transversality drift
+  2 pi~ u~^tau/tau sign flipped           -> viscous Bjorken ODE
+  3 S_T^tau sign flipped (as printed)     -> Bjorken power law
+  4 eta flux divisor without tau          -> linearised eta wave
+  5 transposed gradient in sigma          -> transversality drift
+  6 Christoffel term of nabla_eta u^eta   -> transversality drift / Bjorken
+  7 S_T^eta dropped                       -> linearised eta wave
+  8 EOS argument E instead of E - M v     -> brute-force root solve (Gubser flow)
+"""
+import numpy as np
+import pytest
+
+import oracle
+import test_oracle_flows as F
+
+CASES = {
+    1: F.check_transversality,
+    2: F.check_bjorken_viscous,
+    3: F.check_bjorken_ideal,
+    4: F.check_eta_wave,
+    5: F.check_transversality,
+    6: F.check_bjorken_viscous,
+    7: F.check_eta_wave,
+    8: F.check_gubser,
+}
+
+
+@pytest.mark.parametrize("plant", sorted(CASES))
+def test_pin_catches_planted_mistake(plant):
+    CASES[plant](plant=0)            # the correct oracle passes
+    with pytest.raises(AssertionError):
+        CASES[plant](plant=plant)    # the broken one fails
