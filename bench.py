@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Benchmark: hydro cell-updates/s of one Heun step of (3+1)D viscous hydro
+in Milne coordinates on GB300, through libclv's C ABI.
+
+Workload (default): the viscous hot-spot event -- 97x97x41 cells, dx = dy =
+d_eta = 0.2, dtau = 0.01 fm, tau0 = 0.4 fm, eta/s = 0.08, 2048 Gaussian hot
+spots from Woods-Saxon thickness at b = 7 fm, synthetic crossover EOS table
+(4096 nodes), zero initial velocity.  A step is one full Heun step (both
+stages: KT fluxes, Milne and shear sources, pi update, primitive recovery)
+over the grid; one cell-update is one cell advanced by one step.
+
+value:  device-resident throughput of the FP32 path (the FP64 path is timed on
+        the same grid and reported beside it).  The state (~71 MB in FP32)
+        fits in L2, so a 512 MiB buffer is written between timed steps
+        (L2 flushed; the flush is outside the timed intervals).
+e2e:    the same metric through the public API with host buffers: upload of
+        the initial state from pinned memory, K steps, download of eps and u~.
+With --gpus N (torchrun), each rank evolves its own event (seed + rank):
+independent problems, no data-path collective, weak scaling.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "hydro cell-updates/s on GB300, FP32+learned vs FP64, % HBM roofline"
+UNIT = "cell-updates/s"
+WORDS_STAGE1 = 39   # read T~ 4, pi~ 10, prim 4, u^{n-1} 3; write T~' 4, pi~' 10, prim' 4
+WORDS_STAGE2 = 56   # read T~' 4, pi~' 10, prim' 4, T~^n 4, pi~^n 10, u^n 3, u^{n-1} 3; write 18
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload(seed_offset=0):
+    from paper_1802_04449_gb300 import inputs as I
+    return I.hotspot_event(seed=12345 + seed_offset)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1802_04449_gb300 import build as B
+    from paper_1802_04449_gb300 import clv
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    B.build()
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    case = workload(rank)
+    N = case.ncells
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    def timed_run(precision, steps, warmup, kernel_timing=False):
+        g = clv.from_case(case, precision)
+        g.set_initial(case.eps, case.ux, case.uy, case.ueta)
+        g.step(warmup)
+        torch.cuda.synchronize()
+        g.enable_kernel_timing(kernel_timing)
+        stream = g.stream
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.fill_(i & 0xFF)                    # evict the state from L2 (not timed)
+            evs[i][0].record(stream)
+            g.step(1)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        kt = g.kernel_times() if kernel_timing else None
+        st = g.stats()
+        g.close()
+        return ms, kt, st
+
+    # ---- FP32 path: the headline value, with per-kernel event timing
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    ms32, kt, st32 = timed_run(clv.CLV_FP32, args.steps, args.warmup, kernel_timing=True)
+    clocks = sampler.stop()
+    # ---- FP64 path on the same grid (fewer steps: it is ALU-bound)
+    steps64 = max(3, args.steps // 4)
+    ms64, _, st64 = timed_run(clv.CLV_FP64, steps64, args.warmup)
+
+    t_local = torch.tensor([ms32, ms64], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms32_max, ms64_max = t_local.tolist()
+    value = ws * N * args.steps / (ms32_max / 1e3)
+    value64 = ws * N * steps64 / (ms64_max / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (case.eps, case.ux, case.uy, case.ueta)]
+        out = torch.empty((4, N), dtype=torch.float64).pin_memory()
+        g = clv.from_case(case, clv.CLV_FP32)
+        host_in = [p.numpy() for p in pinned]
+        g.set_initial(*host_in)                      # warm-up
+        g.step(args.warmup)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        g.set_initial(*host_in)
+        stt = g.step(args.steps, stats=True)
+        g.get(["eps", "ux", "uy", "ueta"], out=out.numpy())
+        t1 = time.perf_counter()
+        g.close()
+        et = torch.tensor([t1 - t0], dtype=torch.float64, device=dev)
+        if ws > 1:
+            dist.all_reduce(et, op=dist.ReduceOp.MAX)
+        e2e = {"value": ws * N * args.steps / et.item(), "unit": UNIT,
+               "h2d_bytes_per_step": 4 * N * 8 / args.steps,
+               "d2h_bytes_per_step": (4 * N * 8 + 64) / args.steps,
+               "includes": "H2D of the initial state (pinned), the first-step ideal predictor, "
+                           f"{args.steps} steps, stats read-back, D2H of eps and u~"}
+
+    # ---- roofline of the dominant kernel (stage 2), from live event timing
+    peak, peak_kind = measured_peaks()
+    (ms_s1, ms_s2), (n1, n2) = kt
+    word = 4
+    bytes_s1 = WORDS_STAGE1 * word * N
+    bytes_s2 = WORDS_STAGE2 * word * N
+    dom = 2 if ms_s2 >= ms_s1 else 1
+    avg = (ms_s2 / n2) if dom == 2 else (ms_s1 / n1)
+    alg = bytes_s2 if dom == 2 else bytes_s1
+    achieved = alg / (avg / 1e3) / 1e9
+    traffic = load_traffic(dom)
+    roof = {"bound": "hbm", "kernel": f"stage_kernel<float,{dom},visc>", "achieved": achieved,
+            "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic,
+            "algorithmic_bytes_per_launch": alg,
+            "stage_ms_avg": [ms_s1 / max(n1, 1), ms_s2 / max(n2, 1)],
+            "step_bytes_per_cell_update": (WORDS_STAGE1 + WORDS_STAGE2) * word,
+            "step_frac_of_peak": (value / ws) * (WORDS_STAGE1 + WORDS_STAGE2) * word / 1e9 / peak}
+
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "viscous hot-spot event 97x97x41, eta/s=0.08, crossover EOS table 4096, "
+                               "2048 spots, b=7 fm, dtau=0.01 fm",
+                   "cells_per_event": N, "events_per_gpu": 1, "precision": "fp32 stencil, fp64 root polish + reductions",
+                   "l2": "flushed between timed steps (512 MiB write, untimed)",
+                   "parallelism": f"independent events, {ws} rank(s)"},
+        "fp64": {"value": value64, "unit": UNIT, "steps": steps64, "ms_per_step": ms64_max / steps64},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "stats_fp32": {k: st32[k] for k in ("tau", "eps_max", "T_max", "E_tot", "n_polished", "error_word")},
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(res))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def load_traffic(dom):
+    """dram bytes per launch of the dominant kernel from the committed ncu
+    summary (profiles/stage_kernel_traffic.json), if it matches this kernel."""
+    p = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        v = d.get(f"stage{dom}_dram_bytes_per_launch_full_size")
+        return float(v) if v is not None else None
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_baseline(budget_s):
+    """The FP64 oracle as it stands, all host cores, bounded sample of the
+    same workload: as many steps as fit in ~budget_s seconds (at least 2)."""
+    import oracle
+    case = workload(0)
+    ncores = os.cpu_count() or 1
+    oracle.set_threads(ncores)
+    o = oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
+                      case.eta_over_s, case.eos, nthreads=ncores)
+    o.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < 2 or (time.perf_counter() - t0 < budget_s and steps < 200):
+        o.step(1)
+        steps += 1
+    dt = time.perf_counter() - t0
+    return {"value": case.ncells * steps / dt, "unit": UNIT, "cores": ncores, "kind": "oracle",
+            "sample": f"{steps} full steps of the 97x97x41 event ({case.ncells} cells) in {dt:.1f} s, FP64, "
+                      f"OpenMP over cells"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    case = workload(0)
+    ncores = os.cpu_count() or 1
+    oracle.set_threads(ncores)
+    o = oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
+                      case.eta_over_s, case.eos, nthreads=ncores)
+    o.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    steps = max(1, min(args.steps, 20))
+    warm = max(0, min(args.warmup, 2))
+    o.step(warm)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    v = case.ncells * steps / dt
+    sample = f"{steps} full steps of the 97x97x41 event after {warm} warm-up steps, FP64, OpenMP over cells"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": steps,
+        "warmup": warm, "ms_per_step": dt / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "viscous hot-spot event 97x97x41, eta/s=0.08, crossover EOS table 4096, "
+                               "2048 spots, b=7 fm, dtau=0.01 fm", "implementation": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": ncores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="clv", choices=["clv", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

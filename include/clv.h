@@ -1,0 +1,168 @@
+/*
+ * clv.h -- C ABI of the GB300 (sm_103a) library for the space-time evolution
+ * of (3+1)D second-order viscous hydrodynamics in Milne coordinates
+ * (tau, x, y, eta_s), the CLVisc method of Pang, Petersen and Wang.
+ *
+ * What one step computes (the paper's Sec. 2 and Sec. 3):
+ *   state: T~^{tau mu} (4), pi~^{mu nu} (10 symmetric components) and the
+ *   primitives eps, u~^x, u~^y, u~^eta of the tilde variables of Sec. 2;
+ *   one Heun / two-stage Runge-Kutta step of Sec. 3 with
+ *     - Kurganov-Tadmor central fluxes with a minmod limiter, Eqs. (kt),
+ *       (flux_out),
+ *     - the Milne geometric sources S_T and the Israel-Stewart shear source
+ *       S_pi with the Christoffel terms I^{mu nu} of Eq. (Ipi),
+ *     - the velocity predictor u* = 2u^n - u^{n-1} (first step from one ideal
+ *       step),
+ *     - recovery of (eps, u) from T_ideal = T - pi by a per-cell root solve
+ *       with an equation-of-state table,
+ *     - the vacuum cutoff eps < eps_cut -> eps = 0 (Sec. 5).
+ *
+ * Conventions shared by every entry point:
+ *   - Grid arrays are (nx, ny, neta) in C order, eta_s fastest; cell centres
+ *     are x_i = (i - (nx-1)/2) dx, likewise for y and eta_s.
+ *   - Units: fm, GeV/fm^3, GeV.
+ *   - Host arrays are owned by the caller and only read or written during
+ *     the call.  Device memory is owned by the handle (or by the caller when
+ *     a workspace is passed to clv_create_ws).
+ *   - Every call returns a status and never aborts the process.  A failing
+ *     call leaves a message for clv_last_error.  Kernel-side errors (root
+ *     solve cap, non-finite values) accumulate in a device word that the next
+ *     synchronising call reports.
+ *   - A handle is used by one host thread at a time.  All work is enqueued
+ *     on the stream given at creation; calls that return host data
+ *     synchronise that stream.
+ */
+#ifndef CLV_H
+#define CLV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CLV_OK = 0,
+  CLV_EINVAL = 1,      /* invalid argument or configuration */
+  CLV_ENOMEM = 2,      /* device allocation failed / workspace too small */
+  CLV_ECUDA = 3,       /* a CUDA runtime call failed */
+  CLV_EROOT = 4,       /* a primitive root solve hit its iteration cap */
+  CLV_ENONFINITE = 5,  /* a non-finite value appeared in the state */
+  CLV_ETIMEOUT = 6     /* a bounded device wait gave up */
+} clv_status;
+
+enum { CLV_FP64 = 0, CLV_FP32 = 1 };
+enum { CLV_EOS_CONFORMAL = 0, CLV_EOS_TABLE = 1 };
+
+/* Run configuration.  Pointers are read during clv_create only. */
+typedef struct {
+  int nx, ny, neta;          /* cells per axis, each >= 1 */
+  double dx, dy, deta;       /* spacings (fm, fm, 1) */
+  double tau0, dtau;         /* initial proper time and step h (fm) */
+  double eta_over_s;         /* shear viscosity over entropy; 0 = ideal (pi ignored) */
+  int eos_kind;              /* CLV_EOS_CONFORMAL: P = eps/3, eps = 3 g pi^2 T^4/90 (hbar c)^3, g = 47.5
+                                CLV_EOS_TABLE: P, T, c_s^2 tabulated at nodes uniform in ln eps */
+  int eos_n;                 /* number of table nodes (>= 2) */
+  double eos_lne0;           /* ln(eps) of node 0 */
+  double eos_dlne;           /* node spacing in ln(eps) */
+  const double* eos_P;       /* host, eos_n values; copied */
+  const double* eos_T;       /* host, eos_n values (GeV); copied */
+  const double* eos_cs2;     /* host, eos_n values; copied */
+  int precision;             /* CLV_FP64 or CLV_FP32 (FP32 stencil; FP64 root polish near
+                                vacuum and at high velocity; FP64 reductions) */
+  int cartesian;             /* 1: Christoffel terms off and tau factors 1 (t, x, y, z) */
+  int periodic;              /* 1: periodic boundaries; 0: zero-gradient (outflow) */
+  double eps_cut;            /* vacuum cutoff, GeV/fm^3 (the paper uses 1e-7) */
+} clv_config;
+
+/* Per-run statistics, filled by clv_step / clv_get_stats. */
+typedef struct {
+  double tau;                /* proper time after the last step */
+  int64_t step;              /* completed steps */
+  double eps_max;            /* max eps over the grid (GeV/fm^3) */
+  double T_max;              /* temperature at eps_max (GeV); stopping rule input */
+  double E_tot;              /* sum of T~^{tau tau} dx dy deta, FP64 accumulated */
+  int64_t n_rescaled;        /* cells with |M| > E rescaled before the root solve */
+  int64_t n_rootfail;        /* root solves that hit the iteration cap */
+  int64_t n_polished;        /* FP32 path: cells refined by the FP64 Newton step */
+  uint32_t error_word;       /* bit 0 root cap, bit 1 non-finite, bit 2 wait timeout */
+  uint32_t _pad;
+} clv_stats;
+
+typedef struct clv_handle clv_handle;
+
+/* Device bytes a handle needs for this configuration (fields, stage buffers,
+ * EOS table, reduction scratch).  Returns CLV_EINVAL for a bad config. */
+clv_status clv_workspace_bytes(const clv_config* cfg, size_t* bytes);
+
+/* Create a handle.  cuda_stream is a cudaStream_t (NULL = default stream).
+ * The library allocates the device workspace itself. */
+clv_status clv_create(const clv_config* cfg, void* cuda_stream, clv_handle** out);
+
+/* Same, with a caller-owned device workspace of at least
+ * clv_workspace_bytes bytes, 256-byte aligned, that must outlive the handle. */
+clv_status clv_create_ws(const clv_config* cfg, void* cuda_stream, void* device_ws,
+                         size_t ws_bytes, clv_handle** out);
+
+/* Load the initial state at tau0 from primitives.  eps, ux, uy, ueta: host
+ * arrays of nx*ny*neta doubles (u~^eta = tau u^eta); pi: host array of
+ * 10*nx*ny*neta doubles (components tt tx ty te xx xy xe yy ye ee of pi~,
+ * each a full grid) or NULL for pi = 0.  Cells with eps < eps_cut become
+ * vacuum.  For eta_over_s > 0 this also runs the pi-free first step that
+ * fixes u^{-1} (Sec. 3).  Resets tau and the step count. */
+clv_status clv_set_initial(clv_handle* h, const double* eps, const double* ux, const double* uy,
+                           const double* ueta, const double* pi);
+
+/* Same as clv_set_initial with the five inputs already in device memory
+ * (doubles, same layout); nothing is copied from the host. */
+clv_status clv_set_initial_device(clv_handle* h, const double* d_eps, const double* d_ux,
+                                  const double* d_uy, const double* d_ueta, const double* d_pi);
+
+/* Advance nsteps Heun steps.  If stats is not NULL the call synchronises and
+ * fills it; otherwise it only enqueues work and returns.  Returns CLV_EROOT /
+ * CLV_ENONFINITE when the device error word is set (checked only when stats
+ * is requested). */
+clv_status clv_step(clv_handle* h, int nsteps, clv_stats* stats);
+
+/* Synchronise and report statistics of the current state. */
+clv_status clv_get_stats(clv_handle* h, clv_stats* stats);
+
+/* Field indices for clv_get_fields (bit i of the mask selects field i):
+ *   0 eps, 1 u~^x, 2 u~^y, 3 u~^eta,
+ *   4..7 T~^{tau mu} (mu = tau, x, y, eta),
+ *   8..17 pi~ (tt tx ty te xx xy xe yy ye ee),
+ *   18..20 u~^{x,y,eta} of the previous step.
+ * host_out receives popcount(mask) grids of nx*ny*neta doubles, in
+ * increasing field order.  Synchronises. */
+clv_status clv_get_fields(clv_handle* h, uint32_t mask, double* host_out);
+
+/* Same into device memory (doubles); enqueued, no synchronisation. */
+clv_status clv_get_fields_device(clv_handle* h, uint32_t mask, double* device_out);
+
+/* Proper time and step count of the current state (host-side bookkeeping). */
+clv_status clv_get_time(const clv_handle* h, double* tau, int64_t* step);
+
+/* Instrumentation.  While enabled, CUDA events are recorded on the handle's
+ * stream around every stage-kernel launch of clv_step (at most 16384 steps
+ * between two reads).  clv_get_kernel_times synchronises and returns the
+ * accumulated device milliseconds and launch counts per stage kernel
+ * (index 0: stage 1, index 1: stage 2), then resets them. */
+clv_status clv_enable_kernel_timing(clv_handle* h, int enable);
+clv_status clv_get_kernel_times(clv_handle* h, double ms[2], int64_t launches[2]);
+
+/* Release the handle and the memory it owns.  NULL is ignored. */
+void clv_destroy(clv_handle* h);
+
+/* Message of the last failing call on this handle ("" if none).  With
+ * h == NULL: the last failure of clv_create / clv_create_ws. */
+const char* clv_last_error(const clv_handle* h);
+
+/* Library version string. */
+const char* clv_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLV_H */

@@ -1,0 +1,252 @@
+"""Thin ctypes binding of libclv (include/clv.h).  Argument marshalling only:
+every step of the hydro path runs in the library's CUDA kernels.  PyTorch
+provides the device workspace and the stream.
+
+There is no CPU fallback: if libclv.so is missing or cannot be loaded, the
+first use raises RuntimeError.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libclv.so")
+
+CLV_FP64, CLV_FP32 = 0, 1
+CLV_EOS_CONFORMAL, CLV_EOS_TABLE = 0, 1
+STATUS = {0: "CLV_OK", 1: "CLV_EINVAL", 2: "CLV_ENOMEM", 3: "CLV_ECUDA", 4: "CLV_EROOT",
+          5: "CLV_ENONFINITE", 6: "CLV_ETIMEOUT"}
+
+FIELDS = ["eps", "ux", "uy", "ueta", "Ttt", "Ttx", "Tty", "Tte",
+          "pitt", "pitx", "pity", "pite", "pixx", "pixy", "pixe", "piyy", "piye", "piee",
+          "upx", "upy", "upe"]
+FIELD_BIT = {k: i for i, k in enumerate(FIELDS)}
+
+
+class clv_config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("neta", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("deta", ctypes.c_double),
+        ("tau0", ctypes.c_double), ("dtau", ctypes.c_double),
+        ("eta_over_s", ctypes.c_double),
+        ("eos_kind", ctypes.c_int), ("eos_n", ctypes.c_int),
+        ("eos_lne0", ctypes.c_double), ("eos_dlne", ctypes.c_double),
+        ("eos_P", ctypes.POINTER(ctypes.c_double)),
+        ("eos_T", ctypes.POINTER(ctypes.c_double)),
+        ("eos_cs2", ctypes.POINTER(ctypes.c_double)),
+        ("precision", ctypes.c_int), ("cartesian", ctypes.c_int), ("periodic", ctypes.c_int),
+        ("eps_cut", ctypes.c_double),
+    ]
+
+
+class clv_stats(ctypes.Structure):
+    _fields_ = [
+        ("tau", ctypes.c_double), ("step", ctypes.c_int64),
+        ("eps_max", ctypes.c_double), ("T_max", ctypes.c_double), ("E_tot", ctypes.c_double),
+        ("n_rescaled", ctypes.c_int64), ("n_rootfail", ctypes.c_int64), ("n_polished", ctypes.c_int64),
+        ("error_word", ctypes.c_uint32), ("_pad", ctypes.c_uint32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "_pad"}
+
+
+class ClvError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initial",
+            "clv_set_initial_device", "clv_step", "clv_get_stats", "clv_get_fields",
+            "clv_get_fields_device", "clv_get_time", "clv_enable_kernel_timing", "clv_get_kernel_times",
+            "clv_destroy", "clv_last_error", "clv_version"]
+
+
+def load(path: str | None = None):
+    """Load libclv.so (built by paper_1802_04449_gb300.build).  Raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libclv.so not found at {p}; run paper_1802_04449_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(p)
+        P, V = ctypes.c_void_p, ctypes.c_void_p
+        D = ctypes.POINTER(ctypes.c_double)
+        cfgp = ctypes.POINTER(clv_config)
+        lib.clv_workspace_bytes.argtypes = [cfgp, ctypes.POINTER(ctypes.c_size_t)]
+        lib.clv_create.argtypes = [cfgp, V, ctypes.POINTER(P)]
+        lib.clv_create_ws.argtypes = [cfgp, V, V, ctypes.c_size_t, ctypes.POINTER(P)]
+        lib.clv_set_initial.argtypes = [P, D, D, D, D, D]
+        lib.clv_set_initial_device.argtypes = [P, V, V, V, V, V]
+        lib.clv_step.argtypes = [P, ctypes.c_int, ctypes.POINTER(clv_stats)]
+        lib.clv_get_stats.argtypes = [P, ctypes.POINTER(clv_stats)]
+        lib.clv_get_fields.argtypes = [P, ctypes.c_uint32, D]
+        lib.clv_get_fields_device.argtypes = [P, ctypes.c_uint32, V]
+        lib.clv_get_time.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
+        lib.clv_enable_kernel_timing.argtypes = [P, ctypes.c_int]
+        lib.clv_get_kernel_times.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
+        lib.clv_destroy.argtypes = [P]
+        lib.clv_destroy.restype = None
+        lib.clv_last_error.argtypes = [P]
+        lib.clv_last_error.restype = ctypes.c_char_p
+        lib.clv_version.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name not in ("clv_destroy", "clv_last_error", "clv_version"):
+                getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
+                precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7):
+    c = clv_config()
+    c.nx, c.ny, c.neta = int(nx), int(ny), int(neta)
+    c.dx, c.dy, c.deta = float(dx), float(dy), float(deta)
+    c.tau0, c.dtau, c.eta_over_s = float(tau0), float(dtau), float(eta_over_s)
+    keep = []
+    if eos is None:
+        c.eos_kind = CLV_EOS_CONFORMAL
+    else:
+        c.eos_kind = CLV_EOS_TABLE
+        arrs = [np.ascontiguousarray(eos[k], dtype=np.float64) for k in ("P", "T", "cs2")]
+        keep += arrs
+        c.eos_n = len(arrs[0])
+        c.eos_lne0, c.eos_dlne = float(eos["lne0"]), float(eos["dlne"])
+        c.eos_P, c.eos_T, c.eos_cs2 = (_dp(a) for a in arrs)
+    c.precision = int(precision)
+    c.cartesian, c.periodic = int(bool(cartesian)), int(bool(periodic))
+    c.eps_cut = float(eps_cut)
+    return c, keep
+
+
+class Hydro:
+    """One event on the GPU through the C ABI.  The device workspace is a
+    torch uint8 tensor; work goes to ``stream`` (default: torch's current)."""
+
+    def __init__(self, nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
+                 precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7,
+                 stream=None, device=None, torch_workspace=True):
+        import torch
+        self._lib = load()
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        self.cfg, self._keep = make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s, eos,
+                                           precision, cartesian, periodic, eps_cut)
+        self.shape = (int(nx), int(ny), int(neta))
+        self.N = int(nx) * int(ny) * int(neta)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = ctypes.c_size_t()
+        self._check(self._lib.clv_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(nbytes)), None)
+        self.ws_bytes = nbytes.value
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            if torch_workspace:
+                self._ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+                st = self._lib.clv_create_ws(ctypes.byref(self.cfg), ctypes.c_void_p(self.stream.cuda_stream),
+                                             ctypes.c_void_p(self._ws.data_ptr()), self.ws_bytes,
+                                             ctypes.byref(h))
+            else:
+                self._ws = None
+                st = self._lib.clv_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.stream.cuda_stream),
+                                          ctypes.byref(h))
+        self._check(st, None)
+        self._h = h
+
+    def _check(self, st, h):
+        if st != 0:
+            msg = self._lib.clv_last_error(h)
+            raise ClvError(st, msg.decode() if msg else "")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.clv_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_initial(self, eps, ux, uy, ueta, pi=None):
+        t = self.torch
+        if isinstance(eps, t.Tensor) and eps.is_cuda:
+            arrs = [a.to(t.float64).contiguous() for a in (eps, ux, uy, ueta)]
+            pi_t = pi.to(t.float64).contiguous() if pi is not None else None
+            self._dev_keep = arrs + ([pi_t] if pi_t is not None else [])
+            st = self._lib.clv_set_initial_device(self._h, *(ctypes.c_void_p(a.data_ptr()) for a in arrs),
+                                                  ctypes.c_void_p(pi_t.data_ptr()) if pi_t is not None else None)
+        else:
+            arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(self.shape)) for a in (eps, ux, uy, ueta)]
+            pa = None
+            if pi is not None:
+                pa = np.ascontiguousarray(np.asarray(pi, dtype=np.float64).reshape((10,) + self.shape))
+            st = self._lib.clv_set_initial(self._h, *(_dp(a) for a in arrs), _dp(pa) if pa is not None else None)
+        self._check(st, self._h)
+
+    def step(self, n=1, stats=False):
+        s = clv_stats()
+        st = self._lib.clv_step(self._h, int(n), ctypes.byref(s) if stats else None)
+        self._check(st, self._h)
+        return s.as_dict() if stats else None
+
+    def stats(self):
+        s = clv_stats()
+        self._check(self._lib.clv_get_stats(self._h, ctypes.byref(s)), self._h)
+        return s.as_dict()
+
+    def time(self):
+        tau = ctypes.c_double()
+        step = ctypes.c_int64()
+        self._lib.clv_get_time(self._h, ctypes.byref(tau), ctypes.byref(step))
+        return tau.value, step.value
+
+    def enable_kernel_timing(self, on=True):
+        self._check(self._lib.clv_enable_kernel_timing(self._h, int(bool(on))), self._h)
+
+    def kernel_times(self):
+        """(ms[stage1], ms[stage2]), (launches[stage1], launches[stage2]) since the last read."""
+        ms = (ctypes.c_double * 2)()
+        n = (ctypes.c_int64 * 2)()
+        self._check(self._lib.clv_get_kernel_times(self._h, ms, n), self._h)
+        return (ms[0], ms[1]), (n[0], n[1])
+
+    @staticmethod
+    def mask_of(names):
+        m = 0
+        for n in names:
+            m |= 1 << FIELD_BIT[n]
+        return m
+
+    def get(self, names=None, out=None):
+        """Host copy of the named fields: dict name -> (nx, ny, neta) float64.
+        ``out`` may be a preallocated (len(names), N) float64 array (pinned or not)."""
+        names = list(FIELDS if names is None else ([names] if isinstance(names, str) else names))
+        names = sorted(names, key=lambda k: FIELD_BIT[k])
+        buf = out if out is not None else np.empty((len(names), self.N), dtype=np.float64)
+        self._check(self._lib.clv_get_fields(self._h, self.mask_of(names), _dp(buf)), self._h)
+        return {k: buf[i].reshape(self.shape) for i, k in enumerate(names)}
+
+    def get_device(self, names):
+        t = self.torch
+        names = sorted(list(names), key=lambda k: FIELD_BIT[k])
+        out = t.empty((len(names), self.N), dtype=t.float64, device=self.device)
+        self._check(self._lib.clv_get_fields_device(self._h, self.mask_of(names),
+                                                    ctypes.c_void_p(out.data_ptr())), self._h)
+        return {k: out[i].view(self.shape) for i, k in enumerate(names)}
+
+
+def from_case(case, precision=CLV_FP64, **kw):
+    """Hydro handle for an inputs.HydroCase (grid, spacings, times, EOS)."""
+    return Hydro(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
+                 case.eta_over_s, case.eos, precision, case.cartesian, case.periodic, **kw)

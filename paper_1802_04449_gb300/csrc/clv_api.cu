@@ -1,0 +1,573 @@
+// clv_api.cu -- host implementation of the C ABI declared in include/clv.h.
+// Owns the device layout, buffer rotation and kernel launches of the Heun
+// step (two stage kernels per step); all arithmetic of the method runs in
+// the kernels of clv_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/clv.h"
+#include "clv_kernels.cuh"
+
+using namespace clv;
+
+namespace {
+
+std::string g_create_error;
+
+constexpr int kNumPrimSets = 3;
+constexpr int kPrimFields = 6;  // e, ux, uy, ueta, P, cs
+
+struct DevStats {
+  double esum;
+  double T_at_emax;
+  unsigned long long emax_bits;
+  unsigned long long counters[4];  // rescaled, root cap, polished, spare
+  unsigned int err;
+  unsigned int pad;
+};
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct clv_handle {
+  clv_config cfg;
+  cudaStream_t stream = nullptr;
+  bool own_ws = false;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  long long N = 0;
+  int rsize = 8;
+  bool viscous = false;
+  int nblocks = 0;
+  // device arrays (typed at use)
+  void* T0[4];
+  void* PI0[10];
+  void* T1[4];
+  void* PI1[10];
+  void* PR[kNumPrimSets][kPrimFields];
+  int cur = 0, prev = 1;
+  void* eos[3];
+  double* staging = nullptr;      // N doubles
+  double* block_sum = nullptr;    // nblocks doubles
+  DevStats* dstats = nullptr;
+  double tau = 0.0;
+  long long step = 0;
+  bool initialized = false;
+  std::string last_error;
+  // kernel timing (instrumentation)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<cudaEvent_t> ev_pending;  // triples: before stage 1, between, after stage 2
+  double t_ms[2] = {0.0, 0.0};
+  long long t_launches[2] = {0, 0};
+};
+
+namespace {
+
+clv_status fail(clv_handle* h, clv_status s, const std::string& msg) {
+  if (h) h->last_error = msg; else g_create_error = msg;
+  return s;
+}
+
+#define CLV_CUDA(h, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail((h), CLV_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+  } while (0)
+
+clv_status validate(const clv_config* c) {
+  if (!c) return fail(nullptr, CLV_EINVAL, "config is NULL");
+  if (c->nx < 1 || c->ny < 1 || c->neta < 1) return fail(nullptr, CLV_EINVAL, "grid dims must be >= 1");
+  if (!(c->dx > 0 && c->dy > 0 && c->deta > 0 && c->dtau > 0))
+    return fail(nullptr, CLV_EINVAL, "spacings and dtau must be > 0");
+  if (!c->cartesian && !(c->tau0 > 0)) return fail(nullptr, CLV_EINVAL, "tau0 must be > 0 in Milne coordinates");
+  if (!(c->eta_over_s >= 0)) return fail(nullptr, CLV_EINVAL, "eta_over_s must be >= 0");
+  if (c->precision != CLV_FP64 && c->precision != CLV_FP32) return fail(nullptr, CLV_EINVAL, "unknown precision");
+  if (c->eos_kind == CLV_EOS_TABLE) {
+    if (c->eos_n < 2 || !c->eos_P || !c->eos_T || !c->eos_cs2 || !(c->eos_dlne > 0))
+      return fail(nullptr, CLV_EINVAL, "EOS table needs eos_n >= 2, eos_dlne > 0 and P, T, cs2 arrays");
+  } else if (c->eos_kind != CLV_EOS_CONFORMAL) {
+    return fail(nullptr, CLV_EINVAL, "unknown eos_kind");
+  }
+  if (!(c->eps_cut >= 0)) return fail(nullptr, CLV_EINVAL, "eps_cut must be >= 0");
+  long long N = (long long)c->nx * c->ny * c->neta;
+  if (N > (1LL << 34)) return fail(nullptr, CLV_EINVAL, "grid too large");
+  return CLV_OK;
+}
+
+size_t layout(const clv_config* c, clv_handle* h) {
+  const long long N = (long long)c->nx * c->ny * c->neta;
+  const size_t rs = c->precision == CLV_FP64 ? 8 : 4;
+  const size_t fb = align_up((size_t)N * rs, 256);
+  const int nblocks = (int)((N + kBlock - 1) / kBlock);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes, 256); return o; };
+  size_t oT0[4], oPI0[10], oT1[4], oPI1[10], oPR[kNumPrimSets][kPrimFields], oE[3];
+  for (int m = 0; m < 4; ++m) oT0[m] = take(fb);
+  for (int q = 0; q < 10; ++q) oPI0[q] = take(fb);
+  for (int m = 0; m < 4; ++m) oT1[m] = take(fb);
+  for (int q = 0; q < 10; ++q) oPI1[q] = take(fb);
+  for (int s = 0; s < kNumPrimSets; ++s)
+    for (int f = 0; f < kPrimFields; ++f) oPR[s][f] = take(fb);
+  const int ne = c->eos_kind == CLV_EOS_TABLE ? c->eos_n : 1;
+  for (int t = 0; t < 3; ++t) oE[t] = take((size_t)ne * rs);
+  size_t oStage = take((size_t)N * 8);
+  size_t oBlock = take((size_t)nblocks * 8);
+  size_t oStats = take(sizeof(DevStats));
+  if (h) {
+    char* b = h->ws;
+    for (int m = 0; m < 4; ++m) { h->T0[m] = b + oT0[m]; h->T1[m] = b + oT1[m]; }
+    for (int q = 0; q < 10; ++q) { h->PI0[q] = b + oPI0[q]; h->PI1[q] = b + oPI1[q]; }
+    for (int s = 0; s < kNumPrimSets; ++s)
+      for (int f = 0; f < kPrimFields; ++f) h->PR[s][f] = b + oPR[s][f];
+    for (int t = 0; t < 3; ++t) h->eos[t] = b + oE[t];
+    h->staging = (double*)(b + oStage);
+    h->block_sum = (double*)(b + oBlock);
+    h->dstats = (DevStats*)(b + oStats);
+    h->nblocks = nblocks;
+    h->N = N;
+    h->rsize = (int)rs;
+  }
+  return off;
+}
+
+template <typename R> Prim<R> prim_set(clv_handle* h, int s) {
+  Prim<R> p;
+  p.e = (R*)h->PR[s][0];
+  for (int m = 0; m < 3; ++m) p.u[m] = (R*)h->PR[s][1 + m];
+  p.P = (R*)h->PR[s][4];
+  p.cs = (R*)h->PR[s][5];
+  return p;
+}
+
+template <typename R> EosView<R> eos_view(const clv_handle* h) {
+  const clv_config& c = h->cfg;
+  EosView<R> v;
+  v.kind = c.eos_kind;
+  v.n = c.eos_kind == CLV_EOS_TABLE ? c.eos_n : 1;
+  v.lne0 = c.eos_lne0;
+  v.inv_dlne = c.eos_kind == CLV_EOS_TABLE ? 1.0 / c.eos_dlne : 0.0;
+  v.e0 = std::exp(c.eos_lne0);
+  v.e_top = std::exp(c.eos_lne0 + (v.n - 1) * c.eos_dlne);
+  const double pi = 3.14159265358979323846;
+  v.t_coef = 30.0 * kHbarC * kHbarC * kHbarC / (kDofConformal * pi * pi);
+  v.P = (const R*)h->eos[0];
+  v.T = (const R*)h->eos[1];
+  v.cs2 = (const R*)h->eos[2];
+  return v;
+}
+
+inline unsigned grid_of(long long N) { return (unsigned)((N + kBlock - 1) / kBlock); }
+
+template <typename R>
+StageParams<R> stage_params(clv_handle* h, int stage, double tau_stage, double tau_new) {
+  const clv_config& c = h->cfg;
+  StageParams<R> p;
+  const int st = 3 - h->cur - h->prev;
+  const Prim<R> pcur = prim_set<R>(h, h->cur), pprev = prim_set<R>(h, h->prev), pst = prim_set<R>(h, st);
+  const bool s1 = stage == 1;
+  for (int m = 0; m < 4; ++m) {
+    p.T[m] = (const R*)(s1 ? h->T0[m] : h->T1[m]);
+    p.Tn[m] = (const R*)h->T0[m];
+    p.Tout[m] = (R*)(s1 ? h->T1[m] : h->T0[m]);
+  }
+  for (int q = 0; q < 10; ++q) {
+    p.pi[q] = (const R*)(s1 ? h->PI0[q] : h->PI1[q]);
+    p.pin[q] = (const R*)h->PI0[q];
+    p.piout[q] = (R*)(s1 ? h->PI1[q] : h->PI0[q]);
+  }
+  p.pr = s1 ? pcur : pst;
+  for (int m = 0; m < 3; ++m) { p.un[m] = pcur.u[m]; p.up[m] = pprev.u[m]; }
+  p.prout = s1 ? pst : pprev;
+  p.eos = eos_view<R>(h);
+  p.nx = c.nx; p.ny = c.ny; p.ne = c.neta; p.periodic = c.periodic;
+  p.N = h->N;
+  p.taus = c.cartesian ? 1.0 : tau_stage;
+  p.geo = c.cartesian ? 0.0 : 1.0 / tau_stage;
+  p.taus_new = c.cartesian ? 1.0 : tau_new;
+  p.h = c.dtau;
+  p.inv_dl[0] = 1.0 / c.dx;
+  p.inv_dl[1] = 1.0 / c.dy;
+  p.inv_dl[2] = 1.0 / (p.taus * c.deta);
+  p.st_tau = c.cartesian ? 0.0 : 1.0;
+  p.eps_cut = c.eps_cut;
+  p.eta_over_s = c.eta_over_s;
+  p.polish_E = 1e-2;
+  p.polish_v = 0.9;
+  p.block_sum = h->block_sum;
+  p.emax_bits = &h->dstats->emax_bits;
+  p.counters = h->dstats->counters;
+  p.err = &h->dstats->err;
+  return p;
+}
+
+constexpr size_t kMaxTimedSteps = 16384;
+
+cudaEvent_t timing_event(clv_handle* h) {
+  cudaEvent_t e = nullptr;
+  if (!h->ev_pool.empty()) {
+    e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    return nullptr;
+  }
+  cudaEventRecord(e, h->stream);
+  h->ev_pending.push_back(e);
+  return e;
+}
+
+template <typename R, bool VISC>
+void launch_step(clv_handle* h, bool stats) {
+  const double tn = h->tau, tn1 = h->tau + h->cfg.dtau;
+  const unsigned g = grid_of(h->N);
+  const bool timed = h->timing && h->ev_pending.size() < 3 * kMaxTimedSteps;
+  if (timed) timing_event(h);
+  StageParams<R> p1 = stage_params<R>(h, 1, tn, tn1);
+  stage_kernel<R, 1, VISC, false><<<g, kBlock, 0, h->stream>>>(p1);
+  if (timed) timing_event(h);
+  StageParams<R> p2 = stage_params<R>(h, 2, tn1, tn1);
+  if (stats) stage_kernel<R, 2, VISC, true><<<g, kBlock, 0, h->stream>>>(p2);
+  else stage_kernel<R, 2, VISC, false><<<g, kBlock, 0, h->stream>>>(p2);
+  if (timed) timing_event(h);
+  std::swap(h->cur, h->prev);
+  h->tau = tn1;
+  h->step += 1;
+}
+
+template <typename R> __global__ void stats_scan_kernel(const R* e, const R* T0, long long N, double* block_sum,
+                                                        unsigned long long* emax_bits) {
+  __shared__ double s_sum[kBlock / 32], s_max[kBlock / 32];
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double a = 0.0, b = 0.0;
+  if (c < N) { a = (double)T0[c]; b = (double)e[c]; }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+  }
+  if ((threadIdx.x & 31) == 0) { s_sum[threadIdx.x >> 5] = a; s_max[threadIdx.x >> 5] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) { x += s_sum[w]; y = fmax(y, s_max[w]); }
+    block_sum[blockIdx.x] = x;
+    if (y > 0.0) atomicMax(emax_bits, (unsigned long long)__double_as_longlong(y));
+  }
+}
+
+template <typename R> __global__ void finalize_stats_kernel(DevStats* ds, EosView<R> eos) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double e = __longlong_as_double((long long)ds->emax_bits);
+    double P, T, c2;
+    eos_eval<double, R>(eos, e, P, T, c2);
+    ds->T_at_emax = T;
+  }
+}
+
+template <typename R> clv_status reduce_stats(clv_handle* h, bool scan, clv_stats* out) {
+  // the fused stage-2 launch (scan == false) already wrote block_sum and emax
+  if (scan) {
+    CLV_CUDA(h, cudaMemsetAsync(&h->dstats->emax_bits, 0, sizeof(unsigned long long), h->stream));
+    stats_scan_kernel<R><<<grid_of(h->N), kBlock, 0, h->stream>>>(
+        (const R*)h->PR[h->cur][0], (const R*)h->T0[0], h->N, h->block_sum, &h->dstats->emax_bits);
+  }
+  finalize_sum_kernel<<<1, 1024, 0, h->stream>>>(h->block_sum, h->nblocks, &h->dstats->esum);
+  finalize_stats_kernel<R><<<1, 32, 0, h->stream>>>(h->dstats, eos_view<R>(h));
+  CLV_CUDA(h, cudaGetLastError());
+  DevStats ds;
+  CLV_CUDA(h, cudaMemcpyAsync(&ds, h->dstats, sizeof(DevStats), cudaMemcpyDeviceToHost, h->stream));
+  CLV_CUDA(h, cudaStreamSynchronize(h->stream));
+  const clv_config& c = h->cfg;
+  out->tau = h->tau;
+  out->step = h->step;
+  std::memcpy(&out->eps_max, &ds.emax_bits, sizeof(double));
+  out->T_max = ds.T_at_emax;
+  out->E_tot = ds.esum * c.dx * c.dy * c.deta;
+  out->n_rescaled = (int64_t)ds.counters[0];
+  out->n_rootfail = (int64_t)ds.counters[1];
+  out->n_polished = (int64_t)ds.counters[2];
+  out->error_word = ds.err;
+  out->_pad = 0;
+  if (ds.err & 2u) return fail(h, CLV_ENONFINITE, "non-finite value in the state");
+  if (ds.err & 1u) return fail(h, CLV_EROOT, "primitive root solve hit its iteration cap");
+  if (ds.err & 4u) return fail(h, CLV_ETIMEOUT, "a bounded device wait gave up");
+  return CLV_OK;
+}
+
+template <typename R> __global__ void convert_kernel(const double* s, R* d, long long N) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < N) d[c] = (R)s[c];
+}
+
+template <typename R>
+clv_status set_initial_impl(clv_handle* h, const double* const in[4], const double* pi, bool host) {
+  const long long N = h->N;
+  const unsigned g = grid_of(N);
+  const clv_config& c = h->cfg;
+  Prim<R> pc = prim_set<R>(h, h->cur), pp = prim_set<R>(h, h->prev);
+  // inputs -> R-typed fields (through the staging buffer for host inputs)
+  R* dst_prim[4] = {pc.e, pc.u[0], pc.u[1], pc.u[2]};
+  for (int f = 0; f < 4; ++f) {
+    const double* src = in[f];
+    if (host) {
+      CLV_CUDA(h, cudaMemcpyAsync(h->staging, src, (size_t)N * 8, cudaMemcpyHostToDevice, h->stream));
+      src = h->staging;
+    }
+    convert_kernel<R><<<g, kBlock, 0, h->stream>>>(src, dst_prim[f], N);
+  }
+  Ptr10<R> pi0;
+  for (int q = 0; q < 10; ++q) pi0.p[q] = (R*)h->PI0[q];
+  for (int q = 0; q < 10; ++q) {
+    if (pi && h->viscous) {
+      const double* src = pi + (size_t)q * N;
+      if (host) {
+        CLV_CUDA(h, cudaMemcpyAsync(h->staging, src, (size_t)N * 8, cudaMemcpyHostToDevice, h->stream));
+        src = h->staging;
+      }
+      convert_kernel<R><<<g, kBlock, 0, h->stream>>>(src, pi0.p[q], N);
+    } else {
+      CLV_CUDA(h, cudaMemsetAsync(pi0.p[q], 0, (size_t)N * sizeof(R), h->stream));
+    }
+  }
+  init_primitives_kernel<R><<<g, kBlock, 0, h->stream>>>(pc, pp, pi0, h->viscous, eos_view<R>(h), c.eps_cut, N);
+  const double taus0 = c.cartesian ? 1.0 : c.tau0;
+  h->tau = c.tau0;
+  h->step = 0;
+  R* T0[4] = {(R*)h->T0[0], (R*)h->T0[1], (R*)h->T0[2], (R*)h->T0[3]};
+  if (h->viscous) {
+    // Sec. 3: the first u* comes from one ideal (pi-free) Heun step
+    tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(pc, pi0, false, T0[0], T0[1], T0[2], T0[3], taus0, N);
+    launch_step<R, false>(h, false);
+    std::swap(h->cur, h->prev);  // undo the rotation: cur = u^0, prev = u^1_ideal
+    extrapolate_prev_kernel<R><<<g, kBlock, 0, h->stream>>>(prim_set<R>(h, h->cur), prim_set<R>(h, h->prev), N);
+    h->tau = c.tau0;
+    h->step = 0;
+    tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(prim_set<R>(h, h->cur), pi0, true, T0[0], T0[1], T0[2],
+                                                   T0[3], taus0, N);
+  } else {
+    tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(pc, pi0, false, T0[0], T0[1], T0[2], T0[3], taus0, N);
+  }
+  CLV_CUDA(h, cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream));
+  CLV_CUDA(h, cudaGetLastError());
+  h->initialized = true;
+  return CLV_OK;
+}
+
+template <typename R> clv_status export_field(clv_handle* h, int which, double* dst) {
+  const void* src = nullptr;
+  if (which <= 3) src = h->PR[h->cur][which];
+  else if (which <= 7) src = h->T0[which - 4];
+  else if (which <= 17) src = h->PI0[which - 8];
+  else src = h->PR[h->prev][1 + (which - 18)];
+  export_kernel<R><<<grid_of(h->N), kBlock, 0, h->stream>>>((const R*)src, dst, h->N);
+  CLV_CUDA(h, cudaGetLastError());
+  return CLV_OK;
+}
+
+clv_status create_common(const clv_config* cfg, void* stream, void* ws, size_t ws_bytes, clv_handle** out) {
+  if (!out) return fail(nullptr, CLV_EINVAL, "out is NULL");
+  *out = nullptr;
+  clv_status s = validate(cfg);
+  if (s != CLV_OK) return s;
+  clv_handle* h = new clv_handle();
+  h->cfg = *cfg;
+  h->cfg.eos_P = h->cfg.eos_T = h->cfg.eos_cs2 = nullptr;
+  h->stream = (cudaStream_t)stream;
+  h->viscous = cfg->eta_over_s > 0.0;
+  const size_t need = layout(cfg, nullptr);
+  if (ws) {
+    if (ws_bytes < need || ((uintptr_t)ws & 255u)) {
+      delete h;
+      return fail(nullptr, CLV_ENOMEM, "workspace too small or not 256-byte aligned");
+    }
+    h->ws = (char*)ws;
+    h->own_ws = false;
+  } else {
+    cudaError_t e = cudaMalloc((void**)&h->ws, need);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(nullptr, CLV_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->own_ws = true;
+  }
+  h->ws_bytes = need;
+  layout(cfg, h);
+  h->tau = cfg->tau0;
+  // EOS table in the working precision
+  if (cfg->eos_kind == CLV_EOS_TABLE) {
+    const int n = cfg->eos_n;
+    const double* src[3] = {cfg->eos_P, cfg->eos_T, cfg->eos_cs2};
+    for (int t = 0; t < 3; ++t) {
+      if (h->rsize == 8) {
+        cudaError_t e = cudaMemcpyAsync(h->eos[t], src[t], (size_t)n * 8, cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) { clv_destroy(h); return fail(nullptr, CLV_ECUDA, cudaGetErrorString(e)); }
+      } else {
+        float* tmp = new float[n];
+        for (int i = 0; i < n; ++i) tmp[i] = (float)src[t][i];
+        cudaError_t e = cudaMemcpy(h->eos[t], tmp, (size_t)n * 4, cudaMemcpyHostToDevice);
+        delete[] tmp;
+        if (e != cudaSuccess) { clv_destroy(h); return fail(nullptr, CLV_ECUDA, cudaGetErrorString(e)); }
+      }
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) { clv_destroy(h); return fail(nullptr, CLV_ECUDA, cudaGetErrorString(e)); }
+  *out = h;
+  return CLV_OK;
+}
+
+}  // namespace
+
+// ============================== C ABI =====================================
+extern "C" {
+
+clv_status clv_workspace_bytes(const clv_config* cfg, size_t* bytes) {
+  clv_status s = validate(cfg);
+  if (s != CLV_OK) return s;
+  if (!bytes) return fail(nullptr, CLV_EINVAL, "bytes is NULL");
+  *bytes = layout(cfg, nullptr);
+  return CLV_OK;
+}
+
+clv_status clv_create(const clv_config* cfg, void* cuda_stream, clv_handle** out) {
+  return create_common(cfg, cuda_stream, nullptr, 0, out);
+}
+
+clv_status clv_create_ws(const clv_config* cfg, void* cuda_stream, void* device_ws, size_t ws_bytes,
+                         clv_handle** out) {
+  if (!device_ws) return fail(nullptr, CLV_EINVAL, "device_ws is NULL");
+  return create_common(cfg, cuda_stream, device_ws, ws_bytes, out);
+}
+
+static clv_status set_initial_any(clv_handle* h, const double* eps, const double* ux, const double* uy,
+                                  const double* ueta, const double* pi, bool host) {
+  if (!h) return CLV_EINVAL;
+  if (!eps || !ux || !uy || !ueta) return fail(h, CLV_EINVAL, "eps, ux, uy and ueta are required");
+  const double* in[4] = {eps, ux, uy, ueta};
+  h->cur = 0;
+  h->prev = 1;
+  return h->rsize == 8 ? set_initial_impl<double>(h, in, pi, host) : set_initial_impl<float>(h, in, pi, host);
+}
+
+clv_status clv_set_initial(clv_handle* h, const double* eps, const double* ux, const double* uy,
+                           const double* ueta, const double* pi) {
+  return set_initial_any(h, eps, ux, uy, ueta, pi, true);
+}
+
+clv_status clv_set_initial_device(clv_handle* h, const double* d_eps, const double* d_ux, const double* d_uy,
+                                  const double* d_ueta, const double* d_pi) {
+  return set_initial_any(h, d_eps, d_ux, d_uy, d_ueta, d_pi, false);
+}
+
+clv_status clv_step(clv_handle* h, int nsteps, clv_stats* stats) {
+  if (!h) return CLV_EINVAL;
+  if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
+  if (nsteps < 0) return fail(h, CLV_EINVAL, "nsteps must be >= 0");
+  if (stats && nsteps > 0) CLV_CUDA(h, cudaMemsetAsync(&h->dstats->emax_bits, 0, 8, h->stream));
+  for (int s = 0; s < nsteps; ++s) {
+    const bool last = stats && s == nsteps - 1;
+    if (h->rsize == 8) {
+      if (h->viscous) launch_step<double, true>(h, last); else launch_step<double, false>(h, last);
+    } else {
+      if (h->viscous) launch_step<float, true>(h, last); else launch_step<float, false>(h, last);
+    }
+  }
+  CLV_CUDA(h, cudaGetLastError());
+  if (!stats) return CLV_OK;
+  const bool scan = nsteps == 0;
+  return h->rsize == 8 ? reduce_stats<double>(h, scan, stats) : reduce_stats<float>(h, scan, stats);
+}
+
+clv_status clv_get_stats(clv_handle* h, clv_stats* stats) {
+  if (!h || !stats) return CLV_EINVAL;
+  if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
+  return h->rsize == 8 ? reduce_stats<double>(h, true, stats) : reduce_stats<float>(h, true, stats);
+}
+
+static clv_status get_fields_any(clv_handle* h, uint32_t mask, double* out, bool host) {
+  if (!h || !out) return CLV_EINVAL;
+  if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
+  if (mask >> 21) return fail(h, CLV_EINVAL, "mask selects fields beyond index 20");
+  size_t slot = 0;
+  for (int f = 0; f < 21; ++f) {
+    if (!(mask >> f & 1u)) continue;
+    double* dst = host ? h->staging : out + slot * (size_t)h->N;
+    clv_status s = h->rsize == 8 ? export_field<double>(h, f, dst) : export_field<float>(h, f, dst);
+    if (s != CLV_OK) return s;
+    if (host) {
+      CLV_CUDA(h, cudaMemcpyAsync(out + slot * (size_t)h->N, h->staging, (size_t)h->N * 8,
+                                  cudaMemcpyDeviceToHost, h->stream));
+      CLV_CUDA(h, cudaStreamSynchronize(h->stream));
+    }
+    ++slot;
+  }
+  return CLV_OK;
+}
+
+clv_status clv_get_fields(clv_handle* h, uint32_t mask, double* host_out) {
+  return get_fields_any(h, mask, host_out, true);
+}
+
+clv_status clv_get_fields_device(clv_handle* h, uint32_t mask, double* device_out) {
+  return get_fields_any(h, mask, device_out, false);
+}
+
+clv_status clv_get_time(const clv_handle* h, double* tau, int64_t* step) {
+  if (!h) return CLV_EINVAL;
+  if (tau) *tau = h->tau;
+  if (step) *step = h->step;
+  return CLV_OK;
+}
+
+clv_status clv_enable_kernel_timing(clv_handle* h, int enable) {
+  if (!h) return CLV_EINVAL;
+  h->timing = enable != 0;
+  return CLV_OK;
+}
+
+clv_status clv_get_kernel_times(clv_handle* h, double ms[2], int64_t launches[2]) {
+  if (!h || !ms || !launches) return CLV_EINVAL;
+  CLV_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i + 2 < h->ev_pending.size(); i += 3) {
+    float a = 0.f, b = 0.f;
+    CLV_CUDA(h, cudaEventElapsedTime(&a, h->ev_pending[i], h->ev_pending[i + 1]));
+    CLV_CUDA(h, cudaEventElapsedTime(&b, h->ev_pending[i + 1], h->ev_pending[i + 2]));
+    h->t_ms[0] += a;
+    h->t_ms[1] += b;
+    h->t_launches[0] += 1;
+    h->t_launches[1] += 1;
+  }
+  for (cudaEvent_t e : h->ev_pending) h->ev_pool.push_back(e);
+  h->ev_pending.clear();
+  for (int i = 0; i < 2; ++i) {
+    ms[i] = h->t_ms[i];
+    launches[i] = h->t_launches[i];
+    h->t_ms[i] = 0.0;
+    h->t_launches[i] = 0;
+  }
+  return CLV_OK;
+}
+
+void clv_destroy(clv_handle* h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
+  for (cudaEvent_t e : h->ev_pending) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  delete h;
+}
+
+const char* clv_last_error(const clv_handle* h) {
+  return h ? h->last_error.c_str() : g_create_error.c_str();
+}
+
+const char* clv_version(void) { return "clv-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

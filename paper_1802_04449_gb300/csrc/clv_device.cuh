@@ -1,0 +1,163 @@
+// clv_device.cuh -- device-side building blocks of the viscous Milne hydro
+// step (CLVisc method: Pang, Petersen, Wang).  Templated on the storage /
+// arithmetic type R (float or double).
+//
+// Notation: tilde variables of Sec. 2 of the paper, g~ = diag(1,-1,-1,-1).
+// Symmetric shear components are numbered
+//     0 tt  1 tx  2 ty  3 te  4 xx  5 xy  6 xe  7 yy  8 ye  9 ee
+// (t = tau, e = eta_s).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace clv {
+
+constexpr double kHbarC = 0.1973269804;  // GeV fm
+constexpr double kDofConformal = 47.5;   // u, d, s quarks + gluons
+
+__host__ __device__ constexpr int sym_index(int m, int n) {
+  return (m > n) ? sym_index(n, m)
+                 : (m == 0 ? n : (m == 1 ? 3 + n : (m == 2 ? 5 + n : 9)));
+}
+__host__ __device__ constexpr double metric_sign(int m) { return m == 0 ? 1.0 : -1.0; }
+
+template <typename R> struct Fast;
+template <> struct Fast<float> {
+  static __device__ __forceinline__ float log(float x) { return __logf(x); }
+  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+};
+template <> struct Fast<double> {
+  static __device__ __forceinline__ double log(double x) { return ::log(x); }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+};
+
+// ---------------------------------------------------------------------------
+// Equation of state.  Conformal: P = e/3, c_s^2 = 1/3, T = (e/(3a))^{1/4}
+// with a = g pi^2/(90 (hbar c)^3).  Table: P, T, c_s^2 at nodes uniform in
+// ln e, linear in ln e between nodes; below node 0 P and T scale as e and
+// e^{1/4}; above the last node a conformal continuation.
+// ---------------------------------------------------------------------------
+template <typename R> struct EosView {
+  int kind;        // 0 conformal, 1 table
+  int n;
+  double lne0, inv_dlne;
+  double e0, e_top;        // eps of node 0 and of the last node
+  double t_coef;           // conformal: T^4 = t_coef * e
+  const R* P;
+  const R* T;
+  const R* cs2;
+};
+
+// Evaluate in arithmetic type C (C may be wider than the table type R).
+template <typename C, typename R>
+__device__ __forceinline__ void eos_eval(const EosView<R>& q, C e, C& P, C& T, C& cs2) {
+  if (q.kind == 0) {
+    P = e * C(1.0 / 3.0);
+    cs2 = C(1.0 / 3.0);
+    T = (e > C(0)) ? sqrt(sqrt(C(q.t_coef) * e)) : C(0);
+    return;
+  }
+  if (!(e > C(0))) {
+    P = C(0);
+    T = C(0);
+    cs2 = C(__ldg(q.cs2));
+    return;
+  }
+  C x = (Fast<C>::log(e) - C(q.lne0)) * C(q.inv_dlne);
+  if (x < C(0)) {
+    C r = e / C(q.e0);
+    P = C(__ldg(q.P)) * r;
+    T = C(__ldg(q.T)) * sqrt(sqrt(r));
+    cs2 = C(__ldg(q.cs2));
+    return;
+  }
+  if (x >= C(q.n - 1)) {
+    P = C(__ldg(q.P + q.n - 1)) + (e - C(q.e_top)) * C(1.0 / 3.0);
+    T = C(__ldg(q.T + q.n - 1)) * sqrt(sqrt(e / C(q.e_top)));
+    cs2 = C(1.0 / 3.0);
+    return;
+  }
+  int k = (int)x;
+  if (k > q.n - 2) k = q.n - 2;
+  C w = x - C(k);
+  C p0 = C(__ldg(q.P + k)), p1 = C(__ldg(q.P + k + 1));
+  C t0 = C(__ldg(q.T + k)), t1 = C(__ldg(q.T + k + 1));
+  C c0 = C(__ldg(q.cs2 + k)), c1 = C(__ldg(q.cs2 + k + 1));
+  P = p0 + w * (p1 - p0);
+  T = t0 + w * (t1 - t0);
+  cs2 = c0 + w * (c1 - c0);
+}
+
+// ---------------------------------------------------------------------------
+// Primitive recovery: T_ideal^{tau mu} = (E, M) -> (eps, u~).  Root of
+// f(v) = v - M/(E + P(E - M v)) on [0, M/E] by Newton steps kept inside a
+// shrinking bracket (bisection when a step leaves it).
+// ---------------------------------------------------------------------------
+struct RootResult {
+  int iters;      // -1: cap reached
+  int rescaled;   // |M| > (1-1e-6) E was rescaled
+};
+
+template <typename C, typename R>
+__device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps_cut, C E, C Mx,
+                                                      C My, C Me, C tol, int maxit, C& eps,
+                                                      C& ux, C& uy, C& ue, C* vguess = nullptr) {
+  RootResult rr{0, 0};
+  eps = C(0);
+  ux = uy = ue = C(0);
+  if (!(E >= eps_cut)) return rr;
+  C M2 = Mx * Mx + My * My + Me * Me;
+  C M = sqrt(M2);
+  C Mcap = C(1.0 - 1e-6) * E;
+  if (M > Mcap) {
+    C s = Mcap / M;
+    Mx *= s; My *= s; Me *= s;
+    M = Mcap;
+    rr.rescaled = 1;
+  }
+  if (M == C(0)) {
+    eps = (E >= eps_cut) ? E : C(0);
+    return rr;
+  }
+  C lo = C(0), hi = M / E;
+  C P, T, cs2;
+  C v;
+  if (vguess && *vguess > lo && *vguess < hi) {
+    v = *vguess;
+  } else {
+    eos_eval<C, R>(q, E, P, T, cs2);
+    v = M / (E + P);
+  }
+  int it = 1;
+  bool ok = false;
+  for (; it <= maxit; ++it) {
+    C e = E - M * v;
+    eos_eval<C, R>(q, e, P, T, cs2);
+    C den = E + P;
+    C f = v - M / den;
+    if (f > C(0)) hi = v; else lo = v;
+    C fp = C(1) - cs2 * (M * M) / (den * den);
+    C vn = v - f / fp;
+    if (!(vn > lo && vn < hi)) vn = C(0.5) * (lo + hi);
+    C dv = vn - v;
+    v = vn;
+    if (fabs(dv) <= tol) { ok = true; break; }
+  }
+  rr.iters = ok ? it : -1;
+  if (vguess) *vguess = v;
+  C e = E - M * v;
+  if (e < eps_cut) return rr;
+  eps = e;
+  C gam = C(1) / sqrt(C(1) - v * v);
+  C s = gam * v / M;
+  ux = s * Mx;
+  uy = s * My;
+  ue = s * Me;
+  return rr;
+}
+
+template <typename R> __device__ __forceinline__ R minmod(R a, R b) {
+  return (a > R(0) && b > R(0)) ? fmin(a, b) : ((a < R(0) && b < R(0)) ? fmax(a, b) : R(0));
+}
+
+}  // namespace clv

@@ -1,0 +1,457 @@
+// clv_kernels.cuh -- kernels of one Heun step of (3+1)D viscous hydro in
+// Milne coordinates (CLVisc method).  Storage is structure-of-arrays, one
+// array per field of nx*ny*neta values, eta_s fastest.
+#pragma once
+#include "clv_device.cuh"
+
+namespace clv {
+
+constexpr int kBlock = 256;
+
+template <typename R> struct Ptr10 {
+  R* p[10];
+};
+
+// Primitive set: eps, u~^x, u~^y, u~^eta, P(eps), c_s(eps).
+template <typename R> struct Prim {
+  R* e;
+  R* u[3];
+  R* P;
+  R* cs;
+};
+
+template <typename R> struct StageParams {
+  // fields of the stage being differentiated (stage 1: step n, stage 2: stage-1 result)
+  const R* T[4];
+  const R* pi[10];
+  Prim<R> pr;
+  // own-cell inputs: T~ and pi~ at step n, u~ at n and n-1
+  const R* Tn[4];
+  const R* pin[10];
+  const R* un[3];
+  const R* up[3];
+  // outputs (stage 2 writes T and pi in place over Tn/pin, prim over the n-1 set)
+  R* Tout[4];
+  R* piout[10];
+  Prim<R> prout;
+  EosView<R> eos;
+  int nx, ny, ne, periodic;
+  long long N;
+  double taus;      // tau (Milne) or 1 (Cartesian) at the stage time
+  double geo;       // 1/tau (Milne) or 0 (Cartesian) at the stage time
+  double taus_new;  // tau scale at the end of the step (primitive recovery)
+  double h;         // time step
+  double inv_dl[3]; // 1/dx, 1/dy, 1/(tau deta)
+  double st_tau;    // 1 in Milne (S_T^tau active), 0 in Cartesian
+  double eps_cut, eta_over_s;
+  double polish_E, polish_v;   // FP32: FP64 Newton for E < polish_E or M > polish_v E
+  // reductions and error reporting
+  double* block_sum;             // per block: sum of new T~^{tau tau} (stats launches only)
+  unsigned long long* emax_bits; // max eps as the bits of a non-negative double
+  unsigned long long* counters;  // [0] rescaled, [1] root cap, [2] polished
+  unsigned int* err;             // error word
+};
+
+__device__ __forceinline__ int wrap_index(int i, int n, int periodic) {
+  if (periodic) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+template <typename R> __device__ __forceinline__ R ldg(const R* p) { return __ldg(p); }
+
+template <typename R> struct SolveTraits;
+template <> struct SolveTraits<float> {
+  static constexpr float tol = 2.5e-7f;
+  static constexpr int maxit = 60;
+};
+template <> struct SolveTraits<double> {
+  static constexpr double tol = 1e-15;
+  static constexpr int maxit = 100;
+};
+
+// Reconstructed interface quantities (KT, Eq. flux_out): T~^{tau mu} (4),
+// pi~ (10), u~^tau, v^a = u~^a/u~^tau, P.
+template <bool VISC> struct NRec { static constexpr int n = VISC ? 17 : 7; };
+
+template <typename R, bool VISC>
+__device__ __forceinline__ void interface_flux(const R* L, const R* Rr, R csl, R csr, int axis,
+                                               R taus, R* H) {
+  constexpr int NQ = VISC ? 14 : 4;
+  constexpr int IU = VISC ? 14 : 4, IV = IU + 1, IP = IU + 2;
+  const R vl = L[IV], vr = Rr[IV];
+  const R al = fabs(vl), ar = fabs(vr);
+  const R lam = fmax((al + csl) / (R(1) + al * csl), (ar + csr) / (R(1) + ar * csr));
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    // flux of T~^{tau m} along a: v T~^{tau m} + tau [P (v d_{m tau} + d_{m a}) + pi~^{a m} - v pi~^{tau m}]
+    R fl = vl * L[m], fr = vr * Rr[m];
+    R gl = (m == 0 ? vl : R(0)) + (m == axis ? R(1) : R(0));
+    R gr = (m == 0 ? vr : R(0)) + (m == axis ? R(1) : R(0));
+    R xl = L[IP] * gl, xr = Rr[IP] * gr;
+    if constexpr (VISC) {
+      xl += L[4 + sym_index(axis, m)] - vl * L[4 + sym_index(0, m)];
+      xr += Rr[4 + sym_index(axis, m)] - vr * Rr[4 + sym_index(0, m)];
+    }
+    fl += taus * xl;
+    fr += taus * xr;
+    H[m] = R(0.5) * (fl + fr) - R(0.5) * lam * (Rr[m] - L[m]);
+  }
+  if constexpr (VISC) {
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      R ql = L[IU] * L[4 + q], qr = Rr[IU] * Rr[4 + q];
+      H[4 + q] = R(0.5) * (vl * ql + vr * qr) - R(0.5) * lam * (qr - ql);
+    }
+  }
+  (void)NQ;
+}
+
+// Israel-Stewart source with lambda_i = 0 (Sec. 2): du[a][b] = d~_a u~^b.
+template <typename R>
+__device__ __forceinline__ void shear_source(R geo, const R u[4], R du[4][4], const R pi[10], R e,
+                                             R P, R inv_taupi, R* S) {
+  // corrected tilde covariant derivatives (Eq. dtuz)
+  du[3][0] += geo * u[3];
+  du[3][3] += geo * u[0];
+  const R theta = du[0][0] + du[1][1] + du[2][2] + du[3][3];
+  R Du[4];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) Du[b] = u[0] * du[0][b] + u[1] * du[1][b] + u[2] * du[2][b] + u[3] * du[3][b];
+  // w^m = g~_{bb} pi~^{m b} Du^b
+  R w[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+    w[m] = pi[sym_index(m, 0)] * Du[0] - pi[sym_index(m, 1)] * Du[1] - pi[sym_index(m, 2)] * Du[2] -
+           pi[sym_index(m, 3)] * Du[3];
+  const R ep5 = (e + P) * R(0.2);
+  const R decay = inv_taupi + theta * R(1.0 / 3.0) + geo * u[0];
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+#pragma unroll
+    for (int n = m; n < 4; ++n) {
+      const int q = sym_index(m, n);
+      const R sm = R(metric_sign(m)), sn = R(metric_sign(n));
+      R sigma = sm * du[m][n] + sn * du[n][m] - u[m] * Du[n] - u[n] * Du[m] -
+                R(2.0 / 3.0) * ((m == n ? sm : R(0)) - u[m] * u[n]) * theta;
+      S[q] = ep5 * sigma - decay * pi[q] - (u[m] * w[n] + u[n] * w[m]);
+    }
+  // Christoffel terms I^{mu nu} (Eq. Ipi), with a minus sign in S_pi
+  const R gu = geo * u[3];
+  S[0] -= R(2) * gu * pi[3];
+  S[1] -= gu * pi[6];
+  S[2] -= gu * pi[8];
+  S[3] -= gu * (pi[0] + pi[9]);
+  S[6] -= gu * pi[1];
+  S[8] -= gu * pi[2];
+  S[9] -= R(2) * gu * pi[3];
+}
+
+template <typename R, int STAGE, bool VISC, bool STATS>
+__global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = c < p.N;
+  double my_T0 = 0.0;
+  double my_e = 0.0;
+  bool f_rescaled = false, f_fail = false, f_polished = false, f_nonfinite = false;
+  if (active) {
+    const int k = (int)(c % p.ne);
+    const long long t = c / p.ne;
+    const int j = (int)(t % p.ny);
+    const int i = (int)(t / p.ny);
+    constexpr int NR = NRec<VISC>::n;
+    constexpr int NQ = VISC ? 14 : 4;
+    constexpr int IU = VISC ? 14 : 4, IV = IU + 1;
+    const R taus = R(p.taus);
+    R S[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) S[q] = R(0);
+    // velocities of the stage at +-1 neighbours (for the shear source)
+    R unb[3][2][4];
+    // ---------------- KT flux differences along x, y, eta_s (Eq. kt) ----------------
+#pragma unroll
+    for (int ax = 1; ax <= 3; ++ax) {
+      long long id[5];
+#pragma unroll
+      for (int d = 0; d < 5; ++d) {
+        const int o = d - 2;
+        const int ii = ax == 1 ? wrap_index(i + o, p.nx, p.periodic) : i;
+        const int jj = ax == 2 ? wrap_index(j + o, p.ny, p.periodic) : j;
+        const int kk = ax == 3 ? wrap_index(k + o, p.ne, p.periodic) : k;
+        id[d] = ((long long)ii * p.ny + jj) * p.ne + kk;
+      }
+      R ut[5], va[5], cs[5];
+#pragma unroll
+      for (int d = 0; d < 5; ++d) {
+        const R ux = ldg(p.pr.u[0] + id[d]), uy = ldg(p.pr.u[1] + id[d]), ue = ldg(p.pr.u[2] + id[d]);
+        ut[d] = sqrt(R(1) + ux * ux + uy * uy + ue * ue);
+        const R ua = ax == 1 ? ux : (ax == 2 ? uy : ue);
+        va[d] = ua / ut[d];
+        cs[d] = ldg(p.pr.cs + id[d]);
+        if (d == 1 || d == 3) {
+          const int side = d == 3 ? 1 : 0;
+          unb[ax - 1][side][0] = ut[d];
+          unb[ax - 1][side][1] = ux;
+          unb[ax - 1][side][2] = uy;
+          unb[ax - 1][side][3] = ue;
+        }
+      }
+      // reconstructed states: interface i-1/2 (Lm | Rm) and i+1/2 (Lp | Rp)
+      R Lm[NR], Rm[NR], Lp[NR], Rp[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        R v[5];
+#pragma unroll
+        for (int d = 0; d < 5; ++d) {
+          if (q < 4) v[d] = ldg(p.T[q] + id[d]);
+          else if (VISC && q < 14) v[d] = ldg(p.pi[q - 4] + id[d]);
+          else if (q == IU) v[d] = ut[d];
+          else if (q == IV) v[d] = va[d];
+          else v[d] = ldg(p.pr.P + id[d]);
+        }
+        const R s1 = minmod(v[1] - v[0], v[2] - v[1]);
+        const R s2 = minmod(v[2] - v[1], v[3] - v[2]);
+        const R s3 = minmod(v[3] - v[2], v[4] - v[3]);
+        Lm[q] = v[1] + R(0.5) * s1;
+        Rm[q] = v[2] - R(0.5) * s2;
+        Lp[q] = v[2] + R(0.5) * s2;
+        Rp[q] = v[3] - R(0.5) * s3;
+      }
+      R Hm[NQ], Hp[NQ];
+      interface_flux<R, VISC>(Lm, Rm, cs[1], cs[2], ax, taus, Hm);
+      interface_flux<R, VISC>(Lp, Rp, cs[2], cs[3], ax, taus, Hp);
+      const R inv = R(p.inv_dl[ax - 1]);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) S[q] -= (Hp[q] - Hm[q]) * inv;
+    }
+    // ---------------- own-cell state ----------------
+    const R e = p.pr.e[c];
+    const R Pc = p.pr.P[c];
+    R u[4];
+    u[1] = p.pr.u[0][c]; u[2] = p.pr.u[1][c]; u[3] = p.pr.u[2][c];
+    u[0] = sqrt(R(1) + u[1] * u[1] + u[2] * u[2] + u[3] * u[3]);
+    R pic[10];
+    if constexpr (VISC) {
+#pragma unroll
+      for (int q = 0; q < 10; ++q) pic[q] = p.pi[q][c];
+    }
+    // geometric source S_T = -(T~^{ee}/tau, 0, 0, T~^{te}/tau)
+    {
+      R Tee = e * u[3] * u[3] + Pc * (R(1) + u[3] * u[3]);
+      if constexpr (VISC) Tee += pic[9];
+      S[0] -= R(p.st_tau) * Tee;
+      S[3] -= R(p.geo) * p.T[3][c];
+    }
+    // u~ at step n and the late velocity (u* in stage 1, u' in stage 2)
+    R un[4], ul[4];
+    if constexpr (STAGE == 1) {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) un[b] = u[b];
+    } else {
+      un[1] = p.un[0][c]; un[2] = p.un[1][c]; un[3] = p.un[2][c];
+      un[0] = sqrt(R(1) + un[1] * un[1] + un[2] * un[2] + un[3] * un[3]);
+    }
+    R ustar0 = un[0];
+    if constexpr (VISC) {
+      R us1 = R(2) * un[1] - p.up[0][c];
+      R us2 = R(2) * un[2] - p.up[1][c];
+      R us3 = R(2) * un[3] - p.up[2][c];
+      ustar0 = sqrt(R(1) + us1 * us1 + us2 * us2 + us3 * us3);
+      if constexpr (STAGE == 1) {
+        ul[0] = ustar0; ul[1] = us1; ul[2] = us2; ul[3] = us3;
+      } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) ul[b] = u[b];
+      }
+      // d~_a u~^b: time difference and central differences
+      R du[4][4];
+      const R invh = R(1) / R(p.h);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) du[0][b] = (ul[b] - un[b]) * invh;
+#pragma unroll
+      for (int a = 1; a <= 3; ++a) {
+        const R half_inv = R(0.5) * R(p.inv_dl[a - 1]);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) du[a][b] = (unb[a - 1][1][b] - unb[a - 1][0][b]) * half_inv;
+      }
+      R Pdummy, Tc, c2dummy;
+      eos_eval<R, R>(p.eos, e, Pdummy, Tc, c2dummy);
+      const R inv_taupi = Tc / (R(5) * R(p.eta_over_s) * R(kHbarC));
+      R Spi[10];
+      shear_source<R>(R(p.geo), u, du, pic, e, Pc, inv_taupi, Spi);
+#pragma unroll
+      for (int q = 0; q < 10; ++q) S[4 + q] += Spi[q];
+    }
+    // ---------------- stage update (Sec. 3) ----------------
+    const R h = R(p.h);
+    R Tnew[4], pinew[10];
+    if constexpr (STAGE == 1) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) Tnew[m] = p.T[m][c] + h * S[m];
+      if constexpr (VISC) {
+        const R inv = R(1) / ustar0;
+#pragma unroll
+        for (int q = 0; q < 10; ++q) pinew[q] = (un[0] * pic[q] + h * S[4 + q]) * inv;
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) Tnew[m] = R(0.5) * (p.Tn[m][c] + p.T[m][c] + h * S[m]);
+      if constexpr (VISC) {
+        const R inv = R(0.5) / u[0];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) pinew[q] = (un[0] * p.pin[q][c] + ustar0 * pic[q] + h * S[4 + q]) * inv;
+      }
+    }
+    // ---------------- primitive recovery from T_ideal = T - pi ----------------
+    const R tn = R(p.taus_new);
+    R E = Tnew[0] / tn, Mx = Tnew[1] / tn, My = Tnew[2] / tn, Me = Tnew[3] / tn;
+    if constexpr (VISC) {
+      E -= pinew[0]; Mx -= pinew[1]; My -= pinew[2]; Me -= pinew[3];
+    }
+    R en = R(0), ux = R(0), uy = R(0), ue = R(0);
+    if (!(isfinite(E) && isfinite(Mx) && isfinite(My) && isfinite(Me))) {
+      f_nonfinite = true;
+    } else {
+      R vg = R(-1);
+      RootResult rr = solve_primitive<R, R>(p.eos, R(p.eps_cut), E, Mx, My, Me, SolveTraits<R>::tol,
+                                            SolveTraits<R>::maxit, en, ux, uy, ue, &vg);
+      f_rescaled = rr.rescaled;
+      if constexpr (sizeof(R) == 4) {
+        const R M = sqrt(Mx * Mx + My * My + Me * Me);
+        if (E >= R(p.eps_cut) && M > R(0) && (E < R(p.polish_E) || M > R(p.polish_v) * E)) {
+          double dv = (double)vg, de, dux, duy, due;
+          RootResult r2 = solve_primitive<double, R>(p.eos, p.eps_cut, (double)E, (double)Mx,
+                                                     (double)My, (double)Me, 1e-13, 40, de, dux,
+                                                     duy, due, &dv);
+          en = R(de); ux = R(dux); uy = R(duy); ue = R(due);
+          f_polished = true;
+          rr.iters = r2.iters;
+        }
+      }
+      f_fail = rr.iters < 0;
+    }
+    R Pn, Tn_, c2n;
+    eos_eval<R, R>(p.eos, en, Pn, Tn_, c2n);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) p.Tout[m][c] = Tnew[m];
+    if constexpr (VISC) {
+      const bool vac = !(en > R(0));
+#pragma unroll
+      for (int q = 0; q < 10; ++q) p.piout[q][c] = vac ? R(0) : pinew[q];
+    }
+    p.prout.e[c] = en;
+    p.prout.u[0][c] = ux;
+    p.prout.u[1][c] = uy;
+    p.prout.u[2][c] = ue;
+    p.prout.P[c] = Pn;
+    p.prout.cs[c] = sqrt(c2n);
+    my_T0 = (double)Tnew[0];
+    my_e = (double)en;
+  }
+  // ---------------- counters and reductions ----------------
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned b_res = __ballot_sync(full, f_rescaled);
+  const unsigned b_fail = __ballot_sync(full, f_fail);
+  const unsigned b_pol = __ballot_sync(full, f_polished);
+  const unsigned b_nf = __ballot_sync(full, f_nonfinite);
+  if (lane == 0) {
+    if (b_res) atomicAdd(p.counters + 0, (unsigned long long)__popc(b_res));
+    if (b_fail) { atomicAdd(p.counters + 1, (unsigned long long)__popc(b_fail)); atomicOr(p.err, 1u); }
+    if (b_pol) atomicAdd(p.counters + 2, (unsigned long long)__popc(b_pol));
+    if (b_nf) atomicOr(p.err, 2u);
+  }
+  if constexpr (STATS) {
+    __shared__ double s_sum[kBlock / 32];
+    __shared__ double s_max[kBlock / 32];
+    double sm = my_T0, mx = my_e;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sm += __shfl_down_sync(full, sm, o);
+      mx = fmax(mx, __shfl_down_sync(full, mx, o));
+    }
+    const int wid = threadIdx.x >> 5;
+    if (lane == 0) { s_sum[wid] = sm; s_max[wid] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < kBlock / 32; ++w) { a += s_sum[w]; b = fmax(b, s_max[w]); }
+      p.block_sum[blockIdx.x] = a;
+      if (b > 0.0) atomicMax(p.emax_bits, (unsigned long long)__double_as_longlong(b));
+    }
+  }
+}
+
+// T~^{tau mu} = tau [(e + P) u^tau u^mu - P g~^{tau mu} + pi~^{tau mu}]
+template <typename R>
+__global__ void __launch_bounds__(kBlock) tilde_T_kernel(Prim<R> pr, Ptr10<R> pi, bool with_pi, R* T0,
+                                                         R* T1, R* T2, R* T3, double taus, long long N) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  const R e = pr.e[c], P = pr.P[c];
+  const R u1 = pr.u[0][c], u2 = pr.u[1][c], u3 = pr.u[2][c];
+  const R u0 = sqrt(R(1) + u1 * u1 + u2 * u2 + u3 * u3);
+  const R w = (e + P) * u0;
+  R a0 = w * u0 - P, a1 = w * u1, a2 = w * u2, a3 = w * u3;
+  if (with_pi) { a0 += pi.p[0][c]; a1 += pi.p[1][c]; a2 += pi.p[2][c]; a3 += pi.p[3][c]; }
+  const R ts = R(taus);
+  T0[c] = ts * a0; T1[c] = ts * a1; T2[c] = ts * a2; T3[c] = ts * a3;
+}
+
+// Initial primitives (already converted to R in pr.e and pr.u): vacuum below
+// eps_cut (eps = 0, u = 0, pi = 0), P and c_s from the EOS, copy to the n-1 set.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) init_primitives_kernel(Prim<R> pr, Prim<R> prev, Ptr10<R> pi,
+                                                                 bool with_pi, EosView<R> eos,
+                                                                 double eps_cut, long long N) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  R e = pr.e[c];
+  R a = pr.u[0][c], b = pr.u[1][c], d = pr.u[2][c];
+  const bool vac = !(e >= R(eps_cut));
+  if (vac) {
+    e = R(0); a = R(0); b = R(0); d = R(0);
+    if (with_pi) {
+#pragma unroll
+      for (int q = 0; q < 10; ++q) pi.p[q][c] = R(0);
+    }
+  }
+  R P, T, c2;
+  eos_eval<R, R>(eos, e, P, T, c2);
+  const R cs = sqrt(c2);
+  pr.e[c] = e; pr.u[0][c] = a; pr.u[1][c] = b; pr.u[2][c] = d; pr.P[c] = P; pr.cs[c] = cs;
+  prev.e[c] = e; prev.u[0][c] = a; prev.u[1][c] = b; prev.u[2][c] = d; prev.P[c] = P; prev.cs[c] = cs;
+}
+
+// u~^{-1} = 2 u~^0 - u~^1_ideal, written over the ideal-step result.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) extrapolate_prev_kernel(Prim<R> cur, Prim<R> prev, long long N) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) prev.u[m][c] = R(2) * cur.u[m][c] - prev.u[m][c];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) export_kernel(const R* src, double* dst, long long N) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < N) dst[c] = (double)src[c];
+}
+
+// Deterministic final sum of the per-block partials (one block).
+__global__ void __launch_bounds__(1024) finalize_sum_kernel(const double* partial, int n, double* out) {
+  __shared__ double s[1024];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += partial[i];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+}  // namespace clv

@@ -1,0 +1,200 @@
+"""GPU path (libclv through its C ABI) against the FP64 oracle, element by
+element on the same seeded inputs.
+
+Tolerances:
+  FP64 path: 1e-10 relative on every field, measured against the field's own
+             magnitude (|g - o| <= 1e-10 (|o| + 1e-3 max|o|)), and 1e-10
+             relative on eps wherever eps > 1e-3 GeV/fm^3.
+  FP32 path: 1e-4 relative L-inf on eps wherever eps > 1e-3 GeV/fm^3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_04449_gb300 import clv
+from paper_1802_04449_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-10
+FP32_TOL = 1e-4
+EPS_FLOOR = 1e-3
+
+
+def run_pair(case, nsteps, precision, pi=None):
+    o = oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
+                      case.eta_over_s, case.eos, case.cartesian, case.periodic)
+    o.set_initial(case.eps, case.ux, case.uy, case.ueta, pi)
+    o.step(nsteps)
+    g = clv.from_case(case, precision)
+    g.set_initial(case.eps, case.ux, case.uy, case.ueta, pi)
+    st = g.step(nsteps, stats=True)
+    return o, g, st
+
+
+def compare_fp64(o, g, viscous, fields=None):
+    names = fields or (["eps", "ux", "uy", "ueta", "Ttt", "Ttx", "Tty", "Tte"] +
+                       ([k for k in clv.FIELDS if k.startswith("pi")] + ["upx", "upy", "upe"] if viscous else []))
+    got = g.get(names)
+    worst = {}
+    for k in names:
+        ref = o.get(k)
+        scale = np.abs(ref).max()
+        err = np.abs(got[k] - ref)
+        bound = FP64_TOL * (np.abs(ref) + 1e-3 * scale) + 1e-300
+        worst[k] = float((err / bound).max()) if scale > 0 else float(err.max())
+        assert np.all(err <= bound) or (scale == 0 and err.max() == 0), (k, worst[k], err.max(), scale)
+    e_o, e_g = o.get("eps"), got["eps"]
+    m = e_o > EPS_FLOOR
+    assert np.all(np.abs(e_g[m] / e_o[m] - 1) <= FP64_TOL)
+    return worst
+
+
+def fp32_eps_err(o, g):
+    e_o = o.get("eps")
+    e_g = g.get(["eps"])["eps"]
+    m = e_o > EPS_FLOOR
+    assert m.sum() > 0
+    return float(np.max(np.abs(e_g[m] / e_o[m] - 1)))
+
+
+# ------------------------------------------------------------------ cases
+def small_hotspot(seed=3, nx=21, ny=19, neta=11, eta_over_s=0.08, nspots=60, eos="crossover"):
+    return I.hotspot_event(nx=nx, ny=ny, neta=neta, n_spots=nspots, seed=seed, eta_over_s=eta_over_s,
+                           eos=eos)
+
+
+def test_fp64_gubser_ideal_config():
+    """Ideal Gubser flow on the 33x33x9 grid, tau 1 -> 3 (100 steps)."""
+    case = I.gubser_case()
+    o, g, st = run_pair(case, case.nsteps, clv.CLV_FP64)
+    compare_fp64(o, g, viscous=False)
+    so = o.stats()
+    assert st["tau"] == pytest.approx(so["tau"], rel=1e-14)
+    assert st["eps_max"] == pytest.approx(so["eps_max"], rel=1e-10)
+    assert st["E_tot"] == pytest.approx(so["E_tot"], rel=1e-10)
+    assert st["error_word"] == 0
+
+
+@pytest.mark.parametrize("eta_over_s", [0.08, 0.16])
+def test_fp64_viscous_hotspots_table_eos(eta_over_s):
+    case = small_hotspot(eta_over_s=eta_over_s)
+    o, g, st = run_pair(case, 30, clv.CLV_FP64)
+    compare_fp64(o, g, viscous=True)
+    so = o.stats()
+    assert st["E_tot"] == pytest.approx(so["E_tot"], rel=1e-10)
+    assert st["T_max"] == pytest.approx(so["T_max"], rel=1e-10)
+
+
+def test_fp64_viscous_longitudinal_flow_with_pi():
+    """u~^eta != 0 (exercises I^{mu nu} and the eta flux) and a nonzero initial pi~."""
+    rng = np.random.default_rng(9)
+    nx, ny, ne = 9, 7, 24
+    case = small_hotspot(nx=nx, ny=ny, neta=ne, nspots=20, eos=None, eta_over_s=0.16)
+    eta = I.cell_coords(ne, case.deta)
+    case.ueta = np.broadcast_to(0.2 * np.sin(eta), case.eps.shape).copy()
+    case.ux = 0.05 * rng.normal(size=case.eps.shape)
+    pi = 0.01 * rng.normal(size=(10,) + case.eps.shape) * case.eps.max()
+    o, g, st = run_pair(case, 25, clv.CLV_FP64, pi=pi)
+    compare_fp64(o, g, viscous=True)
+
+
+def test_fp64_cartesian_periodic_box():
+    rng = np.random.default_rng(4)
+    e, ux, uy, ue = I.random_smooth_box(rng, 12, 10, 9)
+    case = I.HydroCase("box", 12, 10, 9, 0.2, 0.2, 0.2, 1.0, 0.02, 0.16, None, e, ux, uy, ue, 40,
+                       cartesian=True, periodic=True)
+    o, g, st = run_pair(case, 40, clv.CLV_FP64)
+    compare_fp64(o, g, viscous=True)
+    keys = ["Ttt", "Ttx", "Tty", "Tte"]
+    got = g.get(keys)
+    ini = oracle.Oracle(12, 10, 9, 0.2, 0.2, 0.2, 1.0, 0.02, 0.16, cartesian=True, periodic=True)
+    ini.set_initial(e, ux, uy, ue)
+    for k in keys:   # GPU conserves sum T^{t mu} too
+        assert abs(got[k].sum() - ini.get(k).sum()) <= 1e-12 * ini.get("Ttt").sum()
+
+
+def test_fp64_riemann_vacuum_front():
+    nx = 241
+    x, e = I.riemann_1d(nx, 0.05, 10.0)
+    sh = (nx, 1, 1)
+    z = np.zeros(sh)
+    case = I.HydroCase("riemann", nx, 1, 1, 0.05, 1.0, 1.0, 0.0, 0.0125, 0.0, None, e.reshape(sh), z, z, z,
+                       200, cartesian=True)
+    o, g, st = run_pair(case, 200, clv.CLV_FP64)
+    compare_fp64(o, g, viscous=False)
+    assert st["n_rescaled"] > 0   # the vacuum front exercises the |M| > E branch
+
+
+@pytest.mark.parametrize("eos", ["crossover", None])
+def test_fp32_viscous_hotspots(eos):
+    case = small_hotspot(seed=7, eos=eos)
+    o, g, st = run_pair(case, 40, clv.CLV_FP32)
+    err = fp32_eps_err(o, g)
+    assert err <= FP32_TOL, err
+    assert st["error_word"] == 0
+
+
+def test_fp32_gubser():
+    case = I.gubser_case()
+    o, g, st = run_pair(case, case.nsteps, clv.CLV_FP32)
+    assert fp32_eps_err(o, g) <= FP32_TOL
+
+
+def test_full_size_viscous_event_one_step():
+    """The 97x97x41 viscous hot-spot event (2048 spots, crossover EOS) in the
+    launch configuration the benchmark times: one full step, every cell."""
+    case = I.hotspot_event()
+    oracle.set_threads(0)
+    o, g64, _ = run_pair(case, 1, clv.CLV_FP64)
+    compare_fp64(o, g64, viscous=True, fields=["eps", "ux", "uy", "ueta", "Ttt", "Tte", "pixx", "piee"])
+    g32 = clv.from_case(case, clv.CLV_FP32)
+    g32.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    g32.step(1)
+    assert fp32_eps_err(o, g32) <= FP32_TOL
+
+
+def test_single_cell_and_degenerate_grids():
+    for shape in [(1, 1, 1), (1, 1, 5), (3, 1, 1), (2, 3, 1)]:
+        nx, ny, ne = shape
+        e = np.full(shape, 4.0)
+        e.flat[0] = 6.0
+        z = np.zeros(shape)
+        case = I.HydroCase("tiny", nx, ny, ne, 0.3, 0.3, 0.3, 0.6, 0.02, 0.1, None, e, z, z, z, 5)
+        o, g, st = run_pair(case, 5, clv.CLV_FP64)
+        compare_fp64(o, g, viscous=True)
+
+
+def test_device_inputs_equal_host_inputs_and_deterministic():
+    import torch
+    case = small_hotspot(seed=11)
+    g1 = clv.from_case(case, clv.CLV_FP32)
+    g1.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    g1.step(10)
+    a = g1.get()
+    g2 = clv.from_case(case, clv.CLV_FP32, torch_workspace=False)
+    dev = [torch.tensor(x, device="cuda") for x in (case.eps, case.ux, case.uy, case.ueta)]
+    g2.set_initial(*dev)
+    g2.step(10)
+    b = g2.get()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_error_paths():
+    with pytest.raises(clv.ClvError) as ei:
+        clv.Hydro(0, 4, 4, 0.1, 0.1, 0.1, 1.0, 0.01)
+    assert ei.value.status == 1
+    with pytest.raises(clv.ClvError):
+        clv.Hydro(4, 4, 4, 0.1, 0.1, 0.1, -1.0, 0.01)   # tau0 <= 0 in Milne coordinates
+    g = clv.Hydro(4, 4, 4, 0.1, 0.1, 0.1, 1.0, 0.01)
+    with pytest.raises(clv.ClvError):
+        g.step(1)                                        # no initial state yet
+    e = np.full((4, 4, 4), 5.0)
+    z = np.zeros_like(e)
+    ux = z.copy()
+    ux[1, 2, 3] = np.nan                                 # non-finite input is reported
+    g.set_initial(e, ux, z, z)
+    with pytest.raises(clv.ClvError) as ei:
+        g.step(2, stats=True)
+    assert ei.value.status == 5
