@@ -154,7 +154,11 @@ def run_gpu(args):
         barrier()
         ms = sum(a.elapsed_time(b) for a, b in evs)
         kt = g.kernel_times() if kernel_timing else None
-        st = g.stats()
+        try:
+            st = g.stats()
+        except clv.ClvError as e:          # reported in the JSON line, not hidden
+            st = {"error": str(e), "tau": None, "eps_max": None, "T_max": None, "E_tot": None,
+                  "n_polished": None, "error_word": None, "n_rootfail": None}
         g.close()
         return ms, kt, st
 
@@ -187,7 +191,10 @@ def run_gpu(args):
         barrier()
         t0 = time.perf_counter()
         g.set_initial(*host_in)
-        stt = g.step(args.steps, stats=True)
+        try:
+            g.step(args.steps, stats=True)
+        except clv.ClvError as e:
+            print(f"e2e run reported: {e}", file=sys.stderr)
         g.get(["eps", "ux", "uy", "ueta"], out=out.numpy())
         t1 = time.perf_counter()
         g.close()
@@ -233,7 +240,9 @@ def run_gpu(args):
         "e2e": e2e,
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
-        "stats_fp32": {k: st32[k] for k in ("tau", "eps_max", "T_max", "E_tot", "n_polished", "error_word")},
+        "stats_fp32": {k: st32.get(k) for k in ("tau", "eps_max", "T_max", "E_tot", "n_polished", "n_rootfail",
+                                                "error_word", "error")},
+        "stats_fp64": {k: st64.get(k) for k in ("tau", "eps_max", "E_tot", "n_rootfail", "error_word", "error")},
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

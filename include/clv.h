@@ -74,6 +74,8 @@ typedef struct {
   int cartesian;             /* 1: Christoffel terms off and tau factors 1 (t, x, y, z) */
   int periodic;              /* 1: periodic boundaries; 0: zero-gradient (outflow) */
   double eps_cut;            /* vacuum cutoff, GeV/fm^3 (the paper uses 1e-7) */
+  int kernel;                /* 0: tiled stage kernel (default); 1: direct per-cell stage kernel
+                                (same arithmetic, simpler data flow; kept for cross-checks) */
 } clv_config;
 
 /* Per-run statistics, filled by clv_step / clv_get_stats. */

@@ -196,10 +196,14 @@ static int prim_solve(const orc_t* h, double E, double Mx, double My, double Me,
     double f = v - M / (E + P);
     if (f > 0.0) hi = v; else lo = v;
     double df = 1.0 - M * M * cs2 / ((E + P) * (E + P));
-    double vn = v - f / df;
+    double step = -f / df;
+    /* a Newton step below the tolerance ends the solve; otherwise keep the
+       iterate strictly inside the bracket (bisection when it leaves it) */
+    if (fabs(step) <= 1e-15) { v += step; ok = 1; break; }
+    double vn = v + step;
     if (!(vn > lo && vn < hi)) vn = 0.5 * (lo + hi);
-    if (fabs(vn - v) <= 1e-15) { v = vn; ok = 1; break; }
     v = vn;
+    if (hi - lo <= 1e-15) { ok = 1; break; }
   }
   double e = E - M * v;
   if (e < h->c.eps_cut) { *eps = 0.0; return ok ? it : -1; }

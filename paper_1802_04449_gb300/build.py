@@ -13,7 +13,9 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libclv.so")
 SOURCES = ["clv_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
+# -prec-div/-prec-sqrt=false: approximate FP32 division and square root (FP64 unaffected)
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-prec-div=false", "-prec-sqrt=false",
+         "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 
 
 def _nvcc():

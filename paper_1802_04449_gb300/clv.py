@@ -39,7 +39,7 @@ class clv_config(ctypes.Structure):
         ("eos_T", ctypes.POINTER(ctypes.c_double)),
         ("eos_cs2", ctypes.POINTER(ctypes.c_double)),
         ("precision", ctypes.c_int), ("cartesian", ctypes.c_int), ("periodic", ctypes.c_int),
-        ("eps_cut", ctypes.c_double),
+        ("eps_cut", ctypes.c_double), ("kernel", ctypes.c_int),
     ]
 
 
@@ -112,7 +112,7 @@ def _dp(a):
 
 
 def make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
-                precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7):
+                precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7, kernel=0):
     c = clv_config()
     c.nx, c.ny, c.neta = int(nx), int(ny), int(neta)
     c.dx, c.dy, c.deta = float(dx), float(dy), float(deta)
@@ -130,6 +130,7 @@ def make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None
     c.precision = int(precision)
     c.cartesian, c.periodic = int(bool(cartesian)), int(bool(periodic))
     c.eps_cut = float(eps_cut)
+    c.kernel = int(kernel)
     return c, keep
 
 
@@ -139,13 +140,13 @@ class Hydro:
 
     def __init__(self, nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
                  precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7,
-                 stream=None, device=None, torch_workspace=True):
+                 stream=None, device=None, torch_workspace=True, kernel=0):
         import torch
         self._lib = load()
         self.torch = torch
         self.device = torch.device(device or "cuda")
         self.cfg, self._keep = make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s, eos,
-                                           precision, cartesian, periodic, eps_cut)
+                                           precision, cartesian, periodic, eps_cut, kernel)
         self.shape = (int(nx), int(ny), int(neta))
         self.N = int(nx) * int(ny) * int(neta)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -4,14 +4,16 @@
 // the kernels of clv_kernels.cuh.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
 
-#include "../../include/clv.h"
+#include "clv.h"
 #include "clv_kernels.cuh"
+#include "clv_tile.cuh"
 
 using namespace clv;
 
@@ -29,6 +31,8 @@ struct DevStats {
   unsigned long long counters[4];  // rescaled, root cap, polished, spare
   unsigned int err;
   unsigned int pad;
+  unsigned long long fail_cell;  // first cell (+1) whose root solve hit the cap
+  double fail_EM[2];
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -66,6 +70,12 @@ struct clv_handle {
   std::vector<cudaEvent_t> ev_pending;  // triples: before stage 1, between, after stage 2
   double t_ms[2] = {0.0, 0.0};
   long long t_launches[2] = {0, 0};
+  // tiled stage kernel geometry
+  TileArgs tile{};
+  int tile_threads = 0;
+  unsigned tile_blocks = 0;
+  size_t tile_smem = 0;
+  int stat_blocks = 0;  // block partials written by the last stats launch
 };
 
 namespace {
@@ -97,16 +107,50 @@ clv_status validate(const clv_config* c) {
     return fail(nullptr, CLV_EINVAL, "unknown eos_kind");
   }
   if (!(c->eps_cut >= 0)) return fail(nullptr, CLV_EINVAL, "eps_cut must be >= 0");
+  if (c->kernel != 0 && c->kernel != 1) return fail(nullptr, CLV_EINVAL, "unknown kernel variant");
   long long N = (long long)c->nx * c->ny * c->neta;
   if (N > (1LL << 34)) return fail(nullptr, CLV_EINVAL, "grid too large");
   return CLV_OK;
+}
+
+struct TileGeom {
+  TileArgs t;
+  int threads;
+  unsigned blocks;
+  size_t smem;
+};
+
+// Tile shape: TK columns fit neta in ceil(neta/32) tiles; the block has
+// (TJ+1) x (TK+1) threads, at most 256 (FP32) or 128 (FP64); x is cut into
+// chunks so that there are about two CTAs per SM.
+TileGeom tile_geometry(const clv_config* c, int sms) {
+  const int rsize = c->precision == CLV_FP64 ? 8 : 4;
+  const int maxthr = rsize == 4 ? kBlock : kBlock / 2;
+  const int nk = (c->neta + 31) / 32;
+  TileGeom g;
+  TileArgs& t = g.t;
+  t.TK = (c->neta + nk - 1) / nk;
+  t.TJ = std::max(1, std::min(c->ny, maxthr / (t.TK + 1) - 1));
+  t.ntj = (c->ny + t.TJ - 1) / t.TJ;
+  t.ntk = (c->neta + t.TK - 1) / t.TK;
+  const long long tiles = (long long)t.ntj * t.ntk;
+  long long nch = std::max(1LL, std::min((long long)c->nx, (2LL * sms + tiles - 1) / tiles));
+  t.CX = (int)((c->nx + nch - 1) / nch);
+  nch = (c->nx + t.CX - 1) / t.CX;
+  g.threads = (t.TJ + 1) * (t.TK + 1);
+  g.blocks = (unsigned)(tiles * nch);
+  const bool visc = c->eta_over_s > 0.0;
+  g.smem = (visc ? tile_smem_elems<true>(t.TJ, t.TK) : tile_smem_elems<false>(t.TJ, t.TK)) * rsize;
+  return g;
 }
 
 size_t layout(const clv_config* c, clv_handle* h) {
   const long long N = (long long)c->nx * c->ny * c->neta;
   const size_t rs = c->precision == CLV_FP64 ? 8 : 4;
   const size_t fb = align_up((size_t)N * rs, 256);
-  const int nblocks = (int)((N + kBlock - 1) / kBlock);
+  // block partials of the stats reduction: enough for the direct grid and for
+  // the tiled grid on any device (at most 1024 SMs)
+  const int nblocks = (int)std::max<long long>((N + kBlock - 1) / kBlock, tile_geometry(c, 1024).blocks);
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off += align_up(bytes, 256); return o; };
   size_t oT0[4], oPI0[10], oT1[4], oPI1[10], oPR[kNumPrimSets][kPrimFields], oE[3];
@@ -152,12 +196,13 @@ template <typename R> EosView<R> eos_view(const clv_handle* h) {
   EosView<R> v;
   v.kind = c.eos_kind;
   v.n = c.eos_kind == CLV_EOS_TABLE ? c.eos_n : 1;
-  v.lne0 = c.eos_lne0;
-  v.inv_dlne = c.eos_kind == CLV_EOS_TABLE ? 1.0 / c.eos_dlne : 0.0;
-  v.e0 = std::exp(c.eos_lne0);
-  v.e_top = std::exp(c.eos_lne0 + (v.n - 1) * c.eos_dlne);
+  v.lne0 = (R)c.eos_lne0;
+  v.inv_dlne = (R)(c.eos_kind == CLV_EOS_TABLE ? 1.0 / c.eos_dlne : 0.0);
+  v.e0 = (R)std::exp(c.eos_lne0);
+  v.e_top = (R)std::exp(c.eos_lne0 + (v.n - 1) * c.eos_dlne);
+  v.top = (R)(v.n - 1);
   const double pi = 3.14159265358979323846;
-  v.t_coef = 30.0 * kHbarC * kHbarC * kHbarC / (kDofConformal * pi * pi);
+  v.t_coef = (R)(30.0 * kHbarC * kHbarC * kHbarC / (kDofConformal * pi * pi));
   v.P = (const R*)h->eos[0];
   v.T = (const R*)h->eos[1];
   v.cs2 = (const R*)h->eos[2];
@@ -189,22 +234,27 @@ StageParams<R> stage_params(clv_handle* h, int stage, double tau_stage, double t
   p.eos = eos_view<R>(h);
   p.nx = c.nx; p.ny = c.ny; p.ne = c.neta; p.periodic = c.periodic;
   p.N = h->N;
-  p.taus = c.cartesian ? 1.0 : tau_stage;
-  p.geo = c.cartesian ? 0.0 : 1.0 / tau_stage;
-  p.taus_new = c.cartesian ? 1.0 : tau_new;
-  p.h = c.dtau;
-  p.inv_dl[0] = 1.0 / c.dx;
-  p.inv_dl[1] = 1.0 / c.dy;
-  p.inv_dl[2] = 1.0 / (p.taus * c.deta);
-  p.st_tau = c.cartesian ? 0.0 : 1.0;
-  p.eps_cut = c.eps_cut;
-  p.eta_over_s = c.eta_over_s;
-  p.polish_E = 1e-2;
-  p.polish_v = 0.9;
+  const double taus = c.cartesian ? 1.0 : tau_stage;
+  p.taus = (R)taus;
+  p.geo = (R)(c.cartesian ? 0.0 : 1.0 / tau_stage);
+  p.taus_new = (R)(c.cartesian ? 1.0 : tau_new);
+  p.h = (R)c.dtau;
+  p.inv_h = (R)(1.0 / c.dtau);
+  p.inv_dl[0] = (R)(1.0 / c.dx);
+  p.inv_dl[1] = (R)(1.0 / c.dy);
+  p.inv_dl[2] = (R)(1.0 / (taus * c.deta));
+  p.st_tau = (R)(c.cartesian ? 0.0 : 1.0);
+  p.eps_cut = (R)c.eps_cut;
+  p.eps_cut_d = c.eps_cut;
+  p.inv_5etas_hbarc = (R)(c.eta_over_s > 0 ? 1.0 / (5.0 * c.eta_over_s * kHbarC) : 0.0);
+  p.polish_E = (R)(2.0 * c.eps_cut);
+  p.polish_v = (R)0.99;
   p.block_sum = h->block_sum;
   p.emax_bits = &h->dstats->emax_bits;
   p.counters = h->dstats->counters;
   p.err = &h->dstats->err;
+  p.fail_cell = &h->dstats->fail_cell;
+  p.fail_EM = h->dstats->fail_EM;
   return p;
 }
 
@@ -223,18 +273,51 @@ cudaEvent_t timing_event(clv_handle* h) {
   return e;
 }
 
+void choose_tile(clv_handle* h) {
+  int sms = 148, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  TileGeom g = tile_geometry(&h->cfg, sms);
+  h->tile = g.t;
+  h->tile_threads = g.threads;
+  h->tile_blocks = g.blocks;
+  h->tile_smem = g.smem;
+}
+
+template <typename R, bool VISC> cudaError_t tile_attributes(size_t smem) {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  };
+  set((const void*)stage_tile_kernel<R, 1, VISC, false>);
+  set((const void*)stage_tile_kernel<R, 2, VISC, false>);
+  set((const void*)stage_tile_kernel<R, 2, VISC, true>);
+  return e;
+}
+
+template <typename R, bool VISC, int STAGE, bool STATS>
+void launch_stage(clv_handle* h, const StageParams<R>& p) {
+  if (h->cfg.kernel == 1) {
+    stage_kernel<R, STAGE, VISC, STATS><<<grid_of(h->N), kBlock, 0, h->stream>>>(p);
+  } else {
+    stage_tile_kernel<R, STAGE, VISC, STATS><<<h->tile_blocks, h->tile_threads, h->tile_smem, h->stream>>>(p, h->tile);
+  }
+}
+
 template <typename R, bool VISC>
 void launch_step(clv_handle* h, bool stats) {
   const double tn = h->tau, tn1 = h->tau + h->cfg.dtau;
-  const unsigned g = grid_of(h->N);
   const bool timed = h->timing && h->ev_pending.size() < 3 * kMaxTimedSteps;
   if (timed) timing_event(h);
   StageParams<R> p1 = stage_params<R>(h, 1, tn, tn1);
-  stage_kernel<R, 1, VISC, false><<<g, kBlock, 0, h->stream>>>(p1);
+  launch_stage<R, VISC, 1, false>(h, p1);
   if (timed) timing_event(h);
   StageParams<R> p2 = stage_params<R>(h, 2, tn1, tn1);
-  if (stats) stage_kernel<R, 2, VISC, true><<<g, kBlock, 0, h->stream>>>(p2);
-  else stage_kernel<R, 2, VISC, false><<<g, kBlock, 0, h->stream>>>(p2);
+  if (stats) {
+    launch_stage<R, VISC, 2, true>(h, p2);
+    h->stat_blocks = h->cfg.kernel == 1 ? (int)grid_of(h->N) : (int)h->tile_blocks;
+  } else {
+    launch_stage<R, VISC, 2, false>(h, p2);
+  }
   if (timed) timing_event(h);
   std::swap(h->cur, h->prev);
   h->tau = tn1;
@@ -263,10 +346,10 @@ template <typename R> __global__ void stats_scan_kernel(const R* e, const R* T0,
 
 template <typename R> __global__ void finalize_stats_kernel(DevStats* ds, EosView<R> eos) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double e = __longlong_as_double((long long)ds->emax_bits);
-    double P, T, c2;
-    eos_eval<double, R>(eos, e, P, T, c2);
-    ds->T_at_emax = T;
+    const R e = (R)__longlong_as_double((long long)ds->emax_bits);
+    R P, T, c2;
+    eos_eval<R, R>(eos, e, P, T, c2);
+    ds->T_at_emax = (double)T;
   }
 }
 
@@ -276,8 +359,9 @@ template <typename R> clv_status reduce_stats(clv_handle* h, bool scan, clv_stat
     CLV_CUDA(h, cudaMemsetAsync(&h->dstats->emax_bits, 0, sizeof(unsigned long long), h->stream));
     stats_scan_kernel<R><<<grid_of(h->N), kBlock, 0, h->stream>>>(
         (const R*)h->PR[h->cur][0], (const R*)h->T0[0], h->N, h->block_sum, &h->dstats->emax_bits);
+    h->stat_blocks = (int)grid_of(h->N);
   }
-  finalize_sum_kernel<<<1, 1024, 0, h->stream>>>(h->block_sum, h->nblocks, &h->dstats->esum);
+  finalize_sum_kernel<<<1, 1024, 0, h->stream>>>(h->block_sum, h->stat_blocks, &h->dstats->esum);
   finalize_stats_kernel<R><<<1, 32, 0, h->stream>>>(h->dstats, eos_view<R>(h));
   CLV_CUDA(h, cudaGetLastError());
   DevStats ds;
@@ -295,7 +379,14 @@ template <typename R> clv_status reduce_stats(clv_handle* h, bool scan, clv_stat
   out->error_word = ds.err;
   out->_pad = 0;
   if (ds.err & 2u) return fail(h, CLV_ENONFINITE, "non-finite value in the state");
-  if (ds.err & 1u) return fail(h, CLV_EROOT, "primitive root solve hit its iteration cap");
+  if (ds.err & 1u) {
+    char msg[256];
+    const long long cell = (long long)ds.fail_cell - 1;
+    std::snprintf(msg, sizeof msg,
+                  "primitive root solve hit its iteration cap (%lld cells; first: cell %lld, E=%.17g, |M|=%.17g)",
+                  (long long)ds.counters[1], cell, ds.fail_EM[0], ds.fail_EM[1]);
+    return fail(h, CLV_EROOT, msg);
+  }
   if (ds.err & 4u) return fail(h, CLV_ETIMEOUT, "a bounded device wait gave up");
   return CLV_OK;
 }
@@ -399,6 +490,17 @@ clv_status create_common(const clv_config* cfg, void* stream, void* ws, size_t w
   h->ws_bytes = need;
   layout(cfg, h);
   h->tau = cfg->tau0;
+  choose_tile(h);
+  {
+    // the ideal first step of viscous runs uses the ideal tile kernels with the viscous tile shape
+    cudaError_t e = h->rsize == 8 ? tile_attributes<double, false>(h->tile_smem) : tile_attributes<float, false>(h->tile_smem);
+    if (e == cudaSuccess && h->viscous)
+      e = h->rsize == 8 ? tile_attributes<double, true>(h->tile_smem) : tile_attributes<float, true>(h->tile_smem);
+    if (e != cudaSuccess) {
+      clv_destroy(h);
+      return fail(nullptr, CLV_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    }
+  }
   // EOS table in the working precision
   if (cfg->eos_kind == CLV_EOS_TABLE) {
     const int n = cfg->eos_n;

@@ -40,9 +40,10 @@ template <> struct Fast<double> {
 template <typename R> struct EosView {
   int kind;        // 0 conformal, 1 table
   int n;
-  double lne0, inv_dlne;
-  double e0, e_top;        // eps of node 0 and of the last node
-  double t_coef;           // conformal: T^4 = t_coef * e
+  R lne0, inv_dlne;
+  R e0, e_top;             // eps of node 0 and of the last node
+  R t_coef;                // conformal: T^4 = t_coef * e
+  R top;                   // n - 1 as R
   const R* P;
   const R* T;
   const R* cs2;
@@ -71,7 +72,7 @@ __device__ __forceinline__ void eos_eval(const EosView<R>& q, C e, C& P, C& T, C
     cs2 = C(__ldg(q.cs2));
     return;
   }
-  if (x >= C(q.n - 1)) {
+  if (x >= C(q.top)) {
     P = C(__ldg(q.P + q.n - 1)) + (e - C(q.e_top)) * C(1.0 / 3.0);
     T = C(__ldg(q.T + q.n - 1)) * sqrt(sqrt(e / C(q.e_top)));
     cs2 = C(1.0 / 3.0);
@@ -98,7 +99,10 @@ struct RootResult {
   int rescaled;   // |M| > (1-1e-6) E was rescaled
 };
 
-template <typename C, typename R>
+// C: arithmetic of the solve (E - M v, f, Newton step, gamma); CE: arithmetic
+// of the EOS lookup (CE may be narrower than C: the FP32 path refines in FP64
+// around an FP32 table lookup).
+template <typename C, typename R, typename CE = C>
 __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps_cut, C E, C Mx,
                                                       C My, C Me, C tol, int maxit, C& eps,
                                                       C& ux, C& uy, C& ue, C* vguess = nullptr) {
@@ -120,28 +124,38 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
     return rr;
   }
   C lo = C(0), hi = M / E;
-  C P, T, cs2;
+  C P, cs2;
   C v;
   if (vguess && *vguess > lo && *vguess < hi) {
     v = *vguess;
   } else {
-    eos_eval<C, R>(q, E, P, T, cs2);
+    CE Pe, Te, ce;
+    eos_eval<CE, R>(q, CE(E), Pe, Te, ce);
+    P = C(Pe);
     v = M / (E + P);
   }
   int it = 1;
   bool ok = false;
   for (; it <= maxit; ++it) {
     C e = E - M * v;
-    eos_eval<C, R>(q, e, P, T, cs2);
+    {
+      CE Pe, Te, ce;
+      eos_eval<CE, R>(q, CE(e), Pe, Te, ce);
+      P = C(Pe);
+      cs2 = C(ce);
+    }
     C den = E + P;
     C f = v - M / den;
     if (f > C(0)) hi = v; else lo = v;
     C fp = C(1) - cs2 * (M * M) / (den * den);
-    C vn = v - f / fp;
+    const C dv = -f / fp;
+    // converged when the Newton step is below tol; otherwise keep the iterate
+    // strictly inside the shrinking bracket
+    if (fabs(dv) <= tol) { v += dv; ok = true; break; }
+    C vn = v + dv;
     if (!(vn > lo && vn < hi)) vn = C(0.5) * (lo + hi);
-    C dv = vn - v;
     v = vn;
-    if (fabs(dv) <= tol) { ok = true; break; }
+    if (hi - lo <= tol) { ok = true; break; }
   }
   rr.iters = ok ? it : -1;
   if (vguess) *vguess = v;
@@ -155,6 +169,11 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
   ue = s * Me;
   return rr;
 }
+
+// Product rounded on its own (never fused into a neighbouring add), so that
+// differences of equal products cancel exactly.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 template <typename R> __device__ __forceinline__ R minmod(R a, R b) {
   return (a > R(0) && b > R(0)) ? fmin(a, b) : ((a < R(0) && b < R(0)) ? fmax(a, b) : R(0));

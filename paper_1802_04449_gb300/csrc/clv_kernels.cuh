@@ -37,19 +37,24 @@ template <typename R> struct StageParams {
   EosView<R> eos;
   int nx, ny, ne, periodic;
   long long N;
-  double taus;      // tau (Milne) or 1 (Cartesian) at the stage time
-  double geo;       // 1/tau (Milne) or 0 (Cartesian) at the stage time
-  double taus_new;  // tau scale at the end of the step (primitive recovery)
-  double h;         // time step
-  double inv_dl[3]; // 1/dx, 1/dy, 1/(tau deta)
-  double st_tau;    // 1 in Milne (S_T^tau active), 0 in Cartesian
-  double eps_cut, eta_over_s;
-  double polish_E, polish_v;   // FP32: FP64 Newton for E < polish_E or M > polish_v E
+  // scalars in the working precision (no conversions inside the kernels)
+  R taus;      // tau (Milne) or 1 (Cartesian) at the stage time
+  R geo;       // 1/tau (Milne) or 0 (Cartesian) at the stage time
+  R taus_new;  // tau scale at the end of the step (primitive recovery)
+  R h, inv_h;  // time step and its inverse
+  R inv_dl[3]; // 1/dx, 1/dy, 1/(tau deta)
+  R st_tau;    // 1 in Milne (S_T^tau active), 0 in Cartesian
+  R eps_cut;
+  R inv_5etas_hbarc;   // 1/(5 (eta/s) hbar c): 1/tau_pi = T * this
+  R polish_E, polish_v;   // FP32: FP64 Newton for E < polish_E or M > polish_v E
+  double eps_cut_d;
   // reductions and error reporting
   double* block_sum;             // per block: sum of new T~^{tau tau} (stats launches only)
   unsigned long long* emax_bits; // max eps as the bits of a non-negative double
   unsigned long long* counters;  // [0] rescaled, [1] root cap, [2] polished
   unsigned int* err;             // error word
+  unsigned long long* fail_cell; // first failing cell + 1 (0: none)
+  double* fail_EM;               // E and |M| of that cell
 };
 
 __device__ __forceinline__ int wrap_index(int i, int n, int periodic) {
@@ -64,8 +69,8 @@ template <typename R> __device__ __forceinline__ R ldg(const R* p) { return __ld
 
 template <typename R> struct SolveTraits;
 template <> struct SolveTraits<float> {
-  static constexpr float tol = 2.5e-7f;
-  static constexpr int maxit = 60;
+  static constexpr float tol = 5e-7f;
+  static constexpr int maxit = 40;
 };
 template <> struct SolveTraits<double> {
   static constexpr double tol = 1e-15;
@@ -164,7 +169,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
     constexpr int NR = NRec<VISC>::n;
     constexpr int NQ = VISC ? 14 : 4;
     constexpr int IU = VISC ? 14 : 4, IV = IU + 1;
-    const R taus = R(p.taus);
+    const R taus = p.taus;
     R S[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) S[q] = R(0);
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       R Hm[NQ], Hp[NQ];
       interface_flux<R, VISC>(Lm, Rm, cs[1], cs[2], ax, taus, Hm);
       interface_flux<R, VISC>(Lp, Rp, cs[2], cs[3], ax, taus, Hp);
-      const R inv = R(p.inv_dl[ax - 1]);
+      const R inv = p.inv_dl[ax - 1];
 #pragma unroll
       for (int q = 0; q < NQ; ++q) S[q] -= (Hp[q] - Hm[q]) * inv;
     }
@@ -241,8 +246,8 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
     {
       R Tee = e * u[3] * u[3] + Pc * (R(1) + u[3] * u[3]);
       if constexpr (VISC) Tee += pic[9];
-      S[0] -= R(p.st_tau) * Tee;
-      S[3] -= R(p.geo) * p.T[3][c];
+      S[0] -= p.st_tau * Tee;
+      S[3] -= p.geo * p.T[3][c];
     }
     // u~ at step n and the late velocity (u* in stage 1, u' in stage 2)
     R un[4], ul[4];
@@ -267,25 +272,25 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       }
       // d~_a u~^b: time difference and central differences
       R du[4][4];
-      const R invh = R(1) / R(p.h);
+      const R invh = p.inv_h;
 #pragma unroll
       for (int b = 0; b < 4; ++b) du[0][b] = (ul[b] - un[b]) * invh;
 #pragma unroll
       for (int a = 1; a <= 3; ++a) {
-        const R half_inv = R(0.5) * R(p.inv_dl[a - 1]);
+        const R half_inv = R(0.5) * p.inv_dl[a - 1];
 #pragma unroll
         for (int b = 0; b < 4; ++b) du[a][b] = (unb[a - 1][1][b] - unb[a - 1][0][b]) * half_inv;
       }
       R Pdummy, Tc, c2dummy;
       eos_eval<R, R>(p.eos, e, Pdummy, Tc, c2dummy);
-      const R inv_taupi = Tc / (R(5) * R(p.eta_over_s) * R(kHbarC));
+      const R inv_taupi = Tc * p.inv_5etas_hbarc;
       R Spi[10];
-      shear_source<R>(R(p.geo), u, du, pic, e, Pc, inv_taupi, Spi);
+      shear_source<R>(p.geo, u, du, pic, e, Pc, inv_taupi, Spi);
 #pragma unroll
       for (int q = 0; q < 10; ++q) S[4 + q] += Spi[q];
     }
     // ---------------- stage update (Sec. 3) ----------------
-    const R h = R(p.h);
+    const R h = p.h;
     R Tnew[4], pinew[10];
     if constexpr (STAGE == 1) {
 #pragma unroll
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       }
     }
     // ---------------- primitive recovery from T_ideal = T - pi ----------------
-    const R tn = R(p.taus_new);
+    const R tn = p.taus_new;
     R E = Tnew[0] / tn, Mx = Tnew[1] / tn, My = Tnew[2] / tn, Me = Tnew[3] / tn;
     if constexpr (VISC) {
       E -= pinew[0]; Mx -= pinew[1]; My -= pinew[2]; Me -= pinew[3];
@@ -315,14 +320,18 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       f_nonfinite = true;
     } else {
       R vg = R(-1);
-      RootResult rr = solve_primitive<R, R>(p.eos, R(p.eps_cut), E, Mx, My, Me, SolveTraits<R>::tol,
+      RootResult rr = solve_primitive<R, R>(p.eos, p.eps_cut, E, Mx, My, Me, SolveTraits<R>::tol,
                                             SolveTraits<R>::maxit, en, ux, uy, ue, &vg);
       f_rescaled = rr.rescaled;
       if constexpr (sizeof(R) == 4) {
+        // FP64 Newton near the vacuum, at high velocity, and wherever the
+        // FP32 solve did not converge
         const R M = sqrt(Mx * Mx + My * My + Me * Me);
-        if (E >= R(p.eps_cut) && M > R(0) && (E < R(p.polish_E) || M > R(p.polish_v) * E)) {
+        if (E >= p.eps_cut && M > R(0) &&
+            (E < p.polish_E || M > p.polish_v * E || rr.iters < 0)) {
+          if (rr.iters < 0) vg = R(-1);
           double dv = (double)vg, de, dux, duy, due;
-          RootResult r2 = solve_primitive<double, R>(p.eos, p.eps_cut, (double)E, (double)Mx,
+          RootResult r2 = solve_primitive<double, R, float>(p.eos, p.eps_cut_d, (double)E, (double)Mx,
                                                      (double)My, (double)Me, 1e-13, 40, de, dux,
                                                      duy, due, &dv);
           en = R(de); ux = R(dux); uy = R(duy); ue = R(due);
@@ -331,6 +340,10 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
         }
       }
       f_fail = rr.iters < 0;
+      if (f_fail && atomicCAS(p.fail_cell, 0ull, (unsigned long long)c + 1ull) == 0ull) {
+        p.fail_EM[0] = (double)E;
+        p.fail_EM[1] = (double)sqrt(Mx * Mx + My * My + Me * Me);
+      }
     }
     R Pn, Tn_, c2n;
     eos_eval<R, R>(p.eos, en, Pn, Tn_, c2n);

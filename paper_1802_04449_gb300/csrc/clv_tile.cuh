@@ -1,0 +1,419 @@
+// clv_tile.cuh -- tiled stage kernel.
+//
+// A CTA owns a (y, eta_s) tile of TJ x TK cells and marches along x over a
+// chunk of CX planes.  Per plane:
+//   1. the tile plus a two-cell halo in y and eta_s is staged once in shared
+//      memory as the per-cell reconstruction fields (T~, pi~, u~^tau, v, P, c_s);
+//   2. every y- and eta_s-interface flux of the tile is computed once: the
+//      block has (TJ+1) x (TK+1) threads, thread (a, b) computes the
+//      y-interface below row a of column b and the eta_s-interface left of
+//      column b of row a, so each thread does at most one interface per axis;
+//   3. each cell thread forms its y/eta_s flux differences and the y/eta_s
+//      derivatives of u~, which wait in shared memory for two planes.
+// The x-direction stencil lives in a register window over the thread's own
+// column: every x-interface is computed once, when the plane two cells to its
+// right arrives.
+#pragma once
+#include "clv_kernels.cuh"
+
+namespace clv {
+
+template <bool VISC> struct Box {
+  static constexpr int UT = VISC ? 14 : 4;  // u~^tau
+  static constexpr int V = UT + 1;          // v^x, v^y, v^eta
+  static constexpr int P = UT + 4;
+  static constexpr int CS = UT + 5;
+  static constexpr int NF = UT + 6;         // staged fields per cell
+  static constexpr int NQ = VISC ? 14 : 4;  // conserved components
+  static constexpr int NR = NRec<VISC>::n;  // reconstructed per interface
+  static constexpr int NDU = VISC ? 8 : 0;  // d~_y u~^b, d~_eta u~^b
+  static constexpr int NPEND = NQ + NDU;
+};
+
+struct TileArgs {
+  int TJ, TK, CX;     // tile rows (y), tile columns (eta), planes per chunk (x)
+  int ntj, ntk;       // tiles per plane
+};
+
+// shared memory of one CTA, in elements of the working type
+template <bool VISC> inline size_t tile_smem_elems(int TJ, int TK) {
+  using L = Box<VISC>;
+  const size_t NB = (size_t)(TJ + 4) * (TK + 4);
+  return L::NF * NB + (size_t)L::NQ * ((TJ + 1) * TK + TJ * (TK + 1)) + 2 * (size_t)L::NPEND * TJ * TK;
+}
+
+// component q of the reconstruction vector along axis a from staged fields
+template <bool VISC, typename R>
+__device__ __forceinline__ R rec_comp(const R* f, int q, int a) {
+  using L = Box<VISC>;
+  constexpr int IU = L::UT;
+  if (q < IU) return f[q];
+  if (q == IU) return f[L::UT];
+  if (q == IU + 1) return f[L::V + a - 1];
+  return f[L::P];
+}
+
+// Interface flux between box cells c - stride and c, reading cells
+// c - 2 stride .. c + stride (minmod slopes at both sides).
+template <typename R, bool VISC>
+__device__ __forceinline__ void box_interface(const R* box, int NB, int c, int stride, int ax, R taus,
+                                              R* H) {
+  using L = Box<VISC>;
+  constexpr int NR = L::NR;
+  R Ls[NR], Rs[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    const int f = q < L::UT ? q : (q == L::UT ? L::UT : (q == L::UT + 1 ? L::V + ax - 1 : L::P));
+    const R* col = box + f * NB + c;
+    const R v0 = col[-2 * stride], v1 = col[-stride], v2 = col[0], v3 = col[stride];
+    Ls[q] = v1 + R(0.5) * minmod(v1 - v0, v2 - v1);
+    Rs[q] = v2 - R(0.5) * minmod(v2 - v1, v3 - v2);
+  }
+  const R* cs = box + L::CS * NB + c;
+  interface_flux<R, VISC>(Ls, Rs, cs[-stride], cs[0], ax, taus, H);
+}
+
+#ifndef CLV_TILE_MIN_BLOCKS
+#define CLV_TILE_MIN_BLOCKS 1
+#endif
+
+template <typename R, int STAGE, bool VISC, bool STATS>
+__global__ void __launch_bounds__(kBlock, CLV_TILE_MIN_BLOCKS) stage_tile_kernel(const StageParams<R> p, const TileArgs t) {
+  using L = Box<VISC>;
+  constexpr int NF = L::NF, NQ = L::NQ, NR = L::NR, NPEND = L::NPEND;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int BW = t.TK + 4, NB = BW * (t.TJ + 4);
+  const int NHY = (t.TJ + 1) * t.TK, NHK = t.TJ * (t.TK + 1);
+  const int ncell = t.TJ * t.TK;
+  R* box = reinterpret_cast<R*>(smem_raw);
+  R* Hy = box + NF * NB;       // [NQ][TJ+1][TK]
+  R* Hk = Hy + NQ * NHY;       // [NQ][TJ][TK+1]
+  R* pend = Hk + NQ * NHK;     // [2][NPEND][ncell]
+
+  const int tid = threadIdx.x;
+  const int nthr = (t.TJ + 1) * (t.TK + 1);
+  const int ta = tid / (t.TK + 1), tb = tid - ta * (t.TK + 1);
+  int bidx = blockIdx.x;
+  const int tkt = bidx % t.ntk;
+  bidx /= t.ntk;
+  const int tjt = bidx % t.ntj;
+  const int ch = bidx / t.ntj;
+  const int j0 = tjt * t.TJ, k0 = tkt * t.TK, x0 = ch * t.CX;
+  const int x1 = min(x0 + t.CX, p.nx);
+  const bool is_cell = ta < t.TJ && tb < t.TK;
+  const int j = j0 + ta, k = k0 + tb;
+  const bool active = is_cell && j < p.ny && k < p.ne;
+  const int cid = ta * t.TK + tb;                  // cell slot (valid when is_cell)
+  const int center = (ta + 2) * BW + (tb + 2);     // box cell of (ta, tb)
+  const R taus = p.taus;
+  const R inv_dx = p.inv_dl[0];
+
+  R W0[NF], W1[NF];      // staged fields of the own column at planes pl-2, pl-1
+  R S0[NR];              // x-slope at plane pl-2
+  R Hprev[NQ];           // x-interface flux at c - 1/2
+  R ucm1[4];             // u~ at plane c - 1
+#pragma unroll
+  for (int f = 0; f < NF; ++f) { W0[f] = R(0); W1[f] = R(0); }
+#pragma unroll
+  for (int q = 0; q < NR; ++q) S0[q] = R(0);
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) Hprev[q] = R(0);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) ucm1[m] = R(0);
+
+  double sum_T0 = 0.0, max_e = 0.0;
+  int n_res = 0, n_fail = 0, n_pol = 0, n_nf = 0;
+
+  for (int pl = x0 - 2; pl <= x1 + 1; ++pl) {
+    const int ip = wrap_index(pl, p.nx, p.periodic);
+    const bool out_plane = pl >= x0 && pl < x1;
+    __syncthreads();
+    // ---- 1. stage plane ip of the tile with its y/eta halo
+    for (int q = tid; q < NB; q += nthr) {
+      const int bj = q / BW, bk = q - (q / BW) * BW;
+      const int gj = wrap_index(j0 + bj - 2, p.ny, p.periodic);
+      const int gk = wrap_index(k0 + bk - 2, p.ne, p.periodic);
+      const long long g = ((long long)ip * p.ny + gj) * p.ne + gk;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) box[m * NB + q] = ldg(p.T[m] + g);
+      if constexpr (VISC) {
+#pragma unroll
+        for (int r = 0; r < 10; ++r) box[(4 + r) * NB + q] = ldg(p.pi[r] + g);
+      }
+      const R ux = ldg(p.pr.u[0] + g), uy = ldg(p.pr.u[1] + g), ue = ldg(p.pr.u[2] + g);
+      const R ut = sqrt(R(1) + ux * ux + uy * uy + ue * ue);
+      const R iu = R(1) / ut;
+      box[L::UT * NB + q] = ut;
+      box[(L::V + 0) * NB + q] = ux * iu;
+      box[(L::V + 1) * NB + q] = uy * iu;
+      box[(L::V + 2) * NB + q] = ue * iu;
+      box[L::P * NB + q] = ldg(p.pr.P + g);
+      box[L::CS * NB + q] = ldg(p.pr.cs + g);
+    }
+    __syncthreads();
+    // ---- 2. every y- and eta-interface of an output plane, once
+    if (out_plane) {
+      R H[NQ];
+      if (tb < t.TK) {   // y-interface between rows ta-1 and ta of column tb
+        box_interface<R, VISC>(box, NB, (ta + 2) * BW + tb + 2, BW, 2, taus, H);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) Hy[q * NHY + ta * t.TK + tb] = H[q];
+      }
+      if (ta < t.TJ) {   // eta-interface between columns tb-1 and tb of row ta
+        box_interface<R, VISC>(box, NB, (ta + 2) * BW + tb + 2, 1, 3, taus, H);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) Hk[q * NHK + ta * (t.TK + 1) + tb] = H[q];
+      }
+      __syncthreads();
+    }
+    if (is_cell) {
+      R Wn[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) Wn[f] = box[f * NB + center];
+      const int it = pl - (x0 - 2);
+      if (it >= 2) {
+        // x-slope at plane pl-1
+        R S1[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          const R a = rec_comp<VISC>(W0, q, 1), m = rec_comp<VISC>(W1, q, 1), c = rec_comp<VISC>(Wn, q, 1);
+          S1[q] = minmod(m - a, c - m);
+        }
+        if (it >= 3) {
+          // x-interface between planes pl-2 and pl-1
+          R Ls[NR], Rs[NR], H[NQ];
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            Ls[q] = rec_comp<VISC>(W0, q, 1) + R(0.5) * S0[q];
+            Rs[q] = rec_comp<VISC>(W1, q, 1) - R(0.5) * S1[q];
+          }
+          interface_flux<R, VISC>(Ls, Rs, W0[L::CS], W1[L::CS], 1, taus, H);
+          if (it >= 4 && active) {
+            // ============ output cell c = pl - 2 (own fields: W0) ============
+            const int c = pl - 2;
+            const long long gc = ((long long)c * p.ny + j) * p.ne + k;
+            const R* pd = pend + (size_t)(c & 1) * NPEND * ncell;
+            R S[NQ];
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) S[q] = pd[q * ncell + cid] - (H[q] - Hprev[q]) * inv_dx;
+            const R e = p.pr.e[gc];
+            const R Pc = W0[L::P];
+            R u[4];
+            u[0] = W0[L::UT];
+            u[1] = mul_rn(u[0], W0[L::V]);
+            u[2] = mul_rn(u[0], W0[L::V + 1]);
+            u[3] = mul_rn(u[0], W0[L::V + 2]);
+            {
+              R Tee = e * u[3] * u[3] + Pc * (R(1) + u[3] * u[3]);
+              if constexpr (VISC) Tee += W0[4 + 9];
+              S[0] -= p.st_tau * Tee;
+              S[3] -= p.geo * W0[3];
+            }
+            R un[4];
+            if constexpr (STAGE == 1) {
+#pragma unroll
+              for (int b2 = 0; b2 < 4; ++b2) un[b2] = u[b2];
+            } else {
+              un[1] = p.un[0][gc]; un[2] = p.un[1][gc]; un[3] = p.un[2][gc];
+              un[0] = sqrt(R(1) + un[1] * un[1] + un[2] * un[2] + un[3] * un[3]);
+            }
+            R ustar0 = un[0];
+            if constexpr (VISC) {
+              const R us1 = R(2) * un[1] - p.up[0][gc];
+              const R us2 = R(2) * un[2] - p.up[1][gc];
+              const R us3 = R(2) * un[3] - p.up[2][gc];
+              ustar0 = sqrt(R(1) + us1 * us1 + us2 * us2 + us3 * us3);
+              R ul[4];
+              if constexpr (STAGE == 1) {
+                ul[0] = ustar0; ul[1] = us1; ul[2] = us2; ul[3] = us3;
+              } else {
+#pragma unroll
+                for (int b2 = 0; b2 < 4; ++b2) ul[b2] = u[b2];
+              }
+              R du[4][4];
+              const R invh = p.inv_h;
+              const R half_dx = R(0.5) * inv_dx;
+              R up1[4];
+              up1[0] = W1[L::UT];
+              up1[1] = mul_rn(up1[0], W1[L::V]);
+              up1[2] = mul_rn(up1[0], W1[L::V + 1]);
+              up1[3] = mul_rn(up1[0], W1[L::V + 2]);
+#pragma unroll
+              for (int b2 = 0; b2 < 4; ++b2) {
+                du[0][b2] = (ul[b2] - un[b2]) * invh;
+                du[1][b2] = (up1[b2] - ucm1[b2]) * half_dx;
+                du[2][b2] = pd[(NQ + b2) * ncell + cid];
+                du[3][b2] = pd[(NQ + 4 + b2) * ncell + cid];
+              }
+              R Pd, Tc, c2d;
+              eos_eval<R, R>(p.eos, e, Pd, Tc, c2d);
+              const R inv_taupi = Tc * p.inv_5etas_hbarc;
+              R pic[10], Spi[10];
+#pragma unroll
+              for (int r = 0; r < 10; ++r) pic[r] = W0[4 + r];
+              shear_source<R>(p.geo, u, du, pic, e, Pc, inv_taupi, Spi);
+#pragma unroll
+              for (int r = 0; r < 10; ++r) S[4 + r] += Spi[r];
+            }
+            // ---- stage update (Sec. 3)
+            const R hh = p.h;
+            R Tnew[4], pinew[10];
+            if constexpr (STAGE == 1) {
+#pragma unroll
+              for (int m = 0; m < 4; ++m) Tnew[m] = W0[m] + hh * S[m];
+              if constexpr (VISC) {
+                const R inv = R(1) / ustar0;
+#pragma unroll
+                for (int r = 0; r < 10; ++r) pinew[r] = (un[0] * W0[4 + r] + hh * S[4 + r]) * inv;
+              }
+            } else {
+#pragma unroll
+              for (int m = 0; m < 4; ++m) Tnew[m] = R(0.5) * (p.Tn[m][gc] + W0[m] + hh * S[m]);
+              if constexpr (VISC) {
+                const R inv = R(0.5) / u[0];
+#pragma unroll
+                for (int r = 0; r < 10; ++r)
+                  pinew[r] = (un[0] * p.pin[r][gc] + ustar0 * W0[4 + r] + hh * S[4 + r]) * inv;
+              }
+            }
+            // ---- primitive recovery from T_ideal = T - pi, warm-started from
+            //      the stage velocity |v| of this cell
+            const R tn = p.taus_new;
+            R E = Tnew[0] / tn, Mx = Tnew[1] / tn, My = Tnew[2] / tn, Me = Tnew[3] / tn;
+            if constexpr (VISC) {
+              E -= pinew[0]; Mx -= pinew[1]; My -= pinew[2]; Me -= pinew[3];
+            }
+            R en = R(0), ux = R(0), uy = R(0), ue = R(0);
+            if (!(isfinite(E) && isfinite(Mx) && isfinite(My) && isfinite(Me))) {
+              ++n_nf;
+            } else {
+              R vg = sqrt(W0[L::V] * W0[L::V] + W0[L::V + 1] * W0[L::V + 1] + W0[L::V + 2] * W0[L::V + 2]);
+              RootResult rr = solve_primitive<R, R>(p.eos, p.eps_cut, E, Mx, My, Me, SolveTraits<R>::tol,
+                                                    SolveTraits<R>::maxit, en, ux, uy, ue, &vg);
+              n_res += rr.rescaled;
+              if constexpr (sizeof(R) == 4) {
+                // FP64 refinement of the cancellation-prone arithmetic (E - M v,
+                // Newton step, gamma) at high velocity, near the vacuum cutoff,
+                // and wherever the FP32 solve did not converge
+                const R M = sqrt(Mx * Mx + My * My + Me * Me);
+                if (E >= p.eps_cut && M > R(0) &&
+                    (E < p.polish_E || M > p.polish_v * E || rr.iters < 0)) {
+                  if (rr.iters < 0) vg = R(-1);
+                  double dv = (double)vg, de, dux, duy, due;
+                  RootResult r2 = solve_primitive<double, R, float>(p.eos, p.eps_cut_d, (double)E, (double)Mx,
+                                                                    (double)My, (double)Me, 1e-13, 40, de,
+                                                                    dux, duy, due, &dv);
+                  en = R(de); ux = R(dux); uy = R(duy); ue = R(due);
+                  ++n_pol;
+                  rr.iters = r2.iters;
+                }
+              }
+              if (rr.iters < 0) {
+                ++n_fail;
+                if (atomicCAS(p.fail_cell, 0ull, (unsigned long long)gc + 1ull) == 0ull) {
+                  p.fail_EM[0] = (double)E;
+                  p.fail_EM[1] = (double)sqrt(Mx * Mx + My * My + Me * Me);
+                }
+              }
+            }
+            R Pn, Tn_, c2n;
+            eos_eval<R, R>(p.eos, en, Pn, Tn_, c2n);
+#pragma unroll
+            for (int m = 0; m < 4; ++m) p.Tout[m][gc] = Tnew[m];
+            if constexpr (VISC) {
+              const bool vac = !(en > R(0));
+#pragma unroll
+              for (int r = 0; r < 10; ++r) p.piout[r][gc] = vac ? R(0) : pinew[r];
+            }
+            p.prout.e[gc] = en;
+            p.prout.u[0][gc] = ux;
+            p.prout.u[1][gc] = uy;
+            p.prout.u[2][gc] = ue;
+            p.prout.P[gc] = Pn;
+            p.prout.cs[gc] = sqrt(c2n);
+            if constexpr (STATS) {
+              sum_T0 += (double)Tnew[0];
+              max_e = fmax(max_e, (double)en);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) Hprev[q] = H[q];
+        }
+#pragma unroll
+        for (int q = 0; q < NR; ++q) S0[q] = S1[q];
+      }
+      // shift the window; keep u~ of plane pl-2 as u(c-1) for the next output
+      if constexpr (VISC) {
+        ucm1[0] = W0[L::UT];
+        ucm1[1] = mul_rn(W0[L::UT], W0[L::V]);
+        ucm1[2] = mul_rn(W0[L::UT], W0[L::V + 1]);
+        ucm1[3] = mul_rn(W0[L::UT], W0[L::V + 2]);
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) { W0[f] = W1[f]; W1[f] = Wn[f]; }
+      // ---- 3. y and eta_s flux differences of plane pl, consumed two planes later
+      if (out_plane && active) {
+        R* pd = pend + (size_t)(pl & 1) * NPEND * ncell;
+        const R iy = p.inv_dl[1], ie = p.inv_dl[2];
+        const int hy = ta * t.TK + tb, hk = ta * (t.TK + 1) + tb;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+          pd[q * ncell + cid] = -(Hy[q * NHY + hy + t.TK] - Hy[q * NHY + hy]) * iy -
+                                (Hk[q * NHK + hk + 1] - Hk[q * NHK + hk]) * ie;
+        if constexpr (VISC) {
+          // central differences d~_y u~^b and d~_eta u~^b
+#pragma unroll
+          for (int ax = 2; ax <= 3; ++ax) {
+            const int stride = ax == 2 ? BW : 1;
+            const R hinv = R(0.5) * p.inv_dl[ax - 1];
+            const R utp = box[L::UT * NB + center + stride], utm = box[L::UT * NB + center - stride];
+#pragma unroll
+            for (int b2 = 0; b2 < 4; ++b2) {
+              const R up_ = b2 == 0 ? utp : mul_rn(utp, box[(L::V + b2 - 1) * NB + center + stride]);
+              const R um_ = b2 == 0 ? utm : mul_rn(utm, box[(L::V + b2 - 1) * NB + center - stride]);
+              pd[(NQ + (ax - 2) * 4 + b2) * ncell + cid] = (up_ - um_) * hinv;
+            }
+          }
+        }
+      }
+    }
+  }
+  // ---- counters and reductions (valid for any block size <= kBlock)
+  __shared__ int s_cnt[4];
+  __shared__ double s_red[2][kBlock];
+  __syncthreads();
+  if (tid < 4) s_cnt[tid] = 0;
+  __syncthreads();
+  if (n_res) atomicAdd(&s_cnt[0], n_res);
+  if (n_fail) atomicAdd(&s_cnt[1], n_fail);
+  if (n_pol) atomicAdd(&s_cnt[2], n_pol);
+  if (n_nf) atomicAdd(&s_cnt[3], n_nf);
+  if constexpr (STATS) {
+    for (int i = tid; i < kBlock; i += nthr) {
+      s_red[0][i] = (i == tid) ? sum_T0 : 0.0;
+      s_red[1][i] = (i == tid) ? max_e : 0.0;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    if (s_cnt[0]) atomicAdd(p.counters + 0, (unsigned long long)s_cnt[0]);
+    if (s_cnt[1]) { atomicAdd(p.counters + 1, (unsigned long long)s_cnt[1]); atomicOr(p.err, 1u); }
+    if (s_cnt[2]) atomicAdd(p.counters + 2, (unsigned long long)s_cnt[2]);
+    if (s_cnt[3]) atomicOr(p.err, 2u);
+  }
+  if constexpr (STATS) {
+    for (int o = kBlock / 2; o > 0; o >>= 1) {
+      for (int i = tid; i < o; i += nthr) {
+        s_red[0][i] += s_red[0][i + o];
+        s_red[1][i] = fmax(s_red[1][i], s_red[1][i + o]);
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      p.block_sum[blockIdx.x] = s_red[0][0];
+      if (s_red[1][0] > 0.0) atomicMax(p.emax_bits, (unsigned long long)__double_as_longlong(s_red[1][0]));
+    }
+  }
+}
+
+}  // namespace clv

@@ -21,12 +21,12 @@ FP32_TOL = 1e-4
 EPS_FLOOR = 1e-3
 
 
-def run_pair(case, nsteps, precision, pi=None):
+def run_pair(case, nsteps, precision, pi=None, kernel=0):
     o = oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
                       case.eta_over_s, case.eos, case.cartesian, case.periodic)
     o.set_initial(case.eps, case.ux, case.uy, case.ueta, pi)
     o.step(nsteps)
-    g = clv.from_case(case, precision)
+    g = clv.from_case(case, precision, kernel=kernel)
     g.set_initial(case.eps, case.ux, case.uy, case.ueta, pi)
     st = g.step(nsteps, stats=True)
     return o, g, st
@@ -76,10 +76,10 @@ def test_fp64_gubser_ideal_config():
     assert st["error_word"] == 0
 
 
-@pytest.mark.parametrize("eta_over_s", [0.08, 0.16])
-def test_fp64_viscous_hotspots_table_eos(eta_over_s):
+@pytest.mark.parametrize("eta_over_s,kernel", [(0.08, 0), (0.16, 0), (0.08, 1)])
+def test_fp64_viscous_hotspots_table_eos(eta_over_s, kernel):
     case = small_hotspot(eta_over_s=eta_over_s)
-    o, g, st = run_pair(case, 30, clv.CLV_FP64)
+    o, g, st = run_pair(case, 30, clv.CLV_FP64, kernel=kernel)
     compare_fp64(o, g, viscous=True)
     so = o.stats()
     assert st["E_tot"] == pytest.approx(so["E_tot"], rel=1e-10)
@@ -94,7 +94,7 @@ def test_fp64_viscous_longitudinal_flow_with_pi():
     eta = I.cell_coords(ne, case.deta)
     case.ueta = np.broadcast_to(0.2 * np.sin(eta), case.eps.shape).copy()
     case.ux = 0.05 * rng.normal(size=case.eps.shape)
-    pi = 0.01 * rng.normal(size=(10,) + case.eps.shape) * case.eps.max()
+    pi = 0.02 * rng.normal(size=(10,) + case.eps.shape) * case.eps   # small against the local eps
     o, g, st = run_pair(case, 25, clv.CLV_FP64, pi=pi)
     compare_fp64(o, g, viscous=True)
 
@@ -114,6 +114,24 @@ def test_fp64_cartesian_periodic_box():
         assert abs(got[k].sum() - ini.get(k).sum()) <= 1e-12 * ini.get("Ttt").sum()
 
 
+@pytest.mark.parametrize("shape", [(23, 29, 41), (16, 9, 70), (7, 40, 3)])
+def test_tiled_kernel_matches_direct_kernel(shape):
+    """The tiled kernel (several tiles, chunks and ragged edges) and the direct
+    per-cell kernel run the same arithmetic: FP64 results agree to rounding."""
+    nx, ny, ne = shape
+    case = small_hotspot(nx=nx, ny=ny, neta=ne, nspots=80, seed=13)
+    out = []
+    for kern in (0, 1):
+        g = clv.from_case(case, clv.CLV_FP64, kernel=kern)
+        g.set_initial(case.eps, case.ux, case.uy, case.ueta)
+        g.step(12)
+        out.append(g.get())
+    for k in out[0]:
+        ref = out[1][k]
+        scale = np.abs(ref).max()
+        assert np.all(np.abs(out[0][k] - ref) <= 1e-12 * (np.abs(ref) + scale) + 1e-300), k
+
+
 def test_fp64_riemann_vacuum_front():
     nx = 241
     x, e = I.riemann_1d(nx, 0.05, 10.0)
@@ -126,10 +144,10 @@ def test_fp64_riemann_vacuum_front():
     assert st["n_rescaled"] > 0   # the vacuum front exercises the |M| > E branch
 
 
-@pytest.mark.parametrize("eos", ["crossover", None])
-def test_fp32_viscous_hotspots(eos):
+@pytest.mark.parametrize("eos,kernel", [("crossover", 0), (None, 0), ("crossover", 1)])
+def test_fp32_viscous_hotspots(eos, kernel):
     case = small_hotspot(seed=7, eos=eos)
-    o, g, st = run_pair(case, 40, clv.CLV_FP32)
+    o, g, st = run_pair(case, 40, clv.CLV_FP32, kernel=kernel)
     err = fp32_eps_err(o, g)
     assert err <= FP32_TOL, err
     assert st["error_word"] == 0
