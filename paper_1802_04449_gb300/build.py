@@ -31,18 +31,21 @@ def _deps():
     return files
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, lib: str | None = None, defines=()) -> str:
+    """Compile libclv.so; ``defines`` are extra -D flags (tuning variants go to ``lib``)."""
     os.makedirs(BUILD, exist_ok=True)
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+    out = lib or LIB
+    if not force and not defines and os.path.exists(out):
+        t = os.path.getmtime(out)
         if all(os.path.getmtime(f) <= t for f in _deps()):
             return LIB
     nvcc = _nvcc()
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [nvcc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        tag = "" if not defines else "_" + str(abs(hash(tuple(defines))))
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + tag + ".o")
+        cmd = [nvcc, *ARCH, *FLAGS, *[f"-D{d}" for d in defines], "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)
@@ -50,10 +53,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, len(SOURCES))) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = out + f".tmp{os.getpid()}"
     subprocess.check_call([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

@@ -122,10 +122,10 @@ struct TileGeom {
 
 // Tile shape: TK columns fit neta in ceil(neta/32) tiles; the block has
 // (TJ+1) x (TK+1) threads, at most 256 (FP32) or 128 (FP64); x is cut into
-// chunks so that there are about two CTAs per SM.
+// chunks of CX planes (see below).
 TileGeom tile_geometry(const clv_config* c, int sms) {
   const int rsize = c->precision == CLV_FP64 ? 8 : 4;
-  const int maxthr = rsize == 4 ? kBlock : kBlock / 2;
+  const int maxthr = rsize == 4 ? CLV_TILE_MAX_THREADS : std::min(CLV_TILE_MAX_THREADS, kBlock / 2);
   const int nk = (c->neta + 31) / 32;
   TileGeom g;
   TileArgs& t = g.t;
@@ -133,10 +133,21 @@ TileGeom tile_geometry(const clv_config* c, int sms) {
   t.TJ = std::max(1, std::min(c->ny, maxthr / (t.TK + 1) - 1));
   t.ntj = (c->ny + t.TJ - 1) / t.TJ;
   t.ntk = (c->neta + t.TK - 1) / t.TK;
+  // CLV_TILE_MIN_BLOCKS CTAs per SM: pick the chunking that minimises
+  // waves x (planes per chunk + the 4 halo planes each chunk also stages)
   const long long tiles = (long long)t.ntj * t.ntk;
-  long long nch = std::max(1LL, std::min((long long)c->nx, (2LL * sms + tiles - 1) / tiles));
-  t.CX = (int)((c->nx + nch - 1) / nch);
-  nch = (c->nx + t.CX - 1) / t.CX;
+  long long best_nch = 1;
+  double best = 1e300;
+  for (long long nch = 1; nch <= c->nx; ++nch) {
+    const long long cx = (c->nx + nch - 1) / nch;
+    const long long used = (c->nx + cx - 1) / cx;
+    const long long slots = (long long)sms * CLV_TILE_MIN_BLOCKS;
+    const long long waves = (tiles * used + slots - 1) / slots;
+    const double cost = (double)waves * (double)(cx + 4);
+    if (cost < best - 1e-9) { best = cost; best_nch = used; }
+  }
+  t.CX = (int)((c->nx + best_nch - 1) / best_nch);
+  const long long nch = (c->nx + t.CX - 1) / t.CX;
   g.threads = (t.TJ + 1) * (t.TK + 1);
   g.blocks = (unsigned)(tiles * nch);
   const bool visc = c->eta_over_s > 0.0;
@@ -161,7 +172,8 @@ size_t layout(const clv_config* c, clv_handle* h) {
   for (int s = 0; s < kNumPrimSets; ++s)
     for (int f = 0; f < kPrimFields; ++f) oPR[s][f] = take(fb);
   const int ne = c->eos_kind == CLV_EOS_TABLE ? c->eos_n : 1;
-  for (int t = 0; t < 3; ++t) oE[t] = take((size_t)ne * rs);
+  oE[0] = take((size_t)4 * ne * rs);  // nodes packed as (P, T, c_s^2, 0)
+  oE[1] = oE[2] = oE[0];
   size_t oStage = take((size_t)N * 8);
   size_t oBlock = take((size_t)nblocks * 8);
   size_t oStats = take(sizeof(DevStats));
@@ -203,9 +215,7 @@ template <typename R> EosView<R> eos_view(const clv_handle* h) {
   v.top = (R)(v.n - 1);
   const double pi = 3.14159265358979323846;
   v.t_coef = (R)(30.0 * kHbarC * kHbarC * kHbarC / (kDofConformal * pi * pi));
-  v.P = (const R*)h->eos[0];
-  v.T = (const R*)h->eos[1];
-  v.cs2 = (const R*)h->eos[2];
+  v.node = (const R*)h->eos[0];
   return v;
 }
 
@@ -248,7 +258,7 @@ StageParams<R> stage_params(clv_handle* h, int stage, double tau_stage, double t
   p.eps_cut_d = c.eps_cut;
   p.inv_5etas_hbarc = (R)(c.eta_over_s > 0 ? 1.0 / (5.0 * c.eta_over_s * kHbarC) : 0.0);
   p.polish_E = (R)(2.0 * c.eps_cut);
-  p.polish_v = (R)0.99;
+  p.polish_v = (R)0.999;
   p.block_sum = h->block_sum;
   p.emax_bits = &h->dstats->emax_bits;
   p.counters = h->dstats->counters;
@@ -288,9 +298,8 @@ template <typename R, bool VISC> cudaError_t tile_attributes(size_t smem) {
   auto set = [&](const void* f) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   };
-  set((const void*)stage_tile_kernel<R, 1, VISC, false>);
-  set((const void*)stage_tile_kernel<R, 2, VISC, false>);
-  set((const void*)stage_tile_kernel<R, 2, VISC, true>);
+  set((const void*)stage_tile_kernel<R, 1, VISC>);
+  set((const void*)stage_tile_kernel<R, 2, VISC>);
   return e;
 }
 
@@ -299,7 +308,8 @@ void launch_stage(clv_handle* h, const StageParams<R>& p) {
   if (h->cfg.kernel == 1) {
     stage_kernel<R, STAGE, VISC, STATS><<<grid_of(h->N), kBlock, 0, h->stream>>>(p);
   } else {
-    stage_tile_kernel<R, STAGE, VISC, STATS><<<h->tile_blocks, h->tile_threads, h->tile_smem, h->stream>>>(p, h->tile);
+    stage_tile_kernel<R, STAGE, VISC><<<h->tile_blocks, h->tile_threads, h->tile_smem, h->stream>>>(p, h->tile);
+    recover_kernel<R, VISC, STATS><<<grid_of(h->N), kBlock, 0, h->stream>>>(p);
   }
 }
 
@@ -314,7 +324,7 @@ void launch_step(clv_handle* h, bool stats) {
   StageParams<R> p2 = stage_params<R>(h, 2, tn1, tn1);
   if (stats) {
     launch_stage<R, VISC, 2, true>(h, p2);
-    h->stat_blocks = h->cfg.kernel == 1 ? (int)grid_of(h->N) : (int)h->tile_blocks;
+    h->stat_blocks = (int)grid_of(h->N);
   } else {
     launch_stage<R, VISC, 2, false>(h, p2);
   }
@@ -501,22 +511,25 @@ clv_status create_common(const clv_config* cfg, void* stream, void* ws, size_t w
       return fail(nullptr, CLV_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     }
   }
-  // EOS table in the working precision
+  // EOS table in the working precision, nodes packed as (P, T, c_s^2, 0)
   if (cfg->eos_kind == CLV_EOS_TABLE) {
     const int n = cfg->eos_n;
-    const double* src[3] = {cfg->eos_P, cfg->eos_T, cfg->eos_cs2};
-    for (int t = 0; t < 3; ++t) {
-      if (h->rsize == 8) {
-        cudaError_t e = cudaMemcpyAsync(h->eos[t], src[t], (size_t)n * 8, cudaMemcpyHostToDevice, h->stream);
-        if (e != cudaSuccess) { clv_destroy(h); return fail(nullptr, CLV_ECUDA, cudaGetErrorString(e)); }
-      } else {
-        float* tmp = new float[n];
-        for (int i = 0; i < n; ++i) tmp[i] = (float)src[t][i];
-        cudaError_t e = cudaMemcpy(h->eos[t], tmp, (size_t)n * 4, cudaMemcpyHostToDevice);
-        delete[] tmp;
-        if (e != cudaSuccess) { clv_destroy(h); return fail(nullptr, CLV_ECUDA, cudaGetErrorString(e)); }
+    cudaError_t e;
+    if (h->rsize == 8) {
+      std::vector<double> pk((size_t)4 * n);
+      for (int i = 0; i < n; ++i) {
+        pk[4 * i] = cfg->eos_P[i]; pk[4 * i + 1] = cfg->eos_T[i]; pk[4 * i + 2] = cfg->eos_cs2[i]; pk[4 * i + 3] = 0.0;
       }
+      e = cudaMemcpy(h->eos[0], pk.data(), pk.size() * 8, cudaMemcpyHostToDevice);
+    } else {
+      std::vector<float> pk((size_t)4 * n);
+      for (int i = 0; i < n; ++i) {
+        pk[4 * i] = (float)cfg->eos_P[i]; pk[4 * i + 1] = (float)cfg->eos_T[i];
+        pk[4 * i + 2] = (float)cfg->eos_cs2[i]; pk[4 * i + 3] = 0.f;
+      }
+      e = cudaMemcpy(h->eos[0], pk.data(), pk.size() * 4, cudaMemcpyHostToDevice);
     }
+    if (e != cudaSuccess) { clv_destroy(h); return fail(nullptr, CLV_ECUDA, cudaGetErrorString(e)); }
   }
   cudaError_t e = cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

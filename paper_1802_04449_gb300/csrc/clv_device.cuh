@@ -44,10 +44,19 @@ template <typename R> struct EosView {
   R e0, e_top;             // eps of node 0 and of the last node
   R t_coef;                // conformal: T^4 = t_coef * e
   R top;                   // n - 1 as R
-  const R* P;
-  const R* T;
-  const R* cs2;
+  const R* node;           // table nodes packed as (P, T, c_s^2, 0), 4 values per node
 };
+
+template <typename R> struct Node { R P, T, c2; };
+__device__ __forceinline__ Node<float> load_node(const float* base, int k) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(base) + k);
+  return {v.x, v.y, v.z};
+}
+__device__ __forceinline__ Node<double> load_node(const double* base, int k) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(base) + 2 * k);
+  const double2 b = __ldg(reinterpret_cast<const double2*>(base) + 2 * k + 1);
+  return {a.x, a.y, b.x};
+}
 
 // Evaluate in arithmetic type C (C may be wider than the table type R).
 template <typename C, typename R>
@@ -61,32 +70,32 @@ __device__ __forceinline__ void eos_eval(const EosView<R>& q, C e, C& P, C& T, C
   if (!(e > C(0))) {
     P = C(0);
     T = C(0);
-    cs2 = C(__ldg(q.cs2));
+    cs2 = C(load_node(q.node, 0).c2);
     return;
   }
   C x = (Fast<C>::log(e) - C(q.lne0)) * C(q.inv_dlne);
   if (x < C(0)) {
+    const Node<R> a = load_node(q.node, 0);
     C r = e / C(q.e0);
-    P = C(__ldg(q.P)) * r;
-    T = C(__ldg(q.T)) * sqrt(sqrt(r));
-    cs2 = C(__ldg(q.cs2));
+    P = C(a.P) * r;
+    T = C(a.T) * sqrt(sqrt(r));
+    cs2 = C(a.c2);
     return;
   }
   if (x >= C(q.top)) {
-    P = C(__ldg(q.P + q.n - 1)) + (e - C(q.e_top)) * C(1.0 / 3.0);
-    T = C(__ldg(q.T + q.n - 1)) * sqrt(sqrt(e / C(q.e_top)));
+    const Node<R> a = load_node(q.node, q.n - 1);
+    P = C(a.P) + (e - C(q.e_top)) * C(1.0 / 3.0);
+    T = C(a.T) * sqrt(sqrt(e / C(q.e_top)));
     cs2 = C(1.0 / 3.0);
     return;
   }
   int k = (int)x;
   if (k > q.n - 2) k = q.n - 2;
   C w = x - C(k);
-  C p0 = C(__ldg(q.P + k)), p1 = C(__ldg(q.P + k + 1));
-  C t0 = C(__ldg(q.T + k)), t1 = C(__ldg(q.T + k + 1));
-  C c0 = C(__ldg(q.cs2 + k)), c1 = C(__ldg(q.cs2 + k + 1));
-  P = p0 + w * (p1 - p0);
-  T = t0 + w * (t1 - t0);
-  cs2 = c0 + w * (c1 - c0);
+  const Node<R> a = load_node(q.node, k), b = load_node(q.node, k + 1);
+  P = C(a.P) + w * (C(b.P) - C(a.P));
+  T = C(a.T) + w * (C(b.T) - C(a.T));
+  cs2 = C(a.c2) + w * (C(b.c2) - C(a.c2));
 }
 
 // ---------------------------------------------------------------------------
@@ -169,6 +178,18 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
   ue = s * Me;
   return rr;
 }
+
+// Asynchronous global -> shared copies (cp.async, 4 or 8 bytes per element).
+__device__ __forceinline__ void cp_async_elem(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double* smem, const double* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Product rounded on its own (never fused into a neighbouring add), so that
 // differences of equal products cancel exactly.

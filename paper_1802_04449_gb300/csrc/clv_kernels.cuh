@@ -397,6 +397,104 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
   }
 }
 
+// Primitive recovery of one stage (used after the tiled stage kernel): reads
+// the new T~^{tau mu} and pi~^{tau mu}, solves for (eps, u~) warm-started
+// from the stage velocity, writes P and c_s, zeroes pi~ in vacuum cells, and
+// (STATS) reduces sum T~^{tau tau} and max eps.
+template <typename R, bool VISC, bool STATS>
+__global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = c < p.N;
+  double my_T0 = 0.0, my_e = 0.0;
+  bool f_rescaled = false, f_fail = false, f_polished = false, f_nonfinite = false;
+  if (active) {
+    const R tn = p.taus_new;
+    const R T0v = p.Tout[0][c];
+    R E = T0v / tn, Mx = p.Tout[1][c] / tn, My = p.Tout[2][c] / tn, Me = p.Tout[3][c] / tn;
+    if constexpr (VISC) {
+      E -= p.piout[0][c]; Mx -= p.piout[1][c]; My -= p.piout[2][c]; Me -= p.piout[3][c];
+    }
+    R en = R(0), ux = R(0), uy = R(0), ue = R(0);
+    if (!(isfinite(E) && isfinite(Mx) && isfinite(My) && isfinite(Me))) {
+      f_nonfinite = true;
+    } else {
+      const R a = p.pr.u[0][c], b = p.pr.u[1][c], d = p.pr.u[2][c];
+      const R w2 = a * a + b * b + d * d;
+      R vg = sqrt(w2 / (R(1) + w2));   // |v| of the stage velocity
+      RootResult rr = solve_primitive<R, R>(p.eos, p.eps_cut, E, Mx, My, Me, SolveTraits<R>::tol,
+                                            SolveTraits<R>::maxit, en, ux, uy, ue, &vg);
+      f_rescaled = rr.rescaled;
+      if constexpr (sizeof(R) == 4) {
+        // FP64 refinement of the cancellation-prone arithmetic (E - M v, Newton
+        // step, gamma) at high velocity, near the vacuum cutoff, and wherever
+        // the FP32 solve did not converge
+        const R M = sqrt(Mx * Mx + My * My + Me * Me);
+        if (E >= p.eps_cut && M > R(0) && (E < p.polish_E || M > p.polish_v * E || rr.iters < 0)) {
+          if (rr.iters < 0) vg = R(-1);
+          double dv = (double)vg, de, dux, duy, due;
+          RootResult r2 = solve_primitive<double, R, float>(p.eos, p.eps_cut_d, (double)E, (double)Mx, (double)My,
+                                                            (double)Me, 1e-13, 40, de, dux, duy, due, &dv);
+          en = R(de); ux = R(dux); uy = R(duy); ue = R(due);
+          f_polished = true;
+          rr.iters = r2.iters;
+        }
+      }
+      f_fail = rr.iters < 0;
+      if (f_fail && atomicCAS(p.fail_cell, 0ull, (unsigned long long)c + 1ull) == 0ull) {
+        p.fail_EM[0] = (double)E;
+        p.fail_EM[1] = (double)sqrt(Mx * Mx + My * My + Me * Me);
+      }
+    }
+    R Pn, Tn_, c2n;
+    eos_eval<R, R>(p.eos, en, Pn, Tn_, c2n);
+    p.prout.e[c] = en;
+    p.prout.u[0][c] = ux;
+    p.prout.u[1][c] = uy;
+    p.prout.u[2][c] = ue;
+    p.prout.P[c] = Pn;
+    p.prout.cs[c] = sqrt(c2n);
+    if constexpr (VISC) {
+      if (!(en > R(0))) {
+#pragma unroll
+        for (int q = 0; q < 10; ++q) p.piout[q][c] = R(0);
+      }
+    }
+    my_T0 = (double)T0v;
+    my_e = (double)en;
+  }
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned b_res = __ballot_sync(full, f_rescaled);
+  const unsigned b_fail = __ballot_sync(full, f_fail);
+  const unsigned b_pol = __ballot_sync(full, f_polished);
+  const unsigned b_nf = __ballot_sync(full, f_nonfinite);
+  if (lane == 0) {
+    if (b_res) atomicAdd(p.counters + 0, (unsigned long long)__popc(b_res));
+    if (b_fail) { atomicAdd(p.counters + 1, (unsigned long long)__popc(b_fail)); atomicOr(p.err, 1u); }
+    if (b_pol) atomicAdd(p.counters + 2, (unsigned long long)__popc(b_pol));
+    if (b_nf) atomicOr(p.err, 2u);
+  }
+  if constexpr (STATS) {
+    __shared__ double s_sum[kBlock / 32];
+    __shared__ double s_max[kBlock / 32];
+    double sm = my_T0, mx = my_e;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sm += __shfl_down_sync(full, sm, o);
+      mx = fmax(mx, __shfl_down_sync(full, mx, o));
+    }
+    const int wid = threadIdx.x >> 5;
+    if (lane == 0) { s_sum[wid] = sm; s_max[wid] = mx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < kBlock / 32; ++w) { a += s_sum[w]; b = fmax(b, s_max[w]); }
+      p.block_sum[blockIdx.x] = a;
+      if (b > 0.0) atomicMax(p.emax_bits, (unsigned long long)__double_as_longlong(b));
+    }
+  }
+}
+
 // T~^{tau mu} = tau [(e + P) u^tau u^mu - P g~^{tau mu} + pi~^{tau mu}]
 template <typename R>
 __global__ void __launch_bounds__(kBlock) tilde_T_kernel(Prim<R> pr, Ptr10<R> pi, bool with_pi, R* T0,

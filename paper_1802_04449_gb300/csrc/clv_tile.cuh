@@ -39,7 +39,33 @@ struct TileArgs {
 template <bool VISC> inline size_t tile_smem_elems(int TJ, int TK) {
   using L = Box<VISC>;
   const size_t NB = (size_t)(TJ + 4) * (TK + 4);
-  return L::NF * NB + (size_t)L::NQ * ((TJ + 1) * TK + TJ * (TK + 1)) + 2 * (size_t)L::NPEND * TJ * TK;
+  return 2 * L::NF * NB + (size_t)L::NQ * ((TJ + 1) * TK + TJ * (TK + 1)) + 2 * (size_t)L::NPEND * TJ * TK;
+}
+
+// Issue the asynchronous copies of plane ip of the tile (with its y/eta halo)
+// into a box buffer: T~, pi~, P, c_s to their slots, u~ into the v slots (the
+// conversion pass turns them into u~^tau and v once the copies land).
+template <typename R, bool VISC>
+__device__ __forceinline__ void stage_plane_async(const StageParams<R>& p, R* box, int NB, int BW, int ip,
+                                                  int j0, int k0, int tid, int nthr) {
+  using L = Box<VISC>;
+  for (int q = tid; q < NB; q += nthr) {
+    const int bj = q / BW, bk = q - bj * BW;
+    const int gj = wrap_index(j0 + bj - 2, p.ny, p.periodic);
+    const int gk = wrap_index(k0 + bk - 2, p.ne, p.periodic);
+    const long long g = ((long long)ip * p.ny + gj) * p.ne + gk;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) cp_async_elem(box + m * NB + q, p.T[m] + g);
+    if constexpr (VISC) {
+#pragma unroll
+      for (int r = 0; r < 10; ++r) cp_async_elem(box + (4 + r) * NB + q, p.pi[r] + g);
+    }
+#pragma unroll
+    for (int m = 0; m < 3; ++m) cp_async_elem(box + (L::V + m) * NB + q, p.pr.u[m] + g);
+    cp_async_elem(box + L::P * NB + q, p.pr.P + g);
+    cp_async_elem(box + L::CS * NB + q, p.pr.cs + g);
+  }
+  cp_async_commit();
 }
 
 // component q of the reconstruction vector along axis a from staged fields
@@ -73,20 +99,23 @@ __device__ __forceinline__ void box_interface(const R* box, int NB, int c, int s
   interface_flux<R, VISC>(Ls, Rs, cs[-stride], cs[0], ax, taus, H);
 }
 
+#ifndef CLV_TILE_MAX_THREADS
+#define CLV_TILE_MAX_THREADS 256
+#endif
 #ifndef CLV_TILE_MIN_BLOCKS
 #define CLV_TILE_MIN_BLOCKS 1
 #endif
 
-template <typename R, int STAGE, bool VISC, bool STATS>
-__global__ void __launch_bounds__(kBlock, CLV_TILE_MIN_BLOCKS) stage_tile_kernel(const StageParams<R> p, const TileArgs t) {
+template <typename R, int STAGE, bool VISC>
+__global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) stage_tile_kernel(const StageParams<R> p, const TileArgs t) {
   using L = Box<VISC>;
   constexpr int NF = L::NF, NQ = L::NQ, NR = L::NR, NPEND = L::NPEND;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int BW = t.TK + 4, NB = BW * (t.TJ + 4);
   const int NHY = (t.TJ + 1) * t.TK, NHK = t.TJ * (t.TK + 1);
   const int ncell = t.TJ * t.TK;
-  R* box = reinterpret_cast<R*>(smem_raw);
-  R* Hy = box + NF * NB;       // [NQ][TJ+1][TK]
+  R* boxbuf = reinterpret_cast<R*>(smem_raw);   // two plane buffers [2][NF][NB]
+  R* Hy = boxbuf + 2 * NF * NB;  // [NQ][TJ+1][TK]
   R* Hk = Hy + NQ * NHY;       // [NQ][TJ][TK+1]
   R* pend = Hk + NQ * NHK;     // [2][NPEND][ncell]
 
@@ -121,36 +150,29 @@ __global__ void __launch_bounds__(kBlock, CLV_TILE_MIN_BLOCKS) stage_tile_kernel
 #pragma unroll
   for (int m = 0; m < 4; ++m) ucm1[m] = R(0);
 
-  double sum_T0 = 0.0, max_e = 0.0;
-  int n_res = 0, n_fail = 0, n_pol = 0, n_nf = 0;
 
+  stage_plane_async<R, VISC>(p, boxbuf + ((x0 - 2) & 1) * NF * NB, NB, BW, wrap_index(x0 - 2, p.nx, p.periodic),
+                             j0, k0, tid, nthr);
   for (int pl = x0 - 2; pl <= x1 + 1; ++pl) {
-    const int ip = wrap_index(pl, p.nx, p.periodic);
     const bool out_plane = pl >= x0 && pl < x1;
+    R* box = boxbuf + (pl & 1) * NF * NB;
+    // ---- 1. plane pl has landed: u~ -> (u~^tau, v) in place
+    cp_async_wait_all();
     __syncthreads();
-    // ---- 1. stage plane ip of the tile with its y/eta halo
     for (int q = tid; q < NB; q += nthr) {
-      const int bj = q / BW, bk = q - (q / BW) * BW;
-      const int gj = wrap_index(j0 + bj - 2, p.ny, p.periodic);
-      const int gk = wrap_index(k0 + bk - 2, p.ne, p.periodic);
-      const long long g = ((long long)ip * p.ny + gj) * p.ne + gk;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) box[m * NB + q] = ldg(p.T[m] + g);
-      if constexpr (VISC) {
-#pragma unroll
-        for (int r = 0; r < 10; ++r) box[(4 + r) * NB + q] = ldg(p.pi[r] + g);
-      }
-      const R ux = ldg(p.pr.u[0] + g), uy = ldg(p.pr.u[1] + g), ue = ldg(p.pr.u[2] + g);
+      const R ux = box[L::V * NB + q], uy = box[(L::V + 1) * NB + q], ue = box[(L::V + 2) * NB + q];
       const R ut = sqrt(R(1) + ux * ux + uy * uy + ue * ue);
       const R iu = R(1) / ut;
       box[L::UT * NB + q] = ut;
-      box[(L::V + 0) * NB + q] = ux * iu;
+      box[L::V * NB + q] = ux * iu;
       box[(L::V + 1) * NB + q] = uy * iu;
       box[(L::V + 2) * NB + q] = ue * iu;
-      box[L::P * NB + q] = ldg(p.pr.P + g);
-      box[L::CS * NB + q] = ldg(p.pr.cs + g);
     }
     __syncthreads();
+    // prefetch the next plane into the other buffer while this one is used
+    if (pl + 1 <= x1 + 1)
+      stage_plane_async<R, VISC>(p, boxbuf + ((pl + 1) & 1) * NF * NB, NB, BW, wrap_index(pl + 1, p.nx, p.periodic),
+                                 j0, k0, tid, nthr);
     // ---- 2. every y- and eta-interface of an output plane, once
     if (out_plane) {
       R H[NQ];
@@ -276,64 +298,13 @@ __global__ void __launch_bounds__(kBlock, CLV_TILE_MIN_BLOCKS) stage_tile_kernel
                   pinew[r] = (un[0] * p.pin[r][gc] + ustar0 * W0[4 + r] + hh * S[4 + r]) * inv;
               }
             }
-            // ---- primitive recovery from T_ideal = T - pi, warm-started from
-            //      the stage velocity |v| of this cell
-            const R tn = p.taus_new;
-            R E = Tnew[0] / tn, Mx = Tnew[1] / tn, My = Tnew[2] / tn, Me = Tnew[3] / tn;
-            if constexpr (VISC) {
-              E -= pinew[0]; Mx -= pinew[1]; My -= pinew[2]; Me -= pinew[3];
-            }
-            R en = R(0), ux = R(0), uy = R(0), ue = R(0);
-            if (!(isfinite(E) && isfinite(Mx) && isfinite(My) && isfinite(Me))) {
-              ++n_nf;
-            } else {
-              R vg = sqrt(W0[L::V] * W0[L::V] + W0[L::V + 1] * W0[L::V + 1] + W0[L::V + 2] * W0[L::V + 2]);
-              RootResult rr = solve_primitive<R, R>(p.eos, p.eps_cut, E, Mx, My, Me, SolveTraits<R>::tol,
-                                                    SolveTraits<R>::maxit, en, ux, uy, ue, &vg);
-              n_res += rr.rescaled;
-              if constexpr (sizeof(R) == 4) {
-                // FP64 refinement of the cancellation-prone arithmetic (E - M v,
-                // Newton step, gamma) at high velocity, near the vacuum cutoff,
-                // and wherever the FP32 solve did not converge
-                const R M = sqrt(Mx * Mx + My * My + Me * Me);
-                if (E >= p.eps_cut && M > R(0) &&
-                    (E < p.polish_E || M > p.polish_v * E || rr.iters < 0)) {
-                  if (rr.iters < 0) vg = R(-1);
-                  double dv = (double)vg, de, dux, duy, due;
-                  RootResult r2 = solve_primitive<double, R, float>(p.eos, p.eps_cut_d, (double)E, (double)Mx,
-                                                                    (double)My, (double)Me, 1e-13, 40, de,
-                                                                    dux, duy, due, &dv);
-                  en = R(de); ux = R(dux); uy = R(duy); ue = R(due);
-                  ++n_pol;
-                  rr.iters = r2.iters;
-                }
-              }
-              if (rr.iters < 0) {
-                ++n_fail;
-                if (atomicCAS(p.fail_cell, 0ull, (unsigned long long)gc + 1ull) == 0ull) {
-                  p.fail_EM[0] = (double)E;
-                  p.fail_EM[1] = (double)sqrt(Mx * Mx + My * My + Me * Me);
-                }
-              }
-            }
-            R Pn, Tn_, c2n;
-            eos_eval<R, R>(p.eos, en, Pn, Tn_, c2n);
+            // conserved quantities of the stage; the primitive recovery runs in
+            // recover_kernel (high occupancy hides its dependent table lookups)
 #pragma unroll
             for (int m = 0; m < 4; ++m) p.Tout[m][gc] = Tnew[m];
             if constexpr (VISC) {
-              const bool vac = !(en > R(0));
 #pragma unroll
-              for (int r = 0; r < 10; ++r) p.piout[r][gc] = vac ? R(0) : pinew[r];
-            }
-            p.prout.e[gc] = en;
-            p.prout.u[0][gc] = ux;
-            p.prout.u[1][gc] = uy;
-            p.prout.u[2][gc] = ue;
-            p.prout.P[gc] = Pn;
-            p.prout.cs[gc] = sqrt(c2n);
-            if constexpr (STATS) {
-              sum_T0 += (double)Tnew[0];
-              max_e = fmax(max_e, (double)en);
+              for (int r = 0; r < 10; ++r) p.piout[r][gc] = pinew[r];
             }
           }
 #pragma unroll
@@ -376,42 +347,6 @@ __global__ void __launch_bounds__(kBlock, CLV_TILE_MIN_BLOCKS) stage_tile_kernel
           }
         }
       }
-    }
-  }
-  // ---- counters and reductions (valid for any block size <= kBlock)
-  __shared__ int s_cnt[4];
-  __shared__ double s_red[2][kBlock];
-  __syncthreads();
-  if (tid < 4) s_cnt[tid] = 0;
-  __syncthreads();
-  if (n_res) atomicAdd(&s_cnt[0], n_res);
-  if (n_fail) atomicAdd(&s_cnt[1], n_fail);
-  if (n_pol) atomicAdd(&s_cnt[2], n_pol);
-  if (n_nf) atomicAdd(&s_cnt[3], n_nf);
-  if constexpr (STATS) {
-    for (int i = tid; i < kBlock; i += nthr) {
-      s_red[0][i] = (i == tid) ? sum_T0 : 0.0;
-      s_red[1][i] = (i == tid) ? max_e : 0.0;
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    if (s_cnt[0]) atomicAdd(p.counters + 0, (unsigned long long)s_cnt[0]);
-    if (s_cnt[1]) { atomicAdd(p.counters + 1, (unsigned long long)s_cnt[1]); atomicOr(p.err, 1u); }
-    if (s_cnt[2]) atomicAdd(p.counters + 2, (unsigned long long)s_cnt[2]);
-    if (s_cnt[3]) atomicOr(p.err, 2u);
-  }
-  if constexpr (STATS) {
-    for (int o = kBlock / 2; o > 0; o >>= 1) {
-      for (int i = tid; i < o; i += nthr) {
-        s_red[0][i] += s_red[0][i + o];
-        s_red[1][i] = fmax(s_red[1][i], s_red[1][i + o]);
-      }
-      __syncthreads();
-    }
-    if (tid == 0) {
-      p.block_sum[blockIdx.x] = s_red[0][0];
-      if (s_red[1][0] > 0.0) atomicMax(p.emax_bits, (unsigned long long)__double_as_longlong(s_red[1][0]));
     }
   }
 }
