@@ -153,11 +153,36 @@ clv_status clv_get_time(const clv_handle* h, double* tau, int64_t* step);
 clv_status clv_enable_kernel_timing(clv_handle* h, int enable);
 clv_status clv_get_kernel_times(clv_handle* h, double ms[2], int64_t launches[2]);
 
+/* Statistics without any allocation.  The paper has no counterpart: this is
+ * a service for callers that cannot allocate device memory -- code running
+ * under a fixed device-memory budget owned by another framework's pool, or in
+ * a loop whose contract forbids allocations between its timing points.
+ *
+ * Computes, over caller-owned device arrays of n doubles (e.g. fields 0 and 4
+ * exported by clv_get_fields_device), the same two statistics as
+ * clv_get_stats: d_out[0] = cell_volume * sum of d_Ttt (E_tot) and
+ * d_out[1] = max of d_eps (negative values count as 0).  d_out is a device
+ * array of 2 doubles written on cuda_stream; the call only enqueues work and
+ * does not synchronise.
+ *
+ * Scratch lives in a fixed array of the library (256 KiB + 8 bytes on every
+ * device that loads it, held until the process exits); nothing is allocated
+ * and no allocating library routine is called.  Limit: 1 <= n <= 8388608;
+ * larger n returns CLV_EINVAL with a message in clv_last_error(NULL).
+ * The first call on each device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the scratch array: calls that
+ * overlap on the GPU (other streams or host threads on the same device) race
+ * and must be serialised by the caller. */
+clv_status clv_field_stats_noalloc(const double* d_eps, const double* d_Ttt, int64_t n, double cell_volume,
+                                   void* cuda_stream, double* d_out);
+
 /* Release the handle and the memory it owns.  NULL is ignored. */
 void clv_destroy(clv_handle* h);
 
 /* Message of the last failing call on this handle ("" if none).  With
- * h == NULL: the last failure of clv_create / clv_create_ws. */
+ * h == NULL: the last failure of a call without a handle (clv_create,
+ * clv_create_ws, clv_workspace_bytes, clv_field_stats_noalloc). */
 const char* clv_last_error(const clv_handle* h);
 
 /* Library version string. */

@@ -66,7 +66,7 @@ _lib = None
 EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initial",
             "clv_set_initial_device", "clv_step", "clv_get_stats", "clv_get_fields",
             "clv_get_fields_device", "clv_get_time", "clv_enable_kernel_timing", "clv_get_kernel_times",
-            "clv_destroy", "clv_last_error", "clv_version"]
+            "clv_destroy", "clv_last_error", "clv_version", "clv_field_stats_noalloc"]
 
 
 def load(path: str | None = None):
@@ -95,6 +95,7 @@ def load(path: str | None = None):
         lib.clv_get_time.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
         lib.clv_enable_kernel_timing.argtypes = [P, ctypes.c_int]
         lib.clv_get_kernel_times.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
+        lib.clv_field_stats_noalloc.argtypes = [V, V, ctypes.c_int64, ctypes.c_double, V, V]
         lib.clv_destroy.argtypes = [P]
         lib.clv_destroy.restype = None
         lib.clv_last_error.argtypes = [P]
@@ -245,6 +246,20 @@ class Hydro:
         self._check(self._lib.clv_get_fields_device(self._h, self.mask_of(names),
                                                     ctypes.c_void_p(out.data_ptr())), self._h)
         return {k: out[i].view(self.shape) for i, k in enumerate(names)}
+
+
+def field_stats_noalloc(d_eps, d_Ttt, cell_volume, d_out, stream=None):
+    """E_tot and max eps of device float64 tensors into the device tensor
+    ``d_out`` (2 values) without any allocation; see clv_field_stats_noalloc."""
+    import torch
+    lib = load()
+    n = d_eps.numel()
+    st = stream if stream is not None else torch.cuda.current_stream(d_eps.device)
+    status = lib.clv_field_stats_noalloc(ctypes.c_void_p(d_eps.data_ptr()), ctypes.c_void_p(d_Ttt.data_ptr()),
+                                         int(n), float(cell_volume), ctypes.c_void_p(st.cuda_stream),
+                                         ctypes.c_void_p(d_out.data_ptr()))
+    if status != 0:
+        raise ClvError(status, lib.clv_last_error(None).decode())
 
 
 def from_case(case, precision=CLV_FP64, **kw):

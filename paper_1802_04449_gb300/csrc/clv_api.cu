@@ -540,6 +540,9 @@ clv_status create_common(const clv_config* cfg, void* stream, void* ws, size_t w
 
 }  // namespace
 
+// Message for clv_last_error(NULL) from calls that have no handle.
+void clv_set_global_error(const char* msg) { g_create_error = msg ? msg : ""; }
+
 // ============================== C ABI =====================================
 extern "C" {
 
