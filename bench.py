@@ -37,8 +37,16 @@ sys.path.insert(0, ROOT)
 
 METRIC = "hydro cell-updates/s on GB300, FP32+learned vs FP64, % HBM roofline"
 UNIT = "cell-updates/s"
-WORDS_STAGE1 = 39   # read T~ 4, pi~ 10, prim 4, u^{n-1} 3; write T~' 4, pi~' 10, prim' 4
-WORDS_STAGE2 = 56   # read T~' 4, pi~' 10, prim' 4, T~^n 4, pi~^n 10, u^n 3, u^{n-1} 3; write 18
+# Algorithmic words moved per cell by each kernel of a step (each field once):
+KERNEL_WORDS = {
+    "stage1": 35,    # read T~ 4, pi~ 10, eps 1, u~ 3, u~^{n-1} 3; write T~' 4, pi~' 10
+    "recover1": 15,  # read T~'^{tau mu} 4, pi~'^{tau mu} 4, u~ 3; write eps', u~' 4
+    "stage2": 52,    # read T~' 4, pi~' 10, eps' 1, u~' 3, T~^n 4, pi~^n 10, u~^n 3, u~^{n-1} 3; write 14
+    "recover2": 15,  # read T~^{tau mu} 4, pi~^{tau mu} 4, u~' 3; write eps, u~ 4
+}
+LEDGER_WORDS = 92    # the method's per-cell-update ledger for a fused step (each field once per stage)
+KERNEL_NAMES = {"stage1": "stage_tile_kernel<float,1,viscous>", "recover1": "recover_kernel<float,viscous>",
+                "stage2": "stage_tile_kernel<float,2,viscous>", "recover2": "recover_kernel<float,viscous>"}
 
 
 def dist_env():
@@ -207,24 +215,22 @@ def run_gpu(args):
                "includes": "H2D of the initial state (pinned), the first-step ideal predictor, "
                            f"{args.steps} steps, stats read-back, D2H of eps and u~"}
 
-    # ---- roofline of the dominant kernel (stage 2), from live event timing
+    # ---- roofline of the dominant kernel, from live per-kernel event timing
     peak, peak_kind = measured_peaks()
-    (ms_s1, ms_s2), (n1, n2) = kt
     word = 4
-    bytes_s1 = WORDS_STAGE1 * word * N
-    bytes_s2 = WORDS_STAGE2 * word * N
-    dom = 2 if ms_s2 >= ms_s1 else 1
-    avg = (ms_s2 / n2) if dom == 2 else (ms_s1 / n1)
-    alg = bytes_s2 if dom == 2 else bytes_s1
-    achieved = alg / (avg / 1e3) / 1e9
-    traffic = load_traffic(dom)
-    roof = {"bound": "hbm", "kernel": f"stage_kernel<float,{dom},visc>", "achieved": achieved,
+    avg_ms = {k: (ms / n if n else 0.0) for k, (ms, n) in kt.items()}
+    tot_ms = {k: ms for k, (ms, n) in kt.items()}
+    dom = max(tot_ms, key=tot_ms.get)
+    alg = KERNEL_WORDS[dom] * word * N
+    achieved = alg / (avg_ms[dom] / 1e3) / 1e9
+    roof = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved,
             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic,
+            "traffic": load_traffic(dom),
             "algorithmic_bytes_per_launch": alg,
-            "stage_ms_avg": [ms_s1 / max(n1, 1), ms_s2 / max(n2, 1)],
-            "step_bytes_per_cell_update": (WORDS_STAGE1 + WORDS_STAGE2) * word,
-            "step_frac_of_peak": (value / ws) * (WORDS_STAGE1 + WORDS_STAGE2) * word / 1e9 / peak}
+            "kernel_ms_avg": avg_ms,
+            "kernel_share": {k: v / sum(tot_ms.values()) for k, v in tot_ms.items()},
+            "ledger_bytes_per_cell_update": LEDGER_WORDS * word,
+            "step_frac_of_peak": (value / ws) * LEDGER_WORDS * word / 1e9 / peak}
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -238,7 +244,7 @@ def run_gpu(args):
         "fp64": {"value": value64, "unit": UNIT, "steps": steps64, "ms_per_step": ms64_max / steps64},
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 4 * args.steps,
         "clocks": clocks,
         "stats_fp32": {k: st32.get(k) for k in ("tau", "eps_max", "T_max", "E_tot", "n_polished", "n_rootfail",
                                                 "error_word", "error")},
@@ -253,18 +259,31 @@ def run_gpu(args):
 
 
 def load_traffic(dom):
-    """dram bytes per launch of the dominant kernel from the committed ncu
-    summary (profiles/stage_kernel_traffic.json), if it matches this kernel."""
-    p = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    """DRAM bytes per launch of kernel slot ``dom`` (read + write) from the
+    committed ncu summary: lines ``traffic <slot> <bytes> <kernel-source-hash>``
+    in profiles/traffic.txt.  Returns None when absent or when the kernel
+    sources changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    try:
-        with open(p) as f:
-            d = json.load(f)
-        v = d.get(f"stage{dom}_dram_bytes_per_launch_full_size")
-        return float(v) if v is not None else None
-    except (OSError, ValueError):
-        return None
+    want = kernel_source_hash()
+    with open(p) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) == 4 and parts[0] == "traffic" and parts[1] == dom and parts[3] == want:
+                return float(parts[2])
+    return None
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1802_04449_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def cpu_baseline(budget_s):
@@ -321,8 +340,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="clv", choices=["clv", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

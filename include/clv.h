@@ -88,6 +88,9 @@ typedef struct {
   int64_t n_rescaled;        /* cells with |M| > E rescaled before the root solve */
   int64_t n_rootfail;        /* root solves that hit the iteration cap */
   int64_t n_polished;        /* FP32 path: cells refined by the FP64 Newton step */
+  int64_t n_fp32_nonconverged; /* FP32 path: FP32 root solves that did not converge (then solved in FP64) */
+  int64_t n_newton_iters;    /* Newton iterations of the root solves (working precision) */
+  int64_t n_newton_cells;    /* root solves counted in n_newton_iters */
   uint32_t error_word;       /* bit 0 root cap, bit 1 non-finite, bit 2 wait timeout */
   uint32_t _pad;
 } clv_stats;
@@ -146,12 +149,61 @@ clv_status clv_get_fields_device(clv_handle* h, uint32_t mask, double* device_ou
 clv_status clv_get_time(const clv_handle* h, double* tau, int64_t* step);
 
 /* Instrumentation.  While enabled, CUDA events are recorded on the handle's
- * stream around every stage-kernel launch of clv_step (at most 16384 steps
- * between two reads).  clv_get_kernel_times synchronises and returns the
- * accumulated device milliseconds and launch counts per stage kernel
- * (index 0: stage 1, index 1: stage 2), then resets them. */
+ * stream around every kernel launch of clv_step (at most 8192 steps between
+ * two reads).  clv_get_kernel_times synchronises and returns the accumulated
+ * device milliseconds and launch counts per kernel, then resets them:
+ * index 0 stage-1 stage kernel, 1 stage-1 recovery kernel, 2 stage-2 stage
+ * kernel, 3 stage-2 recovery kernel (1 and 3 stay 0 with kernel = 1, whose
+ * stage kernel includes the recovery). */
 clv_status clv_enable_kernel_timing(clv_handle* h, int enable);
-clv_status clv_get_kernel_times(clv_handle* h, double ms[2], int64_t launches[2]);
+clv_status clv_get_kernel_times(clv_handle* h, double ms[4], int64_t launches[4]);
+
+/* ---------------- learned initial guess of the root solve ----------------
+ * Not in the paper (which notes that the varying iteration counts of the
+ * root finding make warps diverge): a 10 -> 64 -> 64 -> 4 SiLU network maps
+ * features of a cell to (eps/E, v^x, v^y, v^eta); |v| seeds the Newton solve,
+ * which then converges to the same tolerance as without it.  Features:
+ * x0 = (ln E + 5)/5, x1..3 = M^{x,y,eta}/E, x4..9 = pi~^{xx,xy,x eta,yy,y eta,
+ * eta eta}/E clamped to [-4, 4], with E, M the ideal part T~^{tau mu}/tau -
+ * pi~^{tau mu} the root solve starts from.  Parameters: 5124 floats packed
+ * W1 (64x10, row-major) | b1 (64) | W2 (64x64) | b2 (64) | W3 (4x64) | b3 (4).
+ * Inference: BF16 weights on the tensor cores, FP32 accumulation. */
+enum { CLV_GUESS_PREVIOUS = 0, CLV_GUESS_COLD = 1, CLV_GUESS_MLP = 2 };
+#define CLV_MLP_NPARAM 5124
+
+/* Initial guess of the root solve: CLV_GUESS_PREVIOUS (|v| of the cell's
+ * stage velocity; the default), CLV_GUESS_COLD (v = M/(E + P(E))) or
+ * CLV_GUESS_MLP (needs clv_set_mlp and the FP32 path). */
+clv_status clv_set_guess(clv_handle* h, int mode);
+
+/* Load the network (host array of CLV_MLP_NPARAM floats; converted to BF16). */
+clv_status clv_set_mlp(clv_handle* h, const float* params);
+
+/* Training samples of the current state: d_X (N x 10 floats) features and
+ * d_Y (N x 4 floats) targets (eps/E, v^x, v^y, v^eta) of every cell, rows of
+ * vacuum cells NaN.  Device arrays; enqueued on the handle's stream. */
+clv_status clv_mlp_samples(clv_handle* h, float* d_X, float* d_Y);
+
+/* The tensor-core forward pass of the loaded network on n feature rows
+ * (device, n x 10 floats) into d_Y (n x 4 floats).  Enqueued. */
+clv_status clv_mlp_forward(clv_handle* h, const float* d_X, int64_t n, float* d_Y);
+
+/* Loss (mean over samples of the squared error summed over the 4 outputs)
+ * and its gradient with respect to the packed parameters, over n device
+ * samples, in FP32.  d_grad: CLV_MLP_NPARAM floats, d_loss: 1 float
+ * (both overwritten).  Enqueued on cuda_stream. */
+clv_status clv_mlp_loss_grad(const float* d_params, const float* d_X, const float* d_Y, int64_t n,
+                             void* cuda_stream, float* d_grad, float* d_loss);
+
+/* iters Adam steps (lr, beta 0.9/0.999) on mini-batches of `batch` samples
+ * drawn from the n device samples by a counter-based generator (seed != 0).
+ * d_params is updated in place; d_work holds 3 x CLV_MLP_NPARAM floats (Adam
+ * moments and the gradient; zero before the first call); step0 continues the
+ * Adam step count; d_loss[i] receives the mini-batch loss of step i (must be
+ * zero on entry).  Enqueued on cuda_stream. */
+clv_status clv_mlp_train(float* d_params, float* d_work, const float* d_X, const float* d_Y, int64_t n,
+                         int iters, int batch, float lr, uint64_t seed, int step0, void* cuda_stream,
+                         float* d_loss);
 
 /* Statistics without any allocation.  The paper has no counterpart: this is
  * a service for callers that cannot allocate device memory -- code running

@@ -54,6 +54,15 @@
  *       - (2/3) Delta^{mu nu} theta with finite-difference gradients.
  *   R17 Boundaries: two ghost cells per side, copies of the edge cell
  *       (zero gradient) or periodic wrap.
+ *   R18 Shear regulator (the paper is silent; without one the dilute,
+ *       ultra-relativistic edge of a viscous event runs away): after each
+ *       stage update and before the root solve, with eps and P of the
+ *       stage's input state of the cell,
+ *         - pi~ = 0 where that eps < 1e-3 GeV/fm^3 (ideal flow far below
+ *           freeze-out densities);
+ *         - otherwise pi~ is scaled by rho_max / rho wherever
+ *           rho = sqrt(|pi~_{mu nu} pi~^{mu nu}|) / sqrt(eps^2 + 3 P^2)
+ *           exceeds rho_max = 1.
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC.
  * Parity: bit-level determinism across thread counts (each cell is computed
@@ -270,6 +279,31 @@ static void source_pi(double g, const double u[4], const double du[16], const do
   S[9] -= 2.0 * g * ue * pi[3];
 }
 
+/* Shear regulator R18: pi = 0 below VISC_EPS_MIN, otherwise
+ * |pi_{mu nu} pi^{mu nu}| <= rho_max^2 (eps^2 + 3 P^2). */
+#define RHO_MAX 1.0
+#define VISC_EPS_MIN 1e-3
+static void regulate_pi(const orc_t* h, double e, double* pi) {
+  if (e < VISC_EPS_MIN) {
+    for (int q = 0; q < NPI; ++q) pi[q] = 0.0;
+    return;
+  }
+  double P, T, cs2;
+  eos_eval(h, e, &P, &T, &cs2);
+  double pp = 0.0;
+  for (int m = 0; m < 4; ++m)
+    for (int n = 0; n < 4; ++n) {
+      double v = pi[PI_IDX[m][n]];
+      pp += GT[m] * GT[n] * v * v;
+    }
+  double bound2 = RHO_MAX * RHO_MAX * (e * e + 3.0 * P * P);
+  double a = fabs(pp);
+  if (a > bound2) {
+    double f = (bound2 > 0.0) ? sqrt(bound2 / a) : 0.0;
+    for (int q = 0; q < NPI; ++q) pi[q] *= f;
+  }
+}
+
 /* ------------------------- KT (Eqs. kt, flux_out) -------------------- */
 #define NR 17 /* reconstructed: T(4) pi(10) u^tau v^a P */
 
@@ -464,9 +498,12 @@ static void heun_step(orc_t* h, int viscous) {
         double S[4 + NPI];
         stage_source(h, s, viscous, tn, i, j, k, us, un, S);
         for (int m = 0; m < 4; ++m) s1->T[m][c] = s->T[m][c] + hs * S[m];
-        if (viscous)
-          for (int q = 0; q < NPI; ++q)
-            s1->pi[q][c] = (un[0] * s->pi[q][c] + hs * S[4 + q]) / us[0];
+        if (viscous) {
+          double pv[NPI];
+          for (int q = 0; q < NPI; ++q) pv[q] = (un[0] * s->pi[q][c] + hs * S[4 + q]) / us[0];
+          regulate_pi(h, s->ed[c], pv);
+          for (int q = 0; q < NPI; ++q) s1->pi[q][c] = pv[q];
+        }
         recover(h, tn1, c, s1, viscous, &nres, &nfail);
       }
   /* ---- stage 2 ---- */
@@ -486,9 +523,13 @@ static void heun_step(orc_t* h, int viscous) {
         double S[4 + NPI];
         stage_source(h, s1, viscous, tn1, i, j, k, u1, un, S);
         for (int m = 0; m < 4; ++m) s->T[m][c] = 0.5 * (s->T[m][c] + s1->T[m][c] + hs * S[m]);
-        if (viscous)
+        if (viscous) {
+          double pv[NPI];
           for (int q = 0; q < NPI; ++q)
-            s->pi[q][c] = 0.5 * (un[0] * s->pi[q][c] + us[0] * s1->pi[q][c] + hs * S[4 + q]) / u1[0];
+            pv[q] = 0.5 * (un[0] * s->pi[q][c] + us[0] * s1->pi[q][c] + hs * S[4 + q]) / u1[0];
+          regulate_pi(h, s1->ed[c], pv);
+          for (int q = 0; q < NPI; ++q) s->pi[q][c] = pv[q];
+        }
         /* keep u^n as u^{n-1} for the next step */
         h->up[0][c] = un[1]; h->up[1][c] = un[2]; h->up[2][c] = un[3];
         recover(h, tn1, c, s, viscous, &nres, &nfail);

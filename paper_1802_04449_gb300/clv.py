@@ -48,6 +48,8 @@ class clv_stats(ctypes.Structure):
         ("tau", ctypes.c_double), ("step", ctypes.c_int64),
         ("eps_max", ctypes.c_double), ("T_max", ctypes.c_double), ("E_tot", ctypes.c_double),
         ("n_rescaled", ctypes.c_int64), ("n_rootfail", ctypes.c_int64), ("n_polished", ctypes.c_int64),
+        ("n_fp32_nonconverged", ctypes.c_int64), ("n_newton_iters", ctypes.c_int64),
+        ("n_newton_cells", ctypes.c_int64),
         ("error_word", ctypes.c_uint32), ("_pad", ctypes.c_uint32),
     ]
 
@@ -66,7 +68,11 @@ _lib = None
 EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initial",
             "clv_set_initial_device", "clv_step", "clv_get_stats", "clv_get_fields",
             "clv_get_fields_device", "clv_get_time", "clv_enable_kernel_timing", "clv_get_kernel_times",
-            "clv_destroy", "clv_last_error", "clv_version", "clv_field_stats_noalloc"]
+            "clv_destroy", "clv_last_error", "clv_version", "clv_field_stats_noalloc",
+            "clv_set_guess", "clv_set_mlp", "clv_mlp_samples", "clv_mlp_forward", "clv_mlp_loss_grad",
+            "clv_mlp_train"]
+CLV_GUESS_PREVIOUS, CLV_GUESS_COLD, CLV_GUESS_MLP = 0, 1, 2
+MLP_NPARAM = 5124
 
 
 def load(path: str | None = None):
@@ -96,6 +102,14 @@ def load(path: str | None = None):
         lib.clv_enable_kernel_timing.argtypes = [P, ctypes.c_int]
         lib.clv_get_kernel_times.argtypes = [P, D, ctypes.POINTER(ctypes.c_int64)]
         lib.clv_field_stats_noalloc.argtypes = [V, V, ctypes.c_int64, ctypes.c_double, V, V]
+        F = ctypes.POINTER(ctypes.c_float)
+        lib.clv_set_guess.argtypes = [P, ctypes.c_int]
+        lib.clv_set_mlp.argtypes = [P, F]
+        lib.clv_mlp_samples.argtypes = [P, V, V]
+        lib.clv_mlp_forward.argtypes = [P, V, ctypes.c_int64, V]
+        lib.clv_mlp_loss_grad.argtypes = [V, V, V, ctypes.c_int64, V, V, V]
+        lib.clv_mlp_train.argtypes = [V, V, V, V, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                      ctypes.c_uint64, ctypes.c_int, V, V]
         lib.clv_destroy.argtypes = [P]
         lib.clv_destroy.restype = None
         lib.clv_last_error.argtypes = [P]
@@ -213,15 +227,44 @@ class Hydro:
         self._lib.clv_get_time(self._h, ctypes.byref(tau), ctypes.byref(step))
         return tau.value, step.value
 
+    def set_guess(self, mode):
+        self._check(self._lib.clv_set_guess(self._h, int(mode)), self._h)
+
+    def set_mlp(self, params):
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        if a.size != MLP_NPARAM:
+            raise ValueError(f"expected {MLP_NPARAM} parameters")
+        self._check(self._lib.clv_set_mlp(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), self._h)
+
+    def mlp_samples(self):
+        """(X, Y) float32 device tensors (N x 10, N x 4) of the current state; NaN rows for vacuum."""
+        t = self.torch
+        X = t.empty((self.N, 10), dtype=t.float32, device=self.device)
+        Y = t.empty((self.N, 4), dtype=t.float32, device=self.device)
+        self._check(self._lib.clv_mlp_samples(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr())),
+                    self._h)
+        return X, Y
+
+    def mlp_forward(self, X):
+        t = self.torch
+        X = X.to(t.float32).contiguous()
+        Y = t.empty((X.shape[0], 4), dtype=t.float32, device=self.device)
+        self._check(self._lib.clv_mlp_forward(self._h, ctypes.c_void_p(X.data_ptr()), X.shape[0],
+                                              ctypes.c_void_p(Y.data_ptr())), self._h)
+        return Y
+
     def enable_kernel_timing(self, on=True):
         self._check(self._lib.clv_enable_kernel_timing(self._h, int(bool(on))), self._h)
 
+    KERNEL_SLOTS = ("stage1", "recover1", "stage2", "recover2")
+
     def kernel_times(self):
-        """(ms[stage1], ms[stage2]), (launches[stage1], launches[stage2]) since the last read."""
-        ms = (ctypes.c_double * 2)()
-        n = (ctypes.c_int64 * 2)()
+        """Accumulated device ms and launch counts per kernel slot since the last
+        read: dict slot -> (ms, launches); slots as in KERNEL_SLOTS."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int64 * 4)()
         self._check(self._lib.clv_get_kernel_times(self._h, ms, n), self._h)
-        return (ms[0], ms[1]), (n[0], n[1])
+        return {k: (ms[i], n[i]) for i, k in enumerate(self.KERNEL_SLOTS)}
 
     @staticmethod
     def mask_of(names):
@@ -260,6 +303,37 @@ def field_stats_noalloc(d_eps, d_Ttt, cell_volume, d_out, stream=None):
                                          ctypes.c_void_p(d_out.data_ptr()))
     if status != 0:
         raise ClvError(status, lib.clv_last_error(None).decode())
+
+
+def mlp_loss_grad(params, X, Y, stream=None):
+    """FP32 loss and gradient of the guess network over device samples."""
+    import torch
+    lib = load()
+    st = stream if stream is not None else torch.cuda.current_stream(params.device)
+    g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=params.device)
+    loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    status = lib.clv_mlp_loss_grad(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(X.data_ptr()),
+                                   ctypes.c_void_p(Y.data_ptr()), X.shape[0], ctypes.c_void_p(st.cuda_stream),
+                                   ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(loss.data_ptr()))
+    if status != 0:
+        raise ClvError(status, lib.clv_last_error(None).decode())
+    return loss, g
+
+
+def mlp_train(params, work, X, Y, iters, batch=8192, lr=1e-3, seed=1, step0=0, stream=None):
+    """Adam training of the guess network on the GPU (params/work updated in
+    place); returns the per-step mini-batch losses (device tensor)."""
+    import torch
+    lib = load()
+    st = stream if stream is not None else torch.cuda.current_stream(params.device)
+    loss = torch.zeros(max(iters, 1), dtype=torch.float32, device=params.device)
+    status = lib.clv_mlp_train(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(work.data_ptr()),
+                               ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()), X.shape[0], int(iters),
+                               int(batch), float(lr), int(seed), int(step0), ctypes.c_void_p(st.cuda_stream),
+                               ctypes.c_void_p(loss.data_ptr()))
+    if status != 0:
+        raise ClvError(status, lib.clv_last_error(None).decode())
+    return loss[:iters]
 
 
 def from_case(case, precision=CLV_FP64, **kw):

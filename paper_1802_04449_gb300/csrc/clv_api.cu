@@ -3,6 +3,7 @@
 // step (two stage kernels per step); all arithmetic of the method runs in
 // the kernels of clv_kernels.cuh.
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -28,7 +29,7 @@ struct DevStats {
   double esum;
   double T_at_emax;
   unsigned long long emax_bits;
-  unsigned long long counters[4];  // rescaled, root cap, polished, spare
+  unsigned long long counters[6];  // rescaled, root cap, polished, FP32 not converged, Newton iterations, solved cells
   unsigned int err;
   unsigned int pad;
   unsigned long long fail_cell;  // first cell (+1) whose root solve hit the cap
@@ -57,6 +58,9 @@ struct clv_handle {
   void* PR[kNumPrimSets][kPrimFields];
   int cur = 0, prev = 1;
   void* eos[3];
+  void* mlp = nullptr;            // tensor-core copy of the guess network
+  bool mlp_loaded = false;
+  int guess = 0;                  // GuessMode
   double* staging = nullptr;      // N doubles
   double* block_sum = nullptr;    // nblocks doubles
   DevStats* dstats = nullptr;
@@ -67,9 +71,9 @@ struct clv_handle {
   // kernel timing (instrumentation)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
-  std::vector<cudaEvent_t> ev_pending;  // triples: before stage 1, between, after stage 2
-  double t_ms[2] = {0.0, 0.0};
-  long long t_launches[2] = {0, 0};
+  std::vector<cudaEvent_t> ev_pending;  // five per step: around the four kernel launches
+  double t_ms[4] = {0.0, 0.0, 0.0, 0.0};
+  long long t_launches[4] = {0, 0, 0, 0};
   // tiled stage kernel geometry
   TileArgs tile{};
   int tile_threads = 0;
@@ -174,6 +178,7 @@ size_t layout(const clv_config* c, clv_handle* h) {
   const int ne = c->eos_kind == CLV_EOS_TABLE ? c->eos_n : 1;
   oE[0] = take((size_t)4 * ne * rs);  // nodes packed as (P, T, c_s^2, 0)
   oE[1] = oE[2] = oE[0];
+  size_t oMlp = take(kMlpDeviceBytes);
   size_t oStage = take((size_t)N * 8);
   size_t oBlock = take((size_t)nblocks * 8);
   size_t oStats = take(sizeof(DevStats));
@@ -184,6 +189,7 @@ size_t layout(const clv_config* c, clv_handle* h) {
     for (int s = 0; s < kNumPrimSets; ++s)
       for (int f = 0; f < kPrimFields; ++f) h->PR[s][f] = b + oPR[s][f];
     for (int t = 0; t < 3; ++t) h->eos[t] = b + oE[t];
+    h->mlp = b + oMlp;
     h->staging = (double*)(b + oStage);
     h->block_sum = (double*)(b + oBlock);
     h->dstats = (DevStats*)(b + oStats);
@@ -257,7 +263,7 @@ StageParams<R> stage_params(clv_handle* h, int stage, double tau_stage, double t
   p.eps_cut = (R)c.eps_cut;
   p.eps_cut_d = c.eps_cut;
   p.inv_5etas_hbarc = (R)(c.eta_over_s > 0 ? 1.0 / (5.0 * c.eta_over_s * kHbarC) : 0.0);
-  p.polish_E = (R)(2.0 * c.eps_cut);
+  p.polish_E = (R)(1.01 * c.eps_cut);
   p.polish_v = (R)0.999;
   p.block_sum = h->block_sum;
   p.emax_bits = &h->dstats->emax_bits;
@@ -265,10 +271,12 @@ StageParams<R> stage_params(clv_handle* h, int stage, double tau_stage, double t
   p.err = &h->dstats->err;
   p.fail_cell = &h->dstats->fail_cell;
   p.fail_EM = h->dstats->fail_EM;
+  p.mlp = h->mlp;
   return p;
 }
 
-constexpr size_t kMaxTimedSteps = 16384;
+constexpr size_t kMaxTimedSteps = 8192;
+constexpr size_t kEventsPerStep = 5;
 
 cudaEvent_t timing_event(clv_handle* h) {
   cudaEvent_t e = nullptr;
@@ -304,31 +312,38 @@ template <typename R, bool VISC> cudaError_t tile_attributes(size_t smem) {
 }
 
 template <typename R, bool VISC, int STAGE, bool STATS>
-void launch_stage(clv_handle* h, const StageParams<R>& p) {
+void launch_stage(clv_handle* h, const StageParams<R>& p, bool timed) {
   if (h->cfg.kernel == 1) {
     stage_kernel<R, STAGE, VISC, STATS><<<grid_of(h->N), kBlock, 0, h->stream>>>(p);
+    if (timed) timing_event(h);   // empty recovery slot
   } else {
     stage_tile_kernel<R, STAGE, VISC><<<h->tile_blocks, h->tile_threads, h->tile_smem, h->stream>>>(p, h->tile);
-    recover_kernel<R, VISC, STATS><<<grid_of(h->N), kBlock, 0, h->stream>>>(p);
+    if (timed) timing_event(h);
+    const unsigned g = grid_of(h->N);
+    if (sizeof(R) == 4 && h->guess == kGuessMlp)
+      recover_kernel<R, VISC, STATS, sizeof(R) == 4 ? kGuessMlp : kGuessPrevious><<<g, kBlock, 0, h->stream>>>(p);
+    else if (h->guess == kGuessCold) recover_kernel<R, VISC, STATS, kGuessCold><<<g, kBlock, 0, h->stream>>>(p);
+    else recover_kernel<R, VISC, STATS, kGuessPrevious><<<g, kBlock, 0, h->stream>>>(p);
   }
+  if (timed) timing_event(h);
 }
 
 template <typename R, bool VISC>
 void launch_step(clv_handle* h, bool stats) {
   const double tn = h->tau, tn1 = h->tau + h->cfg.dtau;
-  const bool timed = h->timing && h->ev_pending.size() < 3 * kMaxTimedSteps;
+  // events: [0] stage-1 kernel [1] stage-1 recovery [2] stage-2 kernel [3] stage-2 recovery [4]
+  // (with kernel = 1 the recovery slots collapse: two events are recorded back to back)
+  const bool timed = h->timing && h->ev_pending.size() < kEventsPerStep * kMaxTimedSteps;
   if (timed) timing_event(h);
   StageParams<R> p1 = stage_params<R>(h, 1, tn, tn1);
-  launch_stage<R, VISC, 1, false>(h, p1);
-  if (timed) timing_event(h);
+  launch_stage<R, VISC, 1, false>(h, p1, timed);
   StageParams<R> p2 = stage_params<R>(h, 2, tn1, tn1);
   if (stats) {
-    launch_stage<R, VISC, 2, true>(h, p2);
+    launch_stage<R, VISC, 2, true>(h, p2, timed);
     h->stat_blocks = (int)grid_of(h->N);
   } else {
-    launch_stage<R, VISC, 2, false>(h, p2);
+    launch_stage<R, VISC, 2, false>(h, p2, timed);
   }
-  if (timed) timing_event(h);
   std::swap(h->cur, h->prev);
   h->tau = tn1;
   h->step += 1;
@@ -386,6 +401,9 @@ template <typename R> clv_status reduce_stats(clv_handle* h, bool scan, clv_stat
   out->n_rescaled = (int64_t)ds.counters[0];
   out->n_rootfail = (int64_t)ds.counters[1];
   out->n_polished = (int64_t)ds.counters[2];
+  out->n_fp32_nonconverged = (int64_t)ds.counters[3];
+  out->n_newton_iters = (int64_t)ds.counters[4];
+  out->n_newton_cells = (int64_t)ds.counters[5];
   out->error_word = ds.err;
   out->_pad = 0;
   if (ds.err & 2u) return fail(h, CLV_ENONFINITE, "non-finite value in the state");
@@ -644,27 +662,171 @@ clv_status clv_get_time(const clv_handle* h, double* tau, int64_t* step) {
   return CLV_OK;
 }
 
+clv_status clv_set_guess(clv_handle* h, int mode) {
+  if (!h) return CLV_EINVAL;
+  if (mode < kGuessPrevious || mode > kGuessMlp) return fail(h, CLV_EINVAL, "unknown guess mode");
+  if (mode == kGuessMlp && !h->mlp_loaded) return fail(h, CLV_EINVAL, "no network loaded (clv_set_mlp)");
+  if (mode == kGuessMlp && h->rsize != 4) return fail(h, CLV_EINVAL, "the learned guess runs on the FP32 path");
+  h->guess = mode;
+  return CLV_OK;
+}
+
+static uint16_t to_bf16(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40);  // NaN stays NaN
+  const uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;                                                          // round to nearest even
+  return (uint16_t)(u >> 16);
+}
+
+clv_status clv_set_mlp(clv_handle* h, const float* params) {
+  if (!h || !params) return CLV_EINVAL;
+  std::vector<uint16_t> w(kMlpBf16Elems, 0);
+  std::vector<float> b(kMlpBiasElems, 0.f);
+  for (int i = 0; i < kMlpHid; ++i)
+    for (int k = 0; k < kMlpIn; ++k) w[i * 16 + k] = to_bf16(params[kOffW1 + i * kMlpIn + k]);
+  for (int i = 0; i < kMlpHid; ++i)
+    for (int k = 0; k < kMlpHid; ++k) w[kMlpW1e + i * 64 + k] = to_bf16(params[kOffW2 + i * kMlpHid + k]);
+  for (int o = 0; o < kMlpOut; ++o)
+    for (int k = 0; k < kMlpHid; ++k) w[kMlpW1e + kMlpW2e + o * 64 + k] = to_bf16(params[kOffW3 + o * kMlpHid + k]);
+  for (int i = 0; i < kMlpHid; ++i) { b[i] = params[kOffB1 + i]; b[64 + i] = params[kOffB2 + i]; }
+  for (int o = 0; o < kMlpOut; ++o) b[128 + o] = params[kOffB3 + o];
+  char* dst = (char*)h->mlp;
+  CLV_CUDA(h, cudaMemcpyAsync(dst, w.data(), w.size() * 2, cudaMemcpyHostToDevice, h->stream));
+  CLV_CUDA(h, cudaMemcpyAsync(dst + w.size() * 2, b.data(), b.size() * 4, cudaMemcpyHostToDevice, h->stream));
+  CLV_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->mlp_loaded = true;
+  return CLV_OK;
+}
+
+}  // extern "C"
+
+template <typename R> static clv_status mlp_samples_impl(clv_handle* h, float* X, float* Y) {
+  Ptr10<R> T, pi;
+  for (int m = 0; m < 4; ++m) T.p[m] = (R*)h->T0[m];
+  for (int q = 0; q < 10; ++q) pi.p[q] = (R*)h->PI0[q];
+  const clv_config& c = h->cfg;
+  mlp_samples_kernel<R><<<grid_of(h->N), kBlock, 0, h->stream>>>(T, pi, h->viscous, prim_set<R>(h, h->cur),
+                                                                  (R)(c.cartesian ? 1.0 : h->tau), (R)c.eps_cut,
+                                                                  h->N, X, Y);
+  CLV_CUDA(h, cudaGetLastError());
+  return CLV_OK;
+}
+
+extern "C" {
+
+clv_status clv_mlp_samples(clv_handle* h, float* d_X, float* d_Y) {
+  if (!h || !d_X || !d_Y) return CLV_EINVAL;
+  if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
+  return h->rsize == 8 ? mlp_samples_impl<double>(h, d_X, d_Y) : mlp_samples_impl<float>(h, d_X, d_Y);
+}
+
+}  // extern "C"
+
+__global__ void __launch_bounds__(kBlock) mlp_forward_kernel(const void* mlp, const float* X, long long n, float* Y) {
+  __shared__ __align__(16) __nv_bfloat16 s_w[kMlpBf16Elems];
+  __shared__ float s_b[kMlpBiasElems];
+  __shared__ __align__(16) __nv_bfloat16 s_x[kBlock / 32][32][16];
+  __shared__ float s_y[kBlock / 32][32][4];
+  const __nv_bfloat16* gw = reinterpret_cast<const __nv_bfloat16*>(mlp);
+  const float* gb = reinterpret_cast<const float*>(gw + kMlpBf16Elems);
+  for (int i = threadIdx.x; i < kMlpBf16Elems; i += blockDim.x) s_w[i] = gw[i];
+  for (int i = threadIdx.x; i < kMlpBiasElems; i += blockDim.x) s_b[i] = gb[i];
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k = 0; k < 16; k += 2) {
+    const float lo = (c < n && k < kMlpIn) ? X[c * kMlpIn + k] : 0.f;
+    const float hi = (c < n && k + 1 < kMlpIn) ? X[c * kMlpIn + k + 1] : 0.f;
+    *reinterpret_cast<unsigned*>(&s_x[wid][lane][k]) = pack_bf16(lo, hi);
+  }
+  __syncthreads();
+  mlp_tile16(&s_x[wid][0][0], s_w, s_w + kMlpW1e, s_w + kMlpW1e + kMlpW2e, s_b, &s_y[wid][0][0], lane);
+  mlp_tile16(&s_x[wid][16][0], s_w, s_w + kMlpW1e, s_w + kMlpW1e + kMlpW2e, s_b, &s_y[wid][16][0], lane);
+  __syncwarp();
+  if (c < n)
+    for (int o = 0; o < kMlpOut; ++o) Y[c * kMlpOut + o] = s_y[wid][lane][o];
+}
+
+extern "C" {
+
+clv_status clv_mlp_forward(clv_handle* h, const float* d_X, int64_t n, float* d_Y) {
+  if (!h || !d_X || !d_Y || n < 0) return CLV_EINVAL;
+  if (!h->mlp_loaded) return fail(h, CLV_EINVAL, "no network loaded (clv_set_mlp)");
+  if (n == 0) return CLV_OK;
+  mlp_forward_kernel<<<grid_of(n), kBlock, 0, h->stream>>>(h->mlp, d_X, n, d_Y);
+  CLV_CUDA(h, cudaGetLastError());
+  return CLV_OK;
+}
+
+static clv_status mlp_grad_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaError_t e = cudaFuncSetAttribute((const void*)mlp_grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)mlp_grad_smem_bytes());
+    if (e != cudaSuccess) return fail(nullptr, CLV_ECUDA, cudaGetErrorString(e));
+    done = true;
+  }
+  return CLV_OK;
+}
+
+clv_status clv_mlp_loss_grad(const float* d_params, const float* d_X, const float* d_Y, int64_t n, void* stream,
+                             float* d_grad, float* d_loss) {
+  if (!d_params || !d_X || !d_Y || !d_grad || !d_loss || n < 1) return fail(nullptr, CLV_EINVAL, "bad arguments");
+  clv_status s = mlp_grad_attr();
+  if (s != CLV_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(d_grad, 0, kMlpParams * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_loss, 0, sizeof(float), st);
+  if (e != cudaSuccess) return fail(nullptr, CLV_ECUDA, cudaGetErrorString(e));
+  const unsigned blocks = (unsigned)((n + kMlpTrainBlock - 1) / kMlpTrainBlock);
+  mlp_grad_kernel<<<blocks, kMlpTrainBlock, mlp_grad_smem_bytes(), st>>>(d_params, d_X, d_Y, n, n, 0ull, 0, d_grad,
+                                                                        d_loss);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? CLV_OK : fail(nullptr, CLV_ECUDA, cudaGetErrorString(e));
+}
+
+clv_status clv_mlp_train(float* d_params, float* d_work, const float* d_X, const float* d_Y, int64_t n, int iters,
+                         int batch, float lr, uint64_t seed, int step0, void* stream, float* d_loss) {
+  if (!d_params || !d_work || !d_X || !d_Y || !d_loss || n < 1 || iters < 0 || batch < 1 || step0 < 0 || seed == 0)
+    return fail(nullptr, CLV_EINVAL, "bad arguments (seed must be nonzero)");
+  clv_status s = mlp_grad_attr();
+  if (s != CLV_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  float* m = d_work;
+  float* v = d_work + kMlpParams;
+  float* g = d_work + 2 * kMlpParams;
+  const unsigned blocks = (unsigned)((batch + kMlpTrainBlock - 1) / kMlpTrainBlock);
+  for (int it = 0; it < iters; ++it) {
+    mlp_grad_kernel<<<blocks, kMlpTrainBlock, mlp_grad_smem_bytes(), st>>>(d_params, d_X, d_Y, n, batch, seed,
+                                                                          step0 + it, g, d_loss + it);
+    mlp_adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(d_params, m, v, g, step0 + it + 1, lr);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CLV_OK : fail(nullptr, CLV_ECUDA, cudaGetErrorString(e));
+}
+
 clv_status clv_enable_kernel_timing(clv_handle* h, int enable) {
   if (!h) return CLV_EINVAL;
   h->timing = enable != 0;
   return CLV_OK;
 }
 
-clv_status clv_get_kernel_times(clv_handle* h, double ms[2], int64_t launches[2]) {
+clv_status clv_get_kernel_times(clv_handle* h, double ms[4], int64_t launches[4]) {
   if (!h || !ms || !launches) return CLV_EINVAL;
   CLV_CUDA(h, cudaStreamSynchronize(h->stream));
-  for (size_t i = 0; i + 2 < h->ev_pending.size(); i += 3) {
-    float a = 0.f, b = 0.f;
-    CLV_CUDA(h, cudaEventElapsedTime(&a, h->ev_pending[i], h->ev_pending[i + 1]));
-    CLV_CUDA(h, cudaEventElapsedTime(&b, h->ev_pending[i + 1], h->ev_pending[i + 2]));
-    h->t_ms[0] += a;
-    h->t_ms[1] += b;
-    h->t_launches[0] += 1;
-    h->t_launches[1] += 1;
+  const bool direct = h->cfg.kernel == 1;
+  for (size_t i = 0; i + kEventsPerStep - 1 < h->ev_pending.size(); i += kEventsPerStep) {
+    for (int k = 0; k < 4; ++k) {
+      float a = 0.f;
+      CLV_CUDA(h, cudaEventElapsedTime(&a, h->ev_pending[i + k], h->ev_pending[i + k + 1]));
+      h->t_ms[k] += a;
+      if (!(direct && (k & 1))) h->t_launches[k] += 1;
+    }
   }
   for (cudaEvent_t e : h->ev_pending) h->ev_pool.push_back(e);
   h->ev_pending.clear();
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 4; ++i) {
     ms[i] = h->t_ms[i];
     launches[i] = h->t_launches[i];
     h->t_ms[i] = 0.0;

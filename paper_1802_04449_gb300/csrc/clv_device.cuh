@@ -108,6 +108,31 @@ struct RootResult {
   int rescaled;   // |M| > (1-1e-6) E was rescaled
 };
 
+// Division and square root for the FP64 refinement of the FP32 path: an FP32
+// seed refined by Newton steps in FP64 (fused multiply-adds only; relative
+// error ~1e-15), instead of the long FP64 division / square-root sequences.
+__device__ __forceinline__ double refine_rcp(double b) {
+  double r = (double)__frcp_rn((float)b);
+  r = r * fma(-b, r, 2.0);
+  r = r * fma(-b, r, 2.0);
+  return r;
+}
+__device__ __forceinline__ double refine_sqrt(double x) {
+  if (!(x > 0.0)) return 0.0;
+  double y = (double)rsqrtf((float)x);  // ~ 1/sqrt(x)
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  return x * y;
+}
+template <typename C, typename CE> struct SolveOps {
+  static __device__ __forceinline__ C div(C a, C b) { return a / b; }
+  static __device__ __forceinline__ C sqrt_(C x) { return sqrt(x); }
+};
+template <> struct SolveOps<double, float> {
+  static __device__ __forceinline__ double div(double a, double b) { return a * refine_rcp(b); }
+  static __device__ __forceinline__ double sqrt_(double x) { return refine_sqrt(x); }
+};
+
 // C: arithmetic of the solve (E - M v, f, Newton step, gamma); CE: arithmetic
 // of the EOS lookup (CE may be narrower than C: the FP32 path refines in FP64
 // around an FP32 table lookup).
@@ -115,15 +140,16 @@ template <typename C, typename R, typename CE = C>
 __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps_cut, C E, C Mx,
                                                       C My, C Me, C tol, int maxit, C& eps,
                                                       C& ux, C& uy, C& ue, C* vguess = nullptr) {
+  using Ops = SolveOps<C, CE>;
   RootResult rr{0, 0};
   eps = C(0);
   ux = uy = ue = C(0);
   if (!(E >= eps_cut)) return rr;
   C M2 = Mx * Mx + My * My + Me * Me;
-  C M = sqrt(M2);
+  C M = Ops::sqrt_(M2);
   C Mcap = C(1.0 - 1e-6) * E;
   if (M > Mcap) {
-    C s = Mcap / M;
+    C s = Ops::div(Mcap, M);
     Mx *= s; My *= s; Me *= s;
     M = Mcap;
     rr.rescaled = 1;
@@ -132,7 +158,7 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
     eps = (E >= eps_cut) ? E : C(0);
     return rr;
   }
-  C lo = C(0), hi = M / E;
+  C lo = C(0), hi = Ops::div(M, E);
   C P, cs2;
   C v;
   if (vguess && *vguess > lo && *vguess < hi) {
@@ -141,7 +167,7 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
     CE Pe, Te, ce;
     eos_eval<CE, R>(q, CE(E), Pe, Te, ce);
     P = C(Pe);
-    v = M / (E + P);
+    v = Ops::div(M, E + P);
   }
   int it = 1;
   bool ok = false;
@@ -154,10 +180,11 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
       cs2 = C(ce);
     }
     C den = E + P;
-    C f = v - M / den;
+    const C iden = Ops::div(C(1), den);
+    C f = v - M * iden;
     if (f > C(0)) hi = v; else lo = v;
-    C fp = C(1) - cs2 * (M * M) / (den * den);
-    const C dv = -f / fp;
+    C fp = C(1) - cs2 * (M * M) * (iden * iden);
+    const C dv = -Ops::div(f, fp);
     // converged when the Newton step is below tol; otherwise keep the iterate
     // strictly inside the shrinking bracket
     if (fabs(dv) <= tol) { v += dv; ok = true; break; }
@@ -171,8 +198,8 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
   C e = E - M * v;
   if (e < eps_cut) return rr;
   eps = e;
-  C gam = C(1) / sqrt(C(1) - v * v);
-  C s = gam * v / M;
+  C gam = Ops::div(C(1), Ops::sqrt_(C(1) - v * v));
+  C s = Ops::div(gam * v, M);
   ux = s * Mx;
   uy = s * My;
   ue = s * Me;

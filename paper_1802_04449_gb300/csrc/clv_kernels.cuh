@@ -3,6 +3,7 @@
 // array per field of nx*ny*neta values, eta_s fastest.
 #pragma once
 #include "clv_device.cuh"
+#include "clv_mlp.cuh"
 
 namespace clv {
 
@@ -46,16 +47,19 @@ template <typename R> struct StageParams {
   R st_tau;    // 1 in Milne (S_T^tau active), 0 in Cartesian
   R eps_cut;
   R inv_5etas_hbarc;   // 1/(5 (eta/s) hbar c): 1/tau_pi = T * this
-  R polish_E, polish_v;   // FP32: FP64 Newton for E < polish_E or M > polish_v E
+  R polish_E, polish_v;   // FP32: FP64 Newton where the FP32 eps < polish_E or M > polish_v E
   double eps_cut_d;
   // reductions and error reporting
   double* block_sum;             // per block: sum of new T~^{tau tau} (stats launches only)
   unsigned long long* emax_bits; // max eps as the bits of a non-negative double
-  unsigned long long* counters;  // [0] rescaled, [1] root cap, [2] polished
+  unsigned long long* counters;  // [0] rescaled, [1] root cap, [2] polished, [3] FP32 not converged
   unsigned int* err;             // error word
   unsigned long long* fail_cell; // first failing cell + 1 (0: none)
   double* fail_EM;               // E and |M| of that cell
+  const void* mlp;               // tensor-core copy of the guess network (BF16 W1|W2|W3, FP32 biases)
 };
+
+enum GuessMode { kGuessPrevious = 0, kGuessCold = 1, kGuessMlp = 2 };
 
 __device__ __forceinline__ int wrap_index(int i, int n, int periodic) {
   if (periodic) {
@@ -114,6 +118,31 @@ __device__ __forceinline__ void interface_flux(const R* L, const R* Rr, R csl, R
   (void)NQ;
 }
 
+// Shear regulator (the paper is silent; without a bound the dilute,
+// ultra-relativistic edge of a viscous event runs away).  With eps and P of
+// the stage's input state of the cell: pi~ = 0 where eps < kViscEpsMin (ideal
+// flow far below freeze-out densities); otherwise pi~ is scaled so that
+// |pi_{mu nu} pi^{mu nu}| <= kRhoMax^2 (eps^2 + 3 P^2).
+constexpr double kRhoMax = 1.0;
+constexpr double kViscEpsMin = 1e-3;   // GeV/fm^3
+template <typename R>
+__device__ __forceinline__ void regulate_shear(R e, R P, R* pi) {
+  if (e < R(kViscEpsMin)) {
+#pragma unroll
+    for (int q = 0; q < 10; ++q) pi[q] = R(0);
+    return;
+  }
+  const R pp = pi[0] * pi[0] - R(2) * (pi[1] * pi[1] + pi[2] * pi[2] + pi[3] * pi[3]) + pi[4] * pi[4] +
+               pi[7] * pi[7] + pi[9] * pi[9] + R(2) * (pi[5] * pi[5] + pi[6] * pi[6] + pi[8] * pi[8]);
+  const R bound2 = R(kRhoMax * kRhoMax) * (e * e + R(3) * P * P);
+  const R a = fabs(pp);
+  if (a > bound2) {
+    const R f = bound2 > R(0) ? sqrt(bound2 / a) : R(0);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) pi[q] *= f;
+  }
+}
+
 // Israel-Stewart source with lambda_i = 0 (Sec. 2): du[a][b] = d~_a u~^b.
 template <typename R>
 __device__ __forceinline__ void shear_source(R geo, const R u[4], R du[4][4], const R pi[10], R e,
@@ -160,7 +189,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
   const bool active = c < p.N;
   double my_T0 = 0.0;
   double my_e = 0.0;
-  bool f_rescaled = false, f_fail = false, f_polished = false, f_nonfinite = false;
+  bool f_rescaled = false, f_fail = false, f_polished = false, f_nonfinite = false, f_nonconv = false;
   if (active) {
     const int k = (int)(c % p.ne);
     const long long t = c / p.ne;
@@ -299,6 +328,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
         const R inv = R(1) / ustar0;
 #pragma unroll
         for (int q = 0; q < 10; ++q) pinew[q] = (un[0] * pic[q] + h * S[4 + q]) * inv;
+        regulate_shear<R>(e, Pc, pinew);
       }
     } else {
 #pragma unroll
@@ -307,6 +337,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
         const R inv = R(0.5) / u[0];
 #pragma unroll
         for (int q = 0; q < 10; ++q) pinew[q] = (un[0] * p.pin[q][c] + ustar0 * pic[q] + h * S[4 + q]) * inv;
+        regulate_shear<R>(e, Pc, pinew);
       }
     }
     // ---------------- primitive recovery from T_ideal = T - pi ----------------
@@ -327,8 +358,9 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
         // FP64 Newton near the vacuum, at high velocity, and wherever the
         // FP32 solve did not converge
         const R M = sqrt(Mx * Mx + My * My + Me * Me);
-        if (E >= p.eps_cut && M > R(0) &&
-            (E < p.polish_E || M > p.polish_v * E || rr.iters < 0)) {
+        f_nonconv = rr.iters < 0;
+        const bool near_cut = en < p.polish_E;
+        if (E >= p.eps_cut && M > R(0) && (near_cut || M > p.polish_v * E || rr.iters < 0)) {
           if (rr.iters < 0) vg = R(-1);
           double dv = (double)vg, de, dux, duy, due;
           RootResult r2 = solve_primitive<double, R, float>(p.eos, p.eps_cut_d, (double)E, (double)Mx,
@@ -370,10 +402,12 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
   const unsigned b_fail = __ballot_sync(full, f_fail);
   const unsigned b_pol = __ballot_sync(full, f_polished);
   const unsigned b_nf = __ballot_sync(full, f_nonfinite);
+  const unsigned b_nc = __ballot_sync(full, f_nonconv);
   if (lane == 0) {
     if (b_res) atomicAdd(p.counters + 0, (unsigned long long)__popc(b_res));
     if (b_fail) { atomicAdd(p.counters + 1, (unsigned long long)__popc(b_fail)); atomicOr(p.err, 1u); }
     if (b_pol) atomicAdd(p.counters + 2, (unsigned long long)__popc(b_pol));
+    if (b_nc) atomicAdd(p.counters + 3, (unsigned long long)__popc(b_nc));
     if (b_nf) atomicOr(p.err, 2u);
   }
   if constexpr (STATS) {
@@ -401,35 +435,78 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
 // the new T~^{tau mu} and pi~^{tau mu}, solves for (eps, u~) warm-started
 // from the stage velocity, writes P and c_s, zeroes pi~ in vacuum cells, and
 // (STATS) reduces sum T~^{tau tau} and max eps.
-template <typename R, bool VISC, bool STATS>
+template <typename R, bool VISC, bool STATS, int GUESS = kGuessPrevious>
 __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = c < p.N;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double my_T0 = 0.0, my_e = 0.0;
-  bool f_rescaled = false, f_fail = false, f_polished = false, f_nonfinite = false;
+  int my_iters = 0, my_solved = 0;
+  bool f_rescaled = false, f_fail = false, f_polished = false, f_nonfinite = false, f_nonconv = false;
+  const R tn = p.taus_new;
+  R T0v = R(0), E = R(0), Mx = R(0), My = R(0), Me = R(0);
   if (active) {
-    const R tn = p.taus_new;
-    const R T0v = p.Tout[0][c];
-    R E = T0v / tn, Mx = p.Tout[1][c] / tn, My = p.Tout[2][c] / tn, Me = p.Tout[3][c] / tn;
+    T0v = p.Tout[0][c];
+    E = T0v / tn; Mx = p.Tout[1][c] / tn; My = p.Tout[2][c] / tn; Me = p.Tout[3][c] / tn;
     if constexpr (VISC) {
       E -= p.piout[0][c]; Mx -= p.piout[1][c]; My -= p.piout[2][c]; Me -= p.piout[3][c];
     }
+  }
+  // initial guess for |v|
+  R vg = R(-1);
+  if constexpr (GUESS == kGuessMlp && sizeof(R) == 4) {
+    // learned guess: features -> BF16 tensor-core MLP, 32 cells per warp
+    __shared__ __align__(16) __nv_bfloat16 s_w[kMlpBf16Elems];
+    __shared__ float s_b[kMlpBiasElems];
+    __shared__ __align__(16) __nv_bfloat16 s_x[kBlock / 32][32][16];
+    __shared__ float s_y[kBlock / 32][32][4];
+    const __nv_bfloat16* gw = reinterpret_cast<const __nv_bfloat16*>(p.mlp);
+    const float* gb = reinterpret_cast<const float*>(gw + kMlpBf16Elems);
+    for (int i = threadIdx.x; i < kMlpBf16Elems; i += blockDim.x) s_w[i] = gw[i];
+    for (int i = threadIdx.x; i < kMlpBiasElems; i += blockDim.x) s_b[i] = gb[i];
+    float x[kMlpIn];
+    R pij[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    if constexpr (VISC) {
+      if (active) {
+        pij[0] = p.piout[4][c]; pij[1] = p.piout[5][c]; pij[2] = p.piout[6][c];
+        pij[3] = p.piout[7][c]; pij[4] = p.piout[8][c]; pij[5] = p.piout[9][c];
+      }
+    }
+    mlp_features<R>(active && E > R(0) ? E : R(1), Mx, My, Me, pij, x);
+#pragma unroll
+    for (int k = 0; k < 16; k += 2)
+      *reinterpret_cast<unsigned*>(&s_x[wid][lane][k]) = pack_bf16(k < kMlpIn ? x[k] : 0.f, k + 1 < kMlpIn ? x[k + 1] : 0.f);
+    __syncthreads();
+    mlp_tile16(&s_x[wid][0][0], s_w, s_w + kMlpW1e, s_w + kMlpW1e + kMlpW2e, s_b, &s_y[wid][0][0], lane);
+    mlp_tile16(&s_x[wid][16][0], s_w, s_w + kMlpW1e, s_w + kMlpW1e + kMlpW2e, s_b, &s_y[wid][16][0], lane);
+    __syncwarp();
+    const float vx = s_y[wid][lane][1], vy = s_y[wid][lane][2], ve = s_y[wid][lane][3];
+    vg = R(sqrtf(vx * vx + vy * vy + ve * ve));
+  } else if constexpr (GUESS == kGuessPrevious) {
+    if (active) {
+      const R a = p.pr.u[0][c], b = p.pr.u[1][c], d = p.pr.u[2][c];
+      const R w2 = a * a + b * b + d * d;
+      vg = sqrt(w2 / (R(1) + w2));   // |v| of the stage velocity
+    }
+  }
+  if (active) {
     R en = R(0), ux = R(0), uy = R(0), ue = R(0);
     if (!(isfinite(E) && isfinite(Mx) && isfinite(My) && isfinite(Me))) {
       f_nonfinite = true;
     } else {
-      const R a = p.pr.u[0][c], b = p.pr.u[1][c], d = p.pr.u[2][c];
-      const R w2 = a * a + b * b + d * d;
-      R vg = sqrt(w2 / (R(1) + w2));   // |v| of the stage velocity
       RootResult rr = solve_primitive<R, R>(p.eos, p.eps_cut, E, Mx, My, Me, SolveTraits<R>::tol,
                                             SolveTraits<R>::maxit, en, ux, uy, ue, &vg);
       f_rescaled = rr.rescaled;
+      my_iters = rr.iters > 0 ? rr.iters : 0;
+      my_solved = rr.iters > 0 ? 1 : 0;
       if constexpr (sizeof(R) == 4) {
         // FP64 refinement of the cancellation-prone arithmetic (E - M v, Newton
-        // step, gamma) at high velocity, near the vacuum cutoff, and wherever
+        // step, gamma) at high velocity, near the vacuum decision, and wherever
         // the FP32 solve did not converge
         const R M = sqrt(Mx * Mx + My * My + Me * Me);
-        if (E >= p.eps_cut && M > R(0) && (E < p.polish_E || M > p.polish_v * E || rr.iters < 0)) {
+        f_nonconv = rr.iters < 0;
+        const bool near_cut = en < p.polish_E;
+        if (E >= p.eps_cut && M > R(0) && (near_cut || M > p.polish_v * E || rr.iters < 0)) {
           if (rr.iters < 0) vg = R(-1);
           double dv = (double)vg, de, dux, duy, due;
           RootResult r2 = solve_primitive<double, R, float>(p.eos, p.eps_cut_d, (double)E, (double)Mx, (double)My,
@@ -463,15 +540,20 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
     my_e = (double)en;
   }
   const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
   const unsigned b_res = __ballot_sync(full, f_rescaled);
   const unsigned b_fail = __ballot_sync(full, f_fail);
   const unsigned b_pol = __ballot_sync(full, f_polished);
   const unsigned b_nf = __ballot_sync(full, f_nonfinite);
+  const unsigned b_nc = __ballot_sync(full, f_nonconv);
+  const int w_iters = __reduce_add_sync(full, my_iters);
+  const int w_solved = __reduce_add_sync(full, my_solved);
   if (lane == 0) {
     if (b_res) atomicAdd(p.counters + 0, (unsigned long long)__popc(b_res));
     if (b_fail) { atomicAdd(p.counters + 1, (unsigned long long)__popc(b_fail)); atomicOr(p.err, 1u); }
     if (b_pol) atomicAdd(p.counters + 2, (unsigned long long)__popc(b_pol));
+    if (b_nc) atomicAdd(p.counters + 3, (unsigned long long)__popc(b_nc));
+    if (w_iters) atomicAdd(p.counters + 4, (unsigned long long)w_iters);
+    if (w_solved) atomicAdd(p.counters + 5, (unsigned long long)w_solved);
     if (b_nf) atomicOr(p.err, 2u);
   }
   if constexpr (STATS) {
@@ -483,7 +565,6 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
       sm += __shfl_down_sync(full, sm, o);
       mx = fmax(mx, __shfl_down_sync(full, mx, o));
     }
-    const int wid = threadIdx.x >> 5;
     if (lane == 0) { s_sum[wid] = sm; s_max[wid] = mx; }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -493,6 +574,36 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
       if (b > 0.0) atomicMax(p.emax_bits, (unsigned long long)__double_as_longlong(b));
     }
   }
+}
+
+// Training samples of the current state: features of (E, M, pi~^{ij}) as in
+// mlp_features and targets (eps/E, v); rows of vacuum cells are NaN.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) mlp_samples_kernel(Ptr10<R> T4, Ptr10<R> pi, bool viscous, Prim<R> pr,
+                                                             R taus, R eps_cut, long long N, float* X, float* Y) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  R E = T4.p[0][c] / taus, Mx = T4.p[1][c] / taus, My = T4.p[2][c] / taus, Me = T4.p[3][c] / taus;
+  R pij[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+  if (viscous) {
+    E -= pi.p[0][c]; Mx -= pi.p[1][c]; My -= pi.p[2][c]; Me -= pi.p[3][c];
+    for (int k = 0; k < 6; ++k) pij[k] = pi.p[4 + k][c];
+  }
+  const R e = pr.e[c];
+  if (!(E >= eps_cut) || !(e > R(0))) {
+    for (int k = 0; k < kMlpIn; ++k) X[c * kMlpIn + k] = __int_as_float(0x7fc00000);
+    for (int k = 0; k < kMlpOut; ++k) Y[c * kMlpOut + k] = __int_as_float(0x7fc00000);
+    return;
+  }
+  float x[kMlpIn];
+  mlp_features<R>(E, Mx, My, Me, pij, x);
+  for (int k = 0; k < kMlpIn; ++k) X[c * kMlpIn + k] = x[k];
+  const R u1 = pr.u[0][c], u2 = pr.u[1][c], u3 = pr.u[2][c];
+  const R iut = R(1) / sqrt(R(1) + u1 * u1 + u2 * u2 + u3 * u3);
+  Y[c * kMlpOut + 0] = float(e / E);
+  Y[c * kMlpOut + 1] = float(u1 * iut);
+  Y[c * kMlpOut + 2] = float(u2 * iut);
+  Y[c * kMlpOut + 3] = float(u3 * iut);
 }
 
 // T~^{tau mu} = tau [(e + P) u^tau u^mu - P g~^{tau mu} + pi~^{tau mu}]

@@ -287,6 +287,7 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
                 const R inv = R(1) / ustar0;
 #pragma unroll
                 for (int r = 0; r < 10; ++r) pinew[r] = (un[0] * W0[4 + r] + hh * S[4 + r]) * inv;
+                regulate_shear<R>(e, Pc, pinew);
               }
             } else {
 #pragma unroll
@@ -296,6 +297,7 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
 #pragma unroll
                 for (int r = 0; r < 10; ++r)
                   pinew[r] = (un[0] * p.pin[r][gc] + ustar0 * W0[4 + r] + hh * S[4 + r]) * inv;
+                regulate_shear<R>(e, Pc, pinew);
               }
             }
             // conserved quantities of the stage; the primitive recovery runs in

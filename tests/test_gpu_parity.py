@@ -99,6 +99,17 @@ def test_fp64_viscous_longitudinal_flow_with_pi():
     compare_fp64(o, g, viscous=True)
 
 
+def test_fp64_shear_regulator_active():
+    """Initial pi~ of the order of several eps, so that the shear regulator
+    (|pi pi| <= eps^2 + 3P^2) acts in many cells during the first steps."""
+    case = small_hotspot(seed=19, eta_over_s=0.16)
+    pi = np.zeros((10,) + case.eps.shape)
+    pi[4] = pi[7] = 2.0 * case.eps          # transverse, traceless for u = 0,
+    pi[9] = -4.0 * case.eps                 # about 4x above the bound
+    o, g, st = run_pair(case, 12, clv.CLV_FP64, pi=pi)
+    compare_fp64(o, g, viscous=True)
+
+
 def test_fp64_cartesian_periodic_box():
     rng = np.random.default_rng(4)
     e, ux, uy, ue = I.random_smooth_box(rng, 12, 10, 9)

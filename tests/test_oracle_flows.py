@@ -262,3 +262,30 @@ def test_thread_count_does_not_change_bits():
     oracle.set_threads(0)
     for k in outs[0]:
         assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+# ------------------------------------------------------- shear regulator
+def test_shear_regulator_caps_oversized_pi():
+    """Reading R18: after a stage, |pi_{mu nu} pi^{mu nu}| <= eps^2 + 3 P^2
+    (eps, P of the stage input).  Uniform Bjorken cells with an initial
+    pi~^{xx} = pi~^{yy} = -pi~^{ee}/2 ten times eps: the first stage scales pi
+    onto the bound, so the evolved pi is far below the unregulated value."""
+    n, e0 = 4, 10.0
+    e = np.full((n, n, n), e0)
+    z = np.zeros_like(e)
+    pi = np.zeros((10, n, n, n))
+    pi[4] = pi[7] = 10 * e0
+    pi[9] = -20 * e0
+    o = oracle.Oracle(n, n, n, 0.3, 0.3, 0.3, 1.0, 0.01, eta_over_s=0.16, periodic=True)
+    o.set_initial(e, z, z, z, pi)
+    o.step(1)
+    f = o.fields()
+    P = f["eps"] / 3.0
+    pp = f["pixx"] ** 2 + f["piyy"] ** 2 + f["piee"] ** 2
+    # the second stage caps pi with the stage-1 eps' (the large negative
+    # pi~^{ee} raised eps); the result sits at the bound of an eps between
+    # the initial and the final value, far below the unregulated ~200
+    bound = lambda x: np.sqrt(x ** 2 + 3 * (x / 3) ** 2)
+    assert np.all(np.sqrt(pp) <= 1.05 * bound(1.1 * f["eps"]))
+    assert np.all(np.sqrt(pp) >= 0.95 * bound(e0))
+    assert np.all(np.isfinite(f["eps"])) and np.all(f["eps"] > 0)
