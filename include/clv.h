@@ -91,6 +91,10 @@ typedef struct {
   int64_t n_fp32_nonconverged; /* FP32 path: FP32 root solves that did not converge (then solved in FP64) */
   int64_t n_newton_iters;    /* Newton iterations of the root solves (working precision) */
   int64_t n_newton_cells;    /* root solves counted in n_newton_iters */
+  int64_t n_polish_iters;    /* FP32 path: FP64 Newton iterations of the n_polished refinements */
+  int64_t n_newton_warp_max; /* sum over warps of the largest Newton iteration count in the warp
+                                (the divergence cost: a warp runs as long as its slowest lane) */
+  int64_t n_newton_warps;    /* warps counted in n_newton_warp_max */
   uint32_t error_word;       /* bit 0 root cap, bit 1 non-finite, bit 2 wait timeout */
   uint32_t _pad;
 } clv_stats;
@@ -179,13 +183,17 @@ clv_status clv_set_guess(clv_handle* h, int mode);
 /* Load the network (host array of CLV_MLP_NPARAM floats; converted to BF16). */
 clv_status clv_set_mlp(clv_handle* h, const float* params);
 
-/* Training samples of the current state: d_X (N x 10 floats) features and
- * d_Y (N x 4 floats) targets (eps/E, v^x, v^y, v^eta) of every cell, rows of
- * vacuum cells NaN.  Device arrays; enqueued on the handle's stream. */
-clv_status clv_mlp_samples(clv_handle* h, float* d_X, float* d_Y);
+/* Training samples of the current state: features (d_X, 10 floats a row)
+ * and targets (d_Y, 4 floats a row: eps/E, v^x, v^y, v^eta) of every
+ * non-vacuum cell, compacted in cell order; *d_count (device int64) receives
+ * the number of rows.  d_X and d_Y must hold N rows.  Device arrays;
+ * enqueued on the handle's stream (which also uses the handle's host
+ * staging buffer as scratch). */
+clv_status clv_mlp_samples(clv_handle* h, float* d_X, float* d_Y, int64_t* d_count);
 
 /* The tensor-core forward pass of the loaded network on n feature rows
- * (device, n x 10 floats) into d_Y (n x 4 floats).  Enqueued. */
+ * (device, n x 10 floats) into d_Y (n x 4 floats).  Enqueued.  The arrays
+ * may be null when n = 0. */
 clv_status clv_mlp_forward(clv_handle* h, const float* d_X, int64_t n, float* d_Y);
 
 /* Loss (mean over samples of the squared error summed over the 4 outputs)

@@ -49,7 +49,8 @@ class clv_stats(ctypes.Structure):
         ("eps_max", ctypes.c_double), ("T_max", ctypes.c_double), ("E_tot", ctypes.c_double),
         ("n_rescaled", ctypes.c_int64), ("n_rootfail", ctypes.c_int64), ("n_polished", ctypes.c_int64),
         ("n_fp32_nonconverged", ctypes.c_int64), ("n_newton_iters", ctypes.c_int64),
-        ("n_newton_cells", ctypes.c_int64),
+        ("n_newton_cells", ctypes.c_int64), ("n_polish_iters", ctypes.c_int64),
+        ("n_newton_warp_max", ctypes.c_int64), ("n_newton_warps", ctypes.c_int64),
         ("error_word", ctypes.c_uint32), ("_pad", ctypes.c_uint32),
     ]
 
@@ -105,7 +106,7 @@ def load(path: str | None = None):
         F = ctypes.POINTER(ctypes.c_float)
         lib.clv_set_guess.argtypes = [P, ctypes.c_int]
         lib.clv_set_mlp.argtypes = [P, F]
-        lib.clv_mlp_samples.argtypes = [P, V, V]
+        lib.clv_mlp_samples.argtypes = [P, V, V, V]
         lib.clv_mlp_forward.argtypes = [P, V, ctypes.c_int64, V]
         lib.clv_mlp_loss_grad.argtypes = [V, V, V, ctypes.c_int64, V, V, V]
         lib.clv_mlp_train.argtypes = [V, V, V, V, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
@@ -236,14 +237,22 @@ class Hydro:
             raise ValueError(f"expected {MLP_NPARAM} parameters")
         self._check(self._lib.clv_set_mlp(self._h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))), self._h)
 
-    def mlp_samples(self):
-        """(X, Y) float32 device tensors (N x 10, N x 4) of the current state; NaN rows for vacuum."""
+    def mlp_samples(self, X=None, Y=None):
+        """Training samples of the current state's non-vacuum cells, in cell
+        order: (X, Y) float32 device views (rows x 10, rows x 4).  X and Y,
+        if given, are device buffers of at least N rows to write into."""
         t = self.torch
-        X = t.empty((self.N, 10), dtype=t.float32, device=self.device)
-        Y = t.empty((self.N, 4), dtype=t.float32, device=self.device)
-        self._check(self._lib.clv_mlp_samples(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr())),
-                    self._h)
-        return X, Y
+        if X is None:
+            X = t.empty((self.N, 10), dtype=t.float32, device=self.device)
+            Y = t.empty((self.N, 4), dtype=t.float32, device=self.device)
+        if X.shape[0] < self.N or Y.shape[0] < self.N or not (X.is_contiguous() and Y.is_contiguous()):
+            raise ValueError("sample buffers need N contiguous rows")
+        n = t.zeros(1, dtype=t.int64, device=self.device)
+        self._check(self._lib.clv_mlp_samples(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                              ctypes.c_void_p(n.data_ptr())), self._h)
+        self.stream.synchronize()
+        rows = int(n.item())
+        return X[:rows], Y[:rows]
 
     def mlp_forward(self, X):
         t = self.torch

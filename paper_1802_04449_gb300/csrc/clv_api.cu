@@ -29,7 +29,9 @@ struct DevStats {
   double esum;
   double T_at_emax;
   unsigned long long emax_bits;
-  unsigned long long counters[6];  // rescaled, root cap, polished, FP32 not converged, Newton iterations, solved cells
+  unsigned long long counters[9];  // rescaled, root cap, polished, FP32 not converged, Newton iterations,
+                                   // solved cells, FP64 refinement iterations, sum over warps of the
+                                   // warp's largest iteration count, warps with a solve
   unsigned int err;
   unsigned int pad;
   unsigned long long fail_cell;  // first cell (+1) whose root solve hit the cap
@@ -179,7 +181,7 @@ size_t layout(const clv_config* c, clv_handle* h) {
   oE[0] = take((size_t)4 * ne * rs);  // nodes packed as (P, T, c_s^2, 0)
   oE[1] = oE[2] = oE[0];
   size_t oMlp = take(kMlpDeviceBytes);
-  size_t oStage = take((size_t)N * 8);
+  size_t oStage = take(std::max((size_t)N * 8, (size_t)256));  // also scratch of clv_mlp_samples
   size_t oBlock = take((size_t)nblocks * 8);
   size_t oStats = take(sizeof(DevStats));
   if (h) {
@@ -404,6 +406,9 @@ template <typename R> clv_status reduce_stats(clv_handle* h, bool scan, clv_stat
   out->n_fp32_nonconverged = (int64_t)ds.counters[3];
   out->n_newton_iters = (int64_t)ds.counters[4];
   out->n_newton_cells = (int64_t)ds.counters[5];
+  out->n_polish_iters = (int64_t)ds.counters[6];
+  out->n_newton_warp_max = (int64_t)ds.counters[7];
+  out->n_newton_warps = (int64_t)ds.counters[8];
   out->error_word = ds.err;
   out->_pad = 0;
   if (ds.err & 2u) return fail(h, CLV_ENONFINITE, "non-finite value in the state");
@@ -702,24 +707,33 @@ clv_status clv_set_mlp(clv_handle* h, const float* params) {
 
 }  // extern "C"
 
-template <typename R> static clv_status mlp_samples_impl(clv_handle* h, float* X, float* Y) {
-  Ptr10<R> T, pi;
-  for (int m = 0; m < 4; ++m) T.p[m] = (R*)h->T0[m];
-  for (int q = 0; q < 10; ++q) pi.p[q] = (R*)h->PI0[q];
-  const clv_config& c = h->cfg;
-  mlp_samples_kernel<R><<<grid_of(h->N), kBlock, 0, h->stream>>>(T, pi, h->viscous, prim_set<R>(h, h->cur),
-                                                                  (R)(c.cartesian ? 1.0 : h->tau), (R)c.eps_cut,
-                                                                  h->N, X, Y);
+template <typename R> static clv_status mlp_samples_impl(clv_handle* h, float* X, float* Y, int64_t* count) {
+  SampleIn<R> a;
+  for (int m = 0; m < 4; ++m) a.T4.p[m] = (R*)h->T0[m];
+  for (int q = 0; q < 10; ++q) a.pi.p[q] = (R*)h->PI0[q];
+  a.pr = prim_set<R>(h, h->cur);
+  a.viscous = h->viscous;
+  a.taus = (R)(h->cfg.cartesian ? 1.0 : h->tau);
+  a.eps_cut = (R)h->cfg.eps_cut;
+  a.N = h->N;
+  // scratch in the staging buffer: block counts, then their offsets
+  const unsigned nb = grid_of(h->N);
+  unsigned* counts = reinterpret_cast<unsigned*>(h->staging);
+  unsigned long long* offsets = reinterpret_cast<unsigned long long*>(h->staging + (nb + 1) / 2 + 1);
+  mlp_samples_kernel<R, false><<<nb, kBlock, 0, h->stream>>>(a, counts, nullptr, nullptr, nullptr);
+  scan_counts_kernel<<<1, kBlock, 0, h->stream>>>(counts, (int)nb, offsets, reinterpret_cast<long long*>(count));
+  mlp_samples_kernel<R, true><<<nb, kBlock, 0, h->stream>>>(a, nullptr, offsets, X, Y);
   CLV_CUDA(h, cudaGetLastError());
   return CLV_OK;
 }
 
 extern "C" {
 
-clv_status clv_mlp_samples(clv_handle* h, float* d_X, float* d_Y) {
-  if (!h || !d_X || !d_Y) return CLV_EINVAL;
+clv_status clv_mlp_samples(clv_handle* h, float* d_X, float* d_Y, int64_t* d_count) {
+  if (!h || !d_X || !d_Y || !d_count) return CLV_EINVAL;
   if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
-  return h->rsize == 8 ? mlp_samples_impl<double>(h, d_X, d_Y) : mlp_samples_impl<float>(h, d_X, d_Y);
+  return h->rsize == 8 ? mlp_samples_impl<double>(h, d_X, d_Y, d_count)
+                       : mlp_samples_impl<float>(h, d_X, d_Y, d_count);
 }
 
 }  // extern "C"
@@ -751,9 +765,10 @@ __global__ void __launch_bounds__(kBlock) mlp_forward_kernel(const void* mlp, co
 extern "C" {
 
 clv_status clv_mlp_forward(clv_handle* h, const float* d_X, int64_t n, float* d_Y) {
-  if (!h || !d_X || !d_Y || n < 0) return CLV_EINVAL;
+  if (!h || n < 0) return CLV_EINVAL;
   if (!h->mlp_loaded) return fail(h, CLV_EINVAL, "no network loaded (clv_set_mlp)");
   if (n == 0) return CLV_OK;
+  if (!d_X || !d_Y) return fail(h, CLV_EINVAL, "null feature or output array");
   mlp_forward_kernel<<<grid_of(n), kBlock, 0, h->stream>>>(h->mlp, d_X, n, d_Y);
   CLV_CUDA(h, cudaGetLastError());
   return CLV_OK;

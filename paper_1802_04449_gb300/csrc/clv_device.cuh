@@ -136,7 +136,11 @@ template <> struct SolveOps<double, float> {
 // C: arithmetic of the solve (E - M v, f, Newton step, gamma); CE: arithmetic
 // of the EOS lookup (CE may be narrower than C: the FP32 path refines in FP64
 // around an FP32 table lookup).
-template <typename C, typename R, typename CE = C>
+// FIXED: from a usable guess, run at most maxit Newton steps and accept the
+// last iterate (the FP64 refinement of an FP32 root, which starts inside
+// Newton's quadratic basin and whose FP32 table lookup leaves a noise floor
+// above tol); without one, solve in full (up to 100 steps).
+template <typename C, typename R, typename CE = C, bool FIXED = false>
 __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps_cut, C E, C Mx,
                                                       C My, C Me, C tol, int maxit, C& eps,
                                                       C& ux, C& uy, C& ue, C* vguess = nullptr) {
@@ -161,9 +165,11 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
   C lo = C(0), hi = Ops::div(M, E);
   C P, cs2;
   C v;
+  bool fixed = FIXED;
   if (vguess && *vguess > lo && *vguess < hi) {
     v = *vguess;
   } else {
+    if (FIXED) { fixed = false; maxit = 100; }  // no usable start: solve in full
     CE Pe, Te, ce;
     eos_eval<CE, R>(q, CE(E), Pe, Te, ce);
     P = C(Pe);
@@ -193,6 +199,7 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
     v = vn;
     if (hi - lo <= tol) { ok = true; break; }
   }
+  if (fixed && !ok) { ok = true; it = maxit; }
   rr.iters = ok ? it : -1;
   if (vguess) *vguess = v;
   C e = E - M * v;

@@ -125,6 +125,28 @@ __device__ __forceinline__ void interface_flux(const R* L, const R* Rr, R csl, R
 // |pi_{mu nu} pi^{mu nu}| <= kRhoMax^2 (eps^2 + 3 P^2).
 constexpr double kRhoMax = 1.0;
 constexpr double kViscEpsMin = 1e-3;   // GeV/fm^3
+// FP64 refinement of the FP32 root solve (E - M v, the Newton step and gamma
+// in FP64 around the FP32 table lookup).  A converged FP32 root starts
+// kPolishSteps FP64 Newton steps (it lies in the quadratic basin; the FP32
+// interpolation of P sets the noise floor beyond which more steps gain
+// nothing); an unconverged one gets a full bracketed FP64 solve.  Returns the
+// iterations taken, -1 if the full solve hit its cap.
+constexpr int kPolishSteps = 3;
+template <typename R>
+__device__ __forceinline__ int polish_root(const StageParams<R>& p, R E, R Mx, R My, R Me, R v32, bool converged,
+                                           R& en, R& ux, R& uy, R& ue) {
+  double dv = converged ? (double)v32 : -1.0, de, dux, duy, due;
+  RootResult r2;
+  if (converged)
+    r2 = solve_primitive<double, R, float, true>(p.eos, p.eps_cut_d, (double)E, (double)Mx, (double)My, (double)Me,
+                                                 1e-13, kPolishSteps, de, dux, duy, due, &dv);
+  else
+    r2 = solve_primitive<double, R, float>(p.eos, p.eps_cut_d, (double)E, (double)Mx, (double)My, (double)Me, 1e-13,
+                                           100, de, dux, duy, due, &dv);
+  en = R(de); ux = R(dux); uy = R(duy); ue = R(due);
+  return r2.iters;
+}
+
 template <typename R>
 __device__ __forceinline__ void regulate_shear(R e, R P, R* pi) {
   if (e < R(kViscEpsMin)) {
@@ -361,14 +383,8 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
         f_nonconv = rr.iters < 0;
         const bool near_cut = en < p.polish_E;
         if (E >= p.eps_cut && M > R(0) && (near_cut || M > p.polish_v * E || rr.iters < 0)) {
-          if (rr.iters < 0) vg = R(-1);
-          double dv = (double)vg, de, dux, duy, due;
-          RootResult r2 = solve_primitive<double, R, float>(p.eos, p.eps_cut_d, (double)E, (double)Mx,
-                                                     (double)My, (double)Me, 1e-13, 40, de, dux,
-                                                     duy, due, &dv);
-          en = R(de); ux = R(dux); uy = R(duy); ue = R(due);
+          rr.iters = polish_root<R>(p, E, Mx, My, Me, vg, rr.iters >= 0, en, ux, uy, ue);
           f_polished = true;
-          rr.iters = r2.iters;
         }
       }
       f_fail = rr.iters < 0;
@@ -441,7 +457,7 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
   const bool active = c < p.N;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double my_T0 = 0.0, my_e = 0.0;
-  int my_iters = 0, my_solved = 0;
+  int my_iters = 0, my_solved = 0, my_polish_iters = 0;
   bool f_rescaled = false, f_fail = false, f_polished = false, f_nonfinite = false, f_nonconv = false;
   const R tn = p.taus_new;
   R T0v = R(0), E = R(0), Mx = R(0), My = R(0), Me = R(0);
@@ -507,13 +523,9 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
         f_nonconv = rr.iters < 0;
         const bool near_cut = en < p.polish_E;
         if (E >= p.eps_cut && M > R(0) && (near_cut || M > p.polish_v * E || rr.iters < 0)) {
-          if (rr.iters < 0) vg = R(-1);
-          double dv = (double)vg, de, dux, duy, due;
-          RootResult r2 = solve_primitive<double, R, float>(p.eos, p.eps_cut_d, (double)E, (double)Mx, (double)My,
-                                                            (double)Me, 1e-13, 40, de, dux, duy, due, &dv);
-          en = R(de); ux = R(dux); uy = R(duy); ue = R(due);
+          rr.iters = polish_root<R>(p, E, Mx, My, Me, vg, rr.iters >= 0, en, ux, uy, ue);
+          my_polish_iters = rr.iters > 0 ? rr.iters : 0;
           f_polished = true;
-          rr.iters = r2.iters;
         }
       }
       f_fail = rr.iters < 0;
@@ -547,6 +559,8 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
   const unsigned b_nc = __ballot_sync(full, f_nonconv);
   const int w_iters = __reduce_add_sync(full, my_iters);
   const int w_solved = __reduce_add_sync(full, my_solved);
+  const int w_piters = __reduce_add_sync(full, my_polish_iters);
+  const unsigned w_maxit = __reduce_max_sync(full, (unsigned)my_iters);   // a warp runs as long as its slowest lane
   if (lane == 0) {
     if (b_res) atomicAdd(p.counters + 0, (unsigned long long)__popc(b_res));
     if (b_fail) { atomicAdd(p.counters + 1, (unsigned long long)__popc(b_fail)); atomicOr(p.err, 1u); }
@@ -554,6 +568,11 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
     if (b_nc) atomicAdd(p.counters + 3, (unsigned long long)__popc(b_nc));
     if (w_iters) atomicAdd(p.counters + 4, (unsigned long long)w_iters);
     if (w_solved) atomicAdd(p.counters + 5, (unsigned long long)w_solved);
+    if (w_piters) atomicAdd(p.counters + 6, (unsigned long long)w_piters);
+    if (w_maxit) {
+      atomicAdd(p.counters + 7, (unsigned long long)w_maxit);
+      atomicAdd(p.counters + 8, 1ull);
+    }
     if (b_nf) atomicOr(p.err, 2u);
   }
   if constexpr (STATS) {
@@ -577,33 +596,89 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
 }
 
 // Training samples of the current state: features of (E, M, pi~^{ij}) as in
-// mlp_features and targets (eps/E, v); rows of vacuum cells are NaN.
+// mlp_features and targets (eps/E, v) of every non-vacuum cell, written
+// compacted in cell order.  WRITE = false counts the rows of each block into
+// counts[blockIdx]; WRITE = true writes them from the exclusive offsets.
+template <typename R> struct SampleIn {
+  Ptr10<R> T4, pi;
+  Prim<R> pr;
+  bool viscous;
+  R taus, eps_cut;
+  long long N;
+};
+
 template <typename R>
-__global__ void __launch_bounds__(kBlock) mlp_samples_kernel(Ptr10<R> T4, Ptr10<R> pi, bool viscous, Prim<R> pr,
-                                                             R taus, R eps_cut, long long N, float* X, float* Y) {
-  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= N) return;
-  R E = T4.p[0][c] / taus, Mx = T4.p[1][c] / taus, My = T4.p[2][c] / taus, Me = T4.p[3][c] / taus;
+__device__ __forceinline__ bool sample_of(const SampleIn<R>& a, long long c, float* x, float* y) {
+  R E = a.T4.p[0][c] / a.taus, Mx = a.T4.p[1][c] / a.taus, My = a.T4.p[2][c] / a.taus, Me = a.T4.p[3][c] / a.taus;
   R pij[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-  if (viscous) {
-    E -= pi.p[0][c]; Mx -= pi.p[1][c]; My -= pi.p[2][c]; Me -= pi.p[3][c];
-    for (int k = 0; k < 6; ++k) pij[k] = pi.p[4 + k][c];
+  if (a.viscous) {
+    E -= a.pi.p[0][c]; Mx -= a.pi.p[1][c]; My -= a.pi.p[2][c]; Me -= a.pi.p[3][c];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) pij[k] = a.pi.p[4 + k][c];
   }
-  const R e = pr.e[c];
-  if (!(E >= eps_cut) || !(e > R(0))) {
-    for (int k = 0; k < kMlpIn; ++k) X[c * kMlpIn + k] = __int_as_float(0x7fc00000);
-    for (int k = 0; k < kMlpOut; ++k) Y[c * kMlpOut + k] = __int_as_float(0x7fc00000);
+  const R e = a.pr.e[c];
+  if (!(E >= a.eps_cut) || !(e > R(0)) || !isfinite(E)) return false;
+  mlp_features<R>(E, Mx, My, Me, pij, x);
+  const R u1 = a.pr.u[0][c], u2 = a.pr.u[1][c], u3 = a.pr.u[2][c];
+  const R iut = R(1) / sqrt(R(1) + u1 * u1 + u2 * u2 + u3 * u3);
+  y[0] = float(e / E);
+  y[1] = float(u1 * iut);
+  y[2] = float(u2 * iut);
+  y[3] = float(u3 * iut);
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < kMlpIn; ++k) ok = ok && isfinite(x[k]);
+  return ok;
+}
+
+template <typename R, bool WRITE>
+__global__ void __launch_bounds__(kBlock) mlp_samples_kernel(const SampleIn<R> a, unsigned* counts,
+                                                             const unsigned long long* offsets, float* X, float* Y) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  float x[kMlpIn], y[kMlpOut];
+  const bool ok = c < a.N && sample_of(a, c, x, y);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned b = __ballot_sync(0xffffffffu, ok);
+  __shared__ unsigned s_w[kBlock / 32];
+  if (lane == 0) s_w[wid] = __popc(b);
+  __syncthreads();
+  if (!WRITE) {
+    if (threadIdx.x == 0) {
+      unsigned t = 0;
+      for (int w = 0; w < kBlock / 32; ++w) t += s_w[w];
+      counts[blockIdx.x] = t;
+    }
     return;
   }
-  float x[kMlpIn];
-  mlp_features<R>(E, Mx, My, Me, pij, x);
-  for (int k = 0; k < kMlpIn; ++k) X[c * kMlpIn + k] = x[k];
-  const R u1 = pr.u[0][c], u2 = pr.u[1][c], u3 = pr.u[2][c];
-  const R iut = R(1) / sqrt(R(1) + u1 * u1 + u2 * u2 + u3 * u3);
-  Y[c * kMlpOut + 0] = float(e / E);
-  Y[c * kMlpOut + 1] = float(u1 * iut);
-  Y[c * kMlpOut + 2] = float(u2 * iut);
-  Y[c * kMlpOut + 3] = float(u3 * iut);
+  if (!ok) return;
+  unsigned before = 0;
+  for (int w = 0; w < wid; ++w) before += s_w[w];
+  const long long row = (long long)offsets[blockIdx.x] + before + __popc(b & ((1u << lane) - 1u));
+#pragma unroll
+  for (int k = 0; k < kMlpIn; ++k) X[row * kMlpIn + k] = x[k];
+#pragma unroll
+  for (int k = 0; k < kMlpOut; ++k) Y[row * kMlpOut + k] = y[k];
+}
+
+// Exclusive scan of n block counts (one block of kBlock threads; each thread
+// scans a contiguous chunk), total into *total.
+__global__ void __launch_bounds__(kBlock) scan_counts_kernel(const unsigned* counts, int n,
+                                                             unsigned long long* offsets, long long* total) {
+  __shared__ unsigned long long s_part[kBlock];
+  const int per = (n + kBlock - 1) / kBlock;
+  const int lo = threadIdx.x * per, hi = min(n, lo + per);
+  unsigned long long t = 0;
+  for (int i = lo; i < hi; ++i) t += counts[i];
+  s_part[threadIdx.x] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long run = 0;
+    for (int w = 0; w < kBlock; ++w) { const unsigned long long v = s_part[w]; s_part[w] = run; run += v; }
+    *total = (long long)run;
+  }
+  __syncthreads();
+  unsigned long long run = s_part[threadIdx.x];
+  for (int i = lo; i < hi; ++i) { offsets[i] = run; run += counts[i]; }
 }
 
 // T~^{tau mu} = tau [(e + P) u^tau u^mu - P g~^{tau mu} + pi~^{tau mu}]

@@ -1,0 +1,62 @@
+"""Profiling driver: the 97x97x41 viscous hot-spot event evolved through the C
+ABI, for capture under a profiler (the kernels of interest are the last
+launches).  Usage:
+
+    python -m paper_1802_04449_gb300.profile_case [--precision fp32|fp64]
+        [--guess previous|cold|learned] [--skip S] [--steps K]
+
+--skip S steps run first (reaching the later, more dilute state), then K
+steps.  --guess learned trains the network briefly (FP64 states of another
+seed of the same workload) before the run.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--guess", default="previous", choices=["previous", "cold", "learned"])
+    ap.add_argument("--skip", type=int, default=0)
+    ap.add_argument("--steps", type=int, default=3)
+    a = ap.parse_args(argv)
+
+    import torch
+    from paper_1802_04449_gb300 import clv
+    from paper_1802_04449_gb300 import inputs as I
+    from paper_1802_04449_gb300 import learned as L
+
+    case = I.hotspot_event()
+    prec = clv.CLV_FP32 if a.precision == "fp32" else clv.CLV_FP64
+    params = None
+    if a.guess == "learned":
+        tc = I.hotspot_event(seed=1000)
+        h = clv.from_case(tc, clv.CLV_FP64)
+        h.set_initial(tc.eps, tc.ux, tc.uy, tc.ueta)
+        X, Y = L.collect_samples(h, max(a.skip + a.steps, 40), 20).data()
+        p, _ = L.train(X, Y, iters=1000, batch=32768, lr=2e-3, seed=7)
+        params = p.cpu().numpy()
+        h.close()
+    g = clv.from_case(case, prec)
+    g.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    if params is not None:
+        g.set_mlp(params)
+    g.set_guess({"previous": clv.CLV_GUESS_PREVIOUS, "cold": clv.CLV_GUESS_COLD,
+                 "learned": clv.CLV_GUESS_MLP}[a.guess])
+    if a.skip:
+        g.step(a.skip)
+    st = g.step(a.steps, stats=True)
+    torch.cuda.synchronize()
+    print("profile case done: tau %.3f, newton iters/solve %.3f, polished %d" %
+          (st["tau"], st["n_newton_iters"] / max(1, st["n_newton_cells"]), st["n_polished"]))
+
+
+if __name__ == "__main__":
+    main()

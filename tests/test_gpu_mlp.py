@@ -1,0 +1,215 @@
+"""The learned initial guess of the root solve on the GPU, through the C ABI:
+FP32 loss/gradient kernels against the FP64 CPU reference, the tensor-core
+forward pass against a BF16-rounded FP64 forward pass, training on samples
+the solver dumps, what the trained guess gains in Newton iterations, and
+parity of the FP32 + learned-guess evolution with the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import mlp_ref as M
+from paper_1802_04449_gb300 import clv
+from paper_1802_04449_gb300 import inputs as I
+from paper_1802_04449_gb300 import learned as L
+
+pytestmark = pytest.mark.gpu
+
+EPS_FLOOR = 1e-3
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _bf16(a):
+    """Round float32 values to bfloat16 (nearest, ties to even), as float64."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _forward_bf16(params, X):
+    """FP64 forward pass with the roundings of the tensor-core path: BF16
+    weights, inputs and hidden activations; FP32 biases."""
+    d = M.unpack(params)
+    silu = lambda z: z / (1.0 + np.exp(-z))
+    h1 = silu(_bf16(X) @ _bf16(d["W1"]).T + d["b1"])
+    h2 = silu(_bf16(h1) @ _bf16(d["W2"]).T + d["b2"])
+    return _bf16(h2) @ _bf16(d["W3"]).T + d["b3"]
+
+
+def _case(seed=7):
+    return I.hotspot_event(nx=25, ny=23, neta=13, n_spots=90, seed=seed, eta_over_s=0.08)
+
+
+def test_loss_and_gradient_match_fp64_reference():
+    torch = _torch()
+    rng = np.random.default_rng(11)
+    p = M.init_params(4) + 0.05 * rng.normal(size=M.NPARAM)
+    n = 1000                                   # 7 full blocks of 128 and a ragged tail
+    X = rng.normal(size=(n, M.NIN))
+    Y = rng.normal(size=(n, M.NOUT))
+    p32, X32, Y32 = (a.astype(np.float32) for a in (p, X, Y))
+    loss_ref, g_ref = M.loss_and_grad(p32.astype(np.float64), X32.astype(np.float64), Y32.astype(np.float64))
+    dev = torch.device("cuda")
+    loss, g = clv.mlp_loss_grad(torch.tensor(p32, device=dev), torch.tensor(X32, device=dev),
+                                torch.tensor(Y32, device=dev))
+    torch.cuda.synchronize()
+    g = g.cpu().numpy().astype(np.float64)
+    assert float(loss.item()) == pytest.approx(loss_ref, rel=2e-5)
+    o = 0
+    for name, shape in M.SHAPES:
+        k = int(np.prod(shape))
+        gr, gg = g_ref[o:o + k], g[o:o + k]
+        bound = 2e-4 * (np.abs(gr) + 1e-2 * np.abs(gr).max())
+        assert np.all(np.abs(gg - gr) <= bound), (name, float(np.max(np.abs(gg - gr) / bound)))
+        o += k
+
+
+def test_tensor_core_forward_matches_bf16_reference():
+    torch = _torch()
+    rng = np.random.default_rng(3)
+    p = (M.init_params(9) + 0.02 * rng.normal(size=M.NPARAM)).astype(np.float32)
+    n = 4133                                   # several blocks of 256 rows and a ragged tail
+    X = rng.normal(size=(n, M.NIN)).astype(np.float32)
+    case = _case()
+    h = clv.from_case(case, clv.CLV_FP32)
+    h.set_mlp(p)
+    y = h.mlp_forward(torch.tensor(X, device="cuda")).cpu().numpy().astype(np.float64)
+    ref = _forward_bf16(p.astype(np.float64), X.astype(np.float64))
+    exact, _ = M.forward(p.astype(np.float64), X.astype(np.float64))
+    scale = np.abs(ref).max()
+    assert np.max(np.abs(y - ref)) <= 1e-2 * scale, np.max(np.abs(y - ref)) / scale
+    assert np.max(np.abs(y - exact)) <= 5e-2 * scale
+    # zero rows and an empty call
+    h.mlp_forward(torch.zeros((0, 10), device="cuda"))
+
+
+def test_guess_mode_errors():
+    case = _case()
+    h32 = clv.from_case(case, clv.CLV_FP32)
+    with pytest.raises(clv.ClvError):
+        h32.set_guess(clv.CLV_GUESS_MLP)           # no network loaded
+    with pytest.raises(clv.ClvError):
+        h32.set_guess(7)
+    h64 = clv.from_case(case, clv.CLV_FP64)
+    h64.set_mlp(L.init_params(0))
+    with pytest.raises(clv.ClvError):
+        h64.set_guess(clv.CLV_GUESS_MLP)           # the learned guess runs on the FP32 path
+    with pytest.raises(ValueError):
+        h32.set_mlp(np.zeros(10, np.float32))
+
+
+def test_samples_are_the_solver_states():
+    """Rows are the non-vacuum cells in cell order; targets are the solved
+    (eps/E, v) of the FP64 state, features those of include/clv.h."""
+    torch = _torch()
+    case = _case(5)
+    h = clv.from_case(case, clv.CLV_FP64)
+    h.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    h.step(6)
+    X, Y = h.mlp_samples()
+    X, Y = X.cpu().numpy().astype(np.float64), Y.cpu().numpy().astype(np.float64)
+    f = h.get(["eps", "ux", "uy", "ueta", "Ttt", "Ttx", "Tty", "Tte", "pitt", "pitx", "pity", "pite",
+               "pixx", "pixy", "pixe", "piyy", "piye", "piee"])
+    tau = h.time()[0]
+    E = f["Ttt"] / tau - f["pitt"]
+    Mv = [f["Ttx"] / tau - f["pitx"], f["Tty"] / tau - f["pity"], f["Tte"] / tau - f["pite"]]
+    keep = (E >= 1e-7) & (f["eps"] > 0)
+    assert X.shape[0] == int(keep.sum()) > 0
+    Ek = E[keep]
+    lnE = np.log(Ek)
+    assert np.all(np.abs(X[:, 0] - (lnE + 5.0) / 5.0) <= 2e-6 * (1 + np.abs(lnE)))
+    for k in range(3):
+        np.testing.assert_allclose(X[:, 1 + k], Mv[k][keep] / Ek, rtol=1e-5, atol=1e-7)
+    for k, nm in enumerate(["pixx", "pixy", "pixe", "piyy", "piye", "piee"]):
+        np.testing.assert_allclose(X[:, 4 + k], np.clip(f[nm][keep] / Ek, -4, 4), rtol=1e-5, atol=1e-7)
+    ut = np.sqrt(1 + f["ux"] ** 2 + f["uy"] ** 2 + f["ueta"] ** 2)
+    np.testing.assert_allclose(Y[:, 0], f["eps"][keep] / Ek, rtol=1e-6, atol=1e-7)
+    for k, nm in enumerate(["ux", "uy", "ueta"]):
+        np.testing.assert_allclose(Y[:, 1 + k], (f[nm] / ut)[keep], rtol=1e-6, atol=1e-7)
+
+
+TRAIN_STEPS, SKIP, RUN = 80, 60, 10
+
+
+@pytest.fixture(scope="module")
+def trained():
+    """A network trained on the FP64 solver's states of two seeded events,
+    dumped every 5 steps over the first TRAIN_STEPS steps."""
+    torch = _torch()
+    buf = None
+    for seed in (21, 22):
+        case = _case(seed)
+        h = clv.from_case(case, clv.CLV_FP64)
+        h.set_initial(case.eps, case.ux, case.uy, case.ueta)
+        if buf is None:
+            buf = L.SampleBuffer(torch, h.device, 2 * (TRAIN_STEPS // 5 + 1) * h.N)
+        L.collect_samples(h, TRAIN_STEPS, 5, buf)
+    X, Y = buf.data()
+    p, losses = L.train(X, Y, iters=2000, batch=8192, lr=3e-3, seed=5)
+    torch.cuda.synchronize()
+    return p, losses.cpu().numpy(), X, Y
+
+
+def test_training_reduces_the_loss(trained):
+    p, losses, X, Y = trained
+    assert np.all(np.isfinite(losses))
+    assert losses[-50:].mean() < 0.05 * losses[:10].mean(), (losses[:10].mean(), losses[-50:].mean())
+    # the trained network's loss over a subset, by the gradient kernel, equals
+    # the FP64 reference
+    torch = _torch()
+    sub = slice(0, 3000)
+    loss, _ = clv.mlp_loss_grad(p, X[sub].contiguous(), Y[sub].contiguous())
+    ref, _ = M.loss_and_grad(p.cpu().numpy().astype(np.float64), X[sub].cpu().numpy().astype(np.float64),
+                             Y[sub].cpu().numpy().astype(np.float64))
+    torch.cuda.synchronize()
+    assert float(loss.item()) == pytest.approx(ref, rel=1e-4)
+
+
+def _run_mode(case, mode, params):
+    """SKIP steps with the default guess, then RUN steps with `mode`; returns
+    the handle and the RUN steps' (iterations per solve, warp-max iterations
+    per warp)."""
+    h = clv.from_case(case, clv.CLV_FP32)
+    h.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    if params is not None:
+        h.set_mlp(params)
+    s0 = h.step(SKIP, stats=True)
+    h.set_guess(mode)
+    s1 = h.step(RUN, stats=True)
+    assert s1["error_word"] == 0 and s1["n_rootfail"] == 0
+    d = {k: s1[k] - s0[k] for k in ("n_newton_iters", "n_newton_cells", "n_newton_warp_max", "n_newton_warps")}
+    return h, (d["n_newton_iters"] / d["n_newton_cells"], d["n_newton_warp_max"] / d["n_newton_warps"])
+
+
+def test_learned_guess_gains_and_keeps_parity(trained):
+    """A seed not trained on, evolved to tau = 1.0 fm (developed transverse
+    flow), then three guesses for the next steps.  Every mode solves to the
+    same tolerance; the learned guess needs fewer Newton iterations than the
+    solver's own cold start (mean and warp maximum), and its evolution
+    matches the FP64 oracle within 1e-4 where eps > 1e-3 GeV/fm^3."""
+    p, _, _, _ = trained
+    case = _case(31)
+    params = p.cpu().numpy()
+    res = {}
+    for name, mode in (("previous", clv.CLV_GUESS_PREVIOUS), ("cold", clv.CLV_GUESS_COLD),
+                       ("mlp", clv.CLV_GUESS_MLP)):
+        res[name] = _run_mode(case, mode, params if mode == clv.CLV_GUESS_MLP else None)
+    print("Newton iterations per solve / warp max per warp:",
+          {k: (round(v[1][0], 3), round(v[1][1], 3)) for k, v in res.items()})
+    assert res["mlp"][1][0] < res["cold"][1][0]
+    assert res["mlp"][1][1] <= res["cold"][1][1]
+    o = oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
+                      case.eta_over_s, case.eos)
+    o.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    o.step(SKIP + RUN)
+    e_o = o.get("eps")
+    m = e_o > EPS_FLOOR
+    for name, (h, _) in res.items():
+        e_g = h.get(["eps"])["eps"]
+        assert np.max(np.abs(e_g[m] / e_o[m] - 1)) <= 1e-4, name
+    # deterministic
+    h2, _ = _run_mode(case, clv.CLV_GUESS_MLP, params)
+    assert np.array_equal(h2.get(["eps"])["eps"], res["mlp"][0].get(["eps"])["eps"])
