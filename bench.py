@@ -155,6 +155,7 @@ def run_gpu(args):
             g.set_guess(clv.CLV_GUESS_MLP)
         elif guess is not None:
             g.set_guess(guess)
+        tile = g.autotune(max_candidates=12, reps=3) if args.autotune else g.tile()
         g.step(warmup)
         torch.cuda.synchronize()
         g.enable_kernel_timing(kernel_timing)
@@ -176,6 +177,7 @@ def run_gpu(args):
         except clv.ClvError as e:          # reported in the JSON line, not hidden
             st = {"error": str(e)}
         g.close()
+        st["tile"] = tile
         return ms, kt, st
 
     # ---- the learned guess (setup, not timed): states of the FP64 solver on
@@ -240,6 +242,8 @@ def run_gpu(args):
         g.set_initial(*host_in)                      # warm-up
         g.set_mlp(params_host)
         g.set_guess(clv.CLV_GUESS_MLP)
+        if args.autotune:
+            g.autotune(max_candidates=12, reps=3)
         g.step(args.warmup)
         torch.cuda.synchronize()
         barrier()
@@ -302,8 +306,9 @@ def run_gpu(args):
         "gpu_launches": 4 * args.steps,
         "clocks": clocks,
         "stats_fp32": {k: st32.get(k) for k in ("tau", "eps_max", "T_max", "E_tot", "n_polished", "n_rootfail",
-                                                "n_fp32_nonconverged", "error_word", "error")},
-        "stats_fp64": {k: st64.get(k) for k in ("tau", "eps_max", "E_tot", "n_rootfail", "error_word", "error")},
+                                                "n_fp32_nonconverged", "error_word", "error", "tile")},
+        "stats_fp64": {k: st64.get(k) for k in ("tau", "eps_max", "E_tot", "n_rootfail", "error_word", "error",
+                                                "tile")},
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
@@ -401,6 +406,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default tile shape instead of timing candidates (setup, untimed)")
     ap.add_argument("--train-events", type=int, default=2, help="FP64 events whose states train the guess")
     ap.add_argument("--train-every", type=int, default=20, help="steps between sample dumps")
     ap.add_argument("--train-iters", type=int, default=4000, help="Adam iterations")

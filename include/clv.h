@@ -213,6 +213,30 @@ clv_status clv_mlp_train(float* d_params, float* d_work, const float* d_X, const
                          int iters, int batch, float lr, uint64_t seed, int step0, void* cuda_stream,
                          float* d_loss);
 
+/* ---------------- tile shape of the stage kernel ----------------
+ * The stage kernel works on (y, eta_s) tiles of TJ x TK cells, each CTA
+ * marching along x over CX planes ((TJ + 1)(TK + 1) threads per CTA).  The
+ * shape changes no result, only the speed. */
+typedef struct {
+  int TJ, TK, CX;            /* tile rows (y), columns (eta_s), planes per CTA (x) */
+  int threads;               /* threads per CTA */
+  int blocks;                /* CTAs per stage launch */
+  int smem_bytes;            /* dynamic shared memory per CTA */
+  double ms;                 /* clv_autotune: mean stage-1 time of the chosen shape (ms) */
+} clv_tile_info;
+
+clv_status clv_get_tile(clv_handle* h, clv_tile_info* out);
+
+/* Explicit shape; CX = 0 picks the x chunking by the makespan rule.
+ * CLV_EINVAL if out of range or beyond the thread / shared-memory limits. */
+clv_status clv_set_tile(clv_handle* h, int TJ, int TK, int CX);
+
+/* Autotuner: times the current shape and up to max_candidates modelled-best
+ * shapes (reps stage-1 launches each, on the current state, which they leave
+ * unchanged) on the handle's stream, keeps the fastest and reports it in
+ * *best (nullable).  Needs clv_set_initial; synchronises the stream. */
+clv_status clv_autotune(clv_handle* h, int max_candidates, int reps, clv_tile_info* best);
+
 /* Statistics without any allocation.  The paper has no counterpart: this is
  * a service for callers that cannot allocate device memory -- code running
  * under a fixed device-memory budget owned by another framework's pool, or in

@@ -58,6 +58,14 @@ class clv_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "_pad"}
 
 
+class clv_tile_info(ctypes.Structure):
+    _fields_ = [("TJ", ctypes.c_int), ("TK", ctypes.c_int), ("CX", ctypes.c_int), ("threads", ctypes.c_int),
+                ("blocks", ctypes.c_int), ("smem_bytes", ctypes.c_int), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class ClvError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -71,7 +79,7 @@ EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initi
             "clv_get_fields_device", "clv_get_time", "clv_enable_kernel_timing", "clv_get_kernel_times",
             "clv_destroy", "clv_last_error", "clv_version", "clv_field_stats_noalloc",
             "clv_set_guess", "clv_set_mlp", "clv_mlp_samples", "clv_mlp_forward", "clv_mlp_loss_grad",
-            "clv_mlp_train"]
+            "clv_mlp_train", "clv_get_tile", "clv_set_tile", "clv_autotune"]
 CLV_GUESS_PREVIOUS, CLV_GUESS_COLD, CLV_GUESS_MLP = 0, 1, 2
 MLP_NPARAM = 5124
 
@@ -111,6 +119,10 @@ def load(path: str | None = None):
         lib.clv_mlp_loss_grad.argtypes = [V, V, V, ctypes.c_int64, V, V, V]
         lib.clv_mlp_train.argtypes = [V, V, V, V, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                       ctypes.c_uint64, ctypes.c_int, V, V]
+        TI = ctypes.POINTER(clv_tile_info)
+        lib.clv_get_tile.argtypes = [P, TI]
+        lib.clv_set_tile.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        lib.clv_autotune.argtypes = [P, ctypes.c_int, ctypes.c_int, TI]
         lib.clv_destroy.argtypes = [P]
         lib.clv_destroy.restype = None
         lib.clv_last_error.argtypes = [P]
@@ -227,6 +239,20 @@ class Hydro:
         step = ctypes.c_int64()
         self._lib.clv_get_time(self._h, ctypes.byref(tau), ctypes.byref(step))
         return tau.value, step.value
+
+    def tile(self):
+        t = clv_tile_info()
+        self._check(self._lib.clv_get_tile(self._h, ctypes.byref(t)), self._h)
+        return t.as_dict()
+
+    def set_tile(self, TJ, TK, CX=0):
+        self._check(self._lib.clv_set_tile(self._h, int(TJ), int(TK), int(CX)), self._h)
+
+    def autotune(self, max_candidates=12, reps=3):
+        """Time candidate tile shapes on the current state; keep the fastest."""
+        t = clv_tile_info()
+        self._check(self._lib.clv_autotune(self._h, int(max_candidates), int(reps), ctypes.byref(t)), self._h)
+        return t.as_dict()
 
     def set_guess(self, mode):
         self._check(self._lib.clv_set_guess(self._h, int(mode)), self._h)

@@ -157,8 +157,74 @@ TileGeom tile_geometry(const clv_config* c, int sms) {
   g.threads = (t.TJ + 1) * (t.TK + 1);
   g.blocks = (unsigned)(tiles * nch);
   const bool visc = c->eta_over_s > 0.0;
-  g.smem = (visc ? tile_smem_elems<true>(t.TJ, t.TK) : tile_smem_elems<false>(t.TJ, t.TK)) * rsize;
+  g.smem = visc ? tile_smem_bytes<true>(t.TJ, t.TK, rsize) : tile_smem_bytes<false>(t.TJ, t.TK, rsize);
   return g;
+}
+
+// Geometry of an explicit (TJ, TK) tile shape; CX from the makespan rule of
+// tile_geometry when cx <= 0.
+TileGeom tile_geometry_of(const clv_config* c, int sms, int TJ, int TK, int cx) {
+  const int rsize = c->precision == CLV_FP64 ? 8 : 4;
+  TileGeom g;
+  TileArgs& t = g.t;
+  t.TJ = TJ;
+  t.TK = TK;
+  t.ntj = (c->ny + TJ - 1) / TJ;
+  t.ntk = (c->neta + TK - 1) / TK;
+  const long long tiles = (long long)t.ntj * t.ntk;
+  if (cx <= 0) {
+    long long best_nch = 1;
+    double best = 1e300;
+    for (long long nch = 1; nch <= c->nx; ++nch) {
+      const long long cxx = (c->nx + nch - 1) / nch;
+      const long long used = (c->nx + cxx - 1) / cxx;
+      const long long slots = (long long)sms * CLV_TILE_MIN_BLOCKS;
+      const long long waves = (tiles * used + slots - 1) / slots;
+      const double cost = (double)waves * (double)(cxx + 4);
+      if (cost < best - 1e-9) { best = cost; best_nch = used; }
+    }
+    cx = (int)((c->nx + best_nch - 1) / best_nch);
+  }
+  t.CX = cx;
+  const long long nch = (c->nx + t.CX - 1) / t.CX;
+  g.threads = (TJ + 1) * (TK + 1);
+  g.blocks = (unsigned)(tiles * nch);
+  const bool visc = c->eta_over_s > 0.0;
+  g.smem = visc ? tile_smem_bytes<true>(TJ, TK, rsize) : tile_smem_bytes<false>(TJ, TK, rsize);
+  return g;
+}
+
+inline int tile_max_threads(const clv_config* c) {
+  return c->precision == CLV_FP64 ? std::min(CLV_TILE_MAX_THREADS, kBlock / 2) : CLV_TILE_MAX_THREADS;
+}
+
+// Candidate tile shapes for the autotuner, best modelled makespan first:
+// eta_s split into 1..4 columns of tiles, y tiles from the largest that fits
+// the thread limit down to a third of it, the x chunking of each by the
+// makespan rule.  Model: waves x (planes + 4 halo planes) x staged box cells.
+std::vector<TileGeom> tile_candidates(const clv_config* c, int sms, size_t smem_max) {
+  std::vector<std::pair<double, TileGeom>> v;
+  const int maxthr = tile_max_threads(c);
+  int last_tk = -1;
+  for (int nk = 1; nk <= 4; ++nk) {
+    const int TK = (c->neta + nk - 1) / nk;
+    if (TK == last_tk || TK < 1) continue;
+    last_tk = TK;
+    const int maxTJ = std::min(c->ny, maxthr / (TK + 1) - 1);
+    if (maxTJ < 1) continue;
+    for (int TJ = maxTJ; TJ >= std::max(1, maxTJ / 3); --TJ) {
+      TileGeom g = tile_geometry_of(c, sms, TJ, TK, 0);
+      if (g.smem > smem_max) continue;
+      const long long slots = (long long)sms * CLV_TILE_MIN_BLOCKS;
+      const long long waves = ((long long)g.blocks + slots - 1) / slots;
+      const double cost = (double)waves * (g.t.CX + 4) * (double)((TJ + 4) * (TK + 4));
+      v.push_back({cost, g});
+    }
+  }
+  std::stable_sort(v.begin(), v.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+  std::vector<TileGeom> out;
+  for (auto& x : v) out.push_back(x.second);
+  return out;
 }
 
 size_t layout(const clv_config* c, clv_handle* h) {
@@ -739,14 +805,11 @@ clv_status clv_mlp_samples(clv_handle* h, float* d_X, float* d_Y, int64_t* d_cou
 }  // extern "C"
 
 __global__ void __launch_bounds__(kBlock) mlp_forward_kernel(const void* mlp, const float* X, long long n, float* Y) {
-  __shared__ __align__(16) __nv_bfloat16 s_w[kMlpBf16Elems];
+  __shared__ __align__(16) __nv_bfloat16 s_w[kMlpSmemW];
   __shared__ float s_b[kMlpBiasElems];
-  __shared__ __align__(16) __nv_bfloat16 s_x[kBlock / 32][32][16];
+  __shared__ __align__(16) __nv_bfloat16 s_x[kBlock / 32][32][kMlpSX];
   __shared__ float s_y[kBlock / 32][32][4];
-  const __nv_bfloat16* gw = reinterpret_cast<const __nv_bfloat16*>(mlp);
-  const float* gb = reinterpret_cast<const float*>(gw + kMlpBf16Elems);
-  for (int i = threadIdx.x; i < kMlpBf16Elems; i += blockDim.x) s_w[i] = gw[i];
-  for (int i = threadIdx.x; i < kMlpBiasElems; i += blockDim.x) s_b[i] = gb[i];
+  mlp_load_smem(mlp, s_w, s_b);
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int k = 0; k < 16; k += 2) {
@@ -755,8 +818,8 @@ __global__ void __launch_bounds__(kBlock) mlp_forward_kernel(const void* mlp, co
     *reinterpret_cast<unsigned*>(&s_x[wid][lane][k]) = pack_bf16(lo, hi);
   }
   __syncthreads();
-  mlp_tile16(&s_x[wid][0][0], s_w, s_w + kMlpW1e, s_w + kMlpW1e + kMlpW2e, s_b, &s_y[wid][0][0], lane);
-  mlp_tile16(&s_x[wid][16][0], s_w, s_w + kMlpW1e, s_w + kMlpW1e + kMlpW2e, s_b, &s_y[wid][16][0], lane);
+  mlp_tile16(&s_x[wid][0][0], s_w, s_b, &s_y[wid][0][0], lane);
+  mlp_tile16(&s_x[wid][16][0], s_w, s_b, &s_y[wid][16][0], lane);
   __syncwarp();
   if (c < n)
     for (int o = 0; o < kMlpOut; ++o) Y[c * kMlpOut + o] = s_y[wid][lane][o];
@@ -819,6 +882,118 @@ clv_status clv_mlp_train(float* d_params, float* d_work, const float* d_X, const
   }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CLV_OK : fail(nullptr, CLV_ECUDA, cudaGetErrorString(e));
+}
+
+}  // extern "C"
+
+static void tile_info(const clv_handle* h, double ms, clv_tile_info* out) {
+  out->TJ = h->tile.TJ;
+  out->TK = h->tile.TK;
+  out->CX = h->tile.CX;
+  out->threads = h->tile_threads;
+  out->blocks = (int)h->tile_blocks;
+  out->smem_bytes = (int)h->tile_smem;
+  out->ms = ms;
+}
+
+static cudaError_t apply_tile(clv_handle* h, const TileGeom& g) {
+  cudaError_t e = h->rsize == 8 ? tile_attributes<double, false>(g.smem) : tile_attributes<float, false>(g.smem);
+  if (e == cudaSuccess && h->viscous)
+    e = h->rsize == 8 ? tile_attributes<double, true>(g.smem) : tile_attributes<float, true>(g.smem);
+  if (e != cudaSuccess) return e;
+  h->tile = g.t;
+  h->tile_threads = g.threads;
+  h->tile_blocks = g.blocks;
+  h->tile_smem = g.smem;
+  return cudaSuccess;
+}
+
+// Mean time of `reps` stage-1 tile launches on the current state (stage 1
+// reads the state and writes only the stage buffers, so repeating it leaves
+// the evolution unchanged).
+template <typename R, bool VISC>
+static cudaError_t time_stage1(clv_handle* h, int reps, cudaEvent_t e0, cudaEvent_t e1, double* ms) {
+  const StageParams<R> p = stage_params<R>(h, 1, h->tau, h->tau + h->cfg.dtau);
+  stage_tile_kernel<R, 1, VISC><<<h->tile_blocks, h->tile_threads, h->tile_smem, h->stream>>>(p, h->tile);
+  cudaEventRecord(e0, h->stream);
+  for (int r = 0; r < reps; ++r)
+    stage_tile_kernel<R, 1, VISC><<<h->tile_blocks, h->tile_threads, h->tile_smem, h->stream>>>(p, h->tile);
+  cudaEventRecord(e1, h->stream);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  *ms = (double)t / reps;
+  return e;
+}
+
+static int device_sms(size_t* smem_optin) {
+  int sms = 148, dev = 0, sm = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  if (smem_optin) *smem_optin = (size_t)sm;
+  return sms;
+}
+
+extern "C" {
+
+clv_status clv_get_tile(clv_handle* h, clv_tile_info* out) {
+  if (!h || !out) return CLV_EINVAL;
+  tile_info(h, 0.0, out);
+  return CLV_OK;
+}
+
+clv_status clv_set_tile(clv_handle* h, int TJ, int TK, int CX) {
+  if (!h) return CLV_EINVAL;
+  const clv_config& c = h->cfg;
+  if (TJ < 1 || TJ > c.ny || TK < 1 || TK > c.neta || CX < 0 || CX > c.nx)
+    return fail(h, CLV_EINVAL, "tile shape out of range");
+  if ((TJ + 1) * (TK + 1) > tile_max_threads(&c)) return fail(h, CLV_EINVAL, "tile needs too many threads");
+  size_t smem_max = 0;
+  const int sms = device_sms(&smem_max);
+  const TileGeom g = tile_geometry_of(&c, sms, TJ, TK, CX);
+  if (g.smem > smem_max) return fail(h, CLV_EINVAL, "tile needs more shared memory than a block may have");
+  CLV_CUDA(h, apply_tile(h, g));
+  return CLV_OK;
+}
+
+clv_status clv_autotune(clv_handle* h, int max_candidates, int reps, clv_tile_info* best) {
+  if (!h || max_candidates < 1 || reps < 1) return CLV_EINVAL;
+  if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
+  if (h->cfg.kernel != 0) return fail(h, CLV_EINVAL, "the autotuner tunes the tiled stage kernel");
+  size_t smem_max = 0;
+  const int sms = device_sms(&smem_max);
+  std::vector<TileGeom> cand = tile_candidates(&h->cfg, sms, smem_max);
+  if ((int)cand.size() > max_candidates) cand.resize(max_candidates);
+  // the current shape competes too
+  TileGeom cur;
+  cur.t = h->tile; cur.threads = h->tile_threads; cur.blocks = h->tile_blocks; cur.smem = h->tile_smem;
+  cand.insert(cand.begin(), cur);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CLV_CUDA(h, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(h, CLV_ECUDA, "cudaEventCreate"); }
+  double best_ms = 1e300;
+  size_t best_i = 0;
+  cudaError_t err = cudaSuccess;
+  for (size_t i = 0; i < cand.size() && err == cudaSuccess; ++i) {
+    err = apply_tile(h, cand[i]);
+    double ms = 0.0;
+    if (err == cudaSuccess) {
+      if (h->rsize == 8)
+        err = h->viscous ? time_stage1<double, true>(h, reps, e0, e1, &ms) : time_stage1<double, false>(h, reps, e0, e1, &ms);
+      else
+        err = h->viscous ? time_stage1<float, true>(h, reps, e0, e1, &ms) : time_stage1<float, false>(h, reps, e0, e1, &ms);
+    }
+    if (err == cudaSuccess && ms < best_ms) { best_ms = ms; best_i = i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(h, CLV_ECUDA, std::string("autotune: ") + cudaGetErrorString(err));
+  CLV_CUDA(h, apply_tile(h, cand[best_i]));
+  if (best) tile_info(h, best_ms, best);
+  return CLV_OK;
 }
 
 clv_status clv_enable_kernel_timing(clv_handle* h, int enable) {

@@ -230,8 +230,20 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
-template <typename R> __device__ __forceinline__ R minmod(R a, R b) {
-  return (a > R(0) && b > R(0)) ? fmin(a, b) : ((a < R(0) && b < R(0)) ? fmax(a, b) : R(0));
+// minmod(a, b): 0 unless a and b share a sign, else the one of smaller
+// magnitude.  Branch-free: with s the sign bit of a, min(|a|, s*b) is the
+// smaller magnitude when the signs agree and negative when they differ;
+// clamp at 0 and give it the sign of a.
+__device__ __forceinline__ float minmod(float a, float b) {
+  const unsigned sa = __float_as_uint(a) & 0x80000000u;
+  const float t = fmaxf(fminf(fabsf(a), __uint_as_float(__float_as_uint(b) ^ sa)), 0.0f);
+  return __uint_as_float(__float_as_uint(t) | sa);
+}
+__device__ __forceinline__ double minmod(double a, double b) {
+  const unsigned long long sa = (unsigned long long)__double_as_longlong(a) & 0x8000000000000000ull;
+  const double t =
+      fmax(fmin(fabs(a), __longlong_as_double((long long)((unsigned long long)__double_as_longlong(b) ^ sa))), 0.0);
+  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(t) | sa));
 }
 
 }  // namespace clv

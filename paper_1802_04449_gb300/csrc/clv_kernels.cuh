@@ -472,14 +472,11 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
   R vg = R(-1);
   if constexpr (GUESS == kGuessMlp && sizeof(R) == 4) {
     // learned guess: features -> BF16 tensor-core MLP, 32 cells per warp
-    __shared__ __align__(16) __nv_bfloat16 s_w[kMlpBf16Elems];
+    __shared__ __align__(16) __nv_bfloat16 s_w[kMlpSmemW];
     __shared__ float s_b[kMlpBiasElems];
-    __shared__ __align__(16) __nv_bfloat16 s_x[kBlock / 32][32][16];
+    __shared__ __align__(16) __nv_bfloat16 s_x[kBlock / 32][32][kMlpSX];
     __shared__ float s_y[kBlock / 32][32][4];
-    const __nv_bfloat16* gw = reinterpret_cast<const __nv_bfloat16*>(p.mlp);
-    const float* gb = reinterpret_cast<const float*>(gw + kMlpBf16Elems);
-    for (int i = threadIdx.x; i < kMlpBf16Elems; i += blockDim.x) s_w[i] = gw[i];
-    for (int i = threadIdx.x; i < kMlpBiasElems; i += blockDim.x) s_b[i] = gb[i];
+    mlp_load_smem(p.mlp, s_w, s_b);
     float x[kMlpIn];
     R pij[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
     if constexpr (VISC) {
@@ -493,8 +490,8 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
     for (int k = 0; k < 16; k += 2)
       *reinterpret_cast<unsigned*>(&s_x[wid][lane][k]) = pack_bf16(k < kMlpIn ? x[k] : 0.f, k + 1 < kMlpIn ? x[k + 1] : 0.f);
     __syncthreads();
-    mlp_tile16(&s_x[wid][0][0], s_w, s_w + kMlpW1e, s_w + kMlpW1e + kMlpW2e, s_b, &s_y[wid][0][0], lane);
-    mlp_tile16(&s_x[wid][16][0], s_w, s_w + kMlpW1e, s_w + kMlpW1e + kMlpW2e, s_b, &s_y[wid][16][0], lane);
+    mlp_tile16(&s_x[wid][0][0], s_w, s_b, &s_y[wid][0][0], lane);
+    mlp_tile16(&s_x[wid][16][0], s_w, s_b, &s_y[wid][16][0], lane);
     __syncwarp();
     const float vx = s_y[wid][lane][1], vy = s_y[wid][lane][2], ve = s_y[wid][lane][3];
     vg = R(sqrtf(vx * vx + vy * vy + ve * ve));

@@ -30,6 +30,27 @@ constexpr int kMlpBf16Elems = kMlpW1e + kMlpW2e + kMlpW3e;      // 5632
 constexpr int kMlpBiasElems = 64 + 64 + 8;                       // 136
 constexpr size_t kMlpDeviceBytes = kMlpBf16Elems * 2 + kMlpBiasElems * 4;
 
+// Shared-memory copy: rows padded by 8 BF16 (16 bytes) so that the eight rows
+// a fragment load touches fall in distinct banks.
+constexpr int kMlpS1 = 16 + 8, kMlpS2 = 64 + 8, kMlpSX = 16 + 8;   // row strides (BF16)
+constexpr int kMlpSW1 = 64 * kMlpS1, kMlpSW2 = 64 * kMlpS2, kMlpSW3 = 8 * kMlpS2;
+constexpr int kMlpSmemW = kMlpSW1 + kMlpSW2 + kMlpSW3;             // BF16 elements
+
+// Cooperative copy of the network from global (compact) to shared (padded).
+__device__ __forceinline__ void mlp_load_smem(const void* mlp, __nv_bfloat16* s_w, float* s_b) {
+  const unsigned* gw = reinterpret_cast<const unsigned*>(mlp);   // BF16 pairs
+  const float* gb = reinterpret_cast<const float*>(reinterpret_cast<const __nv_bfloat16*>(mlp) + kMlpBf16Elems);
+  unsigned* sw = reinterpret_cast<unsigned*>(s_w);
+  for (int i = threadIdx.x; i < kMlpBf16Elems / 2; i += blockDim.x) {
+    int d;
+    if (i < kMlpW1e / 2) d = (i >> 3) * (kMlpS1 / 2) + (i & 7);
+    else if (i < (kMlpW1e + kMlpW2e) / 2) { const int j = i - kMlpW1e / 2; d = kMlpSW1 / 2 + (j >> 5) * (kMlpS2 / 2) + (j & 31); }
+    else { const int j = i - (kMlpW1e + kMlpW2e) / 2; d = (kMlpSW1 + kMlpSW2) / 2 + (j >> 5) * (kMlpS2 / 2) + (j & 31); }
+    sw[d] = gw[i];
+  }
+  for (int i = threadIdx.x; i < kMlpBiasElems; i += blockDim.x) s_b[i] = gb[i];
+}
+
 // silu(z) = z sigmoid(z) = z (1 + tanh(z / 2)) / 2: one hardware tanh
 // (tanh.approx.f32, max relative error ~2^-11) instead of an exponential and
 // a reciprocal.
@@ -68,30 +89,30 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-// Forward pass of 16 cells (rows of xs, bf16 [16][16] in shared memory) on
-// one warp; writes the 4 outputs of each row to ys ([16][4] floats).
-// w1: [64][16], w2: [64][64], w3: [8][64] bf16; bias: b1[64] b2[64] b3[8].
-__device__ __forceinline__ void mlp_tile16(const __nv_bfloat16* xs, const __nv_bfloat16* w1,
-                                           const __nv_bfloat16* w2, const __nv_bfloat16* w3,
-                                           const float* bias, float* ys, int lane) {
+// Forward pass of 16 cells (rows of xs, bf16 [16][kMlpSX] in shared memory)
+// on one warp; writes the 4 outputs of each row to ys ([16][4] floats).
+// s_w: the padded shared copy (mlp_load_smem); bias: b1[64] b2[64] b3[8].
+__device__ __forceinline__ void mlp_tile16(const __nv_bfloat16* xs, const __nv_bfloat16* s_w, const float* bias,
+                                           float* ys, int lane) {
   const int g = lane >> 2, t = lane & 3;
-  const unsigned* X = reinterpret_cast<const unsigned*>(xs);   // 8 words per row
-  const unsigned a0 = X[g * 8 + t], a1 = X[(g + 8) * 8 + t], a2 = X[g * 8 + 4 + t], a3 = X[(g + 8) * 8 + 4 + t];
+  constexpr int XW = kMlpSX / 2, W1W = kMlpS1 / 2, W2W = kMlpS2 / 2;   // row strides in 32-bit words
+  const unsigned* X = reinterpret_cast<const unsigned*>(xs);
+  const unsigned a0 = X[g * XW + t], a1 = X[(g + 8) * XW + t], a2 = X[g * XW + 4 + t], a3 = X[(g + 8) * XW + 4 + t];
   // layer 1: 16x16 . 16x64
   float h[8][4];
-  const unsigned* W1 = reinterpret_cast<const unsigned*>(w1);  // 8 words per output row
+  const unsigned* W1 = reinterpret_cast<const unsigned*>(s_w);
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
     const int n = nt * 8 + g;
     const float bl = bias[nt * 8 + 2 * t], bh = bias[nt * 8 + 2 * t + 1];
     h[nt][0] = bl; h[nt][1] = bh; h[nt][2] = bl; h[nt][3] = bh;
-    mma_bf16(h[nt], a0, a1, a2, a3, W1[n * 8 + t], W1[n * 8 + 4 + t]);
+    mma_bf16(h[nt], a0, a1, a2, a3, W1[n * W1W + t], W1[n * W1W + 4 + t]);
 #pragma unroll
     for (int r = 0; r < 4; ++r) h[nt][r] = silu(h[nt][r]);
   }
   // layer 2: 16x64 . 64x64 (accumulators of two n-tiles form one k-tile of A)
   float h2[8][4];
-  const unsigned* W2 = reinterpret_cast<const unsigned*>(w2);  // 32 words per output row
+  const unsigned* W2 = reinterpret_cast<const unsigned*>(s_w + kMlpSW1);
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
     const float bl = bias[64 + nt * 8 + 2 * t], bh = bias[64 + nt * 8 + 2 * t + 1];
@@ -104,7 +125,7 @@ __device__ __forceinline__ void mlp_tile16(const __nv_bfloat16* xs, const __nv_b
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
       const int n = nt * 8 + g;
-      mma_bf16(h2[nt], b0, b1, b2, b3, W2[n * 32 + kk * 8 + t], W2[n * 32 + kk * 8 + 4 + t]);
+      mma_bf16(h2[nt], b0, b1, b2, b3, W2[n * W2W + kk * 8 + t], W2[n * W2W + kk * 8 + 4 + t]);
     }
   }
 #pragma unroll
@@ -117,13 +138,13 @@ __device__ __forceinline__ void mlp_tile16(const __nv_bfloat16* xs, const __nv_b
     const float bl = bias[128 + 2 * t], bh = bias[128 + 2 * t + 1];
     y[0] = bl; y[1] = bh; y[2] = bl; y[3] = bh;
   }
-  const unsigned* W3 = reinterpret_cast<const unsigned*>(w3);
+  const unsigned* W3 = reinterpret_cast<const unsigned*>(s_w + kMlpSW1 + kMlpSW2);
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
     const unsigned b0 = pack_bf16(h2[2 * kk][0], h2[2 * kk][1]), b1 = pack_bf16(h2[2 * kk][2], h2[2 * kk][3]);
     const unsigned b2 = pack_bf16(h2[2 * kk + 1][0], h2[2 * kk + 1][1]),
                    b3 = pack_bf16(h2[2 * kk + 1][2], h2[2 * kk + 1][3]);
-    mma_bf16(y, b0, b1, b2, b3, W3[g * 32 + kk * 8 + t], W3[g * 32 + kk * 8 + 4 + t]);
+    mma_bf16(y, b0, b1, b2, b3, W3[g * W2W + kk * 8 + t], W3[g * W2W + kk * 8 + 4 + t]);
   }
   if (t < 2) {
     ys[g * 4 + 2 * t] = y[0];

@@ -3,7 +3,9 @@
 // A CTA owns a (y, eta_s) tile of TJ x TK cells and marches along x over a
 // chunk of CX planes.  Per plane:
 //   1. the tile plus a two-cell halo in y and eta_s is staged once in shared
-//      memory as the per-cell reconstruction fields (T~, pi~, u~^tau, v, P, c_s);
+//      memory as the per-cell reconstruction fields (T~, pi~, u~^tau, v, P, c_s),
+//      by cp.async one plane ahead, together with the per-cell inputs of the
+//      cell that plane's iteration outputs;
 //   2. every y- and eta_s-interface flux of the tile is computed once: the
 //      block has (TJ+1) x (TK+1) threads, thread (a, b) computes the
 //      y-interface below row a of column b and the eta_s-interface left of
@@ -35,25 +37,42 @@ struct TileArgs {
   int ntj, ntk;       // tiles per plane
 };
 
-// shared memory of one CTA, in elements of the working type
-template <bool VISC> inline size_t tile_smem_elems(int TJ, int TK) {
+// Per-cell inputs of the output cell that are not staged with the planes
+// (eps, u~^{n-1}; in stage 2 also u~^n, T~^n, pi~^n), prefetched one plane
+// ahead into a per-thread double buffer.
+template <int STAGE, bool VISC> struct CellIn {
+  static constexpr int E = 0;
+  static constexpr int UP = 1;                       // u~^{n-1} (VISC)
+  static constexpr int UN = VISC ? 4 : 1;            // u~^n (stage 2)
+  static constexpr int TN = UN + 3;                  // T~^n (stage 2)
+  static constexpr int PIN = TN + 4;                 // pi~^n (stage 2, VISC)
+  static constexpr int n = STAGE == 1 ? (VISC ? 4 : 1) : (VISC ? PIN + 10 : TN + 4);
+};
+
+// shared memory of one CTA, in bytes (sized for stage 2, which prefetches the
+// most per-cell inputs): two plane buffers, the y/eta interface fluxes, the
+// pending y/eta flux differences, the per-cell prefetch and the halo offsets
+template <bool VISC> inline size_t tile_smem_bytes(int TJ, int TK, size_t rsize) {
   using L = Box<VISC>;
   const size_t NB = (size_t)(TJ + 4) * (TK + 4);
-  return 2 * L::NF * NB + (size_t)L::NQ * ((TJ + 1) * TK + TJ * (TK + 1)) + 2 * (size_t)L::NPEND * TJ * TK;
+  const size_t ncell = (size_t)TJ * TK;
+  const size_t elems = 2 * L::NF * NB + (size_t)L::NQ * ((TJ + 1) * TK + TJ * (TK + 1)) + 2 * (size_t)L::NPEND * ncell +
+                       2 * (size_t)CellIn<2, VISC>::n * ncell;
+  return elems * rsize + NB * sizeof(int);
 }
 
-// Issue the asynchronous copies of plane ip of the tile (with its y/eta halo)
-// into a box buffer: T~, pi~, P, c_s to their slots, u~ into the v slots (the
-// conversion pass turns them into u~^tau and v once the copies land).
+// Issue the asynchronous copies of the plane at offset poff (= plane index x
+// ny x ne) of the tile (with its y/eta halo) into a box buffer: T~, pi~, P,
+// c_s to their slots, u~ into the v slots (the conversion pass turns them into
+// u~^tau and v once the copies land).  goff[q]: in-plane offset of box cell q
+// (boundary wrap or clamp already applied).  Thread tid handles the box
+// cells q = tid, tid + nthr, ...; the caller commits the group.
 template <typename R, bool VISC>
-__device__ __forceinline__ void stage_plane_async(const StageParams<R>& p, R* box, int NB, int BW, int ip,
-                                                  int j0, int k0, int tid, int nthr) {
+__device__ __forceinline__ void stage_plane_async(const StageParams<R>& p, R* box, int NB, long long poff,
+                                                  const int* goff, int tid, int nthr) {
   using L = Box<VISC>;
   for (int q = tid; q < NB; q += nthr) {
-    const int bj = q / BW, bk = q - bj * BW;
-    const int gj = wrap_index(j0 + bj - 2, p.ny, p.periodic);
-    const int gk = wrap_index(k0 + bk - 2, p.ne, p.periodic);
-    const long long g = ((long long)ip * p.ny + gj) * p.ne + gk;
+    const long long g = poff + goff[q];
 #pragma unroll
     for (int m = 0; m < 4; ++m) cp_async_elem(box + m * NB + q, p.T[m] + g);
     if constexpr (VISC) {
@@ -65,7 +84,27 @@ __device__ __forceinline__ void stage_plane_async(const StageParams<R>& p, R* bo
     cp_async_elem(box + L::P * NB + q, p.pr.P + g);
     cp_async_elem(box + L::CS * NB + q, p.pr.cs + g);
   }
-  cp_async_commit();
+}
+
+// Prefetch of the per-cell inputs of global cell gc into slot cb (stride ncell).
+template <typename R, int STAGE, bool VISC>
+__device__ __forceinline__ void prefetch_cell(const StageParams<R>& p, R* cb, int ncell, long long gc) {
+  using C = CellIn<STAGE, VISC>;
+  cp_async_elem(cb + C::E * ncell, p.pr.e + gc);
+  if constexpr (VISC) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) cp_async_elem(cb + (C::UP + m) * ncell, p.up[m] + gc);
+  }
+  if constexpr (STAGE == 2) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) cp_async_elem(cb + (C::UN + m) * ncell, p.un[m] + gc);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) cp_async_elem(cb + (C::TN + m) * ncell, p.Tn[m] + gc);
+    if constexpr (VISC) {
+#pragma unroll
+      for (int r = 0; r < 10; ++r) cp_async_elem(cb + (C::PIN + r) * ncell, p.pin[r] + gc);
+    }
+  }
 }
 
 // component q of the reconstruction vector along axis a from staged fields
@@ -118,6 +157,9 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
   R* Hy = boxbuf + 2 * NF * NB;  // [NQ][TJ+1][TK]
   R* Hk = Hy + NQ * NHY;       // [NQ][TJ][TK+1]
   R* pend = Hk + NQ * NHK;     // [2][NPEND][ncell]
+  using CI = CellIn<STAGE, VISC>;
+  R* cellbuf = pend + 2 * NPEND * ncell;             // [2][CI::n][ncell]
+  int* goff = reinterpret_cast<int*>(cellbuf + 2 * CellIn<2, VISC>::n * ncell);  // [NB]
 
   const int tid = threadIdx.x;
   const int nthr = (t.TJ + 1) * (t.TK + 1);
@@ -151,14 +193,22 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
   for (int m = 0; m < 4; ++m) ucm1[m] = R(0);
 
 
-  stage_plane_async<R, VISC>(p, boxbuf + ((x0 - 2) & 1) * NF * NB, NB, BW, wrap_index(x0 - 2, p.nx, p.periodic),
-                             j0, k0, tid, nthr);
+  // in-plane offsets of this thread's box cells (only this thread uses them)
+  for (int q = tid; q < NB; q += nthr) {
+    const int bj = q / BW, bk = q - bj * BW;
+    goff[q] = wrap_index(j0 + bj - 2, p.ny, p.periodic) * p.ne + wrap_index(k0 + bk - 2, p.ne, p.periodic);
+  }
+  const long long plane = (long long)p.ny * p.ne;
+  stage_plane_async<R, VISC>(p, boxbuf + ((x0 - 2) & 1) * NF * NB, NB, wrap_index(x0 - 2, p.nx, p.periodic) * plane,
+                             goff, tid, nthr);
+  cp_async_commit();
   for (int pl = x0 - 2; pl <= x1 + 1; ++pl) {
     const bool out_plane = pl >= x0 && pl < x1;
     R* box = boxbuf + (pl & 1) * NF * NB;
-    // ---- 1. plane pl has landed: u~ -> (u~^tau, v) in place
+    // ---- 1. this thread's copies of plane pl (and of the per-cell inputs of
+    // the output cell) have landed: its u~ -> (u~^tau, v) in place, then one
+    // barrier makes the whole plane visible
     cp_async_wait_all();
-    __syncthreads();
     for (int q = tid; q < NB; q += nthr) {
       const R ux = box[L::V * NB + q], uy = box[(L::V + 1) * NB + q], ue = box[(L::V + 2) * NB + q];
       const R ut = sqrt(R(1) + ux * ux + uy * uy + ue * ue);
@@ -169,10 +219,16 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
       box[(L::V + 2) * NB + q] = ue * iu;
     }
     __syncthreads();
-    // prefetch the next plane into the other buffer while this one is used
-    if (pl + 1 <= x1 + 1)
-      stage_plane_async<R, VISC>(p, boxbuf + ((pl + 1) & 1) * NF * NB, NB, BW, wrap_index(pl + 1, p.nx, p.periodic),
-                                 j0, k0, tid, nthr);
+    // prefetch the next plane into the other buffer while this one is used,
+    // with the per-cell inputs of the cell output two planes on (pl - 1)
+    if (pl + 1 <= x1 + 1) {
+      stage_plane_async<R, VISC>(p, boxbuf + ((pl + 1) & 1) * NF * NB, NB,
+                                 wrap_index(pl + 1, p.nx, p.periodic) * plane, goff, tid, nthr);
+      if (active && pl - 1 >= x0 && pl - 1 < x1)
+        prefetch_cell<R, STAGE, VISC>(p, cellbuf + (size_t)((pl - 1) & 1) * CI::n * ncell + cid, ncell,
+                                      ((long long)(pl - 1) * p.ny + j) * p.ne + k);
+      cp_async_commit();
+    }
     // ---- 2. every y- and eta-interface of an output plane, once
     if (out_plane) {
       R H[NQ];
@@ -215,10 +271,11 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
             const int c = pl - 2;
             const long long gc = ((long long)c * p.ny + j) * p.ne + k;
             const R* pd = pend + (size_t)(c & 1) * NPEND * ncell;
+            const R* cb = cellbuf + (size_t)(c & 1) * CI::n * ncell + cid;
             R S[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) S[q] = pd[q * ncell + cid] - (H[q] - Hprev[q]) * inv_dx;
-            const R e = p.pr.e[gc];
+            const R e = cb[CI::E * ncell];
             const R Pc = W0[L::P];
             R u[4];
             u[0] = W0[L::UT];
@@ -236,14 +293,14 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
 #pragma unroll
               for (int b2 = 0; b2 < 4; ++b2) un[b2] = u[b2];
             } else {
-              un[1] = p.un[0][gc]; un[2] = p.un[1][gc]; un[3] = p.un[2][gc];
+              un[1] = cb[CI::UN * ncell]; un[2] = cb[(CI::UN + 1) * ncell]; un[3] = cb[(CI::UN + 2) * ncell];
               un[0] = sqrt(R(1) + un[1] * un[1] + un[2] * un[2] + un[3] * un[3]);
             }
             R ustar0 = un[0];
             if constexpr (VISC) {
-              const R us1 = R(2) * un[1] - p.up[0][gc];
-              const R us2 = R(2) * un[2] - p.up[1][gc];
-              const R us3 = R(2) * un[3] - p.up[2][gc];
+              const R us1 = R(2) * un[1] - cb[CI::UP * ncell];
+              const R us2 = R(2) * un[2] - cb[(CI::UP + 1) * ncell];
+              const R us3 = R(2) * un[3] - cb[(CI::UP + 2) * ncell];
               ustar0 = sqrt(R(1) + us1 * us1 + us2 * us2 + us3 * us3);
               R ul[4];
               if constexpr (STAGE == 1) {
@@ -291,12 +348,12 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
               }
             } else {
 #pragma unroll
-              for (int m = 0; m < 4; ++m) Tnew[m] = R(0.5) * (p.Tn[m][gc] + W0[m] + hh * S[m]);
+              for (int m = 0; m < 4; ++m) Tnew[m] = R(0.5) * (cb[(CI::TN + m) * ncell] + W0[m] + hh * S[m]);
               if constexpr (VISC) {
                 const R inv = R(0.5) / u[0];
 #pragma unroll
                 for (int r = 0; r < 10; ++r)
-                  pinew[r] = (un[0] * p.pin[r][gc] + ustar0 * W0[4 + r] + hh * S[4 + r]) * inv;
+                  pinew[r] = (un[0] * cb[(CI::PIN + r) * ncell] + ustar0 * W0[4 + r] + hh * S[4 + r]) * inv;
                 regulate_shear<R>(e, Pc, pinew);
               }
             }

@@ -3,10 +3,11 @@ ABI, for capture under a profiler (the kernels of interest are the last
 launches).  Usage:
 
     python -m paper_1802_04449_gb300.profile_case [--precision fp32|fp64]
-        [--guess previous|cold|learned] [--skip S] [--steps K]
+        [--guess previous|cold|learned] [--skip S] [--steps K] [--no-autotune]
 
---skip S steps run first (reaching the later, more dilute state), then K
-steps.  --guess learned trains the network briefly (FP64 states of another
+The tile shape is autotuned first (as bench.py does; its timing launches
+come first), --skip S steps run next (reaching the later, more dilute
+state), then K steps.  --guess learned trains the network briefly (FP64 states of another
 seed of the same workload) before the run.
 """
 from __future__ import annotations
@@ -26,6 +27,7 @@ def main(argv=None):
     ap.add_argument("--guess", default="previous", choices=["previous", "cold", "learned"])
     ap.add_argument("--skip", type=int, default=0)
     ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     a = ap.parse_args(argv)
 
     import torch
@@ -50,6 +52,8 @@ def main(argv=None):
         g.set_mlp(params)
     g.set_guess({"previous": clv.CLV_GUESS_PREVIOUS, "cold": clv.CLV_GUESS_COLD,
                  "learned": clv.CLV_GUESS_MLP}[a.guess])
+    if a.autotune:
+        print("tile:", g.autotune(max_candidates=12, reps=3))
     if a.skip:
         g.step(a.skip)
     st = g.step(a.steps, stats=True)

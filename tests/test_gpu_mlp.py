@@ -131,22 +131,29 @@ def test_samples_are_the_solver_states():
         np.testing.assert_allclose(Y[:, 1 + k], (f[nm] / ut)[keep], rtol=1e-6, atol=1e-7)
 
 
-TRAIN_STEPS, SKIP, RUN = 80, 60, 10
+TRAIN_STEPS, EVERY, SKIP, RUN = 310, 10, 300, 10
+
+
+def _gain_case(seed):
+    """Half the transverse and longitudinal extent of the 97x97x41 event (same
+    spacings and hot-spot recipe), so that its late, fast-expanding state is
+    reached in a few hundred steps."""
+    return I.hotspot_event(nx=49, ny=49, neta=21, n_spots=500, seed=seed)
 
 
 @pytest.fixture(scope="module")
 def trained():
     """A network trained on the FP64 solver's states of two seeded events,
-    dumped every 5 steps over the first TRAIN_STEPS steps."""
+    dumped every EVERY steps over the first TRAIN_STEPS steps."""
     torch = _torch()
     buf = None
     for seed in (21, 22):
-        case = _case(seed)
+        case = _gain_case(seed)
         h = clv.from_case(case, clv.CLV_FP64)
         h.set_initial(case.eps, case.ux, case.uy, case.ueta)
         if buf is None:
-            buf = L.SampleBuffer(torch, h.device, 2 * (TRAIN_STEPS // 5 + 1) * h.N)
-        L.collect_samples(h, TRAIN_STEPS, 5, buf)
+            buf = L.SampleBuffer(torch, h.device, 2 * (TRAIN_STEPS // EVERY + 1) * h.N)
+        L.collect_samples(h, TRAIN_STEPS, EVERY, buf)
     X, Y = buf.data()
     p, losses = L.train(X, Y, iters=2000, batch=8192, lr=3e-3, seed=5)
     torch.cuda.synchronize()
@@ -185,13 +192,13 @@ def _run_mode(case, mode, params):
 
 
 def test_learned_guess_gains_and_keeps_parity(trained):
-    """A seed not trained on, evolved to tau = 1.0 fm (developed transverse
-    flow), then three guesses for the next steps.  Every mode solves to the
-    same tolerance; the learned guess needs fewer Newton iterations than the
-    solver's own cold start (mean and warp maximum), and its evolution
+    """A seed not trained on, evolved to tau = 3.4 fm (fast transverse
+    expansion), then three guesses for the next steps.  Every mode solves to
+    the same tolerance; the learned guess needs fewer Newton iterations than
+    the solver's own cold start (mean and warp maximum), and its evolution
     matches the FP64 oracle within 1e-4 where eps > 1e-3 GeV/fm^3."""
     p, _, _, _ = trained
-    case = _case(31)
+    case = _gain_case(31)
     params = p.cpu().numpy()
     res = {}
     for name, mode in (("previous", clv.CLV_GUESS_PREVIOUS), ("cold", clv.CLV_GUESS_COLD),

@@ -227,3 +227,37 @@ def test_error_paths():
     with pytest.raises(clv.ClvError) as ei:
         g.step(2, stats=True)
     assert ei.value.status == 5
+
+
+def test_tile_shapes_and_autotuner_leave_results_unchanged():
+    """The tile shape is a schedule, not arithmetic: explicit shapes and the
+    autotuner's choice give bit-identical fields to the default shape."""
+    case = small_hotspot(seed=9, nx=23, ny=21, neta=13)
+    names = ["eps", "ux", "uy", "ueta", "pixx", "piee"]
+
+    def run(prec, shape=None, tune=False):
+        g = clv.from_case(case, prec)
+        g.set_initial(case.eps, case.ux, case.uy, case.ueta)
+        if shape is not None:
+            g.set_tile(*shape)
+        if tune:
+            info = g.autotune(max_candidates=6, reps=2)
+            assert info["ms"] > 0 and info["threads"] == (info["TJ"] + 1) * (info["TK"] + 1)
+        g.step(4)
+        return g.get(names), g.tile()
+
+    for prec in (clv.CLV_FP64, clv.CLV_FP32):
+        ref, t0 = run(prec)
+        for shape in ((3, 5, 0), (1, 13, 4), (7, 2, 23), (21, 1, 1)):
+            got, t = run(prec, shape)
+            assert (t["TJ"], t["TK"]) == shape[:2]
+            for k in names:
+                assert np.array_equal(got[k], ref[k]), (prec, shape, k)
+        got, t = run(prec, tune=True)
+        for k in names:
+            assert np.array_equal(got[k], ref[k]), (prec, "autotuned", t, k)
+    g = clv.from_case(case, clv.CLV_FP32)
+    g.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    for bad in ((0, 5, 0), (3, 14, 0), (3, 5, 24), (21, 13, 0)):
+        with pytest.raises(clv.ClvError):
+            g.set_tile(*bad)
