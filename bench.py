@@ -276,7 +276,7 @@ def run_gpu(args):
     achieved = alg / (avg_ms[dom] / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved,
             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": load_traffic(dom),
+            "traffic": load_traffic(dom, st32.get("tile") if dom.startswith("stage") else None),
             "algorithmic_bytes_per_launch": alg,
             "kernel_ms_avg": avg_ms,
             "kernel_share": {k: v / sum(tot_ms.values()) for k, v in tot_ms.items()},
@@ -318,29 +318,34 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def load_traffic(dom):
+def load_traffic(dom, tile):
     """DRAM bytes per launch of kernel slot ``dom`` (read + write) from the
-    committed ncu summary: lines ``traffic <slot> <bytes> <kernel-source-hash>``
-    in profiles/traffic.txt.  Returns None when absent or when the kernel
-    sources changed since the counters were taken."""
+    committed ncu summary: lines ``traffic <slot> <bytes> <kernel-source-hash>
+    <TJxTKxCX>`` in profiles/traffic.txt.  Returns None when absent, when the
+    kernel sources changed since the counters were taken, or (stage slots)
+    when the run used another tile shape."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
     want = kernel_source_hash()
+    shape = f"{tile['TJ']}x{tile['TK']}x{tile['CX']}" if tile else "-"
     with open(p) as f:
         for line in f:
             parts = line.split()
-            if len(parts) == 4 and parts[0] == "traffic" and parts[1] == dom and parts[3] == want:
+            if (len(parts) == 5 and parts[0] == "traffic" and parts[1] == dom and parts[3] == want
+                    and (parts[4] == "-" or parts[4] == shape)):
                 return float(parts[2])
     return None
 
 
 def kernel_source_hash():
+    """Hash of the device-code headers that define the stage and recovery
+    kernels (host-side API changes leave it unchanged)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1802_04449_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
+        if fn.endswith(".cuh"):
             with open(os.path.join(csrc, fn), "rb") as f:
                 h.update(f.read())
     return h.hexdigest()[:16]

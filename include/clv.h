@@ -128,6 +128,18 @@ clv_status clv_set_initial(clv_handle* h, const double* eps, const double* ux, c
 clv_status clv_set_initial_device(clv_handle* h, const double* d_eps, const double* d_ux,
                                   const double* d_uy, const double* d_ueta, const double* d_pi);
 
+/* Initial state from T^{tau mu} with pi = 0 (mini-jet initial flow):
+ * T holds 4 x N doubles, component-major in the cell order of
+ * clv_set_initial: T^{tau tau}, T^{tau x}, T^{tau y} and the orthonormal
+ * tau T^{tau eta} (GeV/fm^3) at tau0.  The primitives are the FP64 root of
+ * the recovery problem of Sec. 3 with E = T^{tau tau}, M = T^{tau i}
+ * (vacuum where the solved eps < eps_cut); the run then starts as from
+ * clv_set_initial with those primitives.  CLV_ENONFINITE for non-finite
+ * input, CLV_EROOT if a solve hit its cap.  Synchronises the stream.
+ * _device: T is a device array. */
+clv_status clv_set_initial_T(clv_handle* h, const double* T);
+clv_status clv_set_initial_T_device(clv_handle* h, const double* d_T);
+
 /* Advance nsteps Heun steps.  If stats is not NULL the call synchronises and
  * fills it; otherwise it only enqueues work and returns.  Returns CLV_EROOT /
  * CLV_ENONFINITE when the device error word is set (checked only when stats
@@ -213,6 +225,18 @@ clv_status clv_mlp_train(float* d_params, float* d_work, const float* d_X, const
                          int iters, int batch, float lr, uint64_t seed, int step0, void* cuda_stream,
                          float* d_loss);
 
+/* ---------------- checkpoint ----------------
+ * The complete evolution state: T~^{tau mu}, pi~^{mu nu} and the primitives
+ * (eps, u~, P, c_s) of the current and the previous step in the working
+ * precision, with tau, the step count and the configuration it belongs to.
+ * Restoring it into a handle of the same configuration continues the run
+ * bit for bit.  Buffers are host memory of clv_state_bytes bytes, owned by
+ * the caller; both calls synchronise the stream.  clv_set_state returns
+ * CLV_EINVAL for a buffer of another configuration and resets the counters. */
+clv_status clv_state_bytes(const clv_handle* h, size_t* bytes);
+clv_status clv_get_state(clv_handle* h, void* buf, size_t bytes);
+clv_status clv_set_state(clv_handle* h, const void* buf, size_t bytes);
+
 /* ---------------- tile shape of the stage kernel ----------------
  * The stage kernel works on (y, eta_s) tiles of TJ x TK cells, each CTA
  * marching along x over CX planes ((TJ + 1)(TK + 1) threads per CTA).  The
@@ -233,8 +257,9 @@ clv_status clv_set_tile(clv_handle* h, int TJ, int TK, int CX);
 
 /* Autotuner: times the current shape and up to max_candidates modelled-best
  * shapes (reps stage-1 launches each, on the current state, which they leave
- * unchanged) on the handle's stream, keeps the fastest and reports it in
- * *best (nullable).  Needs clv_set_initial; synchronises the stream. */
+ * unchanged) on the handle's stream, keeps the fastest (the current shape
+ * unless another is at least 2% faster) and reports it in *best (nullable).
+ * Needs clv_set_initial; synchronises the stream. */
 clv_status clv_autotune(clv_handle* h, int max_candidates, int reps, clv_tile_info* best);
 
 /* Statistics without any allocation.  The paper has no counterpart: this is

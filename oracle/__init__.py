@@ -81,6 +81,7 @@ def _load(plant: int = 0):
             lib.orc_set_threads.argtypes = [ctypes.c_int]
             lib.orc_set_threads.restype = ctypes.c_int
             lib.orc_set_initial.argtypes = [P, D, D, D, D, D]
+            lib.orc_set_initial_T.argtypes = [P, D]
             lib.orc_step.argtypes = [P, ctypes.c_int]
             lib.orc_get.argtypes = [P, ctypes.c_int, D]
             lib.orc_stats.argtypes = [P, D]
@@ -147,6 +148,13 @@ class Oracle:
             pi_arr = np.ascontiguousarray(pi, dtype=np.float64).reshape((10,) + self.shape)
         self._lib.orc_set_initial(self._h, *(_dp(a) for a in arrs),
                                   _dp(pi_arr) if pi_arr is not None else None)
+
+    def set_initial_T(self, T):
+        """Initial state from T^{tau mu} (4 x grid: T^{tau tau}, T^{tau x},
+        T^{tau y}, tau T^{tau eta}) with pi = 0; primitives by the root solve."""
+        a = np.ascontiguousarray(T, dtype=np.float64).reshape((4,) + self.shape)
+        if self._lib.orc_set_initial_T(self._h, _dp(a)) != 0:
+            raise RuntimeError("root solve hit its iteration cap")
 
     def step(self, n=1):
         return self._lib.orc_step(self._h, int(n))

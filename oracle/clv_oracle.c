@@ -695,6 +695,32 @@ int orc_set_initial(orc_t* h, const double* eps, const double* ux, const double*
   return 0;
 }
 
+/* Initial state from T^{tau mu} with pi = 0 (the mini-jet initial flow of
+ * the large-event workload).  T holds 4 x N values T^{tau tau}, T^{tau x},
+ * T^{tau y} and the orthonormal tau T^{tau eta} (all GeV/fm^3).  With pi = 0
+ * these are T_ideal^{tau mu}, and the primitives are the root of the
+ * recovery problem of Sec. 3 (E = T^{tau tau}, M = T^{tau i}); the state then
+ * follows from (eps, u~) as in orc_set_initial.  Returns -1 if a root solve
+ * hit its cap. */
+int orc_set_initial_T(orc_t* h, const double* T) {
+  size_t N = (size_t)h->c.nx * h->c.ny * h->c.neta;
+  double* a = (double*)malloc(4 * N * sizeof(double));
+  if (!a) return -1;
+  int fail = 0;
+  for (size_t l = 0; l < N; ++l) {
+    double e, u[4];
+    int resc;
+    if (prim_solve(h, T[l], T[N + l], T[2 * N + l], T[3 * N + l], &e, u, &resc) < 0) fail = 1;
+    a[l] = e;
+    a[N + l] = u[1];
+    a[2 * N + l] = u[2];
+    a[3 * N + l] = u[3];
+  }
+  int r = fail ? -1 : orc_set_initial(h, a, a + N, a + 2 * N, a + 3 * N, NULL);
+  free(a);
+  return r;
+}
+
 int orc_step(orc_t* h, int n) {
   for (int s = 0; s < n; ++s) heun_step(h, h->viscous);
   compute_stats(h);

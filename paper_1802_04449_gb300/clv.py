@@ -79,7 +79,8 @@ EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initi
             "clv_get_fields_device", "clv_get_time", "clv_enable_kernel_timing", "clv_get_kernel_times",
             "clv_destroy", "clv_last_error", "clv_version", "clv_field_stats_noalloc",
             "clv_set_guess", "clv_set_mlp", "clv_mlp_samples", "clv_mlp_forward", "clv_mlp_loss_grad",
-            "clv_mlp_train", "clv_get_tile", "clv_set_tile", "clv_autotune"]
+            "clv_mlp_train", "clv_get_tile", "clv_set_tile", "clv_autotune", "clv_set_initial_T",
+            "clv_set_initial_T_device", "clv_state_bytes", "clv_get_state", "clv_set_state"]
 CLV_GUESS_PREVIOUS, CLV_GUESS_COLD, CLV_GUESS_MLP = 0, 1, 2
 MLP_NPARAM = 5124
 
@@ -103,6 +104,8 @@ def load(path: str | None = None):
         lib.clv_create_ws.argtypes = [cfgp, V, V, ctypes.c_size_t, ctypes.POINTER(P)]
         lib.clv_set_initial.argtypes = [P, D, D, D, D, D]
         lib.clv_set_initial_device.argtypes = [P, V, V, V, V, V]
+        lib.clv_set_initial_T.argtypes = [P, D]
+        lib.clv_set_initial_T_device.argtypes = [P, V]
         lib.clv_step.argtypes = [P, ctypes.c_int, ctypes.POINTER(clv_stats)]
         lib.clv_get_stats.argtypes = [P, ctypes.POINTER(clv_stats)]
         lib.clv_get_fields.argtypes = [P, ctypes.c_uint32, D]
@@ -119,6 +122,9 @@ def load(path: str | None = None):
         lib.clv_mlp_loss_grad.argtypes = [V, V, V, ctypes.c_int64, V, V, V]
         lib.clv_mlp_train.argtypes = [V, V, V, V, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                       ctypes.c_uint64, ctypes.c_int, V, V]
+        lib.clv_state_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        lib.clv_get_state.argtypes = [P, V, ctypes.c_size_t]
+        lib.clv_set_state.argtypes = [P, V, ctypes.c_size_t]
         TI = ctypes.POINTER(clv_tile_info)
         lib.clv_get_tile.argtypes = [P, TI]
         lib.clv_set_tile.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -223,6 +229,26 @@ class Hydro:
             st = self._lib.clv_set_initial(self._h, *(_dp(a) for a in arrs), _dp(pa) if pa is not None else None)
         self._check(st, self._h)
 
+    def set_initial_T(self, T):
+        """Initial state from T^{tau mu} (4 x grid: T^{tau tau}, T^{tau x},
+        T^{tau y}, tau T^{tau eta}; pi = 0): host array or CUDA tensor."""
+        t = self.torch
+        if isinstance(T, t.Tensor) and T.is_cuda:
+            a = T.to(t.float64).contiguous()
+            self._dev_keep = [a]
+            st = self._lib.clv_set_initial_T_device(self._h, ctypes.c_void_p(a.data_ptr()))
+        else:
+            a = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape((4,) + self.shape))
+            st = self._lib.clv_set_initial_T(self._h, _dp(a))
+        self._check(st, self._h)
+
+    def set_initial_case(self, case):
+        """Initial state of an inputs.HydroCase (T^{tau mu} when it has one)."""
+        if getattr(case, "T0", None) is not None:
+            self.set_initial_T(case.T0)
+        else:
+            self.set_initial(case.eps, case.ux, case.uy, case.ueta)
+
     def step(self, n=1, stats=False):
         s = clv_stats()
         st = self._lib.clv_step(self._h, int(n), ctypes.byref(s) if stats else None)
@@ -239,6 +265,18 @@ class Hydro:
         step = ctypes.c_int64()
         self._lib.clv_get_time(self._h, ctypes.byref(tau), ctypes.byref(step))
         return tau.value, step.value
+
+    def get_state(self):
+        """Checkpoint: the complete evolution state as bytes."""
+        n = ctypes.c_size_t()
+        self._check(self._lib.clv_state_bytes(self._h, ctypes.byref(n)), self._h)
+        buf = ctypes.create_string_buffer(n.value)
+        self._check(self._lib.clv_get_state(self._h, buf, n.value), self._h)
+        return buf.raw
+
+    def set_state(self, state):
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        self._check(self._lib.clv_set_state(self._h, buf, len(state)), self._h)
 
     def tile(self):
         t = clv_tile_info()

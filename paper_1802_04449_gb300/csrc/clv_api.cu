@@ -653,6 +653,65 @@ clv_status clv_create_ws(const clv_config* cfg, void* cuda_stream, void* device_
   return create_common(cfg, cuda_stream, device_ws, ws_bytes, out);
 }
 
+}  // extern "C"
+
+// Primitives of an initial T^{tau mu} with pi = 0 (T_ideal = T): the FP64
+// root solve of Sec. 3 on the handle's EOS table, in place (a[0..3] hold
+// T^{tau tau}, T^{tau x}, T^{tau y}, tau T^{tau eta} on entry and eps, u~^x,
+// u~^y, u~^eta on exit).
+template <typename R>
+__global__ void __launch_bounds__(kBlock) prims_from_T_kernel(double* a0, double* a1, double* a2, double* a3,
+                                                              EosView<R> eos, double eps_cut, long long N,
+                                                              unsigned long long* counters, unsigned* err) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  double e, ux, uy, ue;
+  const double E = a0[c], Mx = a1[c], My = a2[c], Me = a3[c];
+  if (!(isfinite(E) && isfinite(Mx) && isfinite(My) && isfinite(Me))) {
+    atomicOr(err, 2u);
+    e = ux = uy = ue = 0.0;
+  } else {
+    const RootResult rr = solve_primitive<double, R, R>(eos, eps_cut, E, Mx, My, Me, 1e-15, 200, e, ux, uy, ue);
+    if (rr.rescaled) atomicAdd(counters + 0, 1ull);
+    if (rr.iters < 0) { atomicAdd(counters + 1, 1ull); atomicOr(err, 1u); }
+  }
+  a0[c] = e; a1[c] = ux; a2[c] = uy; a3[c] = ue;
+}
+
+extern "C" {
+
+static clv_status set_initial_T_any(clv_handle* h, const double* T, bool host) {
+  if (!h) return CLV_EINVAL;
+  if (!T) return fail(h, CLV_EINVAL, "T is required");
+  const long long N = h->N;
+  // scratch: the stage-2 shear buffers (>= 4 N doubles in either precision),
+  // which the initial state does not use
+  double* a = reinterpret_cast<double*>(h->PI1[0]);
+  CLV_CUDA(h, cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream));
+  for (int m = 0; m < 4; ++m)
+    CLV_CUDA(h, cudaMemcpyAsync(a + (size_t)m * N, T + (size_t)m * N, (size_t)N * 8,
+                                host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->stream));
+  const unsigned g = grid_of(N);
+  if (h->rsize == 8)
+    prims_from_T_kernel<double><<<g, kBlock, 0, h->stream>>>(a, a + N, a + 2 * N, a + 3 * N, eos_view<double>(h),
+                                                             h->cfg.eps_cut, N, h->dstats->counters,
+                                                             &h->dstats->err);
+  else
+    prims_from_T_kernel<float><<<g, kBlock, 0, h->stream>>>(a, a + N, a + 2 * N, a + 3 * N, eos_view<float>(h),
+                                                            h->cfg.eps_cut, N, h->dstats->counters,
+                                                            &h->dstats->err);
+  CLV_CUDA(h, cudaGetLastError());
+  unsigned err = 0;
+  CLV_CUDA(h, cudaMemcpyAsync(&err, &h->dstats->err, 4, cudaMemcpyDeviceToHost, h->stream));
+  CLV_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (err & 2u) return fail(h, CLV_ENONFINITE, "non-finite T^{tau mu} in the initial state");
+  if (err & 1u) return fail(h, CLV_EROOT, "root solve of the initial state hit its iteration cap");
+  const double* in[4] = {a, a + N, a + 2 * N, a + 3 * N};
+  h->cur = 0;
+  h->prev = 1;
+  return h->rsize == 8 ? set_initial_impl<double>(h, in, nullptr, false) : set_initial_impl<float>(h, in, nullptr, false);
+}
+
 static clv_status set_initial_any(clv_handle* h, const double* eps, const double* ux, const double* uy,
                                   const double* ueta, const double* pi, bool host) {
   if (!h) return CLV_EINVAL;
@@ -667,6 +726,10 @@ clv_status clv_set_initial(clv_handle* h, const double* eps, const double* ux, c
                            const double* ueta, const double* pi) {
   return set_initial_any(h, eps, ux, uy, ueta, pi, true);
 }
+
+clv_status clv_set_initial_T(clv_handle* h, const double* T) { return set_initial_T_any(h, T, true); }
+
+clv_status clv_set_initial_T_device(clv_handle* h, const double* d_T) { return set_initial_T_any(h, d_T, false); }
 
 clv_status clv_set_initial_device(clv_handle* h, const double* d_eps, const double* d_ux, const double* d_uy,
                                   const double* d_ueta, const double* d_pi) {
@@ -939,6 +1002,82 @@ static int device_sms(size_t* smem_optin) {
 
 extern "C" {
 
+// ---------------- checkpoint ----------------
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t nx, ny, neta, precision, viscous, pad;
+  double tau, dx, dy, deta, dtau, eta_over_s;
+  int64_t step;
+};
+constexpr uint32_t kStateMagic = 0x53564c43u;  // "CLVS"
+constexpr int kStateFields = 4 + 10 + 2 * kPrimFields;
+
+static size_t state_bytes(const clv_handle* h) {
+  return sizeof(StateHeader) + (size_t)kStateFields * (size_t)h->N * h->rsize;
+}
+
+// device arrays of the state in checkpoint order: T~ (4), pi~ (10), the
+// primitives of the current step (6) and of the previous step (6)
+static void state_arrays(clv_handle* h, void* a[kStateFields]) {
+  int k = 0;
+  for (int m = 0; m < 4; ++m) a[k++] = h->T0[m];
+  for (int q = 0; q < 10; ++q) a[k++] = h->PI0[q];
+  for (int f = 0; f < kPrimFields; ++f) a[k++] = h->PR[h->cur][f];
+  for (int f = 0; f < kPrimFields; ++f) a[k++] = h->PR[h->prev][f];
+}
+
+clv_status clv_state_bytes(const clv_handle* h, size_t* bytes) {
+  if (!h || !bytes) return CLV_EINVAL;
+  *bytes = state_bytes(h);
+  return CLV_OK;
+}
+
+clv_status clv_get_state(clv_handle* h, void* buf, size_t bytes) {
+  if (!h || !buf) return CLV_EINVAL;
+  if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
+  if (bytes < state_bytes(h)) return fail(h, CLV_EINVAL, "state buffer too small (clv_state_bytes)");
+  const clv_config& c = h->cfg;
+  StateHeader hd{kStateMagic, 1u, c.nx, c.ny, c.neta, c.precision, h->viscous ? 1 : 0, 0,
+                 h->tau, c.dx, c.dy, c.deta, c.dtau, c.eta_over_s, h->step};
+  std::memcpy(buf, &hd, sizeof(hd));
+  void* a[kStateFields];
+  state_arrays(h, a);
+  char* dst = static_cast<char*>(buf) + sizeof(hd);
+  const size_t fb = (size_t)h->N * h->rsize;
+  for (int k = 0; k < kStateFields; ++k)
+    CLV_CUDA(h, cudaMemcpyAsync(dst + k * fb, a[k], fb, cudaMemcpyDeviceToHost, h->stream));
+  CLV_CUDA(h, cudaStreamSynchronize(h->stream));
+  return CLV_OK;
+}
+
+clv_status clv_set_state(clv_handle* h, const void* buf, size_t bytes) {
+  if (!h || !buf) return CLV_EINVAL;
+  if (bytes < sizeof(StateHeader)) return fail(h, CLV_EINVAL, "state buffer too small");
+  StateHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  const clv_config& c = h->cfg;
+  if (hd.magic != kStateMagic || hd.version != 1u) return fail(h, CLV_EINVAL, "not a checkpoint of this library");
+  if (hd.nx != c.nx || hd.ny != c.ny || hd.neta != c.neta || hd.precision != c.precision ||
+      hd.viscous != (h->viscous ? 1 : 0) || hd.dx != c.dx || hd.dy != c.dy || hd.deta != c.deta ||
+      hd.dtau != c.dtau || hd.eta_over_s != c.eta_over_s)
+    return fail(h, CLV_EINVAL, "checkpoint of a different configuration");
+  if (bytes < state_bytes(h)) return fail(h, CLV_EINVAL, "state buffer too small (clv_state_bytes)");
+  h->cur = 0;
+  h->prev = 1;
+  void* a[kStateFields];
+  state_arrays(h, a);
+  const char* src = static_cast<const char*>(buf) + sizeof(hd);
+  const size_t fb = (size_t)h->N * h->rsize;
+  for (int k = 0; k < kStateFields; ++k)
+    CLV_CUDA(h, cudaMemcpyAsync(a[k], src + k * fb, fb, cudaMemcpyHostToDevice, h->stream));
+  CLV_CUDA(h, cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream));
+  CLV_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->tau = hd.tau;
+  h->step = hd.step;
+  h->initialized = true;
+  return CLV_OK;
+}
+
 clv_status clv_get_tile(clv_handle* h, clv_tile_info* out) {
   if (!h || !out) return CLV_EINVAL;
   tile_info(h, 0.0, out);
@@ -974,7 +1113,7 @@ clv_status clv_autotune(clv_handle* h, int max_candidates, int reps, clv_tile_in
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CLV_CUDA(h, cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(h, CLV_ECUDA, "cudaEventCreate"); }
-  double best_ms = 1e300;
+  double best_ms = 1e300, cur_ms = 0.0;
   size_t best_i = 0;
   cudaError_t err = cudaSuccess;
   for (size_t i = 0; i < cand.size() && err == cudaSuccess; ++i) {
@@ -986,8 +1125,12 @@ clv_status clv_autotune(clv_handle* h, int max_candidates, int reps, clv_tile_in
       else
         err = h->viscous ? time_stage1<float, true>(h, reps, e0, e1, &ms) : time_stage1<float, false>(h, reps, e0, e1, &ms);
     }
+    if (err == cudaSuccess && i == 0) cur_ms = ms;
     if (err == cudaSuccess && ms < best_ms) { best_ms = ms; best_i = i; }
   }
+  // keep the current shape unless a candidate is clearly (2%) faster: the
+  // timings of near-equal shapes differ by run-to-run noise
+  if (best_i != 0 && best_ms > 0.98 * cur_ms) { best_i = 0; best_ms = cur_ms; }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err != cudaSuccess) return fail(h, CLV_ECUDA, std::string("autotune: ") + cudaGetErrorString(err));

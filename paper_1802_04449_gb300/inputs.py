@@ -227,6 +227,7 @@ class HydroCase:
     nsteps: int
     cartesian: bool = False
     periodic: bool = False
+    T0: np.ndarray | None = None   # (4, nx, ny, neta) T^{tau mu} initial state (then eps/u are unused)
 
     @property
     def ncells(self):
@@ -256,6 +257,33 @@ def hotspot_event(nx=97, ny=97, neta=41, dx=0.2, deta=0.2, b=7.0, n_spots=2048, 
     return HydroCase(name, nx, ny, neta, dx, dx, deta, tau0, dtau, eta_over_s,
                      crossover_eos() if eos == "crossover" else None,
                      eps, z.copy(), z.copy(), z.copy(), nsteps)
+
+
+def minijet_event(nx=261, ny=261, neta=121, dx=0.08, deta=0.1, b=7.0, n_spots=8000, eps_max=55.0,
+                  seed=2024, tau0=0.4, dtau=0.005, eta_over_s=0.16, nsteps=400, eos="crossover",
+                  pt_mean=1.5, m0=1.0, name="hot-spot event with mini-jet initial flow"):
+    """Hot spots (placed as in hotspot_event) that each carry a transverse
+    momentum: p_T exponential with mean pt_mean (GeV), azimuth uniform; a spot
+    deposits T^{tau mu} proportional to its Gaussian profile times
+    (1, p_x / m_T, p_y / m_T, 0), m_T = sqrt(p_T^2 + m0^2).  The common
+    amplitude makes max T^{tau tau} = eps_max.  pi = 0; the primitives follow
+    from the root solve."""
+    rng = np.random.default_rng(seed)
+    eta_half = (neta - 1) / 2.0 * deta
+    xs, ys, etas = sample_spots(rng, n_spots, b, eta_half)
+    pt = rng.exponential(pt_mean, n_spots)
+    phi = rng.uniform(0.0, 2.0 * np.pi, n_spots)
+    mt = np.sqrt(pt ** 2 + m0 ** 2)
+    G = lambda w: deposit_spots(nx, ny, neta, dx, dx, deta, xs, ys, etas, 1.0, weights=w)
+    Ttt = G(None)
+    Ttx = G(pt * np.cos(phi) / mt)
+    Tty = G(pt * np.sin(phi) / mt)
+    scale = eps_max / Ttt.max()
+    T0 = np.stack([Ttt * scale, Ttx * scale, Tty * scale, np.zeros_like(Ttt)])
+    z = np.zeros_like(Ttt)
+    return HydroCase(name, nx, ny, neta, dx, dx, deta, tau0, dtau, eta_over_s,
+                     crossover_eos() if eos == "crossover" else None,
+                     z.copy(), z.copy(), z.copy(), z.copy(), nsteps, T0=T0)
 
 
 def gubser_case(dx=0.3, nx=33, neta=9, deta=0.3, dtau=0.02, tau0=1.0, tau1=3.0, q=1.0):

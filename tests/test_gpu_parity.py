@@ -261,3 +261,72 @@ def test_tile_shapes_and_autotuner_leave_results_unchanged():
     for bad in ((0, 5, 0), (3, 14, 0), (3, 5, 24), (21, 13, 0)):
         with pytest.raises(clv.ClvError):
             g.set_tile(*bad)
+
+
+@pytest.mark.parametrize("eta_over_s,prec", [(0.0, clv.CLV_FP64), (0.16, clv.CLV_FP64), (0.16, clv.CLV_FP32)])
+def test_minijet_initial_flow(eta_over_s, prec):
+    """Initial state from T^{tau mu} with transverse momentum (mini-jet
+    flow): the GPU's root solve of the initial state and the evolution
+    against the oracle's."""
+    case = I.minijet_event(nx=19, ny=17, neta=9, dx=0.2, deta=0.2, n_spots=40, seed=12, eta_over_s=eta_over_s,
+                           dtau=0.01)
+    o = oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
+                      case.eta_over_s, case.eos)
+    o.set_initial_T(case.T0)
+    g = clv.from_case(case, prec)
+    g.set_initial_T(case.T0)
+    if prec == clv.CLV_FP64:
+        compare_fp64(o, g, viscous=eta_over_s > 0)      # the initial state itself
+    o.step(6)
+    st = g.step(6, stats=True)
+    assert st["error_word"] == 0
+    if prec == clv.CLV_FP64:
+        compare_fp64(o, g, viscous=eta_over_s > 0)
+    else:
+        assert fp32_eps_err(o, g) <= FP32_TOL
+    # device input equals host input
+    import torch
+    g2 = clv.from_case(case, prec)
+    g2.set_initial_T(torch.tensor(case.T0, device="cuda"))
+    g2.step(6)
+    assert np.array_equal(g2.get(["eps"])["eps"], g.get(["eps"])["eps"])
+
+
+def test_minijet_initial_state_errors():
+    case = I.minijet_event(nx=9, ny=9, neta=5, dx=0.2, deta=0.2, n_spots=10, seed=2)
+    g = clv.from_case(case, clv.CLV_FP64)
+    bad = case.T0.copy()
+    bad[1, 4, 4, 2] = np.nan
+    with pytest.raises(clv.ClvError) as e:
+        g.set_initial_T(bad)
+    assert e.value.status == 5          # CLV_ENONFINITE
+    g.set_initial_T(case.T0)          # the handle stays usable
+    assert g.step(1, stats=True)["error_word"] == 0
+
+
+@pytest.mark.parametrize("prec", [clv.CLV_FP64, clv.CLV_FP32])
+def test_checkpoint_restart_is_bitwise(prec):
+    """get_state after 7 steps, restore into a fresh handle: 5 more steps
+    there equal 5 more steps of the original run bit for bit."""
+    case = small_hotspot(seed=17)
+    a = clv.from_case(case, prec)
+    a.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    a.step(7)
+    state = a.get_state()
+    a.step(5)
+    b = clv.from_case(case, prec)
+    b.set_state(state)
+    assert b.time()[0] == pytest.approx(case.tau0 + 7 * case.dtau, rel=1e-14) and b.time()[1] == 7
+    b.step(5)
+    names = ["eps", "ux", "uy", "ueta", "Ttt", "Tte", "pixx", "pixe", "upx"]
+    ra, rb = a.get(names), b.get(names)
+    for k in names:
+        assert np.array_equal(ra[k], rb[k]), k
+    assert a.time() == b.time()
+    # another configuration is refused
+    other = small_hotspot(seed=17, nx=19)
+    c = clv.from_case(other, prec)
+    with pytest.raises(clv.ClvError):
+        c.set_state(state)
+    with pytest.raises(clv.ClvError):
+        b.set_state(state[:100])
