@@ -185,25 +185,29 @@ def sample_spots(rng, n_spots, b, eta_max, eta_w=2.0, sigma_eta=1.8):
 
 
 def deposit_spots(nx, ny, neta, dx, dy, deta, xs, ys, etas, amp, sigma_r=0.6, sigma_eta=0.6,
-                  weights=None):
-    """Sum of Gaussians sum_s w_s amp exp(-r^2/2 sigma_r^2 - (eta-eta_s)^2/2 sigma_eta^2)."""
+                  weights=None, chunk=512):
+    """Sum of Gaussians sum_s w_s amp exp(-r^2/2 sigma_r^2 - (eta-eta_s)^2/2 sigma_eta^2).
+    ``weights`` may be a list of weight vectors: then one field per vector."""
+    many = isinstance(weights, (list, tuple))
+    wl = list(weights) if many else [weights]
     x = cell_coords(nx, dx)
     y = cell_coords(ny, dy)
     eta = cell_coords(neta, deta)
-    out = np.zeros((nx, ny, neta))
-    w = np.ones(len(xs)) if weights is None else np.asarray(weights)
-    cut = 5.0
-    for s in range(len(xs)):
-        ix = np.nonzero(np.abs(x - xs[s]) < cut * sigma_r)[0]
-        iy = np.nonzero(np.abs(y - ys[s]) < cut * sigma_r)[0]
-        ie = np.nonzero(np.abs(eta - etas[s]) < cut * sigma_eta)[0]
-        if len(ix) == 0 or len(iy) == 0 or len(ie) == 0:
-            continue
-        gx = np.exp(-(x[ix] - xs[s]) ** 2 / (2 * sigma_r ** 2))
-        gy = np.exp(-(y[iy] - ys[s]) ** 2 / (2 * sigma_r ** 2))
-        ge = np.exp(-(eta[ie] - etas[s]) ** 2 / (2 * sigma_eta ** 2))
-        out[np.ix_(ix, iy, ie)] += w[s] * amp * gx[:, None, None] * gy[None, :, None] * ge[None, None, :]
-    return out
+    xs, ys, etas = (np.asarray(a, dtype=np.float64) for a in (xs, ys, etas))
+    wl = [np.ones(len(xs)) if w is None else np.asarray(w, dtype=np.float64) for w in wl]
+    outs = [np.zeros((nx * ny, neta)) for _ in wl]
+    # each Gaussian is separable: a chunk of spots is one matrix product,
+    # (x, y) profiles (cells x spots) times weighted eta profiles (spots x eta)
+    for s0 in range(0, len(xs), chunk):
+        s1 = min(len(xs), s0 + chunk)
+        gx = np.exp(-(x[None, :] - xs[s0:s1, None]) ** 2 / (2 * sigma_r ** 2)) * amp
+        gy = np.exp(-(y[None, :] - ys[s0:s1, None]) ** 2 / (2 * sigma_r ** 2))
+        ge = np.exp(-(eta[None, :] - etas[s0:s1, None]) ** 2 / (2 * sigma_eta ** 2))
+        At = (gx[:, :, None] * gy[:, None, :]).reshape(s1 - s0, nx * ny).T
+        for o, w in zip(outs, wl):
+            o += At @ (w[s0:s1, None] * ge)
+    outs = [o.reshape(nx, ny, neta) for o in outs]
+    return outs if many else outs[0]
 
 
 @dataclass
@@ -274,10 +278,8 @@ def minijet_event(nx=261, ny=261, neta=121, dx=0.08, deta=0.1, b=7.0, n_spots=80
     pt = rng.exponential(pt_mean, n_spots)
     phi = rng.uniform(0.0, 2.0 * np.pi, n_spots)
     mt = np.sqrt(pt ** 2 + m0 ** 2)
-    G = lambda w: deposit_spots(nx, ny, neta, dx, dx, deta, xs, ys, etas, 1.0, weights=w)
-    Ttt = G(None)
-    Ttx = G(pt * np.cos(phi) / mt)
-    Tty = G(pt * np.sin(phi) / mt)
+    Ttt, Ttx, Tty = deposit_spots(nx, ny, neta, dx, dx, deta, xs, ys, etas, 1.0,
+                                  weights=[None, pt * np.cos(phi) / mt, pt * np.sin(phi) / mt])
     scale = eps_max / Ttt.max()
     T0 = np.stack([Ttt * scale, Ttx * scale, Tty * scale, np.zeros_like(Ttt)])
     z = np.zeros_like(Ttt)
