@@ -225,6 +225,35 @@ clv_status clv_mlp_train(float* d_params, float* d_work, const float* d_X, const
                          int iters, int batch, float lr, uint64_t seed, int step0, void* cuda_stream,
                          float* d_loss);
 
+/* ---------------- batch of events ----------------
+ * Many independent events of different grids (and eta/s) in one handle:
+ * their fields are stored back to back, each stage is one persistent launch
+ * whose CTAs take (event, tile-chunk) work items, most expensive first, and
+ * the root solve is one launch over all cells.  The events must share tau0,
+ * dtau, precision, the EOS, eps_cut, the coordinates and the boundaries
+ * (kernel 0); they may differ in nx, ny, neta, dx, dy, deta and eta/s.
+ * clv_step, the guess calls, clv_get_stats (E_tot = 0: per event below),
+ * clv_get_state / clv_set_state and clv_get_fields (all events back to back)
+ * take a batch handle; clv_set_initial(_T), clv_set_tile and clv_autotune do
+ * not (CLV_EINVAL).  The batch starts (first-step predictor) at the first
+ * clv_step, after every event's initial state was set. */
+clv_status clv_create_batch(const clv_config* cfgs, int nevents, void* cuda_stream, clv_handle** out);
+
+/* Number of events and total cells of a batch (0 events for a single event). */
+clv_status clv_batch_size(const clv_handle* h, int* nevents, int64_t* cells);
+
+/* Initial state of one event, as clv_set_initial (host arrays of that
+ * event's nx*ny*neta cells).  CLV_EINVAL once the batch has started. */
+clv_status clv_batch_set_initial(clv_handle* h, int event, const double* eps, const double* ux,
+                                 const double* uy, const double* ueta, const double* pi);
+
+/* Fields of one event, as clv_get_fields (host). */
+clv_status clv_batch_get_fields(clv_handle* h, int event, uint32_t which_mask, double* host_out);
+
+/* eps_max, T_max and E_tot of one event (the counters are the batch's).
+ * Synchronises the stream. */
+clv_status clv_batch_event_stats(clv_handle* h, int event, clv_stats* out);
+
 /* ---------------- checkpoint ----------------
  * The complete evolution state: T~^{tau mu}, pi~^{mu nu} and the primitives
  * (eps, u~, P, c_s) of the current and the previous step in the working
@@ -236,6 +265,13 @@ clv_status clv_mlp_train(float* d_params, float* d_work, const float* d_X, const
 clv_status clv_state_bytes(const clv_handle* h, size_t* bytes);
 clv_status clv_get_state(clv_handle* h, void* buf, size_t bytes);
 clv_status clv_set_state(clv_handle* h, const void* buf, size_t bytes);
+
+/* Step graphs (on by default): clv_step replays pairs of plain steps from a
+ * CUDA graph captured once per handle and buffer parity (tau lives on the
+ * device, so the launches of a step are the same every step).  The step that
+ * reduces statistics and timed steps (clv_enable_kernel_timing) are launched
+ * directly.  Results are the same bit for bit either way. */
+clv_status clv_set_graphs(clv_handle* h, int enable);
 
 /* ---------------- tile shape of the stage kernel ----------------
  * The stage kernel works on (y, eta_s) tiles of TJ x TK cells, each CTA

@@ -80,7 +80,9 @@ EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initi
             "clv_destroy", "clv_last_error", "clv_version", "clv_field_stats_noalloc",
             "clv_set_guess", "clv_set_mlp", "clv_mlp_samples", "clv_mlp_forward", "clv_mlp_loss_grad",
             "clv_mlp_train", "clv_get_tile", "clv_set_tile", "clv_autotune", "clv_set_initial_T",
-            "clv_set_initial_T_device", "clv_state_bytes", "clv_get_state", "clv_set_state"]
+            "clv_set_initial_T_device", "clv_state_bytes", "clv_get_state", "clv_set_state",
+            "clv_create_batch", "clv_batch_size", "clv_batch_set_initial", "clv_batch_get_fields",
+            "clv_batch_event_stats", "clv_set_graphs"]
 CLV_GUESS_PREVIOUS, CLV_GUESS_COLD, CLV_GUESS_MLP = 0, 1, 2
 MLP_NPARAM = 5124
 
@@ -122,6 +124,12 @@ def load(path: str | None = None):
         lib.clv_mlp_loss_grad.argtypes = [V, V, V, ctypes.c_int64, V, V, V]
         lib.clv_mlp_train.argtypes = [V, V, V, V, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                       ctypes.c_uint64, ctypes.c_int, V, V]
+        lib.clv_set_graphs.argtypes = [P, ctypes.c_int]
+        lib.clv_create_batch.argtypes = [cfgp, ctypes.c_int, V, ctypes.POINTER(P)]
+        lib.clv_batch_size.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]
+        lib.clv_batch_set_initial.argtypes = [P, ctypes.c_int, D, D, D, D, D]
+        lib.clv_batch_get_fields.argtypes = [P, ctypes.c_int, ctypes.c_uint32, D]
+        lib.clv_batch_event_stats.argtypes = [P, ctypes.c_int, ctypes.POINTER(clv_stats)]
         lib.clv_state_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
         lib.clv_get_state.argtypes = [P, V, ctypes.c_size_t]
         lib.clv_set_state.argtypes = [P, V, ctypes.c_size_t]
@@ -266,6 +274,9 @@ class Hydro:
         self._lib.clv_get_time(self._h, ctypes.byref(tau), ctypes.byref(step))
         return tau.value, step.value
 
+    def set_graphs(self, on=True):
+        self._check(self._lib.clv_set_graphs(self._h, int(bool(on))), self._h)
+
     def get_state(self):
         """Checkpoint: the complete evolution state as bytes."""
         n = ctypes.c_size_t()
@@ -376,6 +387,55 @@ def field_stats_noalloc(d_eps, d_Ttt, cell_volume, d_out, stream=None):
                                          ctypes.c_void_p(d_out.data_ptr()))
     if status != 0:
         raise ClvError(status, lib.clv_last_error(None).decode())
+
+
+class Batch(Hydro):
+    """Many events of different grids in one handle (clv_create_batch):
+    one persistent stage launch and one root-solve launch per stage."""
+
+    def __init__(self, cases, precision=CLV_FP64, stream=None, device=None):
+        import torch
+        self._lib = load()
+        self.torch = torch
+        self.device = torch.device(device or "cuda")
+        cfgs = (clv_config * len(cases))()
+        self._keep = []
+        for i, c in enumerate(cases):
+            cfg, keep = make_config(c.nx, c.ny, c.neta, c.dx, c.dy, c.deta, c.tau0, c.dtau, c.eta_over_s, c.eos,
+                                    precision)
+            cfgs[i] = cfg
+            self._keep.append(keep)
+        self.shapes = [(c.nx, c.ny, c.neta) for c in cases]
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self._lib.clv_create_batch(cfgs, len(cases), ctypes.c_void_p(self.stream.cuda_stream),
+                                            ctypes.byref(h))
+        self._check(st, None)
+        self._h = h
+        n, cells = ctypes.c_int(), ctypes.c_int64()
+        self._lib.clv_batch_size(h, ctypes.byref(n), ctypes.byref(cells))
+        self.nevents, self.N = n.value, cells.value
+        self.shape = (self.N, 1, 1)
+
+    def set_event(self, e, eps, ux, uy, ueta, pi=None):
+        shp = self.shapes[e]
+        arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(shp)) for a in (eps, ux, uy, ueta)]
+        pa = None if pi is None else np.ascontiguousarray(np.asarray(pi, dtype=np.float64).reshape((10,) + shp))
+        self._check(self._lib.clv_batch_set_initial(self._h, int(e), *(_dp(a) for a in arrs),
+                                                    _dp(pa) if pa is not None else None), self._h)
+
+    def get_event(self, e, names):
+        names = sorted(list(names), key=lambda k: FIELD_BIT[k])
+        shp = self.shapes[e]
+        buf = np.empty((len(names), int(np.prod(shp))), dtype=np.float64)
+        self._check(self._lib.clv_batch_get_fields(self._h, int(e), self.mask_of(names), _dp(buf)), self._h)
+        return {k: buf[i].reshape(shp) for i, k in enumerate(names)}
+
+    def event_stats(self, e):
+        s = clv_stats()
+        self._check(self._lib.clv_batch_event_stats(self._h, int(e), ctypes.byref(s)), self._h)
+        return s.as_dict()
 
 
 def mlp_loss_grad(params, X, Y, stream=None):

@@ -66,7 +66,8 @@ struct clv_handle {
   double* staging = nullptr;      // N doubles
   double* block_sum = nullptr;    // nblocks doubles
   DevStats* dstats = nullptr;
-  double tau = 0.0;
+  double* tau_dev = nullptr;      // tau of the step on the device (the kernels read it)
+  double tau = 0.0;               // host copy, advanced by the same additions
   long long step = 0;
   bool initialized = false;
   std::string last_error;
@@ -82,6 +83,25 @@ struct clv_handle {
   unsigned tile_blocks = 0;
   size_t tile_smem = 0;
   int stat_blocks = 0;  // block partials written by the last stats launch
+  // batch of events stored back to back (clv_create_batch; empty otherwise)
+  struct Event {
+    clv_config cfg;
+    long long off = 0, N = 0;
+    TileArgs tile{};
+    bool viscous = false, set = false;
+  };
+  std::vector<Event> batch;
+  // replay of captured step pairs (the primitive sets alternate with period 2)
+  bool graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t step_graph[2] = {nullptr, nullptr};   // two steps starting from cur = 0 / cur = 1
+  void* batch_geom = nullptr;       // EventGeom<R>[events]
+  TileArgs* batch_tiles = nullptr;  // TileArgs[events]
+  int2* batch_items = nullptr;      // (event, tile-chunk), most expensive first
+  int* batch_ctr = nullptr;         // work counters of the two stage launches
+  int batch_nitems = 0, batch_threads = 0;
+  unsigned batch_blocks = 0;
+  size_t batch_smem = 0;
 };
 
 namespace {
@@ -144,7 +164,7 @@ TileGeom tile_geometry(const clv_config* c, int sms) {
   const long long tiles = (long long)t.ntj * t.ntk;
   long long best_nch = 1;
   double best = 1e300;
-  for (long long nch = 1; nch <= c->nx; ++nch) {
+  for (long long nch = 1; nch <= std::min<long long>(c->nx, 8LL * sms * CLV_TILE_MIN_BLOCKS); ++nch) {
     const long long cx = (c->nx + nch - 1) / nch;
     const long long used = (c->nx + cx - 1) / cx;
     const long long slots = (long long)sms * CLV_TILE_MIN_BLOCKS;
@@ -175,7 +195,7 @@ TileGeom tile_geometry_of(const clv_config* c, int sms, int TJ, int TK, int cx) 
   if (cx <= 0) {
     long long best_nch = 1;
     double best = 1e300;
-    for (long long nch = 1; nch <= c->nx; ++nch) {
+    for (long long nch = 1; nch <= std::min<long long>(c->nx, 8LL * sms * CLV_TILE_MIN_BLOCKS); ++nch) {
       const long long cxx = (c->nx + nch - 1) / nch;
       const long long used = (c->nx + cxx - 1) / cxx;
       const long long slots = (long long)sms * CLV_TILE_MIN_BLOCKS;
@@ -250,6 +270,7 @@ size_t layout(const clv_config* c, clv_handle* h) {
   size_t oStage = take(std::max((size_t)N * 8, (size_t)256));  // also scratch of clv_mlp_samples
   size_t oBlock = take((size_t)nblocks * 8);
   size_t oStats = take(sizeof(DevStats));
+  size_t oTau = take(sizeof(double));
   if (h) {
     char* b = h->ws;
     for (int m = 0; m < 4; ++m) { h->T0[m] = b + oT0[m]; h->T1[m] = b + oT1[m]; }
@@ -261,6 +282,7 @@ size_t layout(const clv_config* c, clv_handle* h) {
     h->staging = (double*)(b + oStage);
     h->block_sum = (double*)(b + oBlock);
     h->dstats = (DevStats*)(b + oStats);
+    h->tau_dev = (double*)(b + oTau);
     h->nblocks = nblocks;
     h->N = N;
     h->rsize = (int)rs;
@@ -296,7 +318,7 @@ template <typename R> EosView<R> eos_view(const clv_handle* h) {
 inline unsigned grid_of(long long N) { return (unsigned)((N + kBlock - 1) / kBlock); }
 
 template <typename R>
-StageParams<R> stage_params(clv_handle* h, int stage, double tau_stage, double tau_new) {
+StageParams<R> stage_params(clv_handle* h, int stage) {
   const clv_config& c = h->cfg;
   StageParams<R> p;
   const int st = 3 - h->cur - h->prev;
@@ -318,18 +340,17 @@ StageParams<R> stage_params(clv_handle* h, int stage, double tau_stage, double t
   p.eos = eos_view<R>(h);
   p.nx = c.nx; p.ny = c.ny; p.ne = c.neta; p.periodic = c.periodic;
   p.N = h->N;
-  const double taus = c.cartesian ? 1.0 : tau_stage;
-  p.taus = (R)taus;
-  p.geo = (R)(c.cartesian ? 0.0 : 1.0 / tau_stage);
-  p.taus_new = (R)(c.cartesian ? 1.0 : tau_new);
+  p.tau_dev = h->tau_dev;
+  p.dtau_d = c.dtau;
+  p.cartesian = c.cartesian;
   p.h = (R)c.dtau;
   p.inv_h = (R)(1.0 / c.dtau);
   p.inv_dl[0] = (R)(1.0 / c.dx);
   p.inv_dl[1] = (R)(1.0 / c.dy);
-  p.inv_dl[2] = (R)(1.0 / (taus * c.deta));
   p.st_tau = (R)(c.cartesian ? 0.0 : 1.0);
   p.eps_cut = (R)c.eps_cut;
   p.eps_cut_d = c.eps_cut;
+  p.deta_d = c.deta;
   p.inv_5etas_hbarc = (R)(c.eta_over_s > 0 ? 1.0 / (5.0 * c.eta_over_s * kHbarC) : 0.0);
   p.polish_E = (R)(1.01 * c.eps_cut);
   p.polish_v = (R)0.999;
@@ -379,21 +400,42 @@ template <typename R, bool VISC> cudaError_t tile_attributes(size_t smem) {
   return e;
 }
 
+template <typename R, bool VISC, bool STATS> void launch_recover(clv_handle* h, const StageParams<R>& p) {
+  const unsigned g = grid_of(h->N);
+  if (sizeof(R) == 4 && h->guess == kGuessMlp)
+    recover_kernel<R, VISC, STATS, sizeof(R) == 4 ? kGuessMlp : kGuessPrevious><<<g, kBlock, 0, h->stream>>>(p);
+  else if (h->guess == kGuessCold) recover_kernel<R, VISC, STATS, kGuessCold><<<g, kBlock, 0, h->stream>>>(p);
+  else recover_kernel<R, VISC, STATS, kGuessPrevious><<<g, kBlock, 0, h->stream>>>(p);
+}
+
+// One stage: the stage kernel, then the root solve (the direct kernel does
+// both).  With timing on, an event follows each of the two.
 template <typename R, bool VISC, int STAGE, bool STATS>
 void launch_stage(clv_handle* h, const StageParams<R>& p, bool timed) {
-  if (h->cfg.kernel == 1) {
+  if (!h->batch.empty()) {
+    cudaMemsetAsync(h->batch_ctr + (STAGE - 1), 0, sizeof(int), h->stream);
+    stage_batch_kernel<R, STAGE, VISC><<<h->batch_blocks, h->batch_threads, h->batch_smem, h->stream>>>(
+        p, (const EventGeom<R>*)h->batch_geom, h->batch_tiles, h->batch_items, h->batch_nitems,
+        h->batch_ctr + (STAGE - 1));
+    if (timed) timing_event(h);
+    launch_recover<R, VISC, STATS>(h, p);
+  } else if (h->cfg.kernel == 1) {
     stage_kernel<R, STAGE, VISC, STATS><<<grid_of(h->N), kBlock, 0, h->stream>>>(p);
     if (timed) timing_event(h);   // empty recovery slot
   } else {
     stage_tile_kernel<R, STAGE, VISC><<<h->tile_blocks, h->tile_threads, h->tile_smem, h->stream>>>(p, h->tile);
     if (timed) timing_event(h);
-    const unsigned g = grid_of(h->N);
-    if (sizeof(R) == 4 && h->guess == kGuessMlp)
-      recover_kernel<R, VISC, STATS, sizeof(R) == 4 ? kGuessMlp : kGuessPrevious><<<g, kBlock, 0, h->stream>>>(p);
-    else if (h->guess == kGuessCold) recover_kernel<R, VISC, STATS, kGuessCold><<<g, kBlock, 0, h->stream>>>(p);
-    else recover_kernel<R, VISC, STATS, kGuessPrevious><<<g, kBlock, 0, h->stream>>>(p);
+    launch_recover<R, VISC, STATS>(h, p);
   }
   if (timed) timing_event(h);
+}
+
+__global__ void set_tau_kernel(double* tau_dev, double tau) { *tau_dev = tau; }
+__global__ void advance_tau_kernel(double* tau_dev, double dtau) { *tau_dev = *tau_dev + dtau; }
+
+void set_tau(clv_handle* h, double tau) {
+  h->tau = tau;
+  set_tau_kernel<<<1, 1, 0, h->stream>>>(h->tau_dev, tau);
 }
 
 template <typename R, bool VISC>
@@ -403,18 +445,73 @@ void launch_step(clv_handle* h, bool stats) {
   // (with kernel = 1 the recovery slots collapse: two events are recorded back to back)
   const bool timed = h->timing && h->ev_pending.size() < kEventsPerStep * kMaxTimedSteps;
   if (timed) timing_event(h);
-  StageParams<R> p1 = stage_params<R>(h, 1, tn, tn1);
+  StageParams<R> p1 = stage_params<R>(h, 1);
   launch_stage<R, VISC, 1, false>(h, p1, timed);
-  StageParams<R> p2 = stage_params<R>(h, 2, tn1, tn1);
+  StageParams<R> p2 = stage_params<R>(h, 2);
   if (stats) {
     launch_stage<R, VISC, 2, true>(h, p2, timed);
     h->stat_blocks = (int)grid_of(h->N);
   } else {
     launch_stage<R, VISC, 2, false>(h, p2, timed);
   }
+  advance_tau_kernel<<<1, 1, 0, h->stream>>>(h->tau_dev, h->cfg.dtau);
   std::swap(h->cur, h->prev);
   h->tau = tn1;
   h->step += 1;
+}
+
+void invalidate_graphs(clv_handle* h) {
+  for (auto& g : h->step_graph)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+void launch_one_step(clv_handle* h, bool stats) {
+  if (h->rsize == 8) {
+    if (h->viscous) launch_step<double, true>(h, stats); else launch_step<double, false>(h, stats);
+  } else {
+    if (h->viscous) launch_step<float, true>(h, stats); else launch_step<float, false>(h, stats);
+  }
+}
+
+// The executable graph of two plain steps from the current buffer parity,
+// captured once on a private stream (capture issues no work) and replayed on
+// the handle's stream.  nullptr (and graphs off for the handle) if capture is
+// not possible.
+cudaGraphExec_t step_pair_graph(clv_handle* h) {
+  const int key = h->cur;
+  if (h->step_graph[key]) return h->step_graph[key];
+  if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    h->graphs = false;
+    return nullptr;
+  }
+  const cudaStream_t user = h->stream;
+  const double tau = h->tau;
+  const long long step = h->step;
+  const int cur = h->cur, prev = h->prev;
+  h->stream = h->cap_stream;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    launch_one_step(h, false);
+    launch_one_step(h, false);
+    e = cudaStreamEndCapture(h->cap_stream, &graph);
+  }
+  h->stream = user;
+  h->tau = tau;
+  h->step = step;
+  h->cur = cur;
+  h->prev = prev;
+  cudaGraphExec_t ex = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->graphs = false;
+    return nullptr;
+  }
+  h->step_graph[key] = ex;
+  return ex;
 }
 
 template <typename R> __global__ void stats_scan_kernel(const R* e, const R* T0, long long N, double* block_sum,
@@ -465,7 +562,7 @@ template <typename R> clv_status reduce_stats(clv_handle* h, bool scan, clv_stat
   out->step = h->step;
   std::memcpy(&out->eps_max, &ds.emax_bits, sizeof(double));
   out->T_max = ds.T_at_emax;
-  out->E_tot = ds.esum * c.dx * c.dy * c.deta;
+  out->E_tot = h->batch.empty() ? ds.esum * c.dx * c.dy * c.deta : 0.0;  // batch: per event (clv_batch_event_stats)
   out->n_rescaled = (int64_t)ds.counters[0];
   out->n_rootfail = (int64_t)ds.counters[1];
   out->n_polished = (int64_t)ds.counters[2];
@@ -495,39 +592,64 @@ template <typename R> __global__ void convert_kernel(const double* s, R* d, long
   if (c < N) d[c] = (R)s[c];
 }
 
+template <typename R> Prim<R> prim_at(Prim<R> p, long long off) {
+  p.e += off;
+  for (int m = 0; m < 3; ++m) p.u[m] += off;
+  p.P += off;
+  p.cs += off;
+  return p;
+}
+
+// Primitives (and pi~) of the cells [off, off + n) from doubles (host arrays
+// go through the staging buffer): vacuum below the cutoff, P and c_s from the
+// EOS, copied to the previous-step set.
 template <typename R>
-clv_status set_initial_impl(clv_handle* h, const double* const in[4], const double* pi, bool host) {
-  const long long N = h->N;
-  const unsigned g = grid_of(N);
+clv_status load_initial_range(clv_handle* h, long long off, long long n, bool visc, const double* const in[4],
+                              const double* pi, bool host) {
+  const unsigned g = grid_of(n);
   const clv_config& c = h->cfg;
-  Prim<R> pc = prim_set<R>(h, h->cur), pp = prim_set<R>(h, h->prev);
-  // inputs -> R-typed fields (through the staging buffer for host inputs)
+  Prim<R> pc = prim_at(prim_set<R>(h, h->cur), off), pp = prim_at(prim_set<R>(h, h->prev), off);
   R* dst_prim[4] = {pc.e, pc.u[0], pc.u[1], pc.u[2]};
   for (int f = 0; f < 4; ++f) {
     const double* src = in[f];
     if (host) {
-      CLV_CUDA(h, cudaMemcpyAsync(h->staging, src, (size_t)N * 8, cudaMemcpyHostToDevice, h->stream));
+      CLV_CUDA(h, cudaMemcpyAsync(h->staging, src, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream));
       src = h->staging;
     }
-    convert_kernel<R><<<g, kBlock, 0, h->stream>>>(src, dst_prim[f], N);
+    convert_kernel<R><<<g, kBlock, 0, h->stream>>>(src, dst_prim[f], n);
   }
   Ptr10<R> pi0;
-  for (int q = 0; q < 10; ++q) pi0.p[q] = (R*)h->PI0[q];
+  for (int q = 0; q < 10; ++q) pi0.p[q] = (R*)h->PI0[q] + off;
   for (int q = 0; q < 10; ++q) {
-    if (pi && h->viscous) {
-      const double* src = pi + (size_t)q * N;
+    if (pi && visc) {
+      const double* src = pi + (size_t)q * n;
       if (host) {
-        CLV_CUDA(h, cudaMemcpyAsync(h->staging, src, (size_t)N * 8, cudaMemcpyHostToDevice, h->stream));
+        CLV_CUDA(h, cudaMemcpyAsync(h->staging, src, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream));
         src = h->staging;
       }
-      convert_kernel<R><<<g, kBlock, 0, h->stream>>>(src, pi0.p[q], N);
+      convert_kernel<R><<<g, kBlock, 0, h->stream>>>(src, pi0.p[q], n);
     } else {
-      CLV_CUDA(h, cudaMemsetAsync(pi0.p[q], 0, (size_t)N * sizeof(R), h->stream));
+      CLV_CUDA(h, cudaMemsetAsync(pi0.p[q], 0, (size_t)n * sizeof(R), h->stream));
     }
   }
-  init_primitives_kernel<R><<<g, kBlock, 0, h->stream>>>(pc, pp, pi0, h->viscous, eos_view<R>(h), c.eps_cut, N);
+  init_primitives_kernel<R><<<g, kBlock, 0, h->stream>>>(pc, pp, pi0, visc, eos_view<R>(h), c.eps_cut, n);
+  CLV_CUDA(h, cudaGetLastError());
+  return CLV_OK;
+}
+
+// The rest of the initial state, over all cells: T~ from the primitives and
+// (viscous runs) the first-step predictor of Sec. 3.
+template <typename R> clv_status finish_initial(clv_handle* h) {
+  const long long N = h->N;
+  const unsigned g = grid_of(N);
+  const clv_config& c = h->cfg;
+  Prim<R> pc = prim_set<R>(h, h->cur);
+  Ptr10<R> pi0;
+  for (int q = 0; q < 10; ++q) pi0.p[q] = (R*)h->PI0[q];
+  if (!h->batch.empty())   // ideal events of a batch keep pi~ = 0 in the stage buffers too
+    for (int q = 0; q < 10; ++q) CLV_CUDA(h, cudaMemsetAsync(h->PI1[q], 0, (size_t)N * sizeof(R), h->stream));
   const double taus0 = c.cartesian ? 1.0 : c.tau0;
-  h->tau = c.tau0;
+  set_tau(h, c.tau0);
   h->step = 0;
   R* T0[4] = {(R*)h->T0[0], (R*)h->T0[1], (R*)h->T0[2], (R*)h->T0[3]};
   if (h->viscous) {
@@ -536,7 +658,7 @@ clv_status set_initial_impl(clv_handle* h, const double* const in[4], const doub
     launch_step<R, false>(h, false);
     std::swap(h->cur, h->prev);  // undo the rotation: cur = u^0, prev = u^1_ideal
     extrapolate_prev_kernel<R><<<g, kBlock, 0, h->stream>>>(prim_set<R>(h, h->cur), prim_set<R>(h, h->prev), N);
-    h->tau = c.tau0;
+    set_tau(h, c.tau0);
     h->step = 0;
     tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(prim_set<R>(h, h->cur), pi0, true, T0[0], T0[1], T0[2],
                                                    T0[3], taus0, N);
@@ -549,13 +671,19 @@ clv_status set_initial_impl(clv_handle* h, const double* const in[4], const doub
   return CLV_OK;
 }
 
-template <typename R> clv_status export_field(clv_handle* h, int which, double* dst) {
+template <typename R>
+clv_status set_initial_impl(clv_handle* h, const double* const in[4], const double* pi, bool host) {
+  clv_status s = load_initial_range<R>(h, 0, h->N, h->viscous, in, pi, host);
+  return s != CLV_OK ? s : finish_initial<R>(h);
+}
+
+template <typename R> clv_status export_field(clv_handle* h, int which, double* dst, long long off, long long n) {
   const void* src = nullptr;
   if (which <= 3) src = h->PR[h->cur][which];
   else if (which <= 7) src = h->T0[which - 4];
   else if (which <= 17) src = h->PI0[which - 8];
   else src = h->PR[h->prev][1 + (which - 18)];
-  export_kernel<R><<<grid_of(h->N), kBlock, 0, h->stream>>>((const R*)src, dst, h->N);
+  export_kernel<R><<<grid_of(n), kBlock, 0, h->stream>>>((const R*)src + off, dst, n);
   CLV_CUDA(h, cudaGetLastError());
   return CLV_OK;
 }
@@ -682,6 +810,7 @@ extern "C" {
 
 static clv_status set_initial_T_any(clv_handle* h, const double* T, bool host) {
   if (!h) return CLV_EINVAL;
+  if (!h->batch.empty()) return fail(h, CLV_EINVAL, "a batch takes its events' states by clv_batch_set_initial");
   if (!T) return fail(h, CLV_EINVAL, "T is required");
   const long long N = h->N;
   // scratch: the stage-2 shear buffers (>= 4 N doubles in either precision),
@@ -715,6 +844,7 @@ static clv_status set_initial_T_any(clv_handle* h, const double* T, bool host) {
 static clv_status set_initial_any(clv_handle* h, const double* eps, const double* ux, const double* uy,
                                   const double* ueta, const double* pi, bool host) {
   if (!h) return CLV_EINVAL;
+  if (!h->batch.empty()) return fail(h, CLV_EINVAL, "a batch takes its events' states by clv_batch_set_initial");
   if (!eps || !ux || !uy || !ueta) return fail(h, CLV_EINVAL, "eps, ux, uy and ueta are required");
   const double* in[4] = {eps, ux, uy, ueta};
   h->cur = 0;
@@ -738,16 +868,30 @@ clv_status clv_set_initial_device(clv_handle* h, const double* d_eps, const doub
 
 clv_status clv_step(clv_handle* h, int nsteps, clv_stats* stats) {
   if (!h) return CLV_EINVAL;
+  if (!h->initialized && !h->batch.empty()) {
+    for (const auto& ev : h->batch)
+      if (!ev.set) return fail(h, CLV_EINVAL, "clv_batch_set_initial was not called for every event");
+    clv_status s = h->rsize == 8 ? finish_initial<double>(h) : finish_initial<float>(h);
+    if (s != CLV_OK) return s;
+  }
   if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
   if (nsteps < 0) return fail(h, CLV_EINVAL, "nsteps must be >= 0");
   if (stats && nsteps > 0) CLV_CUDA(h, cudaMemsetAsync(&h->dstats->emax_bits, 0, 8, h->stream));
-  for (int s = 0; s < nsteps; ++s) {
+  for (int s = 0; s < nsteps;) {
     const bool last = stats && s == nsteps - 1;
-    if (h->rsize == 8) {
-      if (h->viscous) launch_step<double, true>(h, last); else launch_step<double, false>(h, last);
-    } else {
-      if (h->viscous) launch_step<float, true>(h, last); else launch_step<float, false>(h, last);
+    const int plain_left = nsteps - s - (stats ? 1 : 0);   // steps before the one that reduces stats
+    if (h->graphs && !h->timing && plain_left >= 2) {
+      cudaGraphExec_t g = step_pair_graph(h);
+      if (g) {
+        CLV_CUDA(h, cudaGraphLaunch(g, h->stream));
+        for (int k = 0; k < 2; ++k) h->tau = h->tau + h->cfg.dtau;   // the device's additions
+        h->step += 2;
+        s += 2;
+        continue;
+      }
     }
+    launch_one_step(h, last);
+    ++s;
   }
   CLV_CUDA(h, cudaGetLastError());
   if (!stats) return CLV_OK;
@@ -761,24 +905,29 @@ clv_status clv_get_stats(clv_handle* h, clv_stats* stats) {
   return h->rsize == 8 ? reduce_stats<double>(h, true, stats) : reduce_stats<float>(h, true, stats);
 }
 
-static clv_status get_fields_any(clv_handle* h, uint32_t mask, double* out, bool host) {
+static clv_status get_fields_range(clv_handle* h, uint32_t mask, double* out, bool host, long long off,
+                                   long long n) {
   if (!h || !out) return CLV_EINVAL;
   if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
   if (mask >> 21) return fail(h, CLV_EINVAL, "mask selects fields beyond index 20");
   size_t slot = 0;
   for (int f = 0; f < 21; ++f) {
     if (!(mask >> f & 1u)) continue;
-    double* dst = host ? h->staging : out + slot * (size_t)h->N;
-    clv_status s = h->rsize == 8 ? export_field<double>(h, f, dst) : export_field<float>(h, f, dst);
+    double* dst = host ? h->staging : out + slot * (size_t)n;
+    clv_status s = h->rsize == 8 ? export_field<double>(h, f, dst, off, n) : export_field<float>(h, f, dst, off, n);
     if (s != CLV_OK) return s;
     if (host) {
-      CLV_CUDA(h, cudaMemcpyAsync(out + slot * (size_t)h->N, h->staging, (size_t)h->N * 8,
+      CLV_CUDA(h, cudaMemcpyAsync(out + slot * (size_t)n, h->staging, (size_t)n * 8,
                                   cudaMemcpyDeviceToHost, h->stream));
       CLV_CUDA(h, cudaStreamSynchronize(h->stream));
     }
     ++slot;
   }
   return CLV_OK;
+}
+
+static clv_status get_fields_any(clv_handle* h, uint32_t mask, double* out, bool host) {
+  return get_fields_range(h, mask, out, host, 0, h ? h->N : 0);
 }
 
 clv_status clv_get_fields(clv_handle* h, uint32_t mask, double* host_out) {
@@ -801,6 +950,7 @@ clv_status clv_set_guess(clv_handle* h, int mode) {
   if (mode < kGuessPrevious || mode > kGuessMlp) return fail(h, CLV_EINVAL, "unknown guess mode");
   if (mode == kGuessMlp && !h->mlp_loaded) return fail(h, CLV_EINVAL, "no network loaded (clv_set_mlp)");
   if (mode == kGuessMlp && h->rsize != 4) return fail(h, CLV_EINVAL, "the learned guess runs on the FP32 path");
+  if (h->guess != mode) invalidate_graphs(h);
   h->guess = mode;
   return CLV_OK;
 }
@@ -964,6 +1114,7 @@ static cudaError_t apply_tile(clv_handle* h, const TileGeom& g) {
   if (e == cudaSuccess && h->viscous)
     e = h->rsize == 8 ? tile_attributes<double, true>(g.smem) : tile_attributes<float, true>(g.smem);
   if (e != cudaSuccess) return e;
+  invalidate_graphs(h);
   h->tile = g.t;
   h->tile_threads = g.threads;
   h->tile_blocks = g.blocks;
@@ -976,7 +1127,7 @@ static cudaError_t apply_tile(clv_handle* h, const TileGeom& g) {
 // the evolution unchanged).
 template <typename R, bool VISC>
 static cudaError_t time_stage1(clv_handle* h, int reps, cudaEvent_t e0, cudaEvent_t e1, double* ms) {
-  const StageParams<R> p = stage_params<R>(h, 1, h->tau, h->tau + h->cfg.dtau);
+  const StageParams<R> p = stage_params<R>(h, 1);
   stage_tile_kernel<R, 1, VISC><<<h->tile_blocks, h->tile_threads, h->tile_smem, h->stream>>>(p, h->tile);
   cudaEventRecord(e0, h->stream);
   for (int r = 0; r < reps; ++r)
@@ -1071,10 +1222,17 @@ clv_status clv_set_state(clv_handle* h, const void* buf, size_t bytes) {
   for (int k = 0; k < kStateFields; ++k)
     CLV_CUDA(h, cudaMemcpyAsync(a[k], src + k * fb, fb, cudaMemcpyHostToDevice, h->stream));
   CLV_CUDA(h, cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream));
+  set_tau(h, hd.tau);
   CLV_CUDA(h, cudaStreamSynchronize(h->stream));
-  h->tau = hd.tau;
   h->step = hd.step;
   h->initialized = true;
+  return CLV_OK;
+}
+
+clv_status clv_set_graphs(clv_handle* h, int enable) {
+  if (!h) return CLV_EINVAL;
+  h->graphs = enable != 0;
+  if (!h->graphs) invalidate_graphs(h);
   return CLV_OK;
 }
 
@@ -1086,6 +1244,7 @@ clv_status clv_get_tile(clv_handle* h, clv_tile_info* out) {
 
 clv_status clv_set_tile(clv_handle* h, int TJ, int TK, int CX) {
   if (!h) return CLV_EINVAL;
+  if (!h->batch.empty()) return fail(h, CLV_EINVAL, "a batch sets its tiles per event");
   const clv_config& c = h->cfg;
   if (TJ < 1 || TJ > c.ny || TK < 1 || TK > c.neta || CX < 0 || CX > c.nx)
     return fail(h, CLV_EINVAL, "tile shape out of range");
@@ -1100,6 +1259,7 @@ clv_status clv_set_tile(clv_handle* h, int TJ, int TK, int CX) {
 
 clv_status clv_autotune(clv_handle* h, int max_candidates, int reps, clv_tile_info* best) {
   if (!h || max_candidates < 1 || reps < 1) return CLV_EINVAL;
+  if (!h->batch.empty()) return fail(h, CLV_EINVAL, "the autotuner tunes single-event handles");
   if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
   if (h->cfg.kernel != 0) return fail(h, CLV_EINVAL, "the autotuner tunes the tiled stage kernel");
   size_t smem_max = 0;
@@ -1139,6 +1299,186 @@ clv_status clv_autotune(clv_handle* h, int max_candidates, int reps, clv_tile_in
   return CLV_OK;
 }
 
+// ---------------- batch of events ----------------
+}  // extern "C"
+
+// Tile of one event of a batch: TK from the eta_s extent (at most 32 columns),
+// TJ as large as the thread limit allows, x chunks of about 32 planes.
+static TileArgs batch_tile(const clv_config& c) {
+  TileArgs t;
+  const int maxthr = tile_max_threads(&c);
+  const int nk = (c.neta + 31) / 32;
+  t.TK = (c.neta + nk - 1) / nk;
+  t.TJ = std::max(1, std::min(c.ny, maxthr / (t.TK + 1) - 1));
+  const int nch = (c.nx + 31) / 32;
+  t.CX = (c.nx + nch - 1) / nch;
+  t.ntj = (c.ny + t.TJ - 1) / t.TJ;
+  t.ntk = (c.neta + t.TK - 1) / t.TK;
+  return t;
+}
+
+template <typename R> static cudaError_t batch_upload(clv_handle* h) {
+  const size_t ne = h->batch.size();
+  std::vector<EventGeom<R>> g(ne);
+  std::vector<TileArgs> t(ne);
+  for (size_t e = 0; e < ne; ++e) {
+    const auto& ev = h->batch[e];
+    const clv_config& c = ev.cfg;
+    g[e] = EventGeom<R>{ev.off, c.nx, c.ny, c.neta, (R)(1.0 / c.dx), (R)(1.0 / c.dy),
+                        (R)(c.eta_over_s > 0 ? 1.0 / (5.0 * c.eta_over_s * kHbarC) : 0.0), c.deta,
+                        ev.viscous ? 1 : 0};
+    t[e] = ev.tile;
+  }
+  cudaError_t err = cudaMalloc(&h->batch_geom, ne * sizeof(EventGeom<R>));
+  if (err == cudaSuccess) err = cudaMemcpy(h->batch_geom, g.data(), ne * sizeof(EventGeom<R>), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMalloc((void**)&h->batch_tiles, ne * sizeof(TileArgs));
+  if (err == cudaSuccess) err = cudaMemcpy(h->batch_tiles, t.data(), ne * sizeof(TileArgs), cudaMemcpyHostToDevice);
+  auto attr = [&](const void* f) {
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->batch_smem);
+  };
+  attr((const void*)stage_batch_kernel<R, 1, false>);
+  attr((const void*)stage_batch_kernel<R, 2, false>);
+  attr((const void*)stage_batch_kernel<R, 1, true>);
+  attr((const void*)stage_batch_kernel<R, 2, true>);
+  return err;
+}
+
+extern "C" {
+
+clv_status clv_create_batch(const clv_config* cfgs, int nevents, void* cuda_stream, clv_handle** out) {
+  if (!out || !cfgs || nevents < 1) return fail(nullptr, CLV_EINVAL, "bad arguments");
+  *out = nullptr;
+  const clv_config& c0 = cfgs[0];
+  long long N = 0;
+  double eta_max = 0.0;
+  for (int e = 0; e < nevents; ++e) {
+    const clv_config& c = cfgs[e];
+    clv_status st = validate(&c);
+    if (st != CLV_OK) return st;
+    const bool same_eos =
+        c.eos_kind == c0.eos_kind &&
+        (c.eos_kind != CLV_EOS_TABLE ||
+         (c.eos_n == c0.eos_n && c.eos_lne0 == c0.eos_lne0 && c.eos_dlne == c0.eos_dlne &&
+          std::equal(c.eos_P, c.eos_P + c.eos_n, c0.eos_P) && std::equal(c.eos_T, c.eos_T + c.eos_n, c0.eos_T) &&
+          std::equal(c.eos_cs2, c.eos_cs2 + c.eos_n, c0.eos_cs2)));
+    if (c.tau0 != c0.tau0 || c.dtau != c0.dtau || c.precision != c0.precision || c.cartesian != c0.cartesian ||
+        c.periodic != c0.periodic || c.eps_cut != c0.eps_cut || c.kernel != 0 || !same_eos)
+      return fail(nullptr, CLV_EINVAL,
+                  "batch events must share tau0, dtau, precision, EOS, eps_cut, coordinates and boundaries "
+                  "(kernel 0)");
+    N += (long long)c.nx * c.ny * c.neta;
+    eta_max = std::max(eta_max, c.eta_over_s);
+  }
+  if (N > (1LL << 31) - 1) return fail(nullptr, CLV_EINVAL, "batch too large (at most 2^31 - 1 cells)");
+  clv_config bc = c0;      // the batch as one flat grid of N cells (layout, recovery, stats)
+  bc.nx = (int)N;
+  bc.ny = 1;
+  bc.neta = 1;
+  bc.eta_over_s = eta_max;
+  clv_status st = create_common(&bc, cuda_stream, nullptr, 0, out);
+  if (st != CLV_OK) return st;
+  clv_handle* h = *out;
+  size_t smem_max = 0;
+  const int sms = device_sms(&smem_max);
+  std::vector<std::pair<double, int2>> items;
+  long long off = 0;
+  h->batch.resize(nevents);
+  for (int e = 0; e < nevents; ++e) {
+    auto& ev = h->batch[e];
+    ev.cfg = cfgs[e];
+    ev.cfg.eos_P = ev.cfg.eos_T = ev.cfg.eos_cs2 = nullptr;
+    ev.off = off;
+    ev.N = (long long)ev.cfg.nx * ev.cfg.ny * ev.cfg.neta;
+    ev.viscous = ev.cfg.eta_over_s > 0.0;
+    ev.tile = batch_tile(ev.cfg);
+    off += ev.N;
+    const TileArgs& t = ev.tile;
+    const size_t sm = ev.viscous ? tile_smem_bytes<true>(t.TJ, t.TK, h->rsize) : tile_smem_bytes<false>(t.TJ, t.TK, h->rsize);
+    h->batch_smem = std::max(h->batch_smem, sm);
+    h->batch_threads = std::max(h->batch_threads, (t.TJ + 1) * (t.TK + 1));
+    const int nch = (ev.cfg.nx + t.CX - 1) / t.CX;
+    const int nb = t.ntj * t.ntk * nch;
+    for (int b = 0; b < nb; ++b) {
+      const int ch = b / (t.ntj * t.ntk);
+      const int planes = std::min(t.CX, ev.cfg.nx - ch * t.CX);
+      const double cost = (planes + 4.0) * (t.TJ + 4.0) * (t.TK + 4.0) * (ev.viscous ? 2.0 : 1.0);
+      items.push_back({cost, make_int2(e, b)});
+    }
+  }
+  std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  std::vector<int2> it(items.size());
+  for (size_t i = 0; i < items.size(); ++i) it[i] = items[i].second;
+  h->batch_nitems = (int)it.size();
+  h->batch_blocks = (unsigned)std::min<long long>((long long)sms * CLV_TILE_MIN_BLOCKS, h->batch_nitems);
+  cudaError_t err = h->batch_smem > smem_max ? cudaErrorInvalidValue : cudaSuccess;
+  if (err == cudaSuccess) err = h->rsize == 8 ? batch_upload<double>(h) : batch_upload<float>(h);
+  if (err == cudaSuccess) err = cudaMalloc((void**)&h->batch_items, it.size() * sizeof(int2));
+  if (err == cudaSuccess) err = cudaMemcpy(h->batch_items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  if (err == cudaSuccess) err = cudaMalloc((void**)&h->batch_ctr, 2 * sizeof(int));
+  if (err != cudaSuccess) {
+    clv_destroy(h);
+    *out = nullptr;
+    return fail(nullptr, CLV_ECUDA, std::string("batch setup: ") + cudaGetErrorString(err));
+  }
+  return CLV_OK;
+}
+
+clv_status clv_batch_size(const clv_handle* h, int* nevents, int64_t* cells) {
+  if (!h) return CLV_EINVAL;
+  if (nevents) *nevents = (int)h->batch.size();
+  if (cells) *cells = h->N;
+  return CLV_OK;
+}
+
+clv_status clv_batch_set_initial(clv_handle* h, int event, const double* eps, const double* ux, const double* uy,
+                                 const double* ueta, const double* pi) {
+  if (!h) return CLV_EINVAL;
+  if (h->batch.empty()) return fail(h, CLV_EINVAL, "not a batch (clv_create_batch)");
+  if (event < 0 || event >= (int)h->batch.size()) return fail(h, CLV_EINVAL, "event index out of range");
+  if (h->initialized) return fail(h, CLV_EINVAL, "the batch has started; create a new one");
+  if (!eps || !ux || !uy || !ueta) return fail(h, CLV_EINVAL, "eps, ux, uy and ueta are required");
+  auto& ev = h->batch[event];
+  const double* in[4] = {eps, ux, uy, ueta};
+  clv_status s = h->rsize == 8 ? load_initial_range<double>(h, ev.off, ev.N, ev.viscous, in, pi, true)
+                               : load_initial_range<float>(h, ev.off, ev.N, ev.viscous, in, pi, true);
+  if (s == CLV_OK) ev.set = true;
+  return s;
+}
+
+clv_status clv_batch_get_fields(clv_handle* h, int event, uint32_t mask, double* host_out) {
+  if (!h) return CLV_EINVAL;
+  if (h->batch.empty()) return fail(h, CLV_EINVAL, "not a batch (clv_create_batch)");
+  if (event < 0 || event >= (int)h->batch.size()) return fail(h, CLV_EINVAL, "event index out of range");
+  const auto& ev = h->batch[event];
+  return get_fields_range(h, mask, host_out, true, ev.off, ev.N);
+}
+
+clv_status clv_batch_event_stats(clv_handle* h, int event, clv_stats* out) {
+  if (!h || !out) return CLV_EINVAL;
+  if (h->batch.empty()) return fail(h, CLV_EINVAL, "not a batch (clv_create_batch)");
+  if (event < 0 || event >= (int)h->batch.size()) return fail(h, CLV_EINVAL, "event index out of range");
+  if (!h->initialized) return fail(h, CLV_EINVAL, "the batch has not started (clv_step)");
+  const auto& ev = h->batch[event];
+  const unsigned g = grid_of(ev.N);
+  CLV_CUDA(h, cudaMemsetAsync(&h->dstats->emax_bits, 0, sizeof(unsigned long long), h->stream));
+  if (h->rsize == 8) {
+    stats_scan_kernel<double><<<g, kBlock, 0, h->stream>>>((const double*)h->PR[h->cur][0] + ev.off,
+                                                           (const double*)h->T0[0] + ev.off, ev.N, h->block_sum,
+                                                           &h->dstats->emax_bits);
+  } else {
+    stats_scan_kernel<float><<<g, kBlock, 0, h->stream>>>((const float*)h->PR[h->cur][0] + ev.off,
+                                                          (const float*)h->T0[0] + ev.off, ev.N, h->block_sum,
+                                                          &h->dstats->emax_bits);
+  }
+  h->stat_blocks = (int)g;
+  clv_status s = h->rsize == 8 ? reduce_stats<double>(h, false, out) : reduce_stats<float>(h, false, out);
+  double esum = 0.0;
+  cudaMemcpy(&esum, &h->dstats->esum, sizeof(double), cudaMemcpyDeviceToHost);
+  out->E_tot = esum * ev.cfg.dx * ev.cfg.dy * ev.cfg.deta;
+  return s;
+}
+
 clv_status clv_enable_kernel_timing(clv_handle* h, int enable) {
   if (!h) return CLV_EINVAL;
   h->timing = enable != 0;
@@ -1174,6 +1514,12 @@ void clv_destroy(clv_handle* h) {
   for (cudaEvent_t e : h->ev_pending) cudaEventDestroy(e);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->own_ws && h->ws) cudaFree(h->ws);
+  invalidate_graphs(h);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  cudaFree(h->batch_geom);
+  cudaFree(h->batch_tiles);
+  cudaFree(h->batch_items);
+  cudaFree(h->batch_ctr);
   delete h;
 }
 

@@ -15,9 +15,14 @@ namespace clv {
 constexpr double kHbarC = 0.1973269804;  // GeV fm
 constexpr double kDofConformal = 47.5;   // u, d, s quarks + gluons
 
+// Slot of the symmetric component (m, n) in the packed order tt, tx, ty, te,
+// xx, xy, xe, yy, ye, ee.  Written without recursion: a recursive form is not
+// always folded and then costs a call with a stack frame inside the flux loops.
 __host__ __device__ constexpr int sym_index(int m, int n) {
-  return (m > n) ? sym_index(n, m)
-                 : (m == 0 ? n : (m == 1 ? 3 + n : (m == 2 ? 5 + n : 9)));
+  return (m < n ? m : n) == 0 ? (m < n ? n : m)
+         : (m < n ? m : n) == 1 ? 3 + (m < n ? n : m)
+         : (m < n ? m : n) == 2 ? 5 + (m < n ? n : m)
+                                : 9;
 }
 __host__ __device__ constexpr double metric_sign(int m) { return m == 0 ? 1.0 : -1.0; }
 

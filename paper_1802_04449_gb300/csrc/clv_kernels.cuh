@@ -38,17 +38,21 @@ template <typename R> struct StageParams {
   EosView<R> eos;
   int nx, ny, ne, periodic;
   long long N;
-  // scalars in the working precision (no conversions inside the kernels)
-  R taus;      // tau (Milne) or 1 (Cartesian) at the stage time
-  R geo;       // 1/tau (Milne) or 0 (Cartesian) at the stage time
-  R taus_new;  // tau scale at the end of the step (primitive recovery)
+  // tau of the step lives on the device (advanced by a kernel after every
+  // step), so the launches of a step do not depend on it and a captured step
+  // replays unchanged; tau_scalars() forms the stage's tau factors from it
+  const double* tau_dev;
+  double dtau_d;
+  int cartesian;
+  // scalars in the working precision
   R h, inv_h;  // time step and its inverse
-  R inv_dl[3]; // 1/dx, 1/dy, 1/(tau deta)
+  R inv_dl[2]; // 1/dx, 1/dy
   R st_tau;    // 1 in Milne (S_T^tau active), 0 in Cartesian
   R eps_cut;
   R inv_5etas_hbarc;   // 1/(5 (eta/s) hbar c): 1/tau_pi = T * this
   R polish_E, polish_v;   // FP32: FP64 Newton where the FP32 eps < polish_E or M > polish_v E
   double eps_cut_d;
+  double deta_d;   // d eta_s in FP64 (1/(tau deta) is formed in the kernels, per event in a batch)
   // reductions and error reporting
   double* block_sum;             // per block: sum of new T~^{tau tau} (stats launches only)
   unsigned long long* emax_bits; // max eps as the bits of a non-negative double
@@ -83,6 +87,28 @@ template <> struct SolveTraits<double> {
 
 // Reconstructed interface quantities (KT, Eq. flux_out): T~^{tau mu} (4),
 // pi~ (10), u~^tau, v^a = u~^a/u~^tau, P.
+// The tau factors of a stage, rounded to R exactly as a host computation in
+// FP64 would be: tau_s = tau at the stage (stage 1: tau_n, stage 2:
+// tau_n + dtau), or 1 in Cartesian coordinates.
+template <typename R> struct TauS {
+  double taus_d;   // tau_s in FP64
+  R taus;          // tau_s
+  R geo;           // 1/tau_s (Milne) or 0 (Cartesian)
+  R taus_new;      // tau scale at the end of the step (primitive recovery)
+};
+template <typename R>
+__device__ __forceinline__ TauS<R> tau_scalars(const StageParams<R>& p, int stage) {
+  const double tn = *p.tau_dev;
+  const double tn1 = tn + p.dtau_d;
+  const double tst = stage == 1 ? tn : tn1;
+  TauS<R> t;
+  t.taus_d = p.cartesian ? 1.0 : tst;
+  t.taus = (R)t.taus_d;
+  t.geo = (R)(p.cartesian ? 0.0 : 1.0 / tst);
+  t.taus_new = (R)(p.cartesian ? 1.0 : tn1);
+  return t;
+}
+
 template <bool VISC> struct NRec { static constexpr int n = VISC ? 17 : 7; };
 
 template <typename R, bool VISC>
@@ -220,7 +246,9 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
     constexpr int NR = NRec<VISC>::n;
     constexpr int NQ = VISC ? 14 : 4;
     constexpr int IU = VISC ? 14 : 4, IV = IU + 1;
-    const R taus = p.taus;
+    const TauS<R> ts = tau_scalars(p, STAGE);
+    const R taus = ts.taus;
+    const R inv_dl[3] = {p.inv_dl[0], p.inv_dl[1], (R)(1.0 / (ts.taus_d * p.deta_d))};
     R S[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) S[q] = R(0);
@@ -278,7 +306,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       R Hm[NQ], Hp[NQ];
       interface_flux<R, VISC>(Lm, Rm, cs[1], cs[2], ax, taus, Hm);
       interface_flux<R, VISC>(Lp, Rp, cs[2], cs[3], ax, taus, Hp);
-      const R inv = p.inv_dl[ax - 1];
+      const R inv = inv_dl[ax - 1];
 #pragma unroll
       for (int q = 0; q < NQ; ++q) S[q] -= (Hp[q] - Hm[q]) * inv;
     }
@@ -298,7 +326,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       R Tee = e * u[3] * u[3] + Pc * (R(1) + u[3] * u[3]);
       if constexpr (VISC) Tee += pic[9];
       S[0] -= p.st_tau * Tee;
-      S[3] -= p.geo * p.T[3][c];
+      S[3] -= ts.geo * p.T[3][c];
     }
     // u~ at step n and the late velocity (u* in stage 1, u' in stage 2)
     R un[4], ul[4];
@@ -328,7 +356,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       for (int b = 0; b < 4; ++b) du[0][b] = (ul[b] - un[b]) * invh;
 #pragma unroll
       for (int a = 1; a <= 3; ++a) {
-        const R half_inv = R(0.5) * p.inv_dl[a - 1];
+        const R half_inv = R(0.5) * inv_dl[a - 1];
 #pragma unroll
         for (int b = 0; b < 4; ++b) du[a][b] = (unb[a - 1][1][b] - unb[a - 1][0][b]) * half_inv;
       }
@@ -336,7 +364,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       eos_eval<R, R>(p.eos, e, Pdummy, Tc, c2dummy);
       const R inv_taupi = Tc * p.inv_5etas_hbarc;
       R Spi[10];
-      shear_source<R>(p.geo, u, du, pic, e, Pc, inv_taupi, Spi);
+      shear_source<R>(ts.geo, u, du, pic, e, Pc, inv_taupi, Spi);
 #pragma unroll
       for (int q = 0; q < 10; ++q) S[4 + q] += Spi[q];
     }
@@ -363,7 +391,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       }
     }
     // ---------------- primitive recovery from T_ideal = T - pi ----------------
-    const R tn = p.taus_new;
+    const R tn = tau_scalars(p, 1).taus_new;
     R E = Tnew[0] / tn, Mx = Tnew[1] / tn, My = Tnew[2] / tn, Me = Tnew[3] / tn;
     if constexpr (VISC) {
       E -= pinew[0]; Mx -= pinew[1]; My -= pinew[2]; Me -= pinew[3];
@@ -459,7 +487,7 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
   double my_T0 = 0.0, my_e = 0.0;
   int my_iters = 0, my_solved = 0, my_polish_iters = 0;
   bool f_rescaled = false, f_fail = false, f_polished = false, f_nonfinite = false, f_nonconv = false;
-  const R tn = p.taus_new;
+  const R tn = tau_scalars(p, 1).taus_new;
   R T0v = R(0), E = R(0), Mx = R(0), My = R(0), Me = R(0);
   if (active) {
     T0v = p.Tout[0][c];

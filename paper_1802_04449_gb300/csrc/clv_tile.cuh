@@ -37,6 +37,17 @@ struct TileArgs {
   int ntj, ntk;       // tiles per plane
 };
 
+// Grid of one event: its cells start at `off` in every field array (one
+// event: off = 0; a batch stores its events back to back).
+template <typename R> struct EventGeom {
+  long long off;
+  int nx, ny, ne;
+  R inv_dx, inv_dy;
+  R inv_5etas_hbarc;
+  double deta;
+  int viscous;        // batch: 1 if the event has eta/s > 0
+};
+
 // Per-cell inputs of the output cell that are not staged with the planes
 // (eps, u~^{n-1}; in stage 2 also u~^n, T~^n, pi~^n), prefetched one plane
 // ahead into a per-thread double buffer.
@@ -61,17 +72,18 @@ template <bool VISC> inline size_t tile_smem_bytes(int TJ, int TK, size_t rsize)
   return elems * rsize + NB * sizeof(int);
 }
 
-// Issue the asynchronous copies of the plane at offset poff (= plane index x
-// ny x ne) of the tile (with its y/eta halo) into a box buffer: T~, pi~, P,
-// c_s to their slots, u~ into the v slots (the conversion pass turns them into
-// u~^tau and v once the copies land).  goff[q]: in-plane offset of box cell q
-// (boundary wrap or clamp already applied).  Thread tid handles the box
-// cells q = tid, tid + nthr, ...; the caller commits the group.
+// Issue the asynchronous copies of the plane at offset poff (event offset +
+// plane index x ny x ne) of the tile (with its y/eta halo) into a box buffer
+// of NB cells per field: T~, pi~, P, c_s to their slots, u~ into the v slots
+// (the conversion pass turns them into u~^tau and v once the copies land).
+// goff[q]: in-plane offset of box cell q (boundary wrap or clamp applied).
+// Thread tid handles the box cells q = tid, tid + nthr, ... < qend; the
+// caller commits the group.
 template <typename R, bool VISC>
-__device__ __forceinline__ void stage_plane_async(const StageParams<R>& p, R* box, int NB, long long poff,
-                                                  const int* goff, int tid, int nthr) {
+__device__ __forceinline__ void stage_plane_async(const StageParams<R>& p, R* box, int qend, long long poff,
+                                                  const int* goff, int tid, int nthr, int NB) {
   using L = Box<VISC>;
-  for (int q = tid; q < NB; q += nthr) {
+  for (int q = tid; q < qend; q += nthr) {
     const long long g = poff + goff[q];
 #pragma unroll
     for (int m = 0; m < 4; ++m) cp_async_elem(box + m * NB + q, p.T[m] + g);
@@ -145,11 +157,14 @@ __device__ __forceinline__ void box_interface(const R* box, int NB, int c, int s
 #define CLV_TILE_MIN_BLOCKS 1
 #endif
 
+// One tile-chunk (index bidx within its event) of a stage; every thread of
+// the block calls it (threads beyond the tile's (TJ+1)(TK+1) only take part
+// in the barriers).
 template <typename R, int STAGE, bool VISC>
-__global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) stage_tile_kernel(const StageParams<R> p, const TileArgs t) {
+__device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const EventGeom<R>& ev, const TileArgs& t,
+                                                int bidx, unsigned char* smem_raw) {
   using L = Box<VISC>;
   constexpr int NF = L::NF, NQ = L::NQ, NR = L::NR, NPEND = L::NPEND;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int BW = t.TK + 4, NB = BW * (t.TJ + 4);
   const int NHY = (t.TJ + 1) * t.TK, NHK = t.TJ * (t.TK + 1);
   const int ncell = t.TJ * t.TK;
@@ -161,23 +176,28 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
   R* cellbuf = pend + 2 * NPEND * ncell;             // [2][CI::n][ncell]
   int* goff = reinterpret_cast<int*>(cellbuf + 2 * CellIn<2, VISC>::n * ncell);  // [NB]
 
-  const int tid = threadIdx.x;
   const int nthr = (t.TJ + 1) * (t.TK + 1);
+  const bool worker = threadIdx.x < nthr;
+  // threads beyond the tile act as a copy of thread 0 that skips every
+  // shared-memory write and every output (only the barriers need them)
+  const int tid = worker ? (int)threadIdx.x : 0;
   const int ta = tid / (t.TK + 1), tb = tid - ta * (t.TK + 1);
-  int bidx = blockIdx.x;
   const int tkt = bidx % t.ntk;
   bidx /= t.ntk;
   const int tjt = bidx % t.ntj;
   const int ch = bidx / t.ntj;
   const int j0 = tjt * t.TJ, k0 = tkt * t.TK, x0 = ch * t.CX;
-  const int x1 = min(x0 + t.CX, p.nx);
-  const bool is_cell = ta < t.TJ && tb < t.TK;
+  const int x1 = min(x0 + t.CX, ev.nx);
+  const bool is_cell = worker && ta < t.TJ && tb < t.TK;
   const int j = j0 + ta, k = k0 + tb;
-  const bool active = is_cell && j < p.ny && k < p.ne;
+  const bool active = is_cell && j < ev.ny && k < ev.ne;
   const int cid = ta * t.TK + tb;                  // cell slot (valid when is_cell)
   const int center = (ta + 2) * BW + (tb + 2);     // box cell of (ta, tb)
-  const R taus = p.taus;
-  const R inv_dx = p.inv_dl[0];
+  const TauS<R> ts = tau_scalars(p, STAGE);
+  const R taus = ts.taus;
+  const R inv_dx = ev.inv_dx;
+  const R inv_dy = ev.inv_dy;
+  const R inv_de = (R)(1.0 / (ts.taus_d * ev.deta));   // 1/(tau deta)
 
   R W0[NF], W1[NF];      // staged fields of the own column at planes pl-2, pl-1
   R S0[NR];              // x-slope at plane pl-2
@@ -194,13 +214,14 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
 
 
   // in-plane offsets of this thread's box cells (only this thread uses them)
-  for (int q = tid; q < NB; q += nthr) {
+  const int qend = worker ? NB : 0;   // box cells this thread stages: q = tid, tid + nthr, ... < qend
+  for (int q = tid; q < qend; q += nthr) {
     const int bj = q / BW, bk = q - bj * BW;
-    goff[q] = wrap_index(j0 + bj - 2, p.ny, p.periodic) * p.ne + wrap_index(k0 + bk - 2, p.ne, p.periodic);
+    goff[q] = wrap_index(j0 + bj - 2, ev.ny, p.periodic) * ev.ne + wrap_index(k0 + bk - 2, ev.ne, p.periodic);
   }
-  const long long plane = (long long)p.ny * p.ne;
-  stage_plane_async<R, VISC>(p, boxbuf + ((x0 - 2) & 1) * NF * NB, NB, wrap_index(x0 - 2, p.nx, p.periodic) * plane,
-                             goff, tid, nthr);
+  const long long plane = (long long)ev.ny * ev.ne;
+  stage_plane_async<R, VISC>(p, boxbuf + ((x0 - 2) & 1) * NF * NB, qend,
+                             ev.off + wrap_index(x0 - 2, ev.nx, p.periodic) * plane, goff, tid, nthr, NB);
   cp_async_commit();
   for (int pl = x0 - 2; pl <= x1 + 1; ++pl) {
     const bool out_plane = pl >= x0 && pl < x1;
@@ -209,7 +230,7 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
     // the output cell) have landed: its u~ -> (u~^tau, v) in place, then one
     // barrier makes the whole plane visible
     cp_async_wait_all();
-    for (int q = tid; q < NB; q += nthr) {
+    for (int q = tid; q < qend; q += nthr) {
       const R ux = box[L::V * NB + q], uy = box[(L::V + 1) * NB + q], ue = box[(L::V + 2) * NB + q];
       const R ut = sqrt(R(1) + ux * ux + uy * uy + ue * ue);
       const R iu = R(1) / ut;
@@ -222,22 +243,22 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
     // prefetch the next plane into the other buffer while this one is used,
     // with the per-cell inputs of the cell output two planes on (pl - 1)
     if (pl + 1 <= x1 + 1) {
-      stage_plane_async<R, VISC>(p, boxbuf + ((pl + 1) & 1) * NF * NB, NB,
-                                 wrap_index(pl + 1, p.nx, p.periodic) * plane, goff, tid, nthr);
+      stage_plane_async<R, VISC>(p, boxbuf + ((pl + 1) & 1) * NF * NB, qend,
+                                 ev.off + wrap_index(pl + 1, ev.nx, p.periodic) * plane, goff, tid, nthr, NB);
       if (active && pl - 1 >= x0 && pl - 1 < x1)
         prefetch_cell<R, STAGE, VISC>(p, cellbuf + (size_t)((pl - 1) & 1) * CI::n * ncell + cid, ncell,
-                                      ((long long)(pl - 1) * p.ny + j) * p.ne + k);
+                                      ev.off + ((long long)(pl - 1) * ev.ny + j) * ev.ne + k);
       cp_async_commit();
     }
     // ---- 2. every y- and eta-interface of an output plane, once
     if (out_plane) {
       R H[NQ];
-      if (tb < t.TK) {   // y-interface between rows ta-1 and ta of column tb
+      if (worker && tb < t.TK) {   // y-interface between rows ta-1 and ta of column tb
         box_interface<R, VISC>(box, NB, (ta + 2) * BW + tb + 2, BW, 2, taus, H);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) Hy[q * NHY + ta * t.TK + tb] = H[q];
       }
-      if (ta < t.TJ) {   // eta-interface between columns tb-1 and tb of row ta
+      if (worker && ta < t.TJ) {   // eta-interface between columns tb-1 and tb of row ta
         box_interface<R, VISC>(box, NB, (ta + 2) * BW + tb + 2, 1, 3, taus, H);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) Hk[q * NHK + ta * (t.TK + 1) + tb] = H[q];
@@ -269,7 +290,7 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
           if (it >= 4 && active) {
             // ============ output cell c = pl - 2 (own fields: W0) ============
             const int c = pl - 2;
-            const long long gc = ((long long)c * p.ny + j) * p.ne + k;
+            const long long gc = ev.off + ((long long)c * ev.ny + j) * ev.ne + k;
             const R* pd = pend + (size_t)(c & 1) * NPEND * ncell;
             const R* cb = cellbuf + (size_t)(c & 1) * CI::n * ncell + cid;
             R S[NQ];
@@ -286,7 +307,7 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
               R Tee = e * u[3] * u[3] + Pc * (R(1) + u[3] * u[3]);
               if constexpr (VISC) Tee += W0[4 + 9];
               S[0] -= p.st_tau * Tee;
-              S[3] -= p.geo * W0[3];
+              S[3] -= ts.geo * W0[3];
             }
             R un[4];
             if constexpr (STAGE == 1) {
@@ -326,11 +347,11 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
               }
               R Pd, Tc, c2d;
               eos_eval<R, R>(p.eos, e, Pd, Tc, c2d);
-              const R inv_taupi = Tc * p.inv_5etas_hbarc;
+              const R inv_taupi = Tc * ev.inv_5etas_hbarc;
               R pic[10], Spi[10];
 #pragma unroll
               for (int r = 0; r < 10; ++r) pic[r] = W0[4 + r];
-              shear_source<R>(p.geo, u, du, pic, e, Pc, inv_taupi, Spi);
+              shear_source<R>(ts.geo, u, du, pic, e, Pc, inv_taupi, Spi);
 #pragma unroll
               for (int r = 0; r < 10; ++r) S[4 + r] += Spi[r];
             }
@@ -384,7 +405,7 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
       // ---- 3. y and eta_s flux differences of plane pl, consumed two planes later
       if (out_plane && active) {
         R* pd = pend + (size_t)(pl & 1) * NPEND * ncell;
-        const R iy = p.inv_dl[1], ie = p.inv_dl[2];
+        const R iy = inv_dy, ie = inv_de;
         const int hy = ta * t.TK + tb, hk = ta * (t.TK + 1) + tb;
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
@@ -395,7 +416,7 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
 #pragma unroll
           for (int ax = 2; ax <= 3; ++ax) {
             const int stride = ax == 2 ? BW : 1;
-            const R hinv = R(0.5) * p.inv_dl[ax - 1];
+            const R hinv = R(0.5) * (ax == 2 ? inv_dy : inv_de);
             const R utp = box[L::UT * NB + center + stride], utm = box[L::UT * NB + center - stride];
 #pragma unroll
             for (int b2 = 0; b2 < 4; ++b2) {
@@ -407,6 +428,39 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS) sta
         }
       }
     }
+  }
+}
+
+template <typename R, int STAGE, bool VISC>
+__global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS)
+    stage_tile_kernel(const StageParams<R> p, const TileArgs t) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const EventGeom<R> ev{0, p.nx, p.ny, p.ne, p.inv_dl[0], p.inv_dl[1], p.inv_5etas_hbarc, p.deta_d, VISC ? 1 : 0};
+  stage_tile_body<R, STAGE, VISC>(p, ev, t, blockIdx.x, smem_raw);
+}
+
+// A batch of events stored back to back: one persistent launch (a CTA per
+// SM) takes work items (event, tile-chunk index), most expensive first, from
+// an atomic counter until none is left.  ANY_VISC: viscous events run the
+// viscous body, the others the ideal one (false: all ideal, the first-step
+// predictor).  Counters only grow; no CTA waits for another.
+template <typename R, int STAGE, bool ANY_VISC>
+__global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS)
+    stage_batch_kernel(const StageParams<R> p, const EventGeom<R>* __restrict__ evs,
+                       const TileArgs* __restrict__ tiles, const int2* __restrict__ items, int nitems, int* next) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();   // the previous item is done with shared memory and s_item
+    if (threadIdx.x == 0) s_item = atomicAdd(next, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) return;
+    const int2 w = items[it];
+    const EventGeom<R> ev = evs[w.x];
+    const TileArgs t = tiles[w.x];
+    if (ANY_VISC && ev.viscous) stage_tile_body<R, STAGE, true>(p, ev, t, w.y, smem_raw);
+    else stage_tile_body<R, STAGE, false>(p, ev, t, w.y, smem_raw);
   }
 }
 

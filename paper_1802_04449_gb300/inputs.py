@@ -288,6 +288,53 @@ def minijet_event(nx=261, ny=261, neta=121, dx=0.08, deta=0.1, b=7.0, n_spots=80
                      z.copy(), z.copy(), z.copy(), z.copy(), nsteps, T0=T0)
 
 
+def binary_overlap(b, n=201):
+    """N_bin(b) up to a constant: the integral of T_A(x + b/2, y) T_B(x - b/2, y)."""
+    lim = WS_R + 4 * WS_A + b / 2
+    x = np.linspace(-lim, lim, n)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    return float((thickness(X + b / 2, Y) * thickness(X - b / 2, Y)).sum() * (x[1] - x[0]) ** 2)
+
+
+_SPOT_AMP = {}
+
+
+def spot_amplitude():
+    """Per-spot amplitude of the 97x97x41 hot-spot event (seed 12345): the
+    factor that makes its max eps 55 GeV/fm^3."""
+    if "a" not in _SPOT_AMP:
+        rng = np.random.default_rng(12345)
+        xs, ys, etas = sample_spots(rng, 2048, 7.0, 20 * 0.2)
+        _SPOT_AMP["a"] = 55.0 / deposit_spots(97, 97, 41, 0.2, 0.2, 0.2, xs, ys, etas, 1.0).max()
+    return _SPOT_AMP["a"]
+
+
+def batch_events(n=256, seed0=1000, tau0=0.4, dtau=0.01, eos="crossover", nsteps=200):
+    """Event-by-event batch: event k (seed seed0 + k) draws nx = ny odd in
+    [65, 129], neta odd in [21, 61], dx uniform in [0.15, 0.3] fm with
+    d eta = dx, b uniform in [0, 12] fm and eta/s from {0, 0.08, 0.16}; its
+    N_spots = round(2048 N_bin(b) / N_bin(7)) spots carry the per-spot
+    amplitude of the 97x97x41 event.  Zero initial velocity and pi."""
+    amp = spot_amplitude()
+    nb7 = binary_overlap(7.0)
+    tab = crossover_eos() if eos == "crossover" else None
+    out = []
+    for k in range(n):
+        rng = np.random.default_rng(seed0 + k)
+        nx = int(rng.integers(32, 65)) * 2 + 1
+        neta = int(rng.integers(10, 31)) * 2 + 1
+        dx = float(rng.uniform(0.15, 0.3))
+        b = float(rng.uniform(0.0, 12.0))
+        eta_over_s = float(rng.choice([0.0, 0.08, 0.16]))
+        n_spots = max(1, int(round(2048 * binary_overlap(b) / nb7)))
+        xs, ys, etas = sample_spots(rng, n_spots, b, (neta - 1) / 2.0 * dx)
+        eps = deposit_spots(nx, nx, neta, dx, dx, dx, xs, ys, etas, amp)
+        z = np.zeros_like(eps)
+        out.append(HydroCase(f"batch event {k}", nx, nx, neta, dx, dx, dx, tau0, dtau, eta_over_s, tab,
+                             eps, z, z, z, nsteps))
+    return out
+
+
 def gubser_case(dx=0.3, nx=33, neta=9, deta=0.3, dtau=0.02, tau0=1.0, tau1=3.0, q=1.0):
     """Ideal Gubser flow, conformal EOS, eta/s = 0 (the 33x33x9 check)."""
     x = cell_coords(nx, dx)

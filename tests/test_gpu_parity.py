@@ -330,3 +330,86 @@ def test_checkpoint_restart_is_bitwise(prec):
         c.set_state(state)
     with pytest.raises(clv.ClvError):
         b.set_state(state[:100])
+
+
+@pytest.mark.parametrize("prec", [clv.CLV_FP64, clv.CLV_FP32])
+def test_batch_of_uneven_events_equals_single_events(prec):
+    """Events of different grids and eta/s (ideal and viscous) in one batch:
+    one persistent stage launch and one root-solve launch per stage give
+    each event the fields of its own single-event run -- the same stage body
+    and root solve, so FP64 agrees bit for bit and FP32 to its rounding (the
+    batched kernel is a separate instantiation, free to contract products
+    into fused multiply-adds differently)."""
+    cases = [
+        I.hotspot_event(nx=23, ny=21, neta=13, n_spots=60, seed=41, eta_over_s=0.08),
+        I.hotspot_event(nx=17, ny=25, neta=7, dx=0.25, deta=0.25, n_spots=40, seed=42, eta_over_s=0.0),
+        I.hotspot_event(nx=31, ny=19, neta=41, dx=0.15, deta=0.15, n_spots=80, seed=43, eta_over_s=0.16),
+        I.hotspot_event(nx=5, ny=3, neta=1, n_spots=4, seed=44, eta_over_s=0.08),
+    ]
+    nsteps = 5
+    b = clv.Batch(cases, prec)
+    assert b.nevents == 4 and b.N == sum(c.ncells for c in cases)
+    for e, c in enumerate(cases):
+        b.set_event(e, c.eps, c.ux, c.uy, c.ueta)
+    b.step(1)
+    b.enable_kernel_timing(True)       # per-kernel events: four slots per step, all filled
+    st = b.step(nsteps - 1, stats=True)
+    kt = b.kernel_times()
+    assert all(n == nsteps - 1 and ms > 0 for ms, n in kt.values()), kt
+    assert st["error_word"] == 0 and st["E_tot"] == 0.0
+    names = ["eps", "ux", "uy", "ueta", "Ttt", "Ttx", "Tte", "pixx", "pixy", "piee", "upx"]
+    for e, c in enumerate(cases):
+        g = clv.from_case(c, prec)
+        g.set_initial(c.eps, c.ux, c.uy, c.ueta)
+        sg = g.step(nsteps, stats=True)
+        ref, got = g.get(names), b.get_event(e, names)
+        rtol = 0.0 if prec == clv.CLV_FP64 else 2e-6
+        for k in names:
+            scale = np.abs(ref[k]).max()
+            assert np.all(np.abs(got[k] - ref[k]) <= rtol * (np.abs(ref[k]) + 1e-3 * scale)), (e, k)
+        es = b.event_stats(e)
+        assert es["eps_max"] == pytest.approx(sg["eps_max"], rel=rtol)
+        assert es["E_tot"] == pytest.approx(sg["E_tot"], rel=max(rtol, 1e-12))
+    # calls that do not apply to a batch
+    flat = np.zeros(b.N)
+    with pytest.raises(clv.ClvError):
+        b.set_initial(flat, flat, flat, flat)
+    with pytest.raises(clv.ClvError):
+        b.autotune()
+    with pytest.raises(clv.ClvError):
+        b.set_event(0, cases[0].eps, cases[0].ux, cases[0].uy, cases[0].ueta)   # already started
+
+
+def test_batch_needs_every_event_and_a_common_setup():
+    a = I.hotspot_event(nx=9, ny=9, neta=5, n_spots=10, seed=1)
+    c = I.hotspot_event(nx=11, ny=7, neta=3, n_spots=10, seed=2)
+    b = clv.Batch([a, c], clv.CLV_FP64)
+    b.set_event(0, a.eps, a.ux, a.uy, a.ueta)
+    with pytest.raises(clv.ClvError):
+        b.step(1)                                  # event 1 has no initial state
+    d = I.hotspot_event(nx=9, ny=9, neta=5, n_spots=10, seed=3, dtau=0.02)
+    with pytest.raises(clv.ClvError):
+        clv.Batch([a, d], clv.CLV_FP64)            # different dtau
+
+
+@pytest.mark.parametrize("prec,eta_over_s", [(clv.CLV_FP64, 0.08), (clv.CLV_FP32, 0.16), (clv.CLV_FP32, 0.0)])
+def test_step_graphs_equal_direct_launches(prec, eta_over_s):
+    """Pairs of steps replayed from a captured graph (tau on the device) give
+    the fields and tau of directly launched steps bit for bit, with stats
+    steps and odd counts interleaved, and on a non-default stream."""
+    import torch
+    case = small_hotspot(seed=23, eta_over_s=eta_over_s)
+    runs = []
+    for graphs, stream in ((False, None), (True, None), (True, torch.cuda.Stream())):
+        g = clv.from_case(case, prec, stream=stream)
+        g.set_graphs(graphs)
+        g.set_initial(case.eps, case.ux, case.uy, case.ueta)
+        g.step(5)
+        st = g.step(4, stats=True)
+        g.step(3)
+        runs.append((g.get(["eps", "ux", "ueta", "Ttt", "pixy"]), g.time(), st))
+    for fields, t, st in runs[1:]:
+        assert t == runs[0][1]
+        assert st["eps_max"] == runs[0][2]["eps_max"] and st["E_tot"] == runs[0][2]["E_tot"]
+        for k in fields:
+            assert np.array_equal(fields[k], runs[0][0][k]), k
