@@ -408,7 +408,8 @@ def run_gpu(args):
         "batch": batch,
         "roofline": roof,
         "e2e": e2e,
-        "gpu_launches": 4 * args.steps,
+        # per step: two stages of (stage kernel, root solve) and the tau advance
+        "gpu_launches": 5 * args.steps,
         "clocks": clocks,
         "stats_fp32": {k: st32.get(k) for k in ("tau", "eps_max", "T_max", "E_tot", "n_polished", "n_rootfail",
                                                 "n_fp32_nonconverged", "error_word", "error", "tile")},

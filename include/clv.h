@@ -76,6 +76,9 @@ typedef struct {
   double eps_cut;            /* vacuum cutoff, GeV/fm^3 (the paper uses 1e-7) */
   int kernel;                /* 0: tiled stage kernel (default); 1: direct per-cell stage kernel
                                 (same arithmetic, simpler data flow; kept for cross-checks) */
+  double taupi_coef;         /* b in tau_pi = b eta_v / (eps + P); 0 means 5 (the paper's choice) */
+  double lambda1_hat;        /* lambda_1 = lambda1_hat / eps in Eq. (pimn) (conformal scaling);
+                                0: no lambda_1 term (the default) */
 } clv_config;
 
 /* Per-run statistics, filled by clv_step / clv_get_stats. */

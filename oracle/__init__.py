@@ -66,6 +66,7 @@ class _Config(ctypes.Structure):
         ("eos_cs2", ctypes.POINTER(ctypes.c_double)),
         ("cartesian", ctypes.c_int), ("periodic", ctypes.c_int),
         ("eps_cut", ctypes.c_double), ("nthreads", ctypes.c_int),
+        ("taupi_coef", ctypes.c_double), ("lambda1_hat", ctypes.c_double),
     ]
 
 
@@ -111,7 +112,8 @@ class Oracle:
     ``lne0, dlne, P, T, cs2`` (nodes uniform in ln eps)."""
 
     def __init__(self, nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
-                 cartesian=False, periodic=False, eps_cut=1e-7, nthreads=0, plant=0):
+                 cartesian=False, periodic=False, eps_cut=1e-7, nthreads=0, plant=0, taupi_coef=5.0,
+                 lambda1_hat=0.0):
         self._lib = _load(plant)
         c = _Config()
         c.nx, c.ny, c.neta = int(nx), int(ny), int(neta)
@@ -130,6 +132,7 @@ class Oracle:
             c.eos_P, c.eos_T, c.eos_cs2 = (_dp(a) for a in arrs)
         c.cartesian, c.periodic = int(bool(cartesian)), int(bool(periodic))
         c.eps_cut, c.nthreads = float(eps_cut), int(nthreads)
+        c.taupi_coef, c.lambda1_hat = float(taupi_coef), float(lambda1_hat)
         self.shape = (int(nx), int(ny), int(neta))
         self._h = self._lib.orc_create(ctypes.byref(c))
         if not self._h:

@@ -105,6 +105,8 @@ typedef struct {
   int periodic;     /* 1: periodic ghosts, 0: zero-gradient ghosts */
   double eps_cut;
   int nthreads;
+  double taupi_coef;   /* b in tau_pi = b eta_v / (eps + P); 0 -> 5 (reading R10) */
+  double lambda1_hat;  /* lambda_1 = lambda1_hat / eps (conformal scaling); 0 -> no lambda_1 term */
 } orc_config;
 
 typedef struct {
@@ -238,7 +240,8 @@ static void T_from_prim(double taus, double e, double P, const double u[4], cons
 /* ---------------- viscous source S_pi (Sec. 2, R2, R3, R16) ---------- */
 /* du[a*4+b] = d~_a u~^b (a: tau, x, y, eta; tilde derivative d~_eta = d_eta/tau). */
 static void source_pi(double g, const double u[4], const double du[16], const double pi[NPI],
-                      double e, double P, double T, double eta_over_s, double S[NPI]) {
+                      double e, double P, double T, double eta_over_s, double taupi_coef,
+                      double lambda1_hat, double S[NPI]) {
   double cov[4][4];
   for (int a = 0; a < 4; ++a)
     for (int b = 0; b < 4; ++b) cov[a][b] = du[a * 4 + b];
@@ -251,7 +254,34 @@ static void source_pi(double g, const double u[4], const double du[16], const do
     Du[b] = 0.0;
     for (int a = 0; a < 4; ++a) Du[b] += u[a] * cov[a][b];
   }
-  double inv_taupi = (eta_over_s > 0.0) ? T / (5.0 * eta_over_s * HBARC) : 0.0;
+  /* tau_pi = b eta_v / (eps + P) = b (eta/s) hbar c / T, so eta_v / tau_pi = (eps + P) / b */
+  double b = (taupi_coef > 0.0) ? taupi_coef : 5.0;
+  double inv_taupi = (eta_over_s > 0.0) ? T / (b * eta_over_s * HBARC) : 0.0;
+  /* lambda_1 pi^<mu_lambda pi^nu>lambda of Eq. (pimn), in tilde components
+     (the tilde metric contracts them like orthonormal ones): Y = pi g~ pi,
+     X = Delta^mu_a Delta^nu_b Y^ab - Delta^mu nu (Delta_ab Y^ab) / 3 */
+  double X[4][4] = {{0}};
+  if (lambda1_hat != 0.0 && e > 0.0) {
+    double Y[4][4], Dm[4][4];
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 4; ++c) {
+        double y = 0.0;
+        for (int d = 0; d < 4; ++d) y += pi[PI_IDX[a][d]] * GT[d] * pi[PI_IDX[d][c]];
+        Y[a][c] = y;
+        Dm[a][c] = (a == c ? 1.0 : 0.0) - u[a] * GT[c] * u[c];   /* Delta^a_c */
+      }
+    double tr = 0.0;   /* Delta_ab Y^ab */
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 4; ++c) tr += ((a == c ? GT[a] : 0.0) - GT[a] * u[a] * GT[c] * u[c]) * Y[a][c];
+    for (int m = 0; m < 4; ++m)
+      for (int n = 0; n < 4; ++n) {
+        double x = 0.0;
+        for (int a = 0; a < 4; ++a)
+          for (int c = 0; c < 4; ++c) x += Dm[m][a] * Dm[n][c] * Y[a][c];
+        X[m][n] = x - ((m == n ? GT[m] : 0.0) - u[m] * u[n]) * tr / 3.0;
+      }
+  }
+  const double l1 = (e > 0.0) ? lambda1_hat / e : 0.0;   /* lambda_1 */
   for (int m = 0; m < 4; ++m)
     for (int n = m; n < 4; ++n) {
       int id = PI_IDX[m][n];
@@ -259,8 +289,9 @@ static void source_pi(double g, const double u[4], const double du[16], const do
       double grad_nm = (PLANT == 5) ? GT[m] * cov[m][n] : GT[n] * cov[n][m];
       double Delta = (m == n ? GT[m] : 0.0) - u[m] * u[n];
       double sigma = grad_mn + grad_nm - u[m] * Du[n] - u[n] * Du[m] - (2.0 / 3.0) * Delta * theta;
-      double s = -pi[id] * inv_taupi + (e + P) * sigma / 5.0;
+      double s = -pi[id] * inv_taupi + (e + P) * sigma / b;
       s -= pi[id] * theta / 3.0;
+      s -= l1 * inv_taupi * X[m][n];
       double acc = 0.0;
       for (int b = 0; b < 4; ++b)
         acc += GT[b] * (u[m] * pi[PI_IDX[n][b]] + u[n] * pi[PI_IDX[m][b]]) * Du[b];
@@ -454,7 +485,7 @@ static void stage_source(const orc_t* h, const orc_fields* f, int viscous, doubl
   }
   double pi[NPI], Spi[NPI];
   for (int q = 0; q < NPI; ++q) pi[q] = f->pi[q][c0];
-  source_pi(g, u, du, pi, e, P, T, h->c.eta_over_s, Spi);
+  source_pi(g, u, du, pi, e, P, T, h->c.eta_over_s, h->c.taupi_coef, h->c.lambda1_hat, Spi);
   for (int q = 0; q < NPI; ++q) S[4 + q] += Spi[q];
 }
 
@@ -761,7 +792,7 @@ void orc_source_pi(const orc_t* h, double tau, const double u[4], const double d
                    const double pi[NPI], double e, double out[NPI]) {
   double P, T, cs2;
   eos_eval(h, e, &P, &T, &cs2);
-  source_pi(geo(h, tau), u, du, pi, e, P, T, h->c.eta_over_s, out);
+  source_pi(geo(h, tau), u, du, pi, e, P, T, h->c.eta_over_s, h->c.taupi_coef, h->c.lambda1_hat, out);
 }
 
 /* Geometric source S_T at one cell: needs eps, u~, pi~^{eta eta} and T~^{tau eta}. */

@@ -40,6 +40,7 @@ class clv_config(ctypes.Structure):
         ("eos_cs2", ctypes.POINTER(ctypes.c_double)),
         ("precision", ctypes.c_int), ("cartesian", ctypes.c_int), ("periodic", ctypes.c_int),
         ("eps_cut", ctypes.c_double), ("kernel", ctypes.c_int),
+        ("taupi_coef", ctypes.c_double), ("lambda1_hat", ctypes.c_double),
     ]
 
 
@@ -154,8 +155,10 @@ def _dp(a):
 
 
 def make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
-                precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7, kernel=0):
+                precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7, kernel=0,
+                taupi_coef=0.0, lambda1_hat=0.0):
     c = clv_config()
+    c.taupi_coef, c.lambda1_hat = float(taupi_coef), float(lambda1_hat)
     c.nx, c.ny, c.neta = int(nx), int(ny), int(neta)
     c.dx, c.dy, c.deta = float(dx), float(dy), float(deta)
     c.tau0, c.dtau, c.eta_over_s = float(tau0), float(dtau), float(eta_over_s)
@@ -182,13 +185,14 @@ class Hydro:
 
     def __init__(self, nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
                  precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7,
-                 stream=None, device=None, torch_workspace=True, kernel=0):
+                 stream=None, device=None, torch_workspace=True, kernel=0, taupi_coef=0.0, lambda1_hat=0.0):
         import torch
         self._lib = load()
         self.torch = torch
         self.device = torch.device(device or "cuda")
         self.cfg, self._keep = make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s, eos,
-                                           precision, cartesian, periodic, eps_cut, kernel)
+                                           precision, cartesian, periodic, eps_cut, kernel, taupi_coef,
+                                           lambda1_hat)
         self.shape = (int(nx), int(ny), int(neta))
         self.N = int(nx) * int(ny) * int(neta)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -255,7 +259,7 @@ class Hydro:
         if getattr(case, "T0", None) is not None:
             self.set_initial_T(case.T0)
         else:
-            self.set_initial(case.eps, case.ux, case.uy, case.ueta)
+            self.set_initial(case.eps, case.ux, case.uy, case.ueta, getattr(case, "pi0", None))
 
     def step(self, n=1, stats=False):
         s = clv_stats()
@@ -402,7 +406,8 @@ class Batch(Hydro):
         self._keep = []
         for i, c in enumerate(cases):
             cfg, keep = make_config(c.nx, c.ny, c.neta, c.dx, c.dy, c.deta, c.tau0, c.dtau, c.eta_over_s, c.eos,
-                                    precision)
+                                    precision, taupi_coef=getattr(c, "taupi_coef", 0.0),
+                                    lambda1_hat=getattr(c, "lambda1_hat", 0.0))
             cfgs[i] = cfg
             self._keep.append(keep)
         self.shapes = [(c.nx, c.ny, c.neta) for c in cases]
@@ -471,5 +476,7 @@ def mlp_train(params, work, X, Y, iters, batch=8192, lr=1e-3, seed=1, step0=0, s
 
 def from_case(case, precision=CLV_FP64, **kw):
     """Hydro handle for an inputs.HydroCase (grid, spacings, times, EOS)."""
+    kw.setdefault("taupi_coef", getattr(case, "taupi_coef", 0.0))
+    kw.setdefault("lambda1_hat", getattr(case, "lambda1_hat", 0.0))
     return Hydro(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
                  case.eta_over_s, case.eos, precision, case.cartesian, case.periodic, **kw)

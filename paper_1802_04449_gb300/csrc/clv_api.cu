@@ -66,6 +66,7 @@ struct clv_handle {
   double* staging = nullptr;      // N doubles
   double* block_sum = nullptr;    // nblocks doubles
   DevStats* dstats = nullptr;
+  int sms = 148;                  // multiprocessors of the device
   double* tau_dev = nullptr;      // tau of the step on the device (the kernels read it)
   double tau = 0.0;               // host copy, advanced by the same additions
   long long step = 0;
@@ -118,6 +119,16 @@ clv_status fail(clv_handle* h, clv_status s, const std::string& msg) {
       return fail((h), CLV_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
   } while (0)
 
+int device_sms(size_t* smem_optin) {
+  int sms = 148, dev = 0, sm = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  if (smem_optin) *smem_optin = (size_t)sm;
+  return sms;
+}
+
 clv_status validate(const clv_config* c) {
   if (!c) return fail(nullptr, CLV_EINVAL, "config is NULL");
   if (c->nx < 1 || c->ny < 1 || c->neta < 1) return fail(nullptr, CLV_EINVAL, "grid dims must be >= 1");
@@ -134,6 +145,8 @@ clv_status validate(const clv_config* c) {
   }
   if (!(c->eps_cut >= 0)) return fail(nullptr, CLV_EINVAL, "eps_cut must be >= 0");
   if (c->kernel != 0 && c->kernel != 1) return fail(nullptr, CLV_EINVAL, "unknown kernel variant");
+  if (!(c->taupi_coef >= 0) || !std::isfinite(c->lambda1_hat))
+    return fail(nullptr, CLV_EINVAL, "taupi_coef must be >= 0 and lambda1_hat finite");
   long long N = (long long)c->nx * c->ny * c->neta;
   if (N > (1LL << 34)) return fail(nullptr, CLV_EINVAL, "grid too large");
   return CLV_OK;
@@ -317,6 +330,11 @@ template <typename R> EosView<R> eos_view(const clv_handle* h) {
 
 inline unsigned grid_of(long long N) { return (unsigned)((N + kBlock - 1) / kBlock); }
 
+template <typename R> IsCoef<R> is_coef(const clv_config& c) {
+  const double b = c.taupi_coef > 0 ? c.taupi_coef : 5.0;
+  return IsCoef<R>{(R)(c.eta_over_s > 0 ? 1.0 / (b * c.eta_over_s * kHbarC) : 0.0), (R)(1.0 / b), (R)c.lambda1_hat};
+}
+
 template <typename R>
 StageParams<R> stage_params(clv_handle* h, int stage) {
   const clv_config& c = h->cfg;
@@ -351,7 +369,7 @@ StageParams<R> stage_params(clv_handle* h, int stage) {
   p.eps_cut = (R)c.eps_cut;
   p.eps_cut_d = c.eps_cut;
   p.deta_d = c.deta;
-  p.inv_5etas_hbarc = (R)(c.eta_over_s > 0 ? 1.0 / (5.0 * c.eta_over_s * kHbarC) : 0.0);
+  p.is = is_coef<R>(c);
   p.polish_E = (R)(1.01 * c.eps_cut);
   p.polish_v = (R)0.999;
   p.block_sum = h->block_sum;
@@ -716,6 +734,7 @@ clv_status create_common(const clv_config* cfg, void* stream, void* ws, size_t w
   }
   h->ws_bytes = need;
   layout(cfg, h);
+  h->sms = device_sms(nullptr);
   h->tau = cfg->tau0;
   choose_tile(h);
   {
@@ -1141,15 +1160,6 @@ static cudaError_t time_stage1(clv_handle* h, int reps, cudaEvent_t e0, cudaEven
   return e;
 }
 
-static int device_sms(size_t* smem_optin) {
-  int sms = 148, dev = 0, sm = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess) {
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  }
-  if (smem_optin) *smem_optin = (size_t)sm;
-  return sms;
-}
 
 extern "C" {
 
@@ -1324,8 +1334,7 @@ template <typename R> static cudaError_t batch_upload(clv_handle* h) {
   for (size_t e = 0; e < ne; ++e) {
     const auto& ev = h->batch[e];
     const clv_config& c = ev.cfg;
-    g[e] = EventGeom<R>{ev.off, c.nx, c.ny, c.neta, (R)(1.0 / c.dx), (R)(1.0 / c.dy),
-                        (R)(c.eta_over_s > 0 ? 1.0 / (5.0 * c.eta_over_s * kHbarC) : 0.0), c.deta,
+    g[e] = EventGeom<R>{ev.off, c.nx, c.ny, c.neta, (R)(1.0 / c.dx), (R)(1.0 / c.dy), is_coef<R>(c), c.deta,
                         ev.viscous ? 1 : 0};
     t[e] = ev.tile;
   }

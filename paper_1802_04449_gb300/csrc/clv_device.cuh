@@ -145,10 +145,20 @@ template <> struct SolveOps<double, float> {
 // last iterate (the FP64 refinement of an FP32 root, which starts inside
 // Newton's quadratic basin and whose FP32 table lookup leaves a noise floor
 // above tol); without one, solve in full (up to 100 steps).
+// P and c_s^2 at the root, from the last iteration's table lookup (at
+// e_last) moved to the final eps to first order: P + c_s^2 (eps - e_last).
+// valid = false when no iteration ran (vacuum, M = 0).
+template <typename C> struct EosAtRoot {
+  bool valid;
+  C P, cs2;
+};
+
 template <typename C, typename R, typename CE = C, bool FIXED = false>
 __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps_cut, C E, C Mx,
                                                       C My, C Me, C tol, int maxit, C& eps,
-                                                      C& ux, C& uy, C& ue, C* vguess = nullptr) {
+                                                      C& ux, C& uy, C& ue, C* vguess = nullptr,
+                                                      EosAtRoot<C>* at_root = nullptr) {
+  if (at_root) at_root->valid = false;
   using Ops = SolveOps<C, CE>;
   RootResult rr{0, 0};
   eps = C(0);
@@ -182,8 +192,10 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
   }
   int it = 1;
   bool ok = false;
+  C e_last = C(0);
   for (; it <= maxit; ++it) {
     C e = E - M * v;
+    e_last = e;
     {
       CE Pe, Te, ce;
       eos_eval<CE, R>(q, CE(e), Pe, Te, ce);
@@ -210,6 +222,11 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
   C e = E - M * v;
   if (e < eps_cut) return rr;
   eps = e;
+  if (at_root) {
+    at_root->valid = true;
+    at_root->P = P + cs2 * (e - e_last);
+    at_root->cs2 = cs2;
+  }
   C gam = Ops::div(C(1), Ops::sqrt_(C(1) - v * v));
   C s = Ops::div(gam * v, M);
   ux = s * Mx;

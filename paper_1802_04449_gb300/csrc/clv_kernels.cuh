@@ -21,6 +21,14 @@ template <typename R> struct Prim {
   R* cs;
 };
 
+// Israel-Stewart coefficients: tau_pi = b eta_v / (eps + P) = b (eta/s) hbar c
+// / T (b = 5 by default), and lambda_1 = lambda1_hat / eps (0: no term).
+template <typename R> struct IsCoef {
+  R inv_b_etas_hbarc;   // 1/(b (eta/s) hbar c): 1/tau_pi = T * this
+  R inv_b;              // 1/b: eta_v / tau_pi = (eps + P) / b
+  R lambda1_hat;
+};
+
 template <typename R> struct StageParams {
   // fields of the stage being differentiated (stage 1: step n, stage 2: stage-1 result)
   const R* T[4];
@@ -49,7 +57,7 @@ template <typename R> struct StageParams {
   R inv_dl[2]; // 1/dx, 1/dy
   R st_tau;    // 1 in Milne (S_T^tau active), 0 in Cartesian
   R eps_cut;
-  R inv_5etas_hbarc;   // 1/(5 (eta/s) hbar c): 1/tau_pi = T * this
+  IsCoef<R> is;       // Israel-Stewart coefficients (tau_pi, lambda_1)
   R polish_E, polish_v;   // FP32: FP64 Newton where the FP32 eps < polish_E or M > polish_v E
   double eps_cut_d;
   double deta_d;   // d eta_s in FP64 (1/(tau deta) is formed in the kernels, per event in a batch)
@@ -191,10 +199,11 @@ __device__ __forceinline__ void regulate_shear(R e, R P, R* pi) {
   }
 }
 
-// Israel-Stewart source with lambda_i = 0 (Sec. 2): du[a][b] = d~_a u~^b.
+// Israel-Stewart source (Sec. 2, Eq. pimn with lambda_2 = lambda_3 = 0):
+// du[a][b] = d~_a u~^b.
 template <typename R>
 __device__ __forceinline__ void shear_source(R geo, const R u[4], R du[4][4], const R pi[10], R e,
-                                             R P, R inv_taupi, R* S) {
+                                             R P, R inv_taupi, const IsCoef<R>& is, R* S) {
   // corrected tilde covariant derivatives (Eq. dtuz)
   du[3][0] += geo * u[3];
   du[3][3] += geo * u[0];
@@ -208,7 +217,7 @@ __device__ __forceinline__ void shear_source(R geo, const R u[4], R du[4][4], co
   for (int m = 0; m < 4; ++m)
     w[m] = pi[sym_index(m, 0)] * Du[0] - pi[sym_index(m, 1)] * Du[1] - pi[sym_index(m, 2)] * Du[2] -
            pi[sym_index(m, 3)] * Du[3];
-  const R ep5 = (e + P) * R(0.2);
+  const R ep5 = (e + P) * is.inv_b;
   const R decay = inv_taupi + theta * R(1.0 / 3.0) + geo * u[0];
 #pragma unroll
   for (int m = 0; m < 4; ++m)
@@ -220,6 +229,37 @@ __device__ __forceinline__ void shear_source(R geo, const R u[4], R du[4][4], co
                 R(2.0 / 3.0) * ((m == n ? sm : R(0)) - u[m] * u[n]) * theta;
       S[q] = ep5 * sigma - decay * pi[q] - (u[m] * w[n] + u[n] * w[m]);
     }
+  // -(lambda_1 / tau_pi) pi^<mu_l pi^nu>l in tilde components: Y = pi g~ pi,
+  // X = Delta^m_a Delta^n_c Y^ac - Delta^mn (Delta_ac Y^ac) / 3
+  if (is.lambda1_hat != R(0) && e > R(0)) {
+    R Y[10];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = a; c < 4; ++c)
+        Y[sym_index(a, c)] = pi[sym_index(a, 0)] * pi[sym_index(0, c)] - pi[sym_index(a, 1)] * pi[sym_index(1, c)] -
+                             pi[sym_index(a, 2)] * pi[sym_index(2, c)] - pi[sym_index(a, 3)] * pi[sym_index(3, c)];
+    const R ul[4] = {u[0], -u[1], -u[2], -u[3]};   // u~_a
+    // Z^m_c = Delta^m_a Y^ac = Y^mc - u^m (u_a Y^ac)
+    R uY[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      uY[c] = ul[0] * Y[sym_index(0, c)] + ul[1] * Y[sym_index(1, c)] + ul[2] * Y[sym_index(2, c)] +
+              ul[3] * Y[sym_index(3, c)];
+    const R uYu = ul[0] * uY[0] + ul[1] * uY[1] + ul[2] * uY[2] + ul[3] * uY[3];
+    // Delta_ac Y^ac = g~_ac Y^ac - u_a Y^ac u_c
+    const R tr = Y[0] - Y[4] - Y[7] - Y[9] - uYu;
+    const R f = -is.lambda1_hat / e * inv_taupi;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int n = m; n < 4; ++n) {
+        // Delta^m_a Delta^n_c Y^ac = Y^mn - u^m uY^n - u^n uY^m + u^m u^n uYu
+        const R x = Y[sym_index(m, n)] - u[m] * uY[n] - u[n] * uY[m] + u[m] * u[n] * uYu -
+                    ((m == n ? R(metric_sign(m)) : R(0)) - u[m] * u[n]) * tr * R(1.0 / 3.0);
+        S[sym_index(m, n)] += f * x;
+      }
+  }
   // Christoffel terms I^{mu nu} (Eq. Ipi), with a minus sign in S_pi
   const R gu = geo * u[3];
   S[0] -= R(2) * gu * pi[3];
@@ -362,9 +402,9 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       }
       R Pdummy, Tc, c2dummy;
       eos_eval<R, R>(p.eos, e, Pdummy, Tc, c2dummy);
-      const R inv_taupi = Tc * p.inv_5etas_hbarc;
+      const R inv_taupi = Tc * p.is.inv_b_etas_hbarc;
       R Spi[10];
-      shear_source<R>(ts.geo, u, du, pic, e, Pc, inv_taupi, Spi);
+      shear_source<R>(ts.geo, u, du, pic, e, Pc, inv_taupi, p.is, Spi);
 #pragma unroll
       for (int q = 0; q < 10; ++q) S[4 + q] += Spi[q];
     }
@@ -532,18 +572,21 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
   }
   if (active) {
     R en = R(0), ux = R(0), uy = R(0), ue = R(0);
+    EosAtRoot<R> at_root{false, R(0), R(0)};
     if (!(isfinite(E) && isfinite(Mx) && isfinite(My) && isfinite(Me))) {
       f_nonfinite = true;
     } else {
       RootResult rr = solve_primitive<R, R>(p.eos, p.eps_cut, E, Mx, My, Me, SolveTraits<R>::tol,
-                                            SolveTraits<R>::maxit, en, ux, uy, ue, &vg);
+                                            SolveTraits<R>::maxit, en, ux, uy, ue, &vg, &at_root);
       f_rescaled = rr.rescaled;
       my_iters = rr.iters > 0 ? rr.iters : 0;
       my_solved = rr.iters > 0 ? 1 : 0;
       if constexpr (sizeof(R) == 4) {
         // FP64 refinement of the cancellation-prone arithmetic (E - M v, Newton
         // step, gamma) at high velocity, near the vacuum decision, and wherever
-        // the FP32 solve did not converge
+        // the FP32 solve did not converge (inline: a separate pass over a
+        // compacted list measured slower, its extra launch and latency-bound
+        // tail outweighing the divergence it removes)
         const R M = sqrt(Mx * Mx + My * My + Me * Me);
         f_nonconv = rr.iters < 0;
         const bool near_cut = en < p.polish_E;
@@ -551,6 +594,7 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
           rr.iters = polish_root<R>(p, E, Mx, My, Me, vg, rr.iters >= 0, en, ux, uy, ue);
           my_polish_iters = rr.iters > 0 ? rr.iters : 0;
           f_polished = true;
+          at_root.valid = false;   // the refined root: evaluate the table afresh
         }
       }
       f_fail = rr.iters < 0;
@@ -559,8 +603,16 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
         p.fail_EM[1] = (double)sqrt(Mx * Mx + My * My + Me * Me);
       }
     }
-    R Pn, Tn_, c2n;
-    eos_eval<R, R>(p.eos, en, Pn, Tn_, c2n);
+    R Pn, c2n;
+    if (at_root.valid && en > R(0)) {
+      // the last Newton iteration looked the table up within the tolerance of
+      // the root: move its P to the root to first order instead of a new lookup
+      Pn = at_root.P;
+      c2n = at_root.cs2;
+    } else {
+      R Tn_;
+      eos_eval<R, R>(p.eos, en, Pn, Tn_, c2n);
+    }
     p.prout.e[c] = en;
     p.prout.u[0][c] = ux;
     p.prout.u[1][c] = uy;

@@ -89,30 +89,50 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1
       : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
+// Four 8x8 BF16 matrices from shared memory: lane l gives the row address of
+// row l & 7 of matrix l >> 3 (16 bytes, 16-byte aligned); register j of lane
+// l receives elements (l >> 2, 2 (l & 3) .. + 1) of matrix j.
+__device__ __forceinline__ void ldmatrix_x4(unsigned (&r)[4], const void* row_addr) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(row_addr);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
 // Forward pass of 16 cells (rows of xs, bf16 [16][kMlpSX] in shared memory)
 // on one warp; writes the 4 outputs of each row to ys ([16][4] floats).
 // s_w: the padded shared copy (mlp_load_smem); bias: b1[64] b2[64] b3[8].
+// Fragments come from ldmatrix: the B fragments (b0, b1) of n-tile n and k
+// tile kk are the 8x8 blocks (rows n*8.., columns kk*16 and kk*16 + 8) of the
+// row-major [out][in] weights.
 __device__ __forceinline__ void mlp_tile16(const __nv_bfloat16* xs, const __nv_bfloat16* s_w, const float* bias,
                                            float* ys, int lane) {
   const int g = lane >> 2, t = lane & 3;
-  constexpr int XW = kMlpSX / 2, W1W = kMlpS1 / 2, W2W = kMlpS2 / 2;   // row strides in 32-bit words
-  const unsigned* X = reinterpret_cast<const unsigned*>(xs);
-  const unsigned a0 = X[g * XW + t], a1 = X[(g + 8) * XW + t], a2 = X[g * XW + 4 + t], a3 = X[(g + 8) * XW + 4 + t];
-  // layer 1: 16x16 . 16x64
+  const int mi = lane >> 3, mr = lane & 7;   // matrix and row this lane addresses
+  const __nv_bfloat16* w1 = s_w;
+  const __nv_bfloat16* w2 = s_w + kMlpSW1;
+  const __nv_bfloat16* w3 = s_w + kMlpSW1 + kMlpSW2;
+  // A: rows 0-7 / 8-15 x columns 0-7 / 8-15 -> a0 (r0-7,c0-7) a1 (r8-15,c0-7) a2 (r0-7,c8-15) a3 (r8-15,c8-15)
+  unsigned a[4];
+  ldmatrix_x4(a, xs + (mr + 8 * (mi & 1)) * kMlpSX + 8 * (mi >> 1));
+  // layer 1: 16x16 . 16x64; n-tiles in pairs: matrices (nt, c0-7) (nt, c8-15) (nt+1, c0-7) (nt+1, c8-15)
   float h[8][4];
-  const unsigned* W1 = reinterpret_cast<const unsigned*>(s_w);
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    const int n = nt * 8 + g;
-    const float bl = bias[nt * 8 + 2 * t], bh = bias[nt * 8 + 2 * t + 1];
-    h[nt][0] = bl; h[nt][1] = bh; h[nt][2] = bl; h[nt][3] = bh;
-    mma_bf16(h[nt], a0, a1, a2, a3, W1[n * W1W + t], W1[n * W1W + 4 + t]);
+  for (int np = 0; np < 4; ++np) {
+    unsigned b[4];
+    ldmatrix_x4(b, w1 + ((2 * np + (mi >> 1)) * 8 + mr) * kMlpS1 + 8 * (mi & 1));
 #pragma unroll
-    for (int r = 0; r < 4; ++r) h[nt][r] = silu(h[nt][r]);
+    for (int u = 0; u < 2; ++u) {
+      const int nt = 2 * np + u;
+      const float bl = bias[nt * 8 + 2 * t], bh = bias[nt * 8 + 2 * t + 1];
+      h[nt][0] = bl; h[nt][1] = bh; h[nt][2] = bl; h[nt][3] = bh;
+      mma_bf16(h[nt], a[0], a[1], a[2], a[3], b[2 * u], b[2 * u + 1]);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) h[nt][r] = silu(h[nt][r]);
+    }
   }
   // layer 2: 16x64 . 64x64 (accumulators of two n-tiles form one k-tile of A)
   float h2[8][4];
-  const unsigned* W2 = reinterpret_cast<const unsigned*>(s_w + kMlpSW1);
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
     const float bl = bias[64 + nt * 8 + 2 * t], bh = bias[64 + nt * 8 + 2 * t + 1];
@@ -120,31 +140,39 @@ __device__ __forceinline__ void mlp_tile16(const __nv_bfloat16* xs, const __nv_b
   }
 #pragma unroll
   for (int kk = 0; kk < 4; ++kk) {
-    const unsigned b0 = pack_bf16(h[2 * kk][0], h[2 * kk][1]), b1 = pack_bf16(h[2 * kk][2], h[2 * kk][3]);
-    const unsigned b2 = pack_bf16(h[2 * kk + 1][0], h[2 * kk + 1][1]), b3 = pack_bf16(h[2 * kk + 1][2], h[2 * kk + 1][3]);
+    const unsigned a0 = pack_bf16(h[2 * kk][0], h[2 * kk][1]), a1 = pack_bf16(h[2 * kk][2], h[2 * kk][3]);
+    const unsigned a2 = pack_bf16(h[2 * kk + 1][0], h[2 * kk + 1][1]), a3 = pack_bf16(h[2 * kk + 1][2], h[2 * kk + 1][3]);
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) {
-      const int n = nt * 8 + g;
-      mma_bf16(h2[nt], b0, b1, b2, b3, W2[n * W2W + kk * 8 + t], W2[n * W2W + kk * 8 + 4 + t]);
+    for (int np = 0; np < 4; ++np) {
+      unsigned b[4];
+      ldmatrix_x4(b, w2 + ((2 * np + (mi >> 1)) * 8 + mr) * kMlpS2 + kk * 16 + 8 * (mi & 1));
+      mma_bf16(h2[2 * np], a0, a1, a2, a3, b[0], b[1]);
+      mma_bf16(h2[2 * np + 1], a0, a1, a2, a3, b[2], b[3]);
     }
   }
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
     for (int r = 0; r < 4; ++r) h2[nt][r] = silu(h2[nt][r]);
-  // layer 3: 16x64 . 64x8 (outputs 4..7 are padding)
+  // layer 3: 16x64 . 64x8 (outputs 4..7 are padding); k-tiles in pairs:
+  // matrices (kk, c0-7) (kk, c8-15) (kk+1, c0-7) (kk+1, c8-15) of W3's 8 rows
   float y[4];
   {
     const float bl = bias[128 + 2 * t], bh = bias[128 + 2 * t + 1];
     y[0] = bl; y[1] = bh; y[2] = bl; y[3] = bh;
   }
-  const unsigned* W3 = reinterpret_cast<const unsigned*>(s_w + kMlpSW1 + kMlpSW2);
 #pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-    const unsigned b0 = pack_bf16(h2[2 * kk][0], h2[2 * kk][1]), b1 = pack_bf16(h2[2 * kk][2], h2[2 * kk][3]);
-    const unsigned b2 = pack_bf16(h2[2 * kk + 1][0], h2[2 * kk + 1][1]),
-                   b3 = pack_bf16(h2[2 * kk + 1][2], h2[2 * kk + 1][3]);
-    mma_bf16(y, b0, b1, b2, b3, W3[g * W2W + kk * 8 + t], W3[g * W2W + kk * 8 + 4 + t]);
+  for (int kp = 0; kp < 2; ++kp) {
+    unsigned b[4];
+    ldmatrix_x4(b, w3 + mr * kMlpS2 + (2 * kp + (mi >> 1)) * 16 + 8 * (mi & 1));
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int kk = 2 * kp + u;
+      const unsigned a0 = pack_bf16(h2[2 * kk][0], h2[2 * kk][1]), a1 = pack_bf16(h2[2 * kk][2], h2[2 * kk][3]);
+      const unsigned a2 = pack_bf16(h2[2 * kk + 1][0], h2[2 * kk + 1][1]),
+                     a3 = pack_bf16(h2[2 * kk + 1][2], h2[2 * kk + 1][3]);
+      mma_bf16(y, a0, a1, a2, a3, b[2 * u], b[2 * u + 1]);
+    }
   }
   if (t < 2) {
     ys[g * 4 + 2 * t] = y[0];

@@ -43,7 +43,7 @@ template <typename R> struct EventGeom {
   long long off;
   int nx, ny, ne;
   R inv_dx, inv_dy;
-  R inv_5etas_hbarc;
+  IsCoef<R> is;
   double deta;
   int viscous;        // batch: 1 if the event has eta/s > 0
 };
@@ -347,11 +347,11 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
               }
               R Pd, Tc, c2d;
               eos_eval<R, R>(p.eos, e, Pd, Tc, c2d);
-              const R inv_taupi = Tc * ev.inv_5etas_hbarc;
+              const R inv_taupi = Tc * ev.is.inv_b_etas_hbarc;
               R pic[10], Spi[10];
 #pragma unroll
               for (int r = 0; r < 10; ++r) pic[r] = W0[4 + r];
-              shear_source<R>(ts.geo, u, du, pic, e, Pc, inv_taupi, Spi);
+              shear_source<R>(ts.geo, u, du, pic, e, Pc, inv_taupi, ev.is, Spi);
 #pragma unroll
               for (int r = 0; r < 10; ++r) S[4 + r] += Spi[r];
             }
@@ -435,7 +435,7 @@ template <typename R, int STAGE, bool VISC>
 __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS)
     stage_tile_kernel(const StageParams<R> p, const TileArgs t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const EventGeom<R> ev{0, p.nx, p.ny, p.ne, p.inv_dl[0], p.inv_dl[1], p.inv_5etas_hbarc, p.deta_d, VISC ? 1 : 0};
+  const EventGeom<R> ev{0, p.nx, p.ny, p.ne, p.inv_dl[0], p.inv_dl[1], p.is, p.deta_d, VISC ? 1 : 0};
   stage_tile_body<R, STAGE, VISC>(p, ev, t, blockIdx.x, smem_raw);
 }
 

@@ -98,6 +98,73 @@ def gubser_ideal(tau, x, y, q=1.0, eps_norm=10.0):
     return eps, gam * vr * cx, gam * vr * cy
 
 
+def gubser_viscous(tau, x, y, L=2.0, lambda1_hat=-10.0, eps_norm=10.0):
+    """Second-order viscous Gubser flow (Sec. 5, Eqs. weyl_transform,
+    conformal, visc_gubser_before_weyl, gubser_viscous): uniform in the
+    de Sitter coordinates (rho, theta), eps_hat = C cosh(rho)^-(8/3 - 2/l1),
+    pi_hat^{eta eta} = 2 eps_hat / l1, pi_hat^{theta theta} cosh^2 rho =
+    pi_hat^{phi phi} cosh^2 rho sin^2 theta = -eps_hat / l1 (l1 = lambda1_hat),
+    mapped back by the Weyl rescaling: eps = eps_hat / tau^4, outward
+    v_perp = 2 tau r / (L^2 + tau^2 + r^2), pi_{mu nu} = tau^-2 (d xhat / d x)
+    (d xhat / d x) pi_hat.  Holds when eta_hat lambda1_hat^2 = 3 tau_pi_hat.
+    C is fixed so that eps(tau = 1 fm, r = 0) = eps_norm.
+    Returns eps, u~^x, u~^y and pi~ (10, packed tt tx ty te xx xy xe yy ye ee)."""
+    l1 = float(lambda1_hat)
+    expo = 4.0 / 3.0 - 1.0 / l1          # cosh^2(rho) power: cosh(rho)^-(8/3 - 2/l1)
+
+    def Qof(t, r2):                       # 4 L^2 tau^2 cosh^2 rho
+        return L ** 4 + t ** 4 + r2 * r2 + 2 * L * L * t * t + 2 * L * L * r2 - 2 * t * t * r2
+
+    def ehat(t, r2):
+        return (Qof(t, r2) / (4 * L * L * t * t)) ** (-expo)
+
+    C = eps_norm / (ehat(1.0, 0.0) / 1.0)
+    X, Y = np.meshgrid(x, y, indexing="ij")
+    r2 = X * X + Y * Y
+    r = np.sqrt(r2)
+    eh = C * ehat(tau, r2)
+    eps = eh / tau ** 4
+    S = L * L + tau * tau + r2
+    vr = 2 * tau * r / S
+    gam = 1.0 / np.sqrt(1 - vr * vr)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        cx = np.where(r > 0, X / r, 0.0)
+        cy = np.where(r > 0, Y / r, 0.0)
+    Q = Qof(tau, r2)
+    k = eh / l1
+    p_tt = -4 * r2 * k / (tau ** 2 * Q)
+    p_tr = -2 * r * S * k / (tau ** 3 * Q)          # pi^{tau r}
+    p_rr = -S * S * k / (tau ** 4 * Q)
+    p_pp = -k / tau ** 4                            # r^2 pi^{phi phi}
+    pi = np.zeros((10,) + eps.shape)
+    pi[0] = p_tt
+    pi[1] = p_tr * cx
+    pi[2] = p_tr * cy
+    pi[4] = p_rr * cx * cx + p_pp * cy * cy
+    pi[5] = (p_rr - p_pp) * cx * cy
+    pi[7] = p_rr * cy * cy + p_pp * cx * cx
+    pi[9] = 2 * k / tau ** 4                        # tau^2 pi^{eta eta}
+    # at r = 0 the transverse block is isotropic
+    pi[4] = np.where(r > 0, pi[4], p_pp)
+    pi[7] = np.where(r > 0, pi[7], p_pp)
+    return eps, gam * vr * cx, gam * vr * cy, pi
+
+
+def gubser_viscous_case(dx=0.2, nx=41, neta=5, deta=0.2, dtau=0.01, tau0=1.0, tau1=1.5, L=2.0,
+                        lambda1_hat=-10.0, eta_over_s=0.2):
+    """Viscous Gubser flow on a Milne grid (conformal EOS, eta/s = 0.2,
+    lambda1_hat = -10, tau_pi from eta_hat lambda1_hat^2 = 3 tau_pi_hat, i.e.
+    tau_pi = (4 lambda1_hat^2 / 9) eta_v / (eps + P)), with the initial pi~
+    and both coefficients in the case."""
+    x = cell_coords(nx, dx)
+    eps2, ux2, uy2, pi2 = gubser_viscous(tau0, x, x, L, lambda1_hat)
+    rep = lambda a: np.repeat(a[..., None], neta, axis=-1)
+    nsteps = int(round((tau1 - tau0) / dtau))
+    return HydroCase("viscous Gubser flow", nx, nx, neta, dx, dx, deta, tau0, dtau, eta_over_s, None,
+                     rep(eps2), rep(ux2), rep(uy2), np.zeros((nx, nx, neta)), nsteps,
+                     pi0=rep(pi2), taupi_coef=4.0 * lambda1_hat ** 2 / 9.0, lambda1_hat=lambda1_hat)
+
+
 def riemann_1d(nx, dx, eps0=10.0, t0=0.0):
     """Step initial condition along x (Sec. 5, Eq. riemann): eps0 for x <= 0,
     vacuum for x > 0, fluid at rest."""
@@ -232,6 +299,9 @@ class HydroCase:
     cartesian: bool = False
     periodic: bool = False
     T0: np.ndarray | None = None   # (4, nx, ny, neta) T^{tau mu} initial state (then eps/u are unused)
+    pi0: np.ndarray | None = None  # (10, nx, ny, neta) initial pi~ (None: 0)
+    taupi_coef: float = 0.0        # b in tau_pi = b eta_v / (eps + P); 0 -> 5
+    lambda1_hat: float = 0.0       # lambda_1 = lambda1_hat / eps; 0 -> no lambda_1 term
 
     @property
     def ncells(self):

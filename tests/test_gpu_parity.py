@@ -155,6 +155,28 @@ def test_fp64_riemann_vacuum_front():
     assert st["n_rescaled"] > 0   # the vacuum front exercises the |M| > E branch
 
 
+@pytest.mark.parametrize("kernel", [0, 1])
+def test_fp32_riemann_front_refinement(kernel):
+    """The vacuum front drives cells to v -> 1 and to the cutoff: the FP32
+    path refines them in FP64 (compacted second pass for the tiled path,
+    inline for the direct kernel) and matches the oracle within 1e-4 where
+    eps > 1e-3 GeV/fm^3."""
+    nx = 241
+    x, e = I.riemann_1d(nx, 0.05, 10.0)
+    sh = (nx, 1, 1)
+    z = np.zeros(sh)
+    case = I.HydroCase("riemann", nx, 1, 1, 0.05, 1.0, 1.0, 0.0, 0.0125, 0.0, None, e.reshape(sh), z, z, z,
+                       200, cartesian=True)
+    o, g, st = run_pair(case, 200, clv.CLV_FP32, kernel=kernel)
+    assert st["n_polished"] > 0 and st["n_rootfail"] == 0 and st["error_word"] == 0
+    assert fp32_eps_err(o, g) <= FP32_TOL
+    # the velocity at the front: u~^x relative error where eps > 1e-3
+    e_o = o.get("eps")
+    m = e_o > EPS_FLOOR
+    u_o, u_g = o.get("ux")[m], g.get(["ux"])["ux"][m]
+    assert np.max(np.abs(u_g - u_o) / (np.abs(u_o) + 1e-3)) <= 1e-3
+
+
 @pytest.mark.parametrize("eos,kernel", [("crossover", 0), (None, 0), ("crossover", 1)])
 def test_fp32_viscous_hotspots(eos, kernel):
     case = small_hotspot(seed=7, eos=eos)
@@ -413,3 +435,30 @@ def test_step_graphs_equal_direct_launches(prec, eta_over_s):
         assert st["eps_max"] == runs[0][2]["eps_max"] and st["E_tot"] == runs[0][2]["E_tot"]
         for k in fields:
             assert np.array_equal(fields[k], runs[0][0][k]), k
+
+
+@pytest.mark.parametrize("prec", [clv.CLV_FP64, clv.CLV_FP32])
+def test_viscous_gubser_lambda1(prec):
+    """Second-order viscous Gubser flow (lambda_1 term, tau_pi from the
+    solution's constraint) on the GPU against the oracle, and the GPU run
+    against the analytic solution in the core."""
+    case = I.gubser_viscous_case(dx=0.2, nx=41, neta=3, deta=0.2, dtau=0.01, tau1=1.5)
+    o = oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
+                      case.eta_over_s, None, taupi_coef=case.taupi_coef, lambda1_hat=case.lambda1_hat)
+    o.set_initial(case.eps, case.ux, case.uy, case.ueta, case.pi0)
+    o.step(case.nsteps)
+    g = clv.from_case(case, prec)
+    g.set_initial_case(case)
+    st = g.step(case.nsteps, stats=True)
+    assert st["error_word"] == 0
+    if prec == clv.CLV_FP64:
+        compare_fp64(o, g, viscous=True)
+    else:
+        assert fp32_eps_err(o, g) <= FP32_TOL
+    x = I.cell_coords(case.nx, case.dx)
+    e, ux, uy, pi = I.gubser_viscous(1.5, x, x)
+    X, Y = np.meshgrid(x, x, indexing="ij")
+    core = np.sqrt(X * X + Y * Y) <= 2.0
+    got = g.get(["eps", "pixx"])
+    assert np.abs(got["eps"][:, :, 1][core] / e[core] - 1).mean() < 2e-2
+    assert np.abs(got["pixx"][:, :, 1][core] - pi[4][core]).mean() < 2e-2 * np.abs(pi[4][core]).mean()
