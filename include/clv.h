@@ -79,6 +79,8 @@ typedef struct {
   double taupi_coef;         /* b in tau_pi = b eta_v / (eps + P); 0 means 5 (the paper's choice) */
   double lambda1_hat;        /* lambda_1 = lambda1_hat / eps in Eq. (pimn) (conformal scaling);
                                 0: no lambda_1 term (the default) */
+  int halo_x;                /* 0: the whole grid (default); 2: an x-slab of a larger grid with two halo
+                                planes on each x side, filled by the caller (clv_slab_*) */
 } clv_config;
 
 /* Per-run statistics, filled by clv_step / clv_get_stats. */
@@ -256,6 +258,30 @@ clv_status clv_batch_get_fields(clv_handle* h, int event, uint32_t which_mask, d
 /* eps_max, T_max and E_tot of one event (the counters are the batch's).
  * Synchronises the stream. */
 clv_status clv_batch_event_stats(clv_handle* h, int event, clv_stats* out);
+
+/* ---------------- x-slab of a larger grid (halo_x = 2) ----------------
+ * One event split into slabs along x (one per GPU): each handle owns nx
+ * consecutive x planes (nx >= 2) plus two halo planes on each x side, which
+ * the caller fills before each stage: from the neighbouring slab
+ * (clv_slab_pack on the neighbour, a transfer, clv_slab_unpack here) or, at
+ * the ends of the global grid, by clv_slab_fill_edge (zero gradient).
+ * set 1 = the inputs of stage 1 (T~, pi~, u~, P, c_s of the step), set 2 =
+ * those of stage 2 (the stage-1 results).  side 0 = low x, 1 = high x.  A
+ * packed side (the two boundary planes of every field of the set) holds
+ * clv_slab_halo_bytes bytes of device memory; pack(side 1) of the left
+ * neighbour fills unpack(side 0) here and vice versa.  Stepping:
+ *   after clv_set_initial, viscous runs:  for s in 1, 2: fill set s; clv_slab_predictor(s)
+ *   every step:                           for s in 1, 2: fill set s; clv_stage(s)
+ * clv_step refuses an x-slab.  All calls enqueue on the handle's stream. */
+clv_status clv_slab_halo_bytes(const clv_handle* h, size_t* bytes);
+clv_status clv_slab_pack(clv_handle* h, int set, int side, void* d_buf);
+clv_status clv_slab_unpack(clv_handle* h, int set, int side, const void* d_buf);
+clv_status clv_slab_fill_edge(clv_handle* h, int set, int side);
+/* Stage 1 or 2 of the first-step predictor (Sec. 3) of a viscous x-slab. */
+clv_status clv_slab_predictor(clv_handle* h, int stage);
+/* Stage 1 or 2 of the current step; stage 2 completes it (and, with stats,
+ * reduces them over the handle's cells and synchronises). */
+clv_status clv_stage(clv_handle* h, int stage, clv_stats* stats);
 
 /* ---------------- checkpoint ----------------
  * The complete evolution state: T~^{tau mu}, pi~^{mu nu} and the primitives

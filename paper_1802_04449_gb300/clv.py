@@ -40,7 +40,7 @@ class clv_config(ctypes.Structure):
         ("eos_cs2", ctypes.POINTER(ctypes.c_double)),
         ("precision", ctypes.c_int), ("cartesian", ctypes.c_int), ("periodic", ctypes.c_int),
         ("eps_cut", ctypes.c_double), ("kernel", ctypes.c_int),
-        ("taupi_coef", ctypes.c_double), ("lambda1_hat", ctypes.c_double),
+        ("taupi_coef", ctypes.c_double), ("lambda1_hat", ctypes.c_double), ("halo_x", ctypes.c_int),
     ]
 
 
@@ -83,7 +83,8 @@ EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initi
             "clv_mlp_train", "clv_get_tile", "clv_set_tile", "clv_autotune", "clv_set_initial_T",
             "clv_set_initial_T_device", "clv_state_bytes", "clv_get_state", "clv_set_state",
             "clv_create_batch", "clv_batch_size", "clv_batch_set_initial", "clv_batch_get_fields",
-            "clv_batch_event_stats", "clv_set_graphs"]
+            "clv_batch_event_stats", "clv_set_graphs", "clv_slab_halo_bytes", "clv_slab_pack",
+            "clv_slab_unpack", "clv_slab_fill_edge", "clv_slab_predictor", "clv_stage"]
 CLV_GUESS_PREVIOUS, CLV_GUESS_COLD, CLV_GUESS_MLP = 0, 1, 2
 MLP_NPARAM = 5124
 
@@ -126,6 +127,12 @@ def load(path: str | None = None):
         lib.clv_mlp_train.argtypes = [V, V, V, V, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                       ctypes.c_uint64, ctypes.c_int, V, V]
         lib.clv_set_graphs.argtypes = [P, ctypes.c_int]
+        lib.clv_slab_halo_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        lib.clv_slab_pack.argtypes = [P, ctypes.c_int, ctypes.c_int, V]
+        lib.clv_slab_unpack.argtypes = [P, ctypes.c_int, ctypes.c_int, V]
+        lib.clv_slab_fill_edge.argtypes = [P, ctypes.c_int, ctypes.c_int]
+        lib.clv_slab_predictor.argtypes = [P, ctypes.c_int]
+        lib.clv_stage.argtypes = [P, ctypes.c_int, ctypes.POINTER(clv_stats)]
         lib.clv_create_batch.argtypes = [cfgp, ctypes.c_int, V, ctypes.POINTER(P)]
         lib.clv_batch_size.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int64)]
         lib.clv_batch_set_initial.argtypes = [P, ctypes.c_int, D, D, D, D, D]
@@ -156,9 +163,10 @@ def _dp(a):
 
 def make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
                 precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7, kernel=0,
-                taupi_coef=0.0, lambda1_hat=0.0):
+                taupi_coef=0.0, lambda1_hat=0.0, halo_x=0):
     c = clv_config()
     c.taupi_coef, c.lambda1_hat = float(taupi_coef), float(lambda1_hat)
+    c.halo_x = int(halo_x)
     c.nx, c.ny, c.neta = int(nx), int(ny), int(neta)
     c.dx, c.dy, c.deta = float(dx), float(dy), float(deta)
     c.tau0, c.dtau, c.eta_over_s = float(tau0), float(dtau), float(eta_over_s)
@@ -185,14 +193,15 @@ class Hydro:
 
     def __init__(self, nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
                  precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7,
-                 stream=None, device=None, torch_workspace=True, kernel=0, taupi_coef=0.0, lambda1_hat=0.0):
+                 stream=None, device=None, torch_workspace=True, kernel=0, taupi_coef=0.0, lambda1_hat=0.0,
+                 halo_x=0):
         import torch
         self._lib = load()
         self.torch = torch
         self.device = torch.device(device or "cuda")
         self.cfg, self._keep = make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s, eos,
                                            precision, cartesian, periodic, eps_cut, kernel, taupi_coef,
-                                           lambda1_hat)
+                                           lambda1_hat, halo_x)
         self.shape = (int(nx), int(ny), int(neta))
         self.N = int(nx) * int(ny) * int(neta)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -212,6 +221,7 @@ class Hydro:
                                           ctypes.byref(h))
         self._check(st, None)
         self._h = h
+        self._started = False
 
     def _check(self, st, h):
         if st != 0:
@@ -277,6 +287,36 @@ class Hydro:
         step = ctypes.c_int64()
         self._lib.clv_get_time(self._h, ctypes.byref(tau), ctypes.byref(step))
         return tau.value, step.value
+
+    # ---- x-slab (halo_x = 2): halo planes and stage-level stepping
+    def halo_bytes(self):
+        n = ctypes.c_size_t()
+        self._check(self._lib.clv_slab_halo_bytes(self._h, ctypes.byref(n)), self._h)
+        return n.value
+
+    def slab_pack(self, set_, side, buf):
+        self._check(self._lib.clv_slab_pack(self._h, int(set_), int(side), ctypes.c_void_p(buf.data_ptr())), self._h)
+
+    def slab_unpack(self, set_, side, buf):
+        self._check(self._lib.clv_slab_unpack(self._h, int(set_), int(side), ctypes.c_void_p(buf.data_ptr())),
+                    self._h)
+
+    def slab_fill_edge(self, set_, side):
+        self._check(self._lib.clv_slab_fill_edge(self._h, int(set_), int(side)), self._h)
+
+    def viscous_pending(self):
+        """True for a viscous x-slab right after its initial state: the
+        first-step predictor still has to run (clv_slab_predictor)."""
+        return bool(self.cfg.halo_x) and self.cfg.eta_over_s > 0 and self.time()[1] == 0 and not self._started
+
+    def slab_predictor(self, stage):
+        self._check(self._lib.clv_slab_predictor(self._h, int(stage)), self._h)
+
+    def stage(self, stage, stats=False):
+        self._started = True
+        s = clv_stats()
+        self._check(self._lib.clv_stage(self._h, int(stage), ctypes.byref(s) if stats else None), self._h)
+        return s.as_dict() if stats else None
 
     def set_graphs(self, on=True):
         self._check(self._lib.clv_set_graphs(self._h, int(bool(on))), self._h)

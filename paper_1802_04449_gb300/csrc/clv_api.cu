@@ -71,6 +71,7 @@ struct clv_handle {
   double tau = 0.0;               // host copy, advanced by the same additions
   long long step = 0;
   bool initialized = false;
+  bool predictor_pending = false;   // x-slab: the first-step predictor is driven by clv_slab_predictor
   std::string last_error;
   // kernel timing (instrumentation)
   bool timing = false;
@@ -145,6 +146,8 @@ clv_status validate(const clv_config* c) {
   }
   if (!(c->eps_cut >= 0)) return fail(nullptr, CLV_EINVAL, "eps_cut must be >= 0");
   if (c->kernel != 0 && c->kernel != 1) return fail(nullptr, CLV_EINVAL, "unknown kernel variant");
+  if (c->halo_x != 0 && c->halo_x != 2) return fail(nullptr, CLV_EINVAL, "halo_x must be 0 or 2");
+  if (c->halo_x && (c->nx < 2 || c->kernel != 0)) return fail(nullptr, CLV_EINVAL, "an x-slab needs nx >= 2 and kernel 0");
   if (!(c->taupi_coef >= 0) || !std::isfinite(c->lambda1_hat))
     return fail(nullptr, CLV_EINVAL, "taupi_coef must be >= 0 and lambda1_hat finite");
   long long N = (long long)c->nx * c->ny * c->neta;
@@ -263,7 +266,10 @@ std::vector<TileGeom> tile_candidates(const clv_config* c, int sms, size_t smem_
 size_t layout(const clv_config* c, clv_handle* h) {
   const long long N = (long long)c->nx * c->ny * c->neta;
   const size_t rs = c->precision == CLV_FP64 ? 8 : 4;
-  const size_t fb = align_up((size_t)N * rs, 256);
+  // per-cell fields hold halo_x extra planes on each x side (an x-slab); the
+  // field pointers below point at plane 0, so [0, N) is the interior
+  const size_t hoff = (size_t)c->halo_x * c->ny * c->neta * rs;
+  const size_t fb = align_up((size_t)N * rs + 2 * hoff, 256);
   // block partials of the stats reduction: enough for the direct grid and for
   // the tiled grid on any device (at most 1024 SMs)
   const int nblocks = (int)std::max<long long>((N + kBlock - 1) / kBlock, tile_geometry(c, 1024).blocks);
@@ -286,10 +292,10 @@ size_t layout(const clv_config* c, clv_handle* h) {
   size_t oTau = take(sizeof(double));
   if (h) {
     char* b = h->ws;
-    for (int m = 0; m < 4; ++m) { h->T0[m] = b + oT0[m]; h->T1[m] = b + oT1[m]; }
-    for (int q = 0; q < 10; ++q) { h->PI0[q] = b + oPI0[q]; h->PI1[q] = b + oPI1[q]; }
+    for (int m = 0; m < 4; ++m) { h->T0[m] = b + oT0[m] + hoff; h->T1[m] = b + oT1[m] + hoff; }
+    for (int q = 0; q < 10; ++q) { h->PI0[q] = b + oPI0[q] + hoff; h->PI1[q] = b + oPI1[q] + hoff; }
     for (int s = 0; s < kNumPrimSets; ++s)
-      for (int f = 0; f < kPrimFields; ++f) h->PR[s][f] = b + oPR[s][f];
+      for (int f = 0; f < kPrimFields; ++f) h->PR[s][f] = b + oPR[s][f] + hoff;
     for (int t = 0; t < 3; ++t) h->eos[t] = b + oE[t];
     h->mlp = b + oMlp;
     h->staging = (double*)(b + oStage);
@@ -357,6 +363,7 @@ StageParams<R> stage_params(clv_handle* h, int stage) {
   p.prout = s1 ? pst : pprev;
   p.eos = eos_view<R>(h);
   p.nx = c.nx; p.ny = c.ny; p.ne = c.neta; p.periodic = c.periodic;
+  p.xhalo = c.halo_x > 0 ? 1 : 0;
   p.N = h->N;
   p.tau_dev = h->tau_dev;
   p.dtau_d = c.dtau;
@@ -456,16 +463,15 @@ void set_tau(clv_handle* h, double tau) {
   set_tau_kernel<<<1, 1, 0, h->stream>>>(h->tau_dev, tau);
 }
 
+// Half of a Heun step: stage 1, or stage 2 with the end-of-step bookkeeping
+// (tau advance, rotation of the primitive sets).
 template <typename R, bool VISC>
-void launch_step(clv_handle* h, bool stats) {
-  const double tn = h->tau, tn1 = h->tau + h->cfg.dtau;
-  // events: [0] stage-1 kernel [1] stage-1 recovery [2] stage-2 kernel [3] stage-2 recovery [4]
-  // (with kernel = 1 the recovery slots collapse: two events are recorded back to back)
-  const bool timed = h->timing && h->ev_pending.size() < kEventsPerStep * kMaxTimedSteps;
-  if (timed) timing_event(h);
-  StageParams<R> p1 = stage_params<R>(h, 1);
-  launch_stage<R, VISC, 1, false>(h, p1, timed);
-  StageParams<R> p2 = stage_params<R>(h, 2);
+void launch_half(clv_handle* h, int stage, bool stats, bool timed) {
+  if (stage == 1) {
+    launch_stage<R, VISC, 1, false>(h, stage_params<R>(h, 1), timed);
+    return;
+  }
+  const StageParams<R> p2 = stage_params<R>(h, 2);
   if (stats) {
     launch_stage<R, VISC, 2, true>(h, p2, timed);
     h->stat_blocks = (int)grid_of(h->N);
@@ -474,8 +480,18 @@ void launch_step(clv_handle* h, bool stats) {
   }
   advance_tau_kernel<<<1, 1, 0, h->stream>>>(h->tau_dev, h->cfg.dtau);
   std::swap(h->cur, h->prev);
-  h->tau = tn1;
+  h->tau = h->tau + h->cfg.dtau;
   h->step += 1;
+}
+
+template <typename R, bool VISC>
+void launch_step(clv_handle* h, bool stats) {
+  // events: [0] stage-1 kernel [1] stage-1 recovery [2] stage-2 kernel [3] stage-2 recovery [4]
+  // (with kernel = 1 the recovery slots collapse: two events are recorded back to back)
+  const bool timed = h->timing && h->ev_pending.size() < kEventsPerStep * kMaxTimedSteps;
+  if (timed) timing_event(h);
+  launch_half<R, VISC>(h, 1, false, timed);
+  launch_half<R, VISC>(h, 2, stats, timed);
 }
 
 void invalidate_graphs(clv_handle* h) {
@@ -655,9 +671,10 @@ clv_status load_initial_range(clv_handle* h, long long off, long long n, bool vi
   return CLV_OK;
 }
 
-// The rest of the initial state, over all cells: T~ from the primitives and
-// (viscous runs) the first-step predictor of Sec. 3.
-template <typename R> clv_status finish_initial(clv_handle* h) {
+// The rest of the initial state, over all cells: tau reset and T~ from the
+// primitives -- the ideal T~ that the first-step predictor of Sec. 3 starts
+// from in viscous runs (initial_end completes those after the predictor).
+template <typename R> clv_status initial_begin(clv_handle* h) {
   const long long N = h->N;
   const unsigned g = grid_of(N);
   const clv_config& c = h->cfg;
@@ -669,24 +686,47 @@ template <typename R> clv_status finish_initial(clv_handle* h) {
   const double taus0 = c.cartesian ? 1.0 : c.tau0;
   set_tau(h, c.tau0);
   h->step = 0;
-  R* T0[4] = {(R*)h->T0[0], (R*)h->T0[1], (R*)h->T0[2], (R*)h->T0[3]};
-  if (h->viscous) {
-    // Sec. 3: the first u* comes from one ideal (pi-free) Heun step
-    tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(pc, pi0, false, T0[0], T0[1], T0[2], T0[3], taus0, N);
-    launch_step<R, false>(h, false);
-    std::swap(h->cur, h->prev);  // undo the rotation: cur = u^0, prev = u^1_ideal
-    extrapolate_prev_kernel<R><<<g, kBlock, 0, h->stream>>>(prim_set<R>(h, h->cur), prim_set<R>(h, h->prev), N);
-    set_tau(h, c.tau0);
-    h->step = 0;
-    tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(prim_set<R>(h, h->cur), pi0, true, T0[0], T0[1], T0[2],
-                                                   T0[3], taus0, N);
-  } else {
-    tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(pc, pi0, false, T0[0], T0[1], T0[2], T0[3], taus0, N);
+  tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(pc, pi0, false, (R*)h->T0[0], (R*)h->T0[1], (R*)h->T0[2],
+                                                 (R*)h->T0[3], taus0, N);
+  if (!h->viscous) {
+    CLV_CUDA(h, cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream));
+    h->initialized = true;
   }
+  CLV_CUDA(h, cudaGetLastError());
+  return CLV_OK;
+}
+
+// After the first-step predictor (one pi-free Heun step, Sec. 3): u~^{-1} =
+// 2 u~^0 - u~^1_ideal, tau and T~ (now with pi~) of the initial state again.
+template <typename R> clv_status initial_end(clv_handle* h) {
+  const long long N = h->N;
+  const unsigned g = grid_of(N);
+  const clv_config& c = h->cfg;
+  Ptr10<R> pi0;
+  for (int q = 0; q < 10; ++q) pi0.p[q] = (R*)h->PI0[q];
+  std::swap(h->cur, h->prev);  // undo the rotation: cur = u^0, prev = u^1_ideal
+  extrapolate_prev_kernel<R><<<g, kBlock, 0, h->stream>>>(prim_set<R>(h, h->cur), prim_set<R>(h, h->prev), N);
+  set_tau(h, c.tau0);
+  h->step = 0;
+  tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(prim_set<R>(h, h->cur), pi0, true, (R*)h->T0[0], (R*)h->T0[1],
+                                                 (R*)h->T0[2], (R*)h->T0[3], c.cartesian ? 1.0 : c.tau0, N);
   CLV_CUDA(h, cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream));
   CLV_CUDA(h, cudaGetLastError());
+  h->predictor_pending = false;
   h->initialized = true;
   return CLV_OK;
+}
+
+template <typename R> clv_status finish_initial(clv_handle* h) {
+  clv_status s = initial_begin<R>(h);
+  if (s != CLV_OK || !h->viscous) return s;
+  if (h->cfg.halo_x) {   // an x-slab: the caller drives the predictor with halo exchanges
+    h->predictor_pending = true;
+    return CLV_OK;
+  }
+  launch_half<R, false>(h, 1, false, false);
+  launch_half<R, false>(h, 2, false, false);
+  return initial_end<R>(h);
 }
 
 template <typename R>
@@ -887,6 +927,7 @@ clv_status clv_set_initial_device(clv_handle* h, const double* d_eps, const doub
 
 clv_status clv_step(clv_handle* h, int nsteps, clv_stats* stats) {
   if (!h) return CLV_EINVAL;
+  if (h->cfg.halo_x) return fail(h, CLV_EINVAL, "an x-slab steps by clv_stage with halo exchanges in between");
   if (!h->initialized && !h->batch.empty()) {
     for (const auto& ev : h->batch)
       if (!ev.set) return fail(h, CLV_EINVAL, "clv_batch_set_initial was not called for every event");
@@ -1237,6 +1278,126 @@ clv_status clv_set_state(clv_handle* h, const void* buf, size_t bytes) {
   h->step = hd.step;
   h->initialized = true;
   return CLV_OK;
+}
+
+// ---------------- x-slab: halo planes and stage-level stepping ----------------
+}  // extern "C"
+
+template <typename R> struct Ptr19 { R* p[19]; };
+
+// mode 0: pack planes src, src + 1 of every field into buf [field][2][plane];
+// mode 1: unpack buf into planes dst, dst + 1; mode 2: copy plane src into
+// planes dst, dst + 1 (zero-gradient edge).
+template <typename R>
+__global__ void __launch_bounds__(kBlock) slab_planes_kernel(Ptr19<R> f, int nf, long long plane, long long src,
+                                                             long long dst, R* buf, int mode) {
+  const long long per = 2 * plane;
+  const long long total = per * nf;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const int fi = (int)(i / per);
+    const long long r = i - fi * per;
+    const long long pp = r / plane, cell = r - pp * plane;
+    R* a = f.p[fi];
+    if (mode == 0) buf[i] = a[(src + pp) * plane + cell];
+    else if (mode == 1) a[(dst + pp) * plane + cell] = buf[i];
+    else a[(dst + pp) * plane + cell] = a[src * plane + cell];
+  }
+}
+
+// The fields a stage reads from its x-neighbours: set 1 (stage 1) T~, pi~ and
+// the current primitives u~, P, c_s; set 2 (stage 2) the stage-1 results.
+template <typename R> static int slab_fields(clv_handle* h, int set, Ptr19<R>& f) {
+  int n = 0;
+  const int st = 3 - h->cur - h->prev;
+  for (int m = 0; m < 4; ++m) f.p[n++] = (R*)(set == 1 ? h->T0[m] : h->T1[m]);
+  if (h->viscous)
+    for (int q = 0; q < 10; ++q) f.p[n++] = (R*)(set == 1 ? h->PI0[q] : h->PI1[q]);
+  const int ps = set == 1 ? h->cur : st;
+  for (int k = 1; k < kPrimFields; ++k) f.p[n++] = (R*)h->PR[ps][k];   // u~ (3), P, c_s
+  return n;
+}
+
+template <typename R> static clv_status slab_op(clv_handle* h, int set, int side, R* buf, int mode) {
+  Ptr19<R> f;
+  const int nf = slab_fields<R>(h, set, f);
+  const long long plane = (long long)h->cfg.ny * h->cfg.neta;
+  const long long nx = h->cfg.nx;
+  long long src = 0, dst = 0;
+  if (mode == 0) src = side == 0 ? 0 : nx - 2;
+  if (mode == 1) dst = side == 0 ? -2 : nx;
+  if (mode == 2) { src = side == 0 ? 0 : nx - 1; dst = side == 0 ? -2 : nx; }
+  const long long total = 2 * plane * nf;
+  const unsigned g = (unsigned)std::min<long long>((total + kBlock - 1) / kBlock, (long long)h->sms * 8);
+  slab_planes_kernel<R><<<g, kBlock, 0, h->stream>>>(f, nf, plane, src, dst, buf, mode);
+  CLV_CUDA(h, cudaGetLastError());
+  return CLV_OK;
+}
+
+static clv_status slab_check(clv_handle* h, int set, int side) {
+  if (!h) return CLV_EINVAL;
+  if (!h->cfg.halo_x) return fail(h, CLV_EINVAL, "not an x-slab (halo_x = 0)");
+  if ((set != 1 && set != 2) || (side != 0 && side != 1)) return fail(h, CLV_EINVAL, "set must be 1 or 2, side 0 or 1");
+  return CLV_OK;
+}
+
+extern "C" {
+
+clv_status clv_slab_halo_bytes(const clv_handle* h, size_t* bytes) {
+  if (!h || !bytes) return CLV_EINVAL;
+  const int nf = 4 + (h->viscous ? 10 : 0) + (kPrimFields - 1);
+  *bytes = (size_t)2 * h->cfg.ny * h->cfg.neta * nf * h->rsize;
+  return CLV_OK;
+}
+
+clv_status clv_slab_pack(clv_handle* h, int set, int side, void* d_buf) {
+  clv_status s = slab_check(h, set, side);
+  if (s != CLV_OK) return s;
+  if (!d_buf) return fail(h, CLV_EINVAL, "buffer is NULL");
+  return h->rsize == 8 ? slab_op<double>(h, set, side, (double*)d_buf, 0) : slab_op<float>(h, set, side, (float*)d_buf, 0);
+}
+
+clv_status clv_slab_unpack(clv_handle* h, int set, int side, const void* d_buf) {
+  clv_status s = slab_check(h, set, side);
+  if (s != CLV_OK) return s;
+  if (!d_buf) return fail(h, CLV_EINVAL, "buffer is NULL");
+  return h->rsize == 8 ? slab_op<double>(h, set, side, (double*)d_buf, 1) : slab_op<float>(h, set, side, (float*)d_buf, 1);
+}
+
+clv_status clv_slab_fill_edge(clv_handle* h, int set, int side) {
+  clv_status s = slab_check(h, set, side);
+  if (s != CLV_OK) return s;
+  return h->rsize == 8 ? slab_op<double>(h, set, side, nullptr, 2) : slab_op<float>(h, set, side, nullptr, 2);
+}
+
+clv_status clv_slab_predictor(clv_handle* h, int stage) {
+  if (!h) return CLV_EINVAL;
+  if (!h->predictor_pending) return fail(h, CLV_EINVAL, "no first-step predictor pending");
+  if (stage != 1 && stage != 2) return fail(h, CLV_EINVAL, "stage must be 1 or 2");
+  if (h->rsize == 8) {
+    launch_half<double, false>(h, stage, false, false);
+    if (stage == 2) return initial_end<double>(h);
+  } else {
+    launch_half<float, false>(h, stage, false, false);
+    if (stage == 2) return initial_end<float>(h);
+  }
+  CLV_CUDA(h, cudaGetLastError());
+  return CLV_OK;
+}
+
+clv_status clv_stage(clv_handle* h, int stage, clv_stats* stats) {
+  if (!h) return CLV_EINVAL;
+  if (!h->initialized) return fail(h, CLV_EINVAL, "the initial state (and, for an x-slab, its predictor) is not complete");
+  if (stage != 1 && stage != 2) return fail(h, CLV_EINVAL, "stage must be 1 or 2");
+  const bool st = stats && stage == 2;
+  if (st) CLV_CUDA(h, cudaMemsetAsync(&h->dstats->emax_bits, 0, 8, h->stream));
+  if (h->rsize == 8) {
+    if (h->viscous) launch_half<double, true>(h, stage, st, false); else launch_half<double, false>(h, stage, st, false);
+  } else {
+    if (h->viscous) launch_half<float, true>(h, stage, st, false); else launch_half<float, false>(h, stage, st, false);
+  }
+  CLV_CUDA(h, cudaGetLastError());
+  if (!st) return CLV_OK;
+  return h->rsize == 8 ? reduce_stats<double>(h, false, stats) : reduce_stats<float>(h, false, stats);
 }
 
 clv_status clv_set_graphs(clv_handle* h, int enable) {

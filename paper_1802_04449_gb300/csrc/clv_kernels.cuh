@@ -45,6 +45,7 @@ template <typename R> struct StageParams {
   Prim<R> prout;
   EosView<R> eos;
   int nx, ny, ne, periodic;
+  int xhalo;   // 1: x planes -2, -1, nx, nx + 1 are stored halo planes (an x-slab); no clamping in x
   long long N;
   // tau of the step lives on the device (advanced by a kernel after every
   // step), so the launches of a step do not depend on it and a captured step
@@ -127,10 +128,13 @@ __device__ __forceinline__ void interface_flux(const R* L, const R* Rr, R csl, R
   const R vl = L[IV], vr = Rr[IV];
   const R al = fabs(vl), ar = fabs(vr);
   const R lam = fmax((al + csl) / (R(1) + al * csl), (ar + csr) / (R(1) + ar * csr));
+  // H = (F_l + F_r)/2 - lam (Q_r - Q_l)/2 with F = v Q + tau X regrouped as
+  // wl Q_l + wr Q_r + tau (X_l + X_r)/2, wl = (v_l + lam)/2, wr = (v_r - lam)/2
+  const R wl = R(0.5) * (vl + lam), wr = R(0.5) * (vr - lam);
+  const R ht = R(0.5) * taus;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    // flux of T~^{tau m} along a: v T~^{tau m} + tau [P (v d_{m tau} + d_{m a}) + pi~^{a m} - v pi~^{tau m}]
-    R fl = vl * L[m], fr = vr * Rr[m];
+    // X of T~^{tau m} along a: P (v d_{m tau} + d_{m a}) + pi~^{a m} - v pi~^{tau m}
     R gl = (m == 0 ? vl : R(0)) + (m == axis ? R(1) : R(0));
     R gr = (m == 0 ? vr : R(0)) + (m == axis ? R(1) : R(0));
     R xl = L[IP] * gl, xr = Rr[IP] * gr;
@@ -138,16 +142,13 @@ __device__ __forceinline__ void interface_flux(const R* L, const R* Rr, R csl, R
       xl += L[4 + sym_index(axis, m)] - vl * L[4 + sym_index(0, m)];
       xr += Rr[4 + sym_index(axis, m)] - vr * Rr[4 + sym_index(0, m)];
     }
-    fl += taus * xl;
-    fr += taus * xr;
-    H[m] = R(0.5) * (fl + fr) - R(0.5) * lam * (Rr[m] - L[m]);
+    H[m] = wl * L[m] + wr * Rr[m] + ht * (xl + xr);
   }
   if constexpr (VISC) {
+    // Q_pi = u~^tau pi~ on each side, flux v Q_pi
+    const R al2 = wl * L[IU], ar2 = wr * Rr[IU];
 #pragma unroll
-    for (int q = 0; q < 10; ++q) {
-      R ql = L[IU] * L[4 + q], qr = Rr[IU] * Rr[4 + q];
-      H[4 + q] = R(0.5) * (vl * ql + vr * qr) - R(0.5) * lam * (qr - ql);
-    }
+    for (int q = 0; q < 10; ++q) H[4 + q] = al2 * L[4 + q] + ar2 * Rr[4 + q];
   }
   (void)NQ;
 }
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
 #pragma unroll
       for (int d = 0; d < 5; ++d) {
         const int o = d - 2;
-        const int ii = ax == 1 ? wrap_index(i + o, p.nx, p.periodic) : i;
+        const int ii = ax == 1 ? (p.xhalo ? i + o : wrap_index(i + o, p.nx, p.periodic)) : i;
         const int jj = ax == 2 ? wrap_index(j + o, p.ny, p.periodic) : j;
         const int kk = ax == 3 ? wrap_index(k + o, p.ne, p.periodic) : k;
         id[d] = ((long long)ii * p.ny + jj) * p.ne + kk;

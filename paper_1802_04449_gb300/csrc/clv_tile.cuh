@@ -220,8 +220,10 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
     goff[q] = wrap_index(j0 + bj - 2, ev.ny, p.periodic) * ev.ne + wrap_index(k0 + bk - 2, ev.ne, p.periodic);
   }
   const long long plane = (long long)ev.ny * ev.ne;
-  stage_plane_async<R, VISC>(p, boxbuf + ((x0 - 2) & 1) * NF * NB, qend,
-                             ev.off + wrap_index(x0 - 2, ev.nx, p.periodic) * plane, goff, tid, nthr, NB);
+  // x planes beyond the grid: clamped or wrapped, or (an x-slab) the stored halo planes
+  auto xplane = [&](int x) { return p.xhalo ? x : wrap_index(x, ev.nx, p.periodic); };
+  stage_plane_async<R, VISC>(p, boxbuf + ((x0 - 2) & 1) * NF * NB, qend, ev.off + xplane(x0 - 2) * plane, goff, tid,
+                             nthr, NB);
   cp_async_commit();
   for (int pl = x0 - 2; pl <= x1 + 1; ++pl) {
     const bool out_plane = pl >= x0 && pl < x1;
@@ -244,7 +246,7 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
     // with the per-cell inputs of the cell output two planes on (pl - 1)
     if (pl + 1 <= x1 + 1) {
       stage_plane_async<R, VISC>(p, boxbuf + ((pl + 1) & 1) * NF * NB, qend,
-                                 ev.off + wrap_index(pl + 1, ev.nx, p.periodic) * plane, goff, tid, nthr, NB);
+                                 ev.off + xplane(pl + 1) * plane, goff, tid, nthr, NB);
       if (active && pl - 1 >= x0 && pl - 1 < x1)
         prefetch_cell<R, STAGE, VISC>(p, cellbuf + (size_t)((pl - 1) & 1) * CI::n * ncell + cid, ncell,
                                       ev.off + ((long long)(pl - 1) * ev.ny + j) * ev.ne + k);

@@ -462,3 +462,41 @@ def test_viscous_gubser_lambda1(prec):
     got = g.get(["eps", "pixx"])
     assert np.abs(got["eps"][:, :, 1][core] / e[core] - 1).mean() < 2e-2
     assert np.abs(got["pixx"][:, :, 1][core] - pi[4][core]).mean() < 2e-2 * np.abs(pi[4][core]).mean()
+
+
+@pytest.mark.parametrize("prec,eta_over_s,parts", [(clv.CLV_FP64, 0.08, 2), (clv.CLV_FP64, 0.16, 3),
+                                                   (clv.CLV_FP32, 0.08, 2), (clv.CLV_FP64, 0.0, 3)])
+def test_x_slabs_equal_the_single_domain(prec, eta_over_s, parts):
+    """An event split into x-slabs (halo planes exchanged before every stage,
+    zero-gradient copies at the global ends) evolves exactly as the single
+    domain: every field bit for bit, the first-step predictor included."""
+    from paper_1802_04449_gb300 import slab as S
+    case = small_hotspot(seed=29, nx=25, ny=19, neta=11, eta_over_s=eta_over_s)
+    g = clv.from_case(case, prec)
+    g.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    g.step(6)
+    sl = S.LocalSlabs(case, parts, prec)
+    sl.step(6)
+    names = ["eps", "ux", "uy", "ueta", "Ttt", "Ttx", "Tte"] + (["pixx", "pixe", "piee", "upx", "upe"]
+                                                               if eta_over_s > 0 else [])
+    ref, got = g.get(names), sl.get(names)
+    for k in names:
+        assert np.array_equal(got[k], ref[k]), k
+    assert sl.slabs[0].time() == g.time()
+    with pytest.raises(clv.ClvError):
+        sl.slabs[0].step(1)                      # an x-slab steps by stages
+
+
+def test_x_slab_mini_jet_initial_state():
+    """The T^{tau mu} initial state of a slab (its own root solves) and its
+    evolution equal the single domain's."""
+    from paper_1802_04449_gb300 import slab as S
+    case = I.minijet_event(nx=20, ny=15, neta=7, dx=0.2, deta=0.2, n_spots=30, seed=5, eta_over_s=0.16,
+                           dtau=0.01)
+    g = clv.from_case(case, clv.CLV_FP64)
+    g.set_initial_T(case.T0)
+    g.step(4)
+    sl = S.LocalSlabs(case, 2, clv.CLV_FP64)
+    sl.step(4)
+    for k in ("eps", "ux", "pixy"):
+        assert np.array_equal(sl.get([k])[k], g.get([k])[k]), k

@@ -1,0 +1,66 @@
+"""Host side of the x-slab decomposition, on CPU: the partition and the
+neighbour halo exchange over torch.distributed (gloo, three ranks)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from paper_1802_04449_gb300 import slab as S
+
+
+def test_partition():
+    for nx in (4, 5, 97, 261):
+        for parts in (1, 2, 3, 8):
+            if nx < 2 * parts:
+                with pytest.raises(ValueError):
+                    S.partition(nx, parts)
+                continue
+            p = S.partition(nx, parts)
+            assert [x for x, _ in p] == list(np.cumsum([0] + [n for _, n in p])[:-1])
+            assert sum(n for _, n in p) == nx and min(n for _, n in p) >= 2
+            assert max(n for _, n in p) - min(n for _, n in p) <= 1
+
+
+def _port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        lo = torch.full((5,), 10.0 * rank + 0.0)
+        hi = torch.full((5,), 10.0 * rank + 1.0)
+        rlo, rhi = S.exchange_halos(lo, hi, rank, world)
+        st = S.reduce_stats(1.0 + rank * (rank - 1), 0.1 * rank, 10.0 ** rank)
+        np.save(os.path.join(out, f"x{rank}.npy"),
+                np.array([np.nan if rlo is None else float(rlo[0]), np.nan if rhi is None else float(rhi[0]),
+                          st["eps_max"], st["T_max"], st["E_tot"]]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_exchange_with_three_gloo_ranks(tmp_path):
+    import torch.multiprocessing as mp
+    world = 3
+    mp.start_processes(_worker, args=(world, _port(), str(tmp_path)), nprocs=world, start_method="spawn")
+    got = [np.load(tmp_path / f"x{r}.npy") for r in range(world)]
+    # rank r receives the high planes of r - 1 and the low planes of r + 1
+    assert np.isnan(got[0][0]) and got[0][1] == 10.0
+    assert got[1][0] == 1.0 and got[1][1] == 20.0
+    assert got[2][0] == 11.0 and np.isnan(got[2][1])
+    # event statistics: the largest eps_max (rank 2: 3.0) with its T, E_tot summed
+    for g in got:
+        assert g[2] == 3.0 and g[3] == pytest.approx(0.2) and g[4] == 111.0
+
+
+def test_combine_stats():
+    got = S.combine_stats([(1.0, 0.2, 5.0), (4.0, 0.3, 6.0), (2.0, 0.25, 7.5)])
+    assert got == {"eps_max": 4.0, "T_max": 0.3, "E_tot": 18.5}
