@@ -48,7 +48,9 @@ struct clv_handle {
   bool own_ws = false;
   char* ws = nullptr;
   size_t ws_bytes = 0;
-  long long N = 0;
+  long long N = 0;                // cells of the padded layout (eta rows of pitch nep)
+  long long Nc = 0;               // cells of the grid (compact order of the host arrays)
+  int nep = 1;                    // eta pitch: neta rounded up to a multiple of 4
   int rsize = 8;
   bool viscous = false;
   int nblocks = 0;
@@ -88,7 +90,8 @@ struct clv_handle {
   // batch of events stored back to back (clv_create_batch; empty otherwise)
   struct Event {
     clv_config cfg;
-    long long off = 0, N = 0;
+    long long off = 0, N = 0, Nc = 0;   // padded offset and cells, compact cells
+    int nep = 1;
     TileArgs tile{};
     bool viscous = false, set = false;
   };
@@ -263,12 +266,17 @@ std::vector<TileGeom> tile_candidates(const clv_config* c, int sms, size_t smem_
   return out;
 }
 
+inline int eta_pitch(int neta) { return (neta + 3) & ~3; }
+
 size_t layout(const clv_config* c, clv_handle* h) {
-  const long long N = (long long)c->nx * c->ny * c->neta;
+  // eta rows are padded to a multiple of 4 cells (16-byte aligned rows for
+  // vector copies); the padding slots hold vacuum and are never updated
+  const int nep = eta_pitch(c->neta);
+  const long long N = (long long)c->nx * c->ny * nep;
   const size_t rs = c->precision == CLV_FP64 ? 8 : 4;
   // per-cell fields hold halo_x extra planes on each x side (an x-slab); the
   // field pointers below point at plane 0, so [0, N) is the interior
-  const size_t hoff = (size_t)c->halo_x * c->ny * c->neta * rs;
+  const size_t hoff = (size_t)c->halo_x * c->ny * nep * rs;
   const size_t fb = align_up((size_t)N * rs + 2 * hoff, 256);
   // block partials of the stats reduction: enough for the direct grid and for
   // the tiled grid on any device (at most 1024 SMs)
@@ -304,6 +312,8 @@ size_t layout(const clv_config* c, clv_handle* h) {
     h->tau_dev = (double*)(b + oTau);
     h->nblocks = nblocks;
     h->N = N;
+    h->Nc = (long long)c->nx * c->ny * c->neta;
+    h->nep = nep;
     h->rsize = (int)rs;
   }
   return off;
@@ -363,6 +373,7 @@ StageParams<R> stage_params(clv_handle* h, int stage) {
   p.prout = s1 ? pst : pprev;
   p.eos = eos_view<R>(h);
   p.nx = c.nx; p.ny = c.ny; p.ne = c.neta; p.periodic = c.periodic;
+  p.nep = h->nep;
   p.xhalo = c.halo_x > 0 ? 1 : 0;
   p.N = h->N;
   p.tau_dev = h->tau_dev;
@@ -621,9 +632,10 @@ template <typename R> clv_status reduce_stats(clv_handle* h, bool scan, clv_stat
   return CLV_OK;
 }
 
-template <typename R> __global__ void convert_kernel(const double* s, R* d, long long N) {
+// compact doubles -> the padded layout in R
+template <typename R> __global__ void convert_kernel(const double* s, R* d, long long N, int ne, int nep) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < N) d[c] = (R)s[c];
+  if (c < N) d[padded_index(c, ne, nep)] = (R)s[c];
 }
 
 template <typename R> Prim<R> prim_at(Prim<R> p, long long off) {
@@ -634,39 +646,41 @@ template <typename R> Prim<R> prim_at(Prim<R> p, long long off) {
   return p;
 }
 
-// Primitives (and pi~) of the cells [off, off + n) from doubles (host arrays
-// go through the staging buffer): vacuum below the cutoff, P and c_s from the
-// EOS, copied to the previous-step set.
+// Primitives (and pi~) of one grid from compact doubles (host arrays go
+// through the staging buffer): nc = nx ny neta input cells, stored at
+// padded slots [off, off + npad) with eta pitch nep (padding slots: vacuum);
+// vacuum below the cutoff, P and c_s from the EOS, copied to the
+// previous-step set.
 template <typename R>
-clv_status load_initial_range(clv_handle* h, long long off, long long n, bool visc, const double* const in[4],
-                              const double* pi, bool host) {
-  const unsigned g = grid_of(n);
+clv_status load_initial_range(clv_handle* h, long long off, long long npad, long long nc, int ne, int nep, bool visc,
+                              const double* const in[4], const double* pi, bool host) {
+  const unsigned gc = grid_of(nc), gp = grid_of(npad);
   const clv_config& c = h->cfg;
   Prim<R> pc = prim_at(prim_set<R>(h, h->cur), off), pp = prim_at(prim_set<R>(h, h->prev), off);
   R* dst_prim[4] = {pc.e, pc.u[0], pc.u[1], pc.u[2]};
   for (int f = 0; f < 4; ++f) {
     const double* src = in[f];
     if (host) {
-      CLV_CUDA(h, cudaMemcpyAsync(h->staging, src, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream));
+      CLV_CUDA(h, cudaMemcpyAsync(h->staging, src, (size_t)nc * 8, cudaMemcpyHostToDevice, h->stream));
       src = h->staging;
     }
-    convert_kernel<R><<<g, kBlock, 0, h->stream>>>(src, dst_prim[f], n);
+    if (nep != ne) CLV_CUDA(h, cudaMemsetAsync(dst_prim[f], 0, (size_t)npad * sizeof(R), h->stream));
+    convert_kernel<R><<<gc, kBlock, 0, h->stream>>>(src, dst_prim[f], nc, ne, nep);
   }
   Ptr10<R> pi0;
   for (int q = 0; q < 10; ++q) pi0.p[q] = (R*)h->PI0[q] + off;
   for (int q = 0; q < 10; ++q) {
+    CLV_CUDA(h, cudaMemsetAsync(pi0.p[q], 0, (size_t)npad * sizeof(R), h->stream));
     if (pi && visc) {
-      const double* src = pi + (size_t)q * n;
+      const double* src = pi + (size_t)q * nc;
       if (host) {
-        CLV_CUDA(h, cudaMemcpyAsync(h->staging, src, (size_t)n * 8, cudaMemcpyHostToDevice, h->stream));
+        CLV_CUDA(h, cudaMemcpyAsync(h->staging, src, (size_t)nc * 8, cudaMemcpyHostToDevice, h->stream));
         src = h->staging;
       }
-      convert_kernel<R><<<g, kBlock, 0, h->stream>>>(src, pi0.p[q], n);
-    } else {
-      CLV_CUDA(h, cudaMemsetAsync(pi0.p[q], 0, (size_t)n * sizeof(R), h->stream));
+      convert_kernel<R><<<gc, kBlock, 0, h->stream>>>(src, pi0.p[q], nc, ne, nep);
     }
   }
-  init_primitives_kernel<R><<<g, kBlock, 0, h->stream>>>(pc, pp, pi0, visc, eos_view<R>(h), c.eps_cut, n);
+  init_primitives_kernel<R><<<gp, kBlock, 0, h->stream>>>(pc, pp, pi0, visc, eos_view<R>(h), c.eps_cut, npad);
   CLV_CUDA(h, cudaGetLastError());
   return CLV_OK;
 }
@@ -731,17 +745,20 @@ template <typename R> clv_status finish_initial(clv_handle* h) {
 
 template <typename R>
 clv_status set_initial_impl(clv_handle* h, const double* const in[4], const double* pi, bool host) {
-  clv_status s = load_initial_range<R>(h, 0, h->N, h->viscous, in, pi, host);
+  clv_status s = load_initial_range<R>(h, 0, h->N, h->Nc, h->cfg.neta, h->nep, h->viscous, in, pi, host);
   return s != CLV_OK ? s : finish_initial<R>(h);
 }
 
-template <typename R> clv_status export_field(clv_handle* h, int which, double* dst, long long off, long long n) {
+// field `which` of the grid at padded offset off (n compact cells, eta rows
+// ne of pitch nep) as compact doubles
+template <typename R>
+clv_status export_field(clv_handle* h, int which, double* dst, long long off, long long n, int ne, int nep) {
   const void* src = nullptr;
   if (which <= 3) src = h->PR[h->cur][which];
   else if (which <= 7) src = h->T0[which - 4];
   else if (which <= 17) src = h->PI0[which - 8];
   else src = h->PR[h->prev][1 + (which - 18)];
-  export_kernel<R><<<grid_of(n), kBlock, 0, h->stream>>>((const R*)src + off, dst, n);
+  export_kernel<R><<<grid_of(n), kBlock, 0, h->stream>>>((const R*)src + off, dst, n, ne, nep);
   CLV_CUDA(h, cudaGetLastError());
   return CLV_OK;
 }
@@ -774,6 +791,15 @@ clv_status create_common(const clv_config* cfg, void* stream, void* ws, size_t w
   }
   h->ws_bytes = need;
   layout(cfg, h);
+  {
+    // padding slots of the eta rows (and every field before its first use) hold zeros: vacuum
+    cudaError_t e = cudaMemsetAsync(h->ws, 0, need, h->stream);
+    if (e != cudaSuccess) {
+      if (h->own_ws) cudaFree(h->ws);
+      delete h;
+      return fail(nullptr, CLV_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    }
+  }
   h->sms = device_sms(nullptr);
   h->tau = cfg->tau0;
   choose_tile(h);
@@ -871,7 +897,7 @@ static clv_status set_initial_T_any(clv_handle* h, const double* T, bool host) {
   if (!h) return CLV_EINVAL;
   if (!h->batch.empty()) return fail(h, CLV_EINVAL, "a batch takes its events' states by clv_batch_set_initial");
   if (!T) return fail(h, CLV_EINVAL, "T is required");
-  const long long N = h->N;
+  const long long N = h->Nc;   // compact input cells
   // scratch: the stage-2 shear buffers (>= 4 N doubles in either precision),
   // which the initial state does not use
   double* a = reinterpret_cast<double*>(h->PI1[0]);
@@ -897,7 +923,16 @@ static clv_status set_initial_T_any(clv_handle* h, const double* T, bool host) {
   const double* in[4] = {a, a + N, a + 2 * N, a + 3 * N};
   h->cur = 0;
   h->prev = 1;
-  return h->rsize == 8 ? set_initial_impl<double>(h, in, nullptr, false) : set_initial_impl<float>(h, in, nullptr, false);
+  clv_status st =
+      h->rsize == 8 ? set_initial_impl<double>(h, in, nullptr, false) : set_initial_impl<float>(h, in, nullptr, false);
+  if (st != CLV_OK) return st;
+  // the scratch is consumed (stream order): the stage buffers return to zeros, as the
+  // padding slots of the eta rows, which the stages never write, must stay vacuum
+  for (int q = 0; q < 10; ++q)
+    CLV_CUDA(h, cudaMemsetAsync((char*)h->PI1[q] - (size_t)h->cfg.halo_x * h->cfg.ny * h->nep * h->rsize, 0,
+                                ((size_t)h->N + 2 * (size_t)h->cfg.halo_x * h->cfg.ny * h->nep) * h->rsize,
+                                h->stream));
+  return CLV_OK;
 }
 
 static clv_status set_initial_any(clv_handle* h, const double* eps, const double* ux, const double* uy,
@@ -966,7 +1001,7 @@ clv_status clv_get_stats(clv_handle* h, clv_stats* stats) {
 }
 
 static clv_status get_fields_range(clv_handle* h, uint32_t mask, double* out, bool host, long long off,
-                                   long long n) {
+                                   long long n, int ne, int nep) {
   if (!h || !out) return CLV_EINVAL;
   if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
   if (mask >> 21) return fail(h, CLV_EINVAL, "mask selects fields beyond index 20");
@@ -974,7 +1009,8 @@ static clv_status get_fields_range(clv_handle* h, uint32_t mask, double* out, bo
   for (int f = 0; f < 21; ++f) {
     if (!(mask >> f & 1u)) continue;
     double* dst = host ? h->staging : out + slot * (size_t)n;
-    clv_status s = h->rsize == 8 ? export_field<double>(h, f, dst, off, n) : export_field<float>(h, f, dst, off, n);
+    clv_status s = h->rsize == 8 ? export_field<double>(h, f, dst, off, n, ne, nep)
+                                 : export_field<float>(h, f, dst, off, n, ne, nep);
     if (s != CLV_OK) return s;
     if (host) {
       CLV_CUDA(h, cudaMemcpyAsync(out + slot * (size_t)n, h->staging, (size_t)n * 8,
@@ -987,7 +1023,8 @@ static clv_status get_fields_range(clv_handle* h, uint32_t mask, double* out, bo
 }
 
 static clv_status get_fields_any(clv_handle* h, uint32_t mask, double* out, bool host) {
-  return get_fields_range(h, mask, out, host, 0, h ? h->N : 0);
+  if (!h) return CLV_EINVAL;
+  return get_fields_range(h, mask, out, host, 0, h->Nc, h->cfg.neta, h->nep);
 }
 
 clv_status clv_get_fields(clv_handle* h, uint32_t mask, double* host_out) {
@@ -1320,7 +1357,7 @@ template <typename R> static int slab_fields(clv_handle* h, int set, Ptr19<R>& f
 template <typename R> static clv_status slab_op(clv_handle* h, int set, int side, R* buf, int mode) {
   Ptr19<R> f;
   const int nf = slab_fields<R>(h, set, f);
-  const long long plane = (long long)h->cfg.ny * h->cfg.neta;
+  const long long plane = (long long)h->cfg.ny * h->nep;
   const long long nx = h->cfg.nx;
   long long src = 0, dst = 0;
   if (mode == 0) src = side == 0 ? 0 : nx - 2;
@@ -1345,7 +1382,7 @@ extern "C" {
 clv_status clv_slab_halo_bytes(const clv_handle* h, size_t* bytes) {
   if (!h || !bytes) return CLV_EINVAL;
   const int nf = 4 + (h->viscous ? 10 : 0) + (kPrimFields - 1);
-  *bytes = (size_t)2 * h->cfg.ny * h->cfg.neta * nf * h->rsize;
+  *bytes = (size_t)2 * h->cfg.ny * h->nep * nf * h->rsize;
   return CLV_OK;
 }
 
@@ -1495,7 +1532,7 @@ template <typename R> static cudaError_t batch_upload(clv_handle* h) {
   for (size_t e = 0; e < ne; ++e) {
     const auto& ev = h->batch[e];
     const clv_config& c = ev.cfg;
-    g[e] = EventGeom<R>{ev.off, c.nx, c.ny, c.neta, (R)(1.0 / c.dx), (R)(1.0 / c.dy), is_coef<R>(c), c.deta,
+    g[e] = EventGeom<R>{ev.off, c.nx, c.ny, c.neta, ev.nep, (R)(1.0 / c.dx), (R)(1.0 / c.dy), is_coef<R>(c), c.deta,
                         ev.viscous ? 1 : 0};
     t[e] = ev.tile;
   }
@@ -1537,14 +1574,16 @@ clv_status clv_create_batch(const clv_config* cfgs, int nevents, void* cuda_stre
       return fail(nullptr, CLV_EINVAL,
                   "batch events must share tau0, dtau, precision, EOS, eps_cut, coordinates and boundaries "
                   "(kernel 0)");
-    N += (long long)c.nx * c.ny * c.neta;
+    N += (long long)c.nx * c.ny * eta_pitch(c.neta);
     eta_max = std::max(eta_max, c.eta_over_s);
   }
   if (N > (1LL << 31) - 1) return fail(nullptr, CLV_EINVAL, "batch too large (at most 2^31 - 1 cells)");
-  clv_config bc = c0;      // the batch as one flat grid of N cells (layout, recovery, stats)
-  bc.nx = (int)N;
+  // the batch as one flat grid of N cells (layout, recovery, stats): N / 4
+  // rows of 4 (every event's padded size is a multiple of 4)
+  clv_config bc = c0;
+  bc.nx = (int)(N / 4);
   bc.ny = 1;
-  bc.neta = 1;
+  bc.neta = 4;
   bc.eta_over_s = eta_max;
   clv_status st = create_common(&bc, cuda_stream, nullptr, 0, out);
   if (st != CLV_OK) return st;
@@ -1559,7 +1598,9 @@ clv_status clv_create_batch(const clv_config* cfgs, int nevents, void* cuda_stre
     ev.cfg = cfgs[e];
     ev.cfg.eos_P = ev.cfg.eos_T = ev.cfg.eos_cs2 = nullptr;
     ev.off = off;
-    ev.N = (long long)ev.cfg.nx * ev.cfg.ny * ev.cfg.neta;
+    ev.nep = eta_pitch(ev.cfg.neta);
+    ev.N = (long long)ev.cfg.nx * ev.cfg.ny * ev.nep;
+    ev.Nc = (long long)ev.cfg.nx * ev.cfg.ny * ev.cfg.neta;
     ev.viscous = ev.cfg.eta_over_s > 0.0;
     ev.tile = batch_tile(ev.cfg);
     off += ev.N;
@@ -1597,7 +1638,11 @@ clv_status clv_create_batch(const clv_config* cfgs, int nevents, void* cuda_stre
 clv_status clv_batch_size(const clv_handle* h, int* nevents, int64_t* cells) {
   if (!h) return CLV_EINVAL;
   if (nevents) *nevents = (int)h->batch.size();
-  if (cells) *cells = h->N;
+  if (cells) {
+    long long nc = 0;
+    for (const auto& ev : h->batch) nc += ev.Nc;
+    *cells = h->batch.empty() ? h->Nc : nc;
+  }
   return CLV_OK;
 }
 
@@ -1610,8 +1655,9 @@ clv_status clv_batch_set_initial(clv_handle* h, int event, const double* eps, co
   if (!eps || !ux || !uy || !ueta) return fail(h, CLV_EINVAL, "eps, ux, uy and ueta are required");
   auto& ev = h->batch[event];
   const double* in[4] = {eps, ux, uy, ueta};
-  clv_status s = h->rsize == 8 ? load_initial_range<double>(h, ev.off, ev.N, ev.viscous, in, pi, true)
-                               : load_initial_range<float>(h, ev.off, ev.N, ev.viscous, in, pi, true);
+  clv_status s =
+      h->rsize == 8 ? load_initial_range<double>(h, ev.off, ev.N, ev.Nc, ev.cfg.neta, ev.nep, ev.viscous, in, pi, true)
+                    : load_initial_range<float>(h, ev.off, ev.N, ev.Nc, ev.cfg.neta, ev.nep, ev.viscous, in, pi, true);
   if (s == CLV_OK) ev.set = true;
   return s;
 }
@@ -1621,7 +1667,7 @@ clv_status clv_batch_get_fields(clv_handle* h, int event, uint32_t mask, double*
   if (h->batch.empty()) return fail(h, CLV_EINVAL, "not a batch (clv_create_batch)");
   if (event < 0 || event >= (int)h->batch.size()) return fail(h, CLV_EINVAL, "event index out of range");
   const auto& ev = h->batch[event];
-  return get_fields_range(h, mask, host_out, true, ev.off, ev.N);
+  return get_fields_range(h, mask, host_out, true, ev.off, ev.Nc, ev.cfg.neta, ev.nep);
 }
 
 clv_status clv_batch_event_stats(clv_handle* h, int event, clv_stats* out) {

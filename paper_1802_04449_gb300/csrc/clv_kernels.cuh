@@ -45,6 +45,7 @@ template <typename R> struct StageParams {
   Prim<R> prout;
   EosView<R> eos;
   int nx, ny, ne, periodic;
+  int nep;     // eta pitch of the layout (ne rounded up to a multiple of 4)
   int xhalo;   // 1: x planes -2, -1, nx, nx + 1 are stored halo planes (an x-slab); no clamping in x
   long long N;
   // tau of the step lives on the device (advanced by a kernel after every
@@ -275,13 +276,13 @@ __device__ __forceinline__ void shear_source(R geo, const R u[4], R du[4][4], co
 template <typename R, int STAGE, bool VISC, bool STATS>
 __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = c < p.N;
+  const bool active = c < p.N && (int)(c % p.nep) < p.ne;   // padding slots of the eta rows do no work
   double my_T0 = 0.0;
   double my_e = 0.0;
   bool f_rescaled = false, f_fail = false, f_polished = false, f_nonfinite = false, f_nonconv = false;
   if (active) {
-    const int k = (int)(c % p.ne);
-    const long long t = c / p.ne;
+    const int k = (int)(c % p.nep);
+    const long long t = c / p.nep;
     const int j = (int)(t % p.ny);
     const int i = (int)(t / p.ny);
     constexpr int NR = NRec<VISC>::n;
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
         const int ii = ax == 1 ? (p.xhalo ? i + o : wrap_index(i + o, p.nx, p.periodic)) : i;
         const int jj = ax == 2 ? wrap_index(j + o, p.ny, p.periodic) : j;
         const int kk = ax == 3 ? wrap_index(k + o, p.ne, p.periodic) : k;
-        id[d] = ((long long)ii * p.ny + jj) * p.ne + kk;
+        id[d] = ((long long)ii * p.ny + jj) * p.nep + kk;
       }
       R ut[5], va[5], cs[5];
 #pragma unroll
@@ -809,10 +810,16 @@ __global__ void __launch_bounds__(kBlock) extrapolate_prev_kernel(Prim<R> cur, P
   for (int m = 0; m < 3; ++m) prev.u[m][c] = R(2) * cur.u[m][c] - prev.u[m][c];
 }
 
+// Cell c of the compact order (nx, ny, neta) <-> its slot in the padded
+// layout, whose eta rows have a pitch nep >= neta (a multiple of 4).
+__device__ __forceinline__ long long padded_index(long long c, int ne, int nep) {
+  return (c / ne) * nep + c % ne;
+}
+
 template <typename R>
-__global__ void __launch_bounds__(kBlock) export_kernel(const R* src, double* dst, long long N) {
+__global__ void __launch_bounds__(kBlock) export_kernel(const R* src, double* dst, long long N, int ne, int nep) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (c < N) dst[c] = (double)src[c];
+  if (c < N) dst[c] = (double)src[padded_index(c, ne, nep)];
 }
 
 // Deterministic final sum of the per-block partials (one block).

@@ -42,6 +42,7 @@ struct TileArgs {
 template <typename R> struct EventGeom {
   long long off;
   int nx, ny, ne;
+  int nep;            // eta pitch (ne rounded up to a multiple of 4)
   R inv_dx, inv_dy;
   IsCoef<R> is;
   double deta;
@@ -60,41 +61,72 @@ template <int STAGE, bool VISC> struct CellIn {
   static constexpr int n = STAGE == 1 ? (VISC ? 4 : 1) : (VISC ? PIN + 10 : TN + 4);
 };
 
+// Row width of the staged box (in cells): the tile's TK columns with a
+// two-cell halo on each side, widened so that the box starts at a multiple of
+// 4 columns (rows of the layout are 16-byte aligned) and holds whole
+// 4-cell vectors: round_up(TK + 7, 4).
+__host__ __device__ constexpr int box_width(int TK) { return (TK + 10) & ~3; }
+
 // shared memory of one CTA, in bytes (sized for stage 2, which prefetches the
 // most per-cell inputs): two plane buffers, the y/eta interface fluxes, the
-// pending y/eta flux differences, the per-cell prefetch and the halo offsets
+// pending y/eta flux differences, the per-cell prefetch and the vector table
 template <bool VISC> inline size_t tile_smem_bytes(int TJ, int TK, size_t rsize) {
   using L = Box<VISC>;
-  const size_t NB = (size_t)(TJ + 4) * (TK + 4);
+  const size_t NB = (size_t)(TJ + 4) * box_width(TK);
   const size_t ncell = (size_t)TJ * TK;
   const size_t elems = 2 * L::NF * NB + (size_t)L::NQ * ((TJ + 1) * TK + TJ * (TK + 1)) + 2 * (size_t)L::NPEND * ncell +
                        2 * (size_t)CellIn<2, VISC>::n * ncell;
-  return elems * rsize + NB * sizeof(int);
+  return elems * rsize + 16 + NB * sizeof(int);   // vector table (NB / 4 int4) after up to 15 bytes of alignment
+}
+
+// Asynchronous copy of one 4-cell vector (16 bytes per 4 floats, two 16-byte
+// copies per 4 doubles): both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async_vec4(float* smem, const float* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_vec4(double* smem, const double* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa + 16u), "l"(gmem + 2) : "memory");
 }
 
 // Issue the asynchronous copies of the plane at offset poff (event offset +
-// plane index x ny x ne) of the tile (with its y/eta halo) into a box buffer
-// of NB cells per field: T~, pi~, P, c_s to their slots, u~ into the v slots
-// (the conversion pass turns them into u~^tau and v once the copies land).
-// goff[q]: in-plane offset of box cell q (boundary wrap or clamp applied).
-// Thread tid handles the box cells q = tid, tid + nthr, ... < qend; the
-// caller commits the group.
+// plane index x ny x nep) of the tile's box into a box buffer of NB cells per
+// field: T~, pi~, P, c_s to their slots, u~ into the v slots (the conversion
+// pass turns them into u~^tau and v once the copies land).  The box is made
+// of 4-cell vectors (vector w = box cells 4w .. 4w + 3); voff[w] holds the
+// in-plane offset of a vector inside the grid's eta range (.y < 0: one
+// vector copy) or the four offsets, clamped or wrapped at the boundary, of a
+// vector that crosses it.  Thread tid handles vectors w = tid, tid + nthr,
+// ... < nvec; the caller commits the group.
 template <typename R, bool VISC>
-__device__ __forceinline__ void stage_plane_async(const StageParams<R>& p, R* box, int qend, long long poff,
-                                                  const int* goff, int tid, int nthr, int NB) {
+__device__ __forceinline__ void stage_plane_async(const StageParams<R>& p, R* box, int nvec, long long poff,
+                                                  const int4* voff, int tid, int nthr, int NB) {
   using L = Box<VISC>;
-  for (int q = tid; q < qend; q += nthr) {
-    const long long g = poff + goff[q];
+  for (int w = tid; w < nvec; w += nthr) {
+    const int4 o = voff[w];
+    R* d = box + 4 * w;
+    auto copy = [&](R* dst, const R* src) {
+      if (o.y < 0) {
+        cp_async_vec4(dst, src + poff + o.x);
+      } else {
+        cp_async_elem(dst, src + poff + o.x);
+        cp_async_elem(dst + 1, src + poff + o.y);
+        cp_async_elem(dst + 2, src + poff + o.z);
+        cp_async_elem(dst + 3, src + poff + o.w);
+      }
+    };
 #pragma unroll
-    for (int m = 0; m < 4; ++m) cp_async_elem(box + m * NB + q, p.T[m] + g);
+    for (int m = 0; m < 4; ++m) copy(d + m * NB, p.T[m]);
     if constexpr (VISC) {
 #pragma unroll
-      for (int r = 0; r < 10; ++r) cp_async_elem(box + (4 + r) * NB + q, p.pi[r] + g);
+      for (int r = 0; r < 10; ++r) copy(d + (4 + r) * NB, p.pi[r]);
     }
 #pragma unroll
-    for (int m = 0; m < 3; ++m) cp_async_elem(box + (L::V + m) * NB + q, p.pr.u[m] + g);
-    cp_async_elem(box + L::P * NB + q, p.pr.P + g);
-    cp_async_elem(box + L::CS * NB + q, p.pr.cs + g);
+    for (int m = 0; m < 3; ++m) copy(d + (L::V + m) * NB, p.pr.u[m]);
+    copy(d + L::P * NB, p.pr.P);
+    copy(d + L::CS * NB, p.pr.cs);
   }
 }
 
@@ -165,7 +197,7 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
                                                 int bidx, unsigned char* smem_raw) {
   using L = Box<VISC>;
   constexpr int NF = L::NF, NQ = L::NQ, NR = L::NR, NPEND = L::NPEND;
-  const int BW = t.TK + 4, NB = BW * (t.TJ + 4);
+  const int BW = box_width(t.TK), NB = BW * (t.TJ + 4), NV = NB / 4;
   const int NHY = (t.TJ + 1) * t.TK, NHK = t.TJ * (t.TK + 1);
   const int ncell = t.TJ * t.TK;
   R* boxbuf = reinterpret_cast<R*>(smem_raw);   // two plane buffers [2][NF][NB]
@@ -174,7 +206,9 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
   R* pend = Hk + NQ * NHK;     // [2][NPEND][ncell]
   using CI = CellIn<STAGE, VISC>;
   R* cellbuf = pend + 2 * NPEND * ncell;             // [2][CI::n][ncell]
-  int* goff = reinterpret_cast<int*>(cellbuf + 2 * CellIn<2, VISC>::n * ncell);  // [NB]
+  // [NV] vector table, 16-byte aligned (int4 accesses)
+  int4* voff = reinterpret_cast<int4*>(
+      (reinterpret_cast<uintptr_t>(cellbuf + 2 * CellIn<2, VISC>::n * ncell) + 15) & ~static_cast<uintptr_t>(15));
 
   const int nthr = (t.TJ + 1) * (t.TK + 1);
   const bool worker = threadIdx.x < nthr;
@@ -187,12 +221,14 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
   const int tjt = bidx % t.ntj;
   const int ch = bidx / t.ntj;
   const int j0 = tjt * t.TJ, k0 = tkt * t.TK, x0 = ch * t.CX;
+  const int kb0 = ((k0 - 2) >> 2) << 2;   // first box column: k0 - 2 rounded down to a multiple of 4
+  const int coff = k0 - kb0;              // box column of the tile's first column (2..5)
   const int x1 = min(x0 + t.CX, ev.nx);
   const bool is_cell = worker && ta < t.TJ && tb < t.TK;
   const int j = j0 + ta, k = k0 + tb;
   const bool active = is_cell && j < ev.ny && k < ev.ne;
   const int cid = ta * t.TK + tb;                  // cell slot (valid when is_cell)
-  const int center = (ta + 2) * BW + (tb + 2);     // box cell of (ta, tb)
+  const int center = (ta + 2) * BW + (tb + coff);  // box cell of (ta, tb)
   const TauS<R> ts = tau_scalars(p, STAGE);
   const R taus = ts.taus;
   const R inv_dx = ev.inv_dx;
@@ -213,16 +249,21 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
   for (int m = 0; m < 4; ++m) ucm1[m] = R(0);
 
 
-  // in-plane offsets of this thread's box cells (only this thread uses them)
-  const int qend = worker ? NB : 0;   // box cells this thread stages: q = tid, tid + nthr, ... < qend
-  for (int q = tid; q < qend; q += nthr) {
-    const int bj = q / BW, bk = q - bj * BW;
-    goff[q] = wrap_index(j0 + bj - 2, ev.ny, p.periodic) * ev.ne + wrap_index(k0 + bk - 2, ev.ne, p.periodic);
+  // in-plane offsets of this thread's box vectors (only this thread uses them)
+  const int vend = worker ? NV : 0;   // vectors this thread stages: w = tid, tid + nthr, ... < vend
+  for (int w = tid; w < vend; w += nthr) {
+    const int bj = (4 * w) / BW, c0 = kb0 + 4 * w - bj * BW;
+    const int row = wrap_index(j0 + bj - 2, ev.ny, p.periodic) * ev.nep;
+    if (c0 >= 0 && c0 + 3 < ev.ne)
+      voff[w] = make_int4(row + c0, -1, 0, 0);
+    else
+      voff[w] = make_int4(row + wrap_index(c0, ev.ne, p.periodic), row + wrap_index(c0 + 1, ev.ne, p.periodic),
+                          row + wrap_index(c0 + 2, ev.ne, p.periodic), row + wrap_index(c0 + 3, ev.ne, p.periodic));
   }
-  const long long plane = (long long)ev.ny * ev.ne;
+  const long long plane = (long long)ev.ny * ev.nep;
   // x planes beyond the grid: clamped or wrapped, or (an x-slab) the stored halo planes
   auto xplane = [&](int x) { return p.xhalo ? x : wrap_index(x, ev.nx, p.periodic); };
-  stage_plane_async<R, VISC>(p, boxbuf + ((x0 - 2) & 1) * NF * NB, qend, ev.off + xplane(x0 - 2) * plane, goff, tid,
+  stage_plane_async<R, VISC>(p, boxbuf + ((x0 - 2) & 1) * NF * NB, vend, ev.off + xplane(x0 - 2) * plane, voff, tid,
                              nthr, NB);
   cp_async_commit();
   for (int pl = x0 - 2; pl <= x1 + 1; ++pl) {
@@ -232,36 +273,40 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
     // the output cell) have landed: its u~ -> (u~^tau, v) in place, then one
     // barrier makes the whole plane visible
     cp_async_wait_all();
-    for (int q = tid; q < qend; q += nthr) {
-      const R ux = box[L::V * NB + q], uy = box[(L::V + 1) * NB + q], ue = box[(L::V + 2) * NB + q];
-      const R ut = sqrt(R(1) + ux * ux + uy * uy + ue * ue);
-      const R iu = R(1) / ut;
-      box[L::UT * NB + q] = ut;
-      box[L::V * NB + q] = ux * iu;
-      box[(L::V + 1) * NB + q] = uy * iu;
-      box[(L::V + 2) * NB + q] = ue * iu;
+    for (int w = tid; w < vend; w += nthr) {   // the cells of its vectors
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int q = 4 * w + i;
+        const R ux = box[L::V * NB + q], uy = box[(L::V + 1) * NB + q], ue = box[(L::V + 2) * NB + q];
+        const R ut = sqrt(R(1) + ux * ux + uy * uy + ue * ue);
+        const R iu = R(1) / ut;
+        box[L::UT * NB + q] = ut;
+        box[L::V * NB + q] = ux * iu;
+        box[(L::V + 1) * NB + q] = uy * iu;
+        box[(L::V + 2) * NB + q] = ue * iu;
+      }
     }
     __syncthreads();
     // prefetch the next plane into the other buffer while this one is used,
     // with the per-cell inputs of the cell output two planes on (pl - 1)
     if (pl + 1 <= x1 + 1) {
-      stage_plane_async<R, VISC>(p, boxbuf + ((pl + 1) & 1) * NF * NB, qend,
-                                 ev.off + xplane(pl + 1) * plane, goff, tid, nthr, NB);
+      stage_plane_async<R, VISC>(p, boxbuf + ((pl + 1) & 1) * NF * NB, vend,
+                                 ev.off + xplane(pl + 1) * plane, voff, tid, nthr, NB);
       if (active && pl - 1 >= x0 && pl - 1 < x1)
         prefetch_cell<R, STAGE, VISC>(p, cellbuf + (size_t)((pl - 1) & 1) * CI::n * ncell + cid, ncell,
-                                      ev.off + ((long long)(pl - 1) * ev.ny + j) * ev.ne + k);
+                                      ev.off + ((long long)(pl - 1) * ev.ny + j) * ev.nep + k);
       cp_async_commit();
     }
     // ---- 2. every y- and eta-interface of an output plane, once
     if (out_plane) {
       R H[NQ];
       if (worker && tb < t.TK) {   // y-interface between rows ta-1 and ta of column tb
-        box_interface<R, VISC>(box, NB, (ta + 2) * BW + tb + 2, BW, 2, taus, H);
+        box_interface<R, VISC>(box, NB, (ta + 2) * BW + tb + coff, BW, 2, taus, H);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) Hy[q * NHY + ta * t.TK + tb] = H[q];
       }
       if (worker && ta < t.TJ) {   // eta-interface between columns tb-1 and tb of row ta
-        box_interface<R, VISC>(box, NB, (ta + 2) * BW + tb + 2, 1, 3, taus, H);
+        box_interface<R, VISC>(box, NB, (ta + 2) * BW + tb + coff, 1, 3, taus, H);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) Hk[q * NHK + ta * (t.TK + 1) + tb] = H[q];
       }
@@ -292,7 +337,7 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
           if (it >= 4 && active) {
             // ============ output cell c = pl - 2 (own fields: W0) ============
             const int c = pl - 2;
-            const long long gc = ev.off + ((long long)c * ev.ny + j) * ev.ne + k;
+            const long long gc = ev.off + ((long long)c * ev.ny + j) * ev.nep + k;
             const R* pd = pend + (size_t)(c & 1) * NPEND * ncell;
             const R* cb = cellbuf + (size_t)(c & 1) * CI::n * ncell + cid;
             R S[NQ];
@@ -437,7 +482,7 @@ template <typename R, int STAGE, bool VISC>
 __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS)
     stage_tile_kernel(const StageParams<R> p, const TileArgs t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const EventGeom<R> ev{0, p.nx, p.ny, p.ne, p.inv_dl[0], p.inv_dl[1], p.is, p.deta_d, VISC ? 1 : 0};
+  const EventGeom<R> ev{0, p.nx, p.ny, p.ne, p.nep, p.inv_dl[0], p.inv_dl[1], p.is, p.deta_d, VISC ? 1 : 0};
   stage_tile_body<R, STAGE, VISC>(p, ev, t, blockIdx.x, smem_raw);
 }
 
