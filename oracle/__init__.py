@@ -31,6 +31,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "clv_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "clv_freezeout.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libclv_oracle.so")
 _lock = threading.Lock()
@@ -44,10 +45,10 @@ def build(force: bool = False, plant: int = 0) -> str:
     in; only the pin meta-test uses it."""
     os.makedirs(_BUILD, exist_ok=True)
     lib = _LIB if plant == 0 else os.path.join(_BUILD, f"libclv_oracle_plant{plant}.so")
-    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < max(map(os.path.getmtime, _SRCS)):
         tmp = lib + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fno-fast-math",
-               "-fopenmp", "-fPIC", "-shared", f"-DPLANT={int(plant)}", "-o", tmp, _SRC, "-lm"]
+               "-fopenmp", "-fPIC", "-shared", f"-DPLANT={int(plant)}", "-o", tmp, *_SRCS, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, lib)
     return lib
@@ -67,6 +68,14 @@ class _Config(ctypes.Structure):
         ("cartesian", ctypes.c_int), ("periodic", ctypes.c_int),
         ("eps_cut", ctypes.c_double), ("nthreads", ctypes.c_int),
         ("taupi_coef", ctypes.c_double), ("lambda1_hat", ctypes.c_double),
+    ]
+
+
+class _FoGrid(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("neta", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("deta", ctypes.c_double),
+        ("tau0", ctypes.c_double), ("tau1", ctypes.c_double), ("cartesian", ctypes.c_int),
     ]
 
 
@@ -92,6 +101,12 @@ def _load(plant: int = 0):
             lib.orc_source_pi.argtypes = [P, ctypes.c_double, D, D, D, ctypes.c_double, D]
             lib.orc_source_T.argtypes = [P, ctypes.c_double, D, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, D]
+            G = ctypes.POINTER(_FoGrid)
+            lib.orc_freezeout.restype = ctypes.c_int64
+            lib.orc_freezeout.argtypes = [G, D, D, D, D, ctypes.c_double, D,
+                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int64]
+            lib.orc_freezeout_simplex.argtypes = [G, D, D, ctypes.c_double, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_int, ctypes.c_int, D]
             _libs[plant] = lib
     return _libs[plant]
 
@@ -204,3 +219,53 @@ class Oracle:
 
 def set_threads(n: int) -> int:
     return _load().orc_set_threads(int(n))
+
+
+FO_RECORD = ["dS_tau", "dS_x", "dS_y", "dS_eta", "tau", "x", "y", "eta", "ut", "ux", "uy", "ueta",
+             *[f"pi{k}" for k in ("tt", "tx", "ty", "te", "xx", "xy", "xe", "yy", "ye", "ee")]]
+
+
+def _fo_grid(shape, dx, dy, deta, tau0, tau1, cartesian):
+    g = _FoGrid()
+    g.nx, g.ny, g.neta = (int(n) for n in shape)
+    g.dx, g.dy, g.deta = float(dx), float(dy), float(deta)
+    g.tau0, g.tau1, g.cartesian = float(tau0), float(tau1), int(bool(cartesian))
+    return g
+
+
+def freezeout(e0, e1, eps_f, dx, dy, deta, tau0, tau1, fields0=None, fields1=None, cartesian=False,
+              capacity=None, plant=0):
+    """Surface elements of eps = eps_f between the slices e0 (tau0) and e1
+    (tau1), grids of shape (nx, ny, neta); fields*: (13, nx, ny, neta) arrays
+    of u~^x, u~^y, u~^eta and pi~ (tt..ee), or None for zeros.  Returns
+    (records (n, 22) in FO_RECORD order, hypercube indices (n,)), in
+    increasing hypercube order (clv_freezeout.c, readings F1-F6)."""
+    e0 = np.ascontiguousarray(e0, dtype=np.float64)
+    e1 = np.ascontiguousarray(e1, dtype=np.float64).reshape(e0.shape)
+    z = np.zeros((13,) + e0.shape)
+    f0 = z if fields0 is None else np.ascontiguousarray(fields0, dtype=np.float64).reshape(z.shape)
+    f1 = z if fields1 is None else np.ascontiguousarray(fields1, dtype=np.float64).reshape(z.shape)
+    g = _fo_grid(e0.shape, dx, dy, deta, tau0, tau1, cartesian)
+    lib = _load(plant)
+    if capacity is None:
+        capacity = int(np.prod([n - 1 for n in e0.shape]))
+    rec = np.zeros((max(capacity, 1), 22))
+    cube = np.zeros(max(capacity, 1), dtype=np.int64)
+    n = lib.orc_freezeout(ctypes.byref(g), _dp(e0), _dp(e1), _dp(f0), _dp(f1), float(eps_f), _dp(rec),
+                          cube.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(capacity))
+    if n < 0:
+        raise ValueError("bad freeze-out grid")
+    m = min(n, capacity)
+    return rec[:m].copy(), cube[:m].copy(), int(n)
+
+
+def freezeout_simplex(e0, e1, eps_f, dx, dy, deta, tau0, tau1, i, j, k, s, cartesian=False, plant=0):
+    """dSigma_mu of simplex s (lexicographic ordering of the axes) of
+    hypercube (i, j, k) alone."""
+    e0 = np.ascontiguousarray(e0, dtype=np.float64)
+    e1 = np.ascontiguousarray(e1, dtype=np.float64).reshape(e0.shape)
+    g = _fo_grid(e0.shape, dx, dy, deta, tau0, tau1, cartesian)
+    out = np.zeros(4)
+    _load(plant).orc_freezeout_simplex(ctypes.byref(g), _dp(e0), _dp(e1), float(eps_f), int(i), int(j),
+                                       int(k), int(s), _dp(out))
+    return out

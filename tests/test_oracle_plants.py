@@ -10,12 +10,18 @@ the CPU only) and at least one pin must then fail:
   6 Christoffel term of nabla_eta u^eta   -> transversality drift / Bjorken
   7 S_T^eta dropped                       -> linearised eta wave
   8 EOS argument E instead of E - M v     -> brute-force root solve (Gubser flow)
+Freeze-out surface (clv_freezeout.c):
+  9 normal along +grad eps                -> planar level set in time
+ 10 one tetrahedron of the prism dropped  -> coarea closed form per simplex
+ 11 Milne weight tau0 instead of the piece's tau -> planar level sets in space
+ 12 one simplex of the 24 left out        -> closed level set / planar in time
 """
 import numpy as np
 import pytest
 
 import oracle
 import test_oracle_flows as F
+import test_oracle_freezeout as FO
 
 CASES = {
     1: F.check_transversality,
@@ -26,6 +32,10 @@ CASES = {
     6: F.check_bjorken_viscous,
     7: F.check_eta_wave,
     8: F.check_gubser,
+    9: FO.check_planar_tau,
+    10: FO.check_simplices,
+    11: FO.check_planar_axes,
+    12: FO.check_closed_surface,
 }
 
 
