@@ -31,7 +31,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "clv_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "clv_freezeout.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "clv_freezeout.c"), os.path.join(_HERE, "clv_cooperfrye.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libclv_oracle.so")
 _lock = threading.Lock()
@@ -79,6 +79,12 @@ class _FoGrid(ctypes.Structure):
     ]
 
 
+class _CfSpecies(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("g", ctypes.c_double), ("stat", ctypes.c_int),
+                ("mu", ctypes.c_double), ("Tf", ctypes.c_double), ("ePf", ctypes.c_double),
+                ("viscous", ctypes.c_int)]
+
+
 def _load(plant: int = 0):
     with _lock:
         if plant not in _libs:
@@ -105,6 +111,8 @@ def _load(plant: int = 0):
             lib.orc_freezeout.restype = ctypes.c_int64
             lib.orc_freezeout.argtypes = [G, D, D, D, D, ctypes.c_double, D,
                                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int64]
+            lib.orc_cooper_frye.argtypes = [ctypes.POINTER(_CfSpecies), D, ctypes.c_int64, D, ctypes.c_int,
+                                            D, ctypes.c_int, D, ctypes.c_int, D]
             lib.orc_freezeout_simplex.argtypes = [G, D, D, ctypes.c_double, ctypes.c_int,
                                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, D]
             _libs[plant] = lib
@@ -268,4 +276,22 @@ def freezeout_simplex(e0, e1, eps_f, dx, dy, deta, tau0, tau1, i, j, k, s, carte
     out = np.zeros(4)
     _load(plant).orc_freezeout_simplex(ctypes.byref(g), _dp(e0), _dp(e1), float(eps_f), int(i), int(j),
                                        int(k), int(s), _dp(out))
+    return out
+
+
+def cooper_frye(rec, Y, pT, phi, mass, g, stat, Tf, ePf=1.0, mu=0.0, viscous=True, plant=0):
+    """dN/(dY pT dpT dphi) (GeV^-2) of one species on the (Y, pT, phi) grid
+    from element records (n, 22) in FO_RECORD order (clv_cooperfrye.c,
+    readings C1-C4); stat +1 Fermi-Dirac, -1 Bose-Einstein, 0 Boltzmann.
+    Returns an array of shape (len(Y), len(pT), len(phi))."""
+    rec = np.ascontiguousarray(rec, dtype=np.float64).reshape(-1, 22)
+    Y, pT, phi = (np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (Y, pT, phi))
+    sp = _CfSpecies()
+    sp.mass, sp.g, sp.stat, sp.mu = float(mass), float(g), int(stat), float(mu)
+    sp.Tf, sp.ePf, sp.viscous = float(Tf), float(ePf), int(bool(viscous))
+    out = np.zeros((len(Y), len(pT), len(phi)))
+    st = _load(plant).orc_cooper_frye(ctypes.byref(sp), _dp(rec), rec.shape[0], _dp(Y), len(Y), _dp(pT),
+                                      len(pT), _dp(phi), len(phi), _dp(out))
+    if st != 0:
+        raise ValueError("bad Cooper-Frye arguments")
     return out

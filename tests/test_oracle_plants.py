@@ -15,12 +15,17 @@ Freeze-out surface (clv_freezeout.c):
  10 one tetrahedron of the prism dropped  -> coarea closed form per simplex
  11 Milne weight tau0 instead of the piece's tau -> planar level sets in space
  12 one simplex of the 24 left out        -> closed level set / planar in time
+Cooper-Frye spectra (clv_cooperfrye.c):
+ 13 tau p^eta dSigma_eta multiplied by tau instead of divided -> particle number n u.dSigma
+ 14 quantum statistics sign flipped       -> Bessel closed form of the boost-invariant surface
+ 15 sign of the p~^eta u~^eta term of p.u -> particle number n u.dSigma
 """
 import numpy as np
 import pytest
 
 import oracle
 import test_oracle_flows as F
+import test_oracle_cooperfrye as CF
 import test_oracle_freezeout as FO
 
 CASES = {
@@ -36,6 +41,9 @@ CASES = {
     10: FO.check_simplices,
     11: FO.check_planar_axes,
     12: FO.check_closed_surface,
+    13: CF.check_particle_number,
+    14: CF.check_bjorken_bessel,
+    15: CF.check_particle_number,
 }
 
 
