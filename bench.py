@@ -48,6 +48,11 @@ KERNEL_WORDS = {
     "recover2": 15,  # read T~^{tau mu} 4, pi~^{tau mu} 4, u~' 3; write eps, u~ 4
 }
 LEDGER_WORDS = 92    # the method's per-cell-update ledger for a fused step (each field once per stage)
+# Freeze-out surface finder (FP32): algorithmic bytes per hypercube (eps of
+# both slices, each cell once) and per element (the 22-value record and its
+# hypercube index written, u~ and pi~ of one cell of each slice read)
+FO_BYTES_PER_CUBE = 2 * 4
+FO_BYTES_PER_ELEMENT = 22 * 4 + 8 + 2 * 13 * 4
 KERNEL_NAMES = {"stage1": "stage_tile_kernel<float,1,viscous>", "recover1": "recover_kernel<float,viscous>",
                 "stage2": "stage_tile_kernel<float,2,viscous>", "recover2": "recover_kernel<float,viscous>"}
 
@@ -321,6 +326,50 @@ def run_gpu(args):
                  "stats_fp64": {k: stL64.get(k) for k in ("tau", "eps_max", "n_rootfail", "error_word", "error",
                                                           "tile")}}
 
+    # ---- freeze-out surface of the same event: T_f = 137 MeV (the paper's
+    # stopping temperature) through the EOS table, between the slices at
+    # tau = 2.4 and 2.5 fm; the four launches of clv_fo_find timed with
+    # events on the handle's stream, L2 flushed between calls (untimed)
+    freezeout = None
+    if args.freezeout:
+        g = clv.from_case(case, clv.CLV_FP32)
+        g.set_initial_case(case)
+        g.set_mlp(params_host)
+        g.set_guess(clv.CLV_GUESS_MLP)
+        g.step(200)
+        snap = g.fo_snapshot()
+        g.step(10)
+        cur = g.fo_current()
+        eos = case.eos
+        lne = eos["lne0"] + eos["dlne"] * np.arange(len(eos["T"]))
+        eps_f = float(np.float32(np.exp(np.interp(0.137, eos["T"], lne))))
+        finder = clv.FreezeoutFinder(g.fo_grid(), device=dev, stream=g.stream)
+        for _ in range(3):
+            finder.find(snap, cur, eps_f)
+        reps = 50
+        fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        torch.cuda.synchronize()
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            fev[i][0].record(g.stream)
+            finder.find(snap, cur, eps_f)
+            fev[i][1].record(g.stream)
+        torch.cuda.synchronize()
+        fms = sum(a.elapsed_time(b) for a, b in fev) / reps
+        _, _, nel = finder.result()
+        gr = g.fo_grid()
+        ncube = (gr.nx - 1) * (gr.ny - 1) * (gr.neta - 1)
+        fo_alg = FO_BYTES_PER_CUBE * ncube + FO_BYTES_PER_ELEMENT * nel
+        fo_ach = fo_alg / (fms / 1e3) / 1e9
+        freezeout = {"workload": "the same event at tau = 2.4 -> 2.5 fm (10 steps apart), T_f = 137 MeV",
+                     "eps_f": eps_f, "hypercubes": ncube, "elements": nel, "ms_per_find": fms,
+                     "value": ncube / (fms / 1e3), "unit": "hypercubes/s", "launches_per_find": 4,
+                     "l2": "flushed between calls (512 MiB write, untimed)",
+                     "roofline": {"bound": "hbm", "kernel": "clv_fo_find (classify, scan, compact, elements)",
+                                  "achieved": fo_ach, "peak": peak, "unit": "GB/s", "frac": fo_ach / peak,
+                                  "algorithmic_bytes_per_find": fo_alg}}
+        g.close()
+
     # ---- event-by-event batch: uneven grids in one handle, one persistent
     # stage launch per stage (state ~19 GB FP32, far larger than L2)
     batch = None
@@ -406,6 +455,7 @@ def run_gpu(args):
         "learned_guess": learned,
         "large_event": large,
         "batch": batch,
+        "freezeout": freezeout,
         "roofline": roof,
         "e2e": e2e,
         # per step: two stages of (stage kernel, root solve) and the tau advance
@@ -521,6 +571,8 @@ def main():
                     help="events of the event-by-event batch measured beside the headline (0: skip)")
     ap.add_argument("--no-large", dest="large", action="store_false",
                     help="skip the 261x261x121 mini-jet event measured beside the headline")
+    ap.add_argument("--no-freezeout", dest="freezeout", action="store_false",
+                    help="skip the freeze-out surface measured beside the headline")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default tile shape instead of timing candidates (setup, untimed)")
     ap.add_argument("--train-events", type=int, default=2, help="FP64 events whose states train the guess")

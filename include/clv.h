@@ -351,12 +351,137 @@ clv_status clv_autotune(clv_handle* h, int max_candidates, int reps, clv_tile_in
 clv_status clv_field_stats_noalloc(const double* d_eps, const double* d_Ttt, int64_t n, double cell_volume,
                                    void* cuda_stream, double* d_out);
 
+/* ---------------- freeze-out hypersurface ----------------
+ * Surface elements dSigma_mu of the hypersurface eps = eps_f between two
+ * time slices: the input of the Cooper-Frye integral, Eq. (cooper_frye) of
+ * Sec. 4 (a constant T_f is a constant eps_f through the monotone equation
+ * of state).  The paper runs its surface finder on the GPU (appendix on the
+ * parallel reduction) and cites it without describing it.  Here the surface
+ * is the level set of the piecewise-linear interpolant of eps over the
+ * Freudenthal triangulation of every space-time hypercube:
+ *   - hypercube (i, j, k) has its 16 corners at the cell centres i..i+1,
+ *     j..j+1, k..k+1 of both slices: (nx-1)(ny-1)(neta-1) hypercubes;
+ *   - it is cut into the 24 4-simplices of the orderings of the axes
+ *     (tau, x, y, eta_s).  Inside a simplex the level set is a planar
+ *     tetrahedron or triangular prism.  A corner is inside when eps >= eps_f;
+ *   - dSigma_mu sums, over the pieces, -grad_mu eps / |grad eps| times the
+ *     integral of tau over the piece (1 in Cartesian mode).  The geometry
+ *     is taken in the coordinates (tau, x, y, eta_s) as R^4;
+ *   - dSigma_mu is covariant, with dSigma_eta in fm^4.  It points to lower
+ *     eps, so p^mu dSigma_mu > 0 for outgoing particles;
+ *   - each crossed hypercube gives one element, placed at the
+ *     3-volume-weighted mean of the piece centroids;
+ *   - u~ and pi~ are interpolated at that point by the same interpolant, and
+ *     u~^tau = sqrt(1 + u~_x^2 + u~_y^2 + u~_eta^2).
+ * Element record: CLV_FO_NREC values of the slices' type, in this order:
+ *   dSigma_tau, dSigma_x, dSigma_y, dSigma_eta, tau, x, y, eta_s,
+ *   u~^tau, u~^x, u~^y, u~^eta, pi~ (tt tx ty te xx xy xe yy ye ee).
+ * Elements come in increasing hypercube order ((i (ny-1) + j)(neta-1) + k);
+ * the result does not depend on the launch. */
+#define CLV_FO_NREC 22
+
+typedef struct {
+  int nx, ny, neta;          /* cells per axis of each slice, each >= 2; cell centres as in clv_config */
+  int eta_pitch;             /* elements between consecutive eta rows (>= neta; 0 means neta) */
+  double dx, dy, deta;       /* spacings (> 0) */
+  int precision;             /* CLV_FP64: slice arrays and records are doubles; CLV_FP32: floats */
+  int cartesian;             /* 1: no tau weight (coordinates t, x, y, z) */
+} clv_fo_grid;
+
+typedef struct {
+  double tau;                /* proper time of the slice (> 0 unless cartesian) */
+  const void* eps;           /* device array, nx*ny*eta_pitch values, eta_s fastest */
+  const void* u[3];          /* u~^x, u~^y, u~^eta (device, same layout) */
+  const void* pi[10];        /* pi~ tt..ee (device, same layout); all NULL means pi = 0 */
+} clv_fo_slice;
+
+/* Device scratch bytes that clv_fo_find needs for this grid. */
+clv_status clv_fo_scratch_bytes(const clv_fo_grid* g, size_t* bytes);
+
+/* Elements of eps = eps_f between the slices s0 and s1 (s1->tau > s0->tau).
+ *   d_rec     device array of `capacity` records; records past capacity are not written;
+ *   d_cube    nullable device int64 array of `capacity` hypercube indices;
+ *   d_count   device int64; receives the number of elements, which may exceed capacity;
+ *   d_scratch clv_fo_scratch_bytes bytes of device memory, 16-byte aligned.
+ * Enqueued on cuda_stream (a cudaStream_t; NULL is the default stream); it
+ * does not synchronise.  CLV_EINVAL for a bad argument: clv_last_error(NULL)
+ * names it. */
+clv_status clv_fo_find(const clv_fo_grid* g, const clv_fo_slice* s0, const clv_fo_slice* s1, double eps_f,
+                       void* d_rec, int64_t* d_cube, int64_t capacity, int64_t* d_count, void* d_scratch,
+                       void* cuda_stream);
+
+/* The grid of a single-event handle (not a batch or an x-slab) and a slice
+ * viewing its current state: eps, u~ and pi~ in the working precision at the
+ * handle's tau.  The view is valid until the next step. */
+clv_status clv_fo_grid_of(clv_handle* h, clv_fo_grid* out);
+clv_status clv_fo_current(clv_handle* h, clv_fo_slice* out);
+
+/* Device bytes of one slice copy.  clv_fo_snapshot copies the current slice
+ * into d_buf (that many bytes, 256-byte aligned, caller-owned), enqueued on
+ * the handle's stream; *out views the copy. */
+clv_status clv_fo_slice_bytes(clv_handle* h, size_t* bytes);
+clv_status clv_fo_snapshot(clv_handle* h, void* d_buf, clv_fo_slice* out);
+
+/* ---------------- smooth Cooper-Frye spectra ----------------
+ * The invariant momentum distribution of hadron species from freeze-out
+ * surface elements, Sec. 4, Eqs. (cooper_frye) and (feq):
+ *   dN/(dY pT dpT dphi) = g / (2 pi hbar c)^3  sum over elements of
+ *                         p^mu dSigma_mu f_eq (1 + delta f),
+ *   f_eq    = 1 / (exp[(p.u - mu)/T_f] + s),
+ *   delta f = (1 - s f_eq) p_mu p_nu pi^{mu nu} / (2 T_f^2 (eps + P)),
+ * with s = +1 (Fermi-Dirac), -1 (Bose-Einstein) or 0 (Boltzmann), in GeV^-2.
+ *   - The elements are clv_fo_find records (CLV_FO_NREC values each).
+ *   - Momentum at the element's eta_s: p^tau = mT cosh(Y - eta_s),
+ *     tau p^eta = mT sinh(Y - eta_s), p^x = pT cos phi, p^y = pT sin phi.
+ *   - p.u and p_mu p_nu pi^{mu nu} are taken in the tilde components of u~
+ *     and pi~ (metric diag(1, -1, -1, -1)).
+ *   - Elements with p^mu dSigma_mu < 0 are summed as they are.
+ * The spectrum is evaluated at the points of a (Y, pT, phi) grid; the paper
+ * uses 41 x 15 x 48 points, with pT and phi at Gauss quadrature nodes.
+ * Several species share one pass over the elements (up to
+ * CLV_CF_MAX_SPECIES per call). */
+#define CLV_CF_MAX_SPECIES 32
+
+typedef struct {
+  double mass;               /* GeV, >= 0 */
+  double g;                  /* degeneracy, > 0 */
+  int stat;                  /* +1 Fermi-Dirac, -1 Bose-Einstein, 0 Boltzmann */
+  double mu;                 /* chemical potential, GeV */
+} clv_cf_species;
+
+typedef struct {
+  double Tf;                 /* freeze-out temperature, GeV (> 0) */
+  double ePf;                /* eps + P at the freeze-out, GeV/fm^3 (> 0 when viscous) */
+  int viscous;               /* 1: include delta f from the elements' pi~ */
+  int precision;             /* CLV_FP64 or CLV_FP32: the type of the records; FP32 sums each
+                                tile of 128 elements in FP32 and the tiles in FP64 */
+} clv_cf_params;
+
+/* Device scratch bytes of clv_cf_spectra for these sizes. */
+clv_status clv_cf_scratch_bytes(const clv_cf_params* p, int64_t nel, int nsp, int nY, int npt, int nphi,
+                                size_t* bytes);
+
+/* Spectra of nsp species (host array) into d_out: nsp x nY x npt x nphi
+ * doubles on the device, in the order [species][Y][pT][phi].
+ *   d_rec          device records of the elements (type per p->precision);
+ *   nel            number of records, or an upper bound when d_nel is given;
+ *   d_nel          nullable device int64: the number of records (for example
+ *                  the d_count of clv_fo_find), read on the device and
+ *                  capped at nel, so nothing is synchronised;
+ *   d_Y, d_pT, d_phi  device arrays (doubles) of the grid axes;
+ *   d_scratch      clv_cf_scratch_bytes bytes of device memory, 256-byte aligned.
+ * The sum over elements is deterministic (fixed order).  Enqueued on
+ * cuda_stream; CLV_EINVAL for a bad argument (clv_last_error(NULL)). */
+clv_status clv_cf_spectra(const clv_cf_params* p, const clv_cf_species* species, int nsp, const void* d_rec,
+                          int64_t nel, const int64_t* d_nel, const double* d_Y, int nY, const double* d_pT, int npt,
+                          const double* d_phi, int nphi, double* d_out, void* d_scratch, void* cuda_stream);
+
 /* Release the handle and the memory it owns.  NULL is ignored. */
 void clv_destroy(clv_handle* h);
 
 /* Message of the last failing call on this handle ("" if none).  With
  * h == NULL: the last failure of a call without a handle (clv_create,
- * clv_create_ws, clv_workspace_bytes, clv_field_stats_noalloc). */
+ * clv_create_ws, clv_workspace_bytes, clv_field_stats_noalloc, clv_fo_*, clv_cf_*). */
 const char* clv_last_error(const clv_handle* h);
 
 /* Library version string. */

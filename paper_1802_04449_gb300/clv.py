@@ -67,6 +67,22 @@ class clv_tile_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class clv_fo_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("neta", ctypes.c_int), ("eta_pitch", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("deta", ctypes.c_double),
+                ("precision", ctypes.c_int), ("cartesian", ctypes.c_int)]
+
+
+class clv_fo_slice(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("eps", ctypes.c_void_p), ("u", ctypes.c_void_p * 3),
+                ("pi", ctypes.c_void_p * 10)]
+
+
+FO_NREC = 22
+FO_RECORD = ["dS_tau", "dS_x", "dS_y", "dS_eta", "tau", "x", "y", "eta", "ut", "ux", "uy", "ueta",
+             "pitt", "pitx", "pity", "pite", "pixx", "pixy", "pixe", "piyy", "piye", "piee"]
+
+
 class ClvError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -84,7 +100,9 @@ EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initi
             "clv_set_initial_T_device", "clv_state_bytes", "clv_get_state", "clv_set_state",
             "clv_create_batch", "clv_batch_size", "clv_batch_set_initial", "clv_batch_get_fields",
             "clv_batch_event_stats", "clv_set_graphs", "clv_slab_halo_bytes", "clv_slab_pack",
-            "clv_slab_unpack", "clv_slab_fill_edge", "clv_slab_predictor", "clv_stage"]
+            "clv_slab_unpack", "clv_slab_fill_edge", "clv_slab_predictor", "clv_stage",
+            "clv_fo_scratch_bytes", "clv_fo_find", "clv_fo_grid_of", "clv_fo_current", "clv_fo_slice_bytes",
+            "clv_fo_snapshot"]
 CLV_GUESS_PREVIOUS, CLV_GUESS_COLD, CLV_GUESS_MLP = 0, 1, 2
 MLP_NPARAM = 5124
 
@@ -145,6 +163,13 @@ def load(path: str | None = None):
         lib.clv_get_tile.argtypes = [P, TI]
         lib.clv_set_tile.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         lib.clv_autotune.argtypes = [P, ctypes.c_int, ctypes.c_int, TI]
+        FG, FS = ctypes.POINTER(clv_fo_grid), ctypes.POINTER(clv_fo_slice)
+        lib.clv_fo_scratch_bytes.argtypes = [FG, ctypes.POINTER(ctypes.c_size_t)]
+        lib.clv_fo_find.argtypes = [FG, FS, FS, ctypes.c_double, V, V, ctypes.c_int64, V, V, V]
+        lib.clv_fo_grid_of.argtypes = [P, FG]
+        lib.clv_fo_current.argtypes = [P, FS]
+        lib.clv_fo_slice_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        lib.clv_fo_snapshot.argtypes = [P, V, FS]
         lib.clv_destroy.argtypes = [P]
         lib.clv_destroy.restype = None
         lib.clv_last_error.argtypes = [P]
@@ -159,6 +184,94 @@ def load(path: str | None = None):
 
 def _dp(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _raise(lib, st):
+    if st != 0:
+        msg = lib.clv_last_error(None)
+        raise ClvError(st, msg.decode() if msg else "")
+
+
+class FoSlice:
+    """A time slice for the freeze-out finder: the clv_fo_slice struct and
+    the device memory it points into (kept alive here)."""
+
+    def __init__(self, tau, eps, u, pi=None, keep=()):
+        self.s = clv_fo_slice()
+        self.s.tau = float(tau)
+        self.s.eps = eps
+        for m in range(3):
+            self.s.u[m] = u[m]
+        for q in range(10):
+            self.s.pi[q] = pi[q] if pi is not None else None
+        self.keep = list(keep)
+
+    @classmethod
+    def from_tensors(cls, tau, eps, u, pi=None):
+        """Slice from CUDA tensors (grid-shaped, one dtype): eps, u = (u~^x,
+        u~^y, u~^eta), pi = ten pi~ components (tt..ee) or None."""
+        ts = [eps, *u] + (list(pi) if pi is not None else [])
+        for t in ts:
+            if not (t.is_cuda and t.is_contiguous() and t.dtype == eps.dtype and t.shape == eps.shape):
+                raise ValueError("slice arrays must be contiguous CUDA tensors of one dtype and shape")
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+        return cls(tau, ptr(eps), [ptr(t) for t in u], [ptr(t) for t in pi] if pi is not None else None, keep=ts)
+
+    @property
+    def tau(self):
+        return self.s.tau
+
+
+def fo_grid(shape, dx, dy, deta, precision=CLV_FP64, cartesian=False, eta_pitch=0):
+    g = clv_fo_grid()
+    g.nx, g.ny, g.neta = (int(n) for n in shape)
+    g.eta_pitch = int(eta_pitch)
+    g.dx, g.dy, g.deta = float(dx), float(dy), float(deta)
+    g.precision, g.cartesian = int(precision), int(bool(cartesian))
+    return g
+
+
+class FreezeoutFinder:
+    """clv_fo_find with device buffers kept for one grid: find() enqueues the
+    four launches on ``stream``; result() synchronises and returns
+    (records (n, 22) tensor view, hypercube indices (n,), n)."""
+
+    def __init__(self, grid, capacity=None, device=None, stream=None):
+        import torch
+        self.torch = torch
+        self._lib = load()
+        self.grid = grid
+        self.device = torch.device(device or "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        n = ctypes.c_size_t()
+        _raise(self._lib, self._lib.clv_fo_scratch_bytes(ctypes.byref(grid), ctypes.byref(n)))
+        ncube = (grid.nx - 1) * (grid.ny - 1) * (grid.neta - 1)
+        self.capacity = ncube if capacity is None else int(capacity)
+        dt = torch.float64 if grid.precision == CLV_FP64 else torch.float32
+        self.rec = torch.empty((max(self.capacity, 1), FO_NREC), dtype=dt, device=self.device)
+        self.cube = torch.empty(max(self.capacity, 1), dtype=torch.int64, device=self.device)
+        self.count = torch.zeros(1, dtype=torch.int64, device=self.device)
+        self.scratch = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+
+    def find(self, s0, s1, eps_f):
+        V = ctypes.c_void_p
+        _raise(self._lib, self._lib.clv_fo_find(ctypes.byref(self.grid), ctypes.byref(s0.s), ctypes.byref(s1.s),
+                                                float(eps_f), V(self.rec.data_ptr()), V(self.cube.data_ptr()),
+                                                self.capacity, V(self.count.data_ptr()),
+                                                V(self.scratch.data_ptr()), V(self.stream.cuda_stream)))
+
+    def result(self):
+        self.stream.synchronize()
+        n = int(self.count.item())
+        m = min(n, self.capacity)
+        return self.rec[:m], self.cube[:m], n
+
+
+def fo_find(grid, s0, s1, eps_f, capacity=None, device=None, stream=None):
+    """One call of clv_fo_find with fresh buffers: (records, hypercube indices, count)."""
+    f = FreezeoutFinder(grid, capacity, device, stream)
+    f.find(s0, s1, eps_f)
+    return f.result()
 
 
 def make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
@@ -380,6 +493,39 @@ class Hydro:
         self._check(self._lib.clv_mlp_forward(self._h, ctypes.c_void_p(X.data_ptr()), X.shape[0],
                                               ctypes.c_void_p(Y.data_ptr())), self._h)
         return Y
+
+    # ---- freeze-out surface (clv_fo_*)
+    def fo_grid(self):
+        g = clv_fo_grid()
+        self._check(self._lib.clv_fo_grid_of(self._h, ctypes.byref(g)), self._h)
+        return g
+
+    def fo_current(self):
+        """A slice viewing the current state (valid until the next step)."""
+        sl = FoSlice(0.0, None, [None] * 3)
+        self._check(self._lib.clv_fo_current(self._h, ctypes.byref(sl.s)), self._h)
+        sl.keep.append(self)
+        return sl
+
+    def fo_snapshot(self):
+        """A device copy of the current slice (eps, u~, pi~ at the handle's tau)."""
+        n = ctypes.c_size_t()
+        self._check(self._lib.clv_fo_slice_bytes(self._h, ctypes.byref(n)), self._h)
+        buf = self.torch.empty(n.value, dtype=self.torch.uint8, device=self.device)
+        sl = FoSlice(0.0, None, [None] * 3, keep=[buf])
+        self._check(self._lib.clv_fo_snapshot(self._h, ctypes.c_void_p(buf.data_ptr()), ctypes.byref(sl.s)),
+                    self._h)
+        return sl
+
+    def freezeout(self, eps_f, since, capacity=None):
+        """Surface elements of eps = eps_f between the slice `since` (an
+        earlier fo_snapshot) and the current state: (records, hypercube
+        indices, count); synchronises."""
+        f = getattr(self, "_fo_finder", None)
+        if f is None or (capacity is not None and f.capacity != capacity):
+            f = self._fo_finder = FreezeoutFinder(self.fo_grid(), capacity, self.device, self.stream)
+        f.find(since, self.fo_current(), eps_f)
+        return f.result()
 
     def enable_kernel_timing(self, on=True):
         self._check(self._lib.clv_enable_kernel_timing(self._h, int(bool(on))), self._h)

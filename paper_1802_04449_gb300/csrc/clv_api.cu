@@ -1724,6 +1724,66 @@ clv_status clv_get_kernel_times(clv_handle* h, double ms[4], int64_t launches[4]
   return CLV_OK;
 }
 
+// ---- freeze-out surface: the handle's state as slices (clv_fo_find is in clv_freezeout.cu)
+
+clv_status clv_fo_grid_of(clv_handle* h, clv_fo_grid* out) {
+  if (!h || !out) return fail(h, CLV_EINVAL, "handle or out is NULL");
+  if (!h->batch.empty() || h->cfg.halo_x)
+    return fail(h, CLV_EINVAL, "freeze-out slices: single-event handles only (not a batch or an x-slab)");
+  if (h->cfg.nx < 2 || h->cfg.ny < 2 || h->cfg.neta < 2)
+    return fail(h, CLV_EINVAL, "freeze-out slices need nx, ny, neta >= 2");
+  out->nx = h->cfg.nx;
+  out->ny = h->cfg.ny;
+  out->neta = h->cfg.neta;
+  out->eta_pitch = h->nep;
+  out->dx = h->cfg.dx;
+  out->dy = h->cfg.dy;
+  out->deta = h->cfg.deta;
+  out->precision = h->cfg.precision;
+  out->cartesian = h->cfg.cartesian;
+  return CLV_OK;
+}
+
+clv_status clv_fo_current(clv_handle* h, clv_fo_slice* out) {
+  clv_fo_grid g;
+  clv_status s = clv_fo_grid_of(h, &g);
+  if (s != CLV_OK) return s;
+  if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
+  out->tau = h->tau;
+  out->eps = h->PR[h->cur][0];
+  for (int m = 0; m < 3; ++m) out->u[m] = h->PR[h->cur][1 + m];
+  for (int q = 0; q < 10; ++q) out->pi[q] = h->viscous ? h->PI0[q] : nullptr;
+  return CLV_OK;
+}
+
+clv_status clv_fo_slice_bytes(clv_handle* h, size_t* bytes) {
+  clv_fo_grid g;
+  clv_status s = clv_fo_grid_of(h, &g);
+  if (s != CLV_OK) return s;
+  if (!bytes) return fail(h, CLV_EINVAL, "bytes is NULL");
+  *bytes = 14 * align_up((size_t)h->N * h->rsize, 256);
+  return CLV_OK;
+}
+
+clv_status clv_fo_snapshot(clv_handle* h, void* d_buf, clv_fo_slice* out) {
+  clv_fo_slice cur;
+  clv_status s = clv_fo_current(h, &cur);
+  if (s != CLV_OK) return s;
+  if (!d_buf || (reinterpret_cast<uintptr_t>(d_buf) & 255)) return fail(h, CLV_EINVAL, "d_buf is NULL or not 256-byte aligned");
+  if (!out) return fail(h, CLV_EINVAL, "out is NULL");
+  const size_t fb = align_up((size_t)h->N * h->rsize, 256), n = (size_t)h->N * h->rsize;
+  char* b = static_cast<char*>(d_buf);
+  const void* src[14] = {cur.eps, cur.u[0], cur.u[1], cur.u[2]};
+  for (int q = 0; q < 10; ++q) src[4 + q] = cur.pi[q];
+  const int nf = h->viscous ? 14 : 4;
+  for (int f = 0; f < nf; ++f) CLV_CUDA(h, cudaMemcpyAsync(b + f * fb, src[f], n, cudaMemcpyDeviceToDevice, h->stream));
+  out->tau = cur.tau;
+  out->eps = b;
+  for (int m = 0; m < 3; ++m) out->u[m] = b + (1 + m) * fb;
+  for (int q = 0; q < 10; ++q) out->pi[q] = h->viscous ? b + (4 + q) * fb : nullptr;
+  return CLV_OK;
+}
+
 void clv_destroy(clv_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();

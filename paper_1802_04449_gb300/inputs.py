@@ -430,3 +430,38 @@ def random_smooth_box(rng, nx, ny, neta, eps_mean=5.0, amp=0.3, vamp=0.2, modes=
     uy = field(0.0, vamp)
     ue = field(0.0, vamp)
     return eps, ux, uy, ue
+
+
+def freezeout_slices(shape=(13, 11, 9), d=(0.3, 0.3, 0.25), tau0=2.0, tau1=2.12, n_blobs=10, seed=0,
+                     eps_peak=2.0):
+    """Two time slices of a smooth synthetic fluid for the freeze-out surface
+    finder: eps is a sum of Gaussian blobs that dilute as tau^(-4/3) while
+    their widths grow linearly in tau (a crude expanding fireball, so that
+    the surface eps = eps_f has both time-like and space-like parts); u~ and
+    pi~ are smooth random fields.  Returns a dict with tau0, tau1, d (dx, dy,
+    deta), eps0, eps1 (grids) and f0, f1 ((13,) + grid: u~^x, u~^y, u~^eta,
+    pi~ tt tx ty te xx xy xe yy ye ee)."""
+    rng = np.random.default_rng(seed)
+    nx, ny, ne = shape
+    X, Y, Z = np.meshgrid(cell_coords(nx, d[0]), cell_coords(ny, d[1]), cell_coords(ne, d[2]), indexing="ij")
+    half = np.array([(n - 1) * dd / 2 for n, dd in zip(shape, d)])
+    c = rng.uniform(-0.7, 0.7, (n_blobs, 3)) * half
+    sig = rng.uniform(0.25, 0.5, (n_blobs, 3)) * half
+    amp = rng.uniform(0.3, 1.0, n_blobs) * eps_peak
+    kx = rng.normal(size=(13, 3)) / half
+    ph = rng.uniform(0, 2 * np.pi, 13)
+    scale = np.concatenate([[0.4] * 3, [0.02] * 10])
+
+    def at(tau):
+        g = tau / tau0
+        e = np.zeros(shape)
+        for b in range(n_blobs):
+            r2 = sum(((V - c[b, a]) / (sig[b, a] * g)) ** 2 for a, V in enumerate((X, Y, Z)))
+            e += amp[b] * g ** (-4.0 / 3.0) * np.exp(-0.5 * r2)
+        f = np.stack([scale[q] * np.sin(kx[q, 0] * X + kx[q, 1] * Y + kx[q, 2] * Z + ph[q] + 0.3 * tau)
+                      for q in range(13)])
+        return e, f
+
+    e0, f0 = at(tau0)
+    e1, f1 = at(tau1)
+    return {"tau0": tau0, "tau1": tau1, "d": tuple(d), "eps0": e0, "eps1": e1, "f0": f0, "f1": f1}

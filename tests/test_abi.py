@@ -59,3 +59,40 @@ def test_host_only_entry_points(lib):
     bad, _ = clv.make_config(0, 1, 1, 0.2, 0.2, 0.2, 0.4, 0.01)
     assert so.clv_workspace_bytes(ctypes.byref(bad), ctypes.byref(n)) == 1
     assert "grid dims" in so.clv_last_error(None).decode()
+
+
+def test_freezeout_host_checks(lib):
+    """clv_fo_scratch_bytes and the argument checks of clv_fo_find run on the
+    host (no launch happens when an argument is bad)."""
+    so = clv.load()
+    g = clv.fo_grid((97, 97, 41), 0.2, 0.2, 0.2, clv.CLV_FP32)
+    n = ctypes.c_size_t()
+    assert so.clv_fo_scratch_bytes(ctypes.byref(g), ctypes.byref(n)) == 0
+    ncube = 96 * 96 * 40
+    assert 5 * ncube <= n.value <= 5 * ncube + 16 * (ncube // 256 + 1) + 128
+    assert so.clv_fo_scratch_bytes(ctypes.byref(clv.fo_grid((1, 4, 4), 0.2, 0.2, 0.2)), ctypes.byref(n)) == 1
+    assert ">= 2" in so.clv_last_error(None).decode()
+    g2 = clv.fo_grid((4, 4, 4), 0.2, 0.2, 0.2, clv.CLV_FP64, eta_pitch=3)
+    assert so.clv_fo_scratch_bytes(ctypes.byref(g2), ctypes.byref(n)) == 1
+    buf = (ctypes.c_double * 64)()
+    p = ctypes.c_void_p(ctypes.addressof(buf))
+    s0 = clv.FoSlice(1.0, p, [p, p, p])
+    s1 = clv.FoSlice(1.1, p, [p, p, p])
+    g = clv.fo_grid((4, 4, 4), 0.2, 0.2, 0.2, clv.CLV_FP64)
+    V = ctypes.c_void_p
+
+    def find(a, b, rec=p, cap=1, count=p, scratch=p, ef=0.5):
+        return so.clv_fo_find(ctypes.byref(g), ctypes.byref(a.s), ctypes.byref(b.s), ef, rec, None, cap, count,
+                              scratch, None)
+    assert find(s1, s0) == 1 and "tau" in so.clv_last_error(None).decode()
+    assert find(s0, s1, rec=None) == 1 and "d_rec" in so.clv_last_error(None).decode()
+    assert find(s0, s1, cap=-1) == 1
+    assert find(s0, s1, count=None) == 1
+    assert find(s0, s1, scratch=V(ctypes.addressof(buf) + 8)) == 1 and "16-byte" in so.clv_last_error(None).decode()
+    assert find(s0, s1, ef=float("nan")) == 1
+    s_half = clv.FoSlice(1.1, p, [p, p, p], [p] * 5 + [None] * 5)
+    assert find(s0, s_half) == 1 and "pi" in so.clv_last_error(None).decode()
+    s_noeps = clv.FoSlice(1.1, None, [p, p, p])
+    assert find(s0, s_noeps) == 1 and "eps" in so.clv_last_error(None).decode()
+    s_neg = clv.FoSlice(-1.0, p, [p, p, p])
+    assert find(s_neg, s1) == 1 and "Milne" in so.clv_last_error(None).decode()
