@@ -53,6 +53,14 @@ LEDGER_WORDS = 92    # the method's per-cell-update ledger for a fused step (eac
 # hypercube index written, u~ and pi~ of one cell of each slice read)
 FO_BYTES_PER_CUBE = 2 * 4
 FO_BYTES_PER_ELEMENT = 22 * 4 + 8 + 2 * 13 * 4
+# Cooper-Frye sum: flops of one (element, momentum) pair with delta f, an FMA
+# counted as 2 and exp2 / reciprocal as 1 each.  What depends on the element
+# and (Y, pT) only is formed once for the 4 phi points of a thread: e^(Y-eta),
+# cosh, sinh 8, p^tau and tau p^eta 2, their parts of p.dSigma and p.u 6, of
+# p p pi 14 -> 30 / 4 = 7.5 per pair; per phi point: p.dSigma 4, p.u 4,
+# exponent 2, exp2 1, f 2, p p pi 10, (1 - s f) q + 1 4, product and sum 3 -> 30
+CF_FLOPS_PER_PAIR = 37.5
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 KERNEL_NAMES = {"stage1": "stage_tile_kernel<float,1,viscous>", "recover1": "recover_kernel<float,viscous>",
                 "stage2": "stage_tile_kernel<float,2,viscous>", "recover2": "recover_kernel<float,viscous>"}
 
@@ -330,8 +338,9 @@ def run_gpu(args):
     # stopping temperature) through the EOS table, between the slices at
     # tau = 2.4 and 2.5 fm; the four launches of clv_fo_find timed with
     # events on the handle's stream, L2 flushed between calls (untimed)
-    freezeout = None
+    freezeout = cooperfrye = None
     if args.freezeout:
+        from paper_1802_04449_gb300 import inputs as I
         g = clv.from_case(case, clv.CLV_FP32)
         g.set_initial_case(case)
         g.set_mlp(params_host)
@@ -361,6 +370,35 @@ def run_gpu(args):
         ncube = (gr.nx - 1) * (gr.ny - 1) * (gr.neta - 1)
         fo_alg = FO_BYTES_PER_CUBE * ncube + FO_BYTES_PER_ELEMENT * nel
         fo_ach = fo_alg / (fms / 1e3) / 1e9
+        # ---- smooth Cooper-Frye spectra of pi+, K+ and p on the paper's
+        # 41 x 15 x 48 grid over that surface, straight from the finder's
+        # device records and count (ALU-bound: FP32 lanes)
+        Yg, pTg, _, phig, _ = I.spectra_grid()
+        lne_P = np.interp(np.log(eps_f), lne, eos["P"])
+        cf = clv.CooperFrye(["pi+", "K+", "p"], Yg, pTg, phig, 0.137, eps_f + float(lne_P), True, clv.CLV_FP32,
+                            device=dev, stream=g.stream)
+        for _ in range(3):
+            cf.spectra(finder.rec, d_nel=finder.count)
+        creps = 20
+        cev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(creps)]
+        torch.cuda.synchronize()
+        for i in range(creps):
+            flush.fill_(i & 0xFF)
+            cev[i][0].record(g.stream)
+            cf.spectra(finder.rec, d_nel=finder.count)
+            cev[i][1].record(g.stream)
+        torch.cuda.synchronize()
+        cms = sum(a.elapsed_time(b) for a, b in cev) / creps
+        pairs = 3 * nel * len(Yg) * len(pTg) * len(phig)
+        cf_ach = CF_FLOPS_PER_PAIR * pairs / (cms / 1e3) / 1e12
+        cooperfrye = {"workload": f"pi+, K+, p on 41 x 15 x 48 (Y, pT, phi) points over the {nel} elements above, "
+                                  "delta f on", "ms_per_call": cms, "pairs": pairs,
+                      "value": pairs / (cms / 1e3), "unit": "element-momentum pairs/s", "launches_per_call": 3,
+                      "l2": "flushed between calls (512 MiB write, untimed)",
+                      "roofline": {"bound": "alu", "kernel": "cf_sum_kernel<float, viscous>",
+                                   "achieved": cf_ach, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                                   "frac": cf_ach / FP32_ALU_TFLOPS, "flops_per_pair": CF_FLOPS_PER_PAIR,
+                                   "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}}
         freezeout = {"workload": "the same event at tau = 2.4 -> 2.5 fm (10 steps apart), T_f = 137 MeV",
                      "eps_f": eps_f, "hypercubes": ncube, "elements": nel, "ms_per_find": fms,
                      "value": ncube / (fms / 1e3), "unit": "hypercubes/s", "launches_per_find": 4,
@@ -456,6 +494,7 @@ def run_gpu(args):
         "large_event": large,
         "batch": batch,
         "freezeout": freezeout,
+        "cooperfrye": cooperfrye,
         "roofline": roof,
         "e2e": e2e,
         # per step: two stages of (stage kernel, root solve) and the tau advance

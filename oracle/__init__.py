@@ -112,7 +112,7 @@ def _load(plant: int = 0):
             lib.orc_freezeout.argtypes = [G, D, D, D, D, ctypes.c_double, D,
                                           ctypes.POINTER(ctypes.c_int64), ctypes.c_int64]
             lib.orc_cooper_frye.argtypes = [ctypes.POINTER(_CfSpecies), D, ctypes.c_int64, D, ctypes.c_int,
-                                            D, ctypes.c_int, D, ctypes.c_int, D]
+                                            D, ctypes.c_int, D, ctypes.c_int, ctypes.c_int, D]
             lib.orc_freezeout_simplex.argtypes = [G, D, D, ctypes.c_double, ctypes.c_int,
                                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, D]
             _libs[plant] = lib
@@ -279,10 +279,12 @@ def freezeout_simplex(e0, e1, eps_f, dx, dy, deta, tau0, tau1, i, j, k, s, carte
     return out
 
 
-def cooper_frye(rec, Y, pT, phi, mass, g, stat, Tf, ePf=1.0, mu=0.0, viscous=True, plant=0):
+def cooper_frye(rec, Y, pT, phi, mass, g, stat, Tf, ePf=1.0, mu=0.0, viscous=True, plant=0, absolute=False):
     """dN/(dY pT dpT dphi) (GeV^-2) of one species on the (Y, pT, phi) grid
     from element records (n, 22) in FO_RECORD order (clv_cooperfrye.c,
     readings C1-C4); stat +1 Fermi-Dirac, -1 Bose-Einstein, 0 Boltzmann.
+    absolute: the sum of the summands' magnitudes instead (the scale of
+    the rounding error of a sum in any order).
     Returns an array of shape (len(Y), len(pT), len(phi))."""
     rec = np.ascontiguousarray(rec, dtype=np.float64).reshape(-1, 22)
     Y, pT, phi = (np.ascontiguousarray(a, dtype=np.float64).ravel() for a in (Y, pT, phi))
@@ -291,7 +293,7 @@ def cooper_frye(rec, Y, pT, phi, mass, g, stat, Tf, ePf=1.0, mu=0.0, viscous=Tru
     sp.Tf, sp.ePf, sp.viscous = float(Tf), float(ePf), int(bool(viscous))
     out = np.zeros((len(Y), len(pT), len(phi)))
     st = _load(plant).orc_cooper_frye(ctypes.byref(sp), _dp(rec), rec.shape[0], _dp(Y), len(Y), _dp(pT),
-                                      len(pT), _dp(phi), len(phi), _dp(out))
+                                      len(pT), _dp(phi), len(phi), int(bool(absolute)), _dp(out))
     if st != 0:
         raise ValueError("bad Cooper-Frye arguments")
     return out

@@ -76,10 +76,12 @@ static double cf_term(const orc_cf_species* sp, const double* r, double Y, doubl
 }
 
 /* dN/(dY pT dpT dphi) at every (Y[a], pT[b], phi[c]) into out[(a*npt + b)*nphi + c]
- * from the nel element records (22 doubles each).  Returns 0, or -1 for a
- * bad argument. */
+ * from the nel element records (22 doubles each).  With absolute != 0 the
+ * sum of the magnitudes of the summands instead (the scale that bounds the
+ * rounding error of any summation order).  Returns 0, or -1 for a bad
+ * argument. */
 int orc_cooper_frye(const orc_cf_species* sp, const double* rec, int64_t nel, const double* Y, int nY,
-                    const double* pT, int npt, const double* phi, int nphi, double* out) {
+                    const double* pT, int npt, const double* phi, int nphi, int absolute, double* out) {
   if (!(sp->Tf > 0) || nY < 0 || npt < 0 || nphi < 0 || nel < 0) return -1;
   if (sp->viscous && !(sp->ePf > 0)) return -1;
   const double norm = sp->g / pow(2.0 * M_PI * CF_HBARC, 3);
@@ -90,7 +92,10 @@ int orc_cooper_frye(const orc_cf_species* sp, const double* rec, int64_t nel, co
     double mT = sqrt(pT[b] * pT[b] + sp->mass * sp->mass);
     double px = pT[b] * cos(phi[c]), py = pT[b] * sin(phi[c]);
     double s = 0.0;
-    for (int64_t e = 0; e < nel; ++e) s += cf_term(sp, rec + e * CF_NREC, Y[a], mT, px, py);
+    for (int64_t e = 0; e < nel; ++e) {
+      double t = cf_term(sp, rec + e * CF_NREC, Y[a], mT, px, py);
+      s += absolute ? fabs(t) : t;
+    }
     out[q] = norm * s;
   }
   return 0;

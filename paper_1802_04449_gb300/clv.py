@@ -83,6 +83,20 @@ FO_RECORD = ["dS_tau", "dS_x", "dS_y", "dS_eta", "tau", "x", "y", "eta", "ut", "
              "pitt", "pitx", "pity", "pite", "pixx", "pixy", "pixe", "piyy", "piye", "piee"]
 
 
+class clv_cf_species(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("g", ctypes.c_double), ("stat", ctypes.c_int), ("mu", ctypes.c_double)]
+
+
+class clv_cf_params(ctypes.Structure):
+    _fields_ = [("Tf", ctypes.c_double), ("ePf", ctypes.c_double), ("viscous", ctypes.c_int),
+                ("precision", ctypes.c_int)]
+
+
+CF_MAX_SPECIES = 32
+# name: (mass GeV, degeneracy, statistics: -1 Bose-Einstein, +1 Fermi-Dirac)
+SPECIES = {"pi+": (0.13957, 1.0, -1), "K+": (0.493677, 1.0, -1), "p": (0.938272, 2.0, 1)}
+
+
 class ClvError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -102,7 +116,7 @@ EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initi
             "clv_batch_event_stats", "clv_set_graphs", "clv_slab_halo_bytes", "clv_slab_pack",
             "clv_slab_unpack", "clv_slab_fill_edge", "clv_slab_predictor", "clv_stage",
             "clv_fo_scratch_bytes", "clv_fo_find", "clv_fo_grid_of", "clv_fo_current", "clv_fo_slice_bytes",
-            "clv_fo_snapshot"]
+            "clv_fo_snapshot", "clv_cf_scratch_bytes", "clv_cf_spectra"]
 CLV_GUESS_PREVIOUS, CLV_GUESS_COLD, CLV_GUESS_MLP = 0, 1, 2
 MLP_NPARAM = 5124
 
@@ -170,6 +184,11 @@ def load(path: str | None = None):
         lib.clv_fo_current.argtypes = [P, FS]
         lib.clv_fo_slice_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
         lib.clv_fo_snapshot.argtypes = [P, V, FS]
+        CP = ctypes.POINTER(clv_cf_params)
+        lib.clv_cf_scratch_bytes.argtypes = [CP, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.POINTER(ctypes.c_size_t)]
+        lib.clv_cf_spectra.argtypes = [CP, ctypes.POINTER(clv_cf_species), ctypes.c_int, V, ctypes.c_int64, V,
+                                       V, ctypes.c_int, V, ctypes.c_int, V, ctypes.c_int, V, V, V]
         lib.clv_destroy.argtypes = [P]
         lib.clv_destroy.restype = None
         lib.clv_last_error.argtypes = [P]
@@ -265,6 +284,60 @@ class FreezeoutFinder:
         n = int(self.count.item())
         m = min(n, self.capacity)
         return self.rec[:m], self.cube[:m], n
+
+
+class CooperFrye:
+    """clv_cf_spectra for a list of species on one (Y, pT, phi) grid.
+    ``species``: names of SPECIES or (mass, g, stat[, mu]) tuples.
+    spectra(rec, nel=None, d_nel=None) enqueues the launches and returns the
+    device tensor (n_species, nY, npt, nphi) of dN/(dY pT dpT dphi) in GeV^-2;
+    rec is a device tensor of records (rows of FO_NREC values); with d_nel
+    (a device int64 tensor, e.g. a finder's count) the element count stays on
+    the device and rec's rows are only an upper bound."""
+
+    def __init__(self, species, Y, pT, phi, Tf, ePf=1.0, viscous=True, precision=CLV_FP32, device=None,
+                 stream=None):
+        import torch
+        self.torch = torch
+        self._lib = load()
+        self.device = torch.device(device or "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        sp = [SPECIES[k] if isinstance(k, str) else tuple(k) for k in species]
+        if not 1 <= len(sp) <= CF_MAX_SPECIES:
+            raise ValueError(f"1 to {CF_MAX_SPECIES} species per call")
+        self.nsp = len(sp)
+        self._sp = (clv_cf_species * self.nsp)()
+        for z, t in enumerate(sp):
+            self._sp[z].mass, self._sp[z].g, self._sp[z].stat = float(t[0]), float(t[1]), int(t[2])
+            self._sp[z].mu = float(t[3]) if len(t) > 3 else 0.0
+        self.p = clv_cf_params()
+        self.p.Tf, self.p.ePf, self.p.viscous, self.p.precision = float(Tf), float(ePf), int(bool(viscous)), int(precision)
+        axes = [torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64).ravel()).to(self.device) for a in (Y, pT, phi)]
+        self.Y, self.pT, self.phi = axes
+        self.shape = (self.nsp, len(self.Y), len(self.pT), len(self.phi))
+        self.out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        self.scratch = None
+        self._cap = -1
+
+    def spectra(self, rec, nel=None, d_nel=None):
+        t = self.torch
+        V = ctypes.c_void_p
+        want = t.float64 if self.p.precision == CLV_FP64 else t.float32
+        if rec.dtype != want or not rec.is_contiguous() or (rec.dim() == 2 and rec.shape[1] != FO_NREC):
+            raise ValueError("records must be a contiguous (n, 22) tensor of the precision's type")
+        cap = rec.shape[0] if nel is None else int(nel)
+        if cap != self._cap:
+            n = ctypes.c_size_t()
+            _raise(self._lib, self._lib.clv_cf_scratch_bytes(ctypes.byref(self.p), cap, self.nsp, *self.shape[1:],
+                                                             ctypes.byref(n)))
+            self.scratch = t.empty(n.value, dtype=t.uint8, device=self.device)
+            self._cap = cap
+        _raise(self._lib, self._lib.clv_cf_spectra(
+            ctypes.byref(self.p), self._sp, self.nsp, V(rec.data_ptr()) if cap > 0 else None, cap,
+            V(d_nel.data_ptr()) if d_nel is not None else None, V(self.Y.data_ptr()), self.shape[1],
+            V(self.pT.data_ptr()), self.shape[2], V(self.phi.data_ptr()), self.shape[3], V(self.out.data_ptr()),
+            V(self.scratch.data_ptr()), V(self.stream.cuda_stream)))
+        return self.out
 
 
 def fo_find(grid, s0, s1, eps_f, capacity=None, device=None, stream=None):

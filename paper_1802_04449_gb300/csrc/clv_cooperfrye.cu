@@ -5,10 +5,12 @@
 //
 // Three launches on the caller's stream:
 //   prep     one thread per element: the per-element constants of the sum
-//            (cosh and sinh eta_s, dSigma with dSigma_eta / tau, u~, pi~
+//            (e^eta_s and e^-eta_s, dSigma with dSigma_eta / tau, u~, pi~
 //            scaled by 1/(2 T^2 (eps + P)) with the off-diagonal factor 2),
 //            24 values, 16-byte aligned;
-//   sum      grid (momentum tiles, element chunks, species): each thread owns
+//   sum      grid (momentum tiles, element chunks, species): the elements
+//            present (the device count when given) split in whole tiles over
+//            the chunks; each thread owns
 //            one (Y, pT) and kPhi consecutive phi points; the CTA stages tiles
 //            of prepared elements in shared memory (every thread reads the
 //            same element: broadcast) and each thread accumulates its points
@@ -54,7 +56,7 @@ __device__ __forceinline__ long long element_count(long long n, const int64_t* d
   return m < n ? m : n;
 }
 
-// prepared element: 0 cosh eta, 1 sinh eta, 2-5 dSigma_tau, dSigma_x, dSigma_y,
+// prepared element: 0 e^eta, 1 e^-eta, 2-5 dSigma_tau, dSigma_x, dSigma_y,
 // dSigma_eta/tau, 6-9 u~, 10-19 scaled pi~ (tt, tx, ty, te, xx, xy, xe, yy,
 // ye, ee), 20-23 padding
 template <typename R>
@@ -65,8 +67,8 @@ __global__ void cf_prep_kernel(const R* __restrict__ rec, long long cap, const i
   const R* r = rec + e * CLV_FO_NREC;
   R* o = prep + e * kPrep;
   const R eta = r[7], tau = r[4];
-  o[0] = cosh(eta);
-  o[1] = sinh(eta);
+  o[0] = exp(eta);
+  o[1] = exp(-eta);
   o[2] = r[0];
   o[3] = r[1];
   o[4] = r[2];
@@ -91,7 +93,7 @@ __device__ __forceinline__ double fast_exp2<double>(double x) { return exp2(x); 
 
 template <typename R, bool VISC>
 __global__ void __launch_bounds__(kThreads) cf_sum_kernel(const R* __restrict__ prep, long long cap,
-                                                          const int64_t* __restrict__ d_nel, long long chunk,
+                                                          const int64_t* __restrict__ d_nel,
                                                           const double* __restrict__ Y, int nY,
                                                           const double* __restrict__ pT, int npt,
                                                           const double* __restrict__ phi, int nphi,
@@ -113,7 +115,7 @@ __global__ void __launch_bounds__(kThreads) cf_sum_kernel(const R* __restrict__ 
   }
   // per-thread momentum constants
   const R y = active ? (R)Y[a] : R(0);
-  const R chY = cosh(y), shY = sinh(y);
+  const R eY = exp(y), emY = exp(-y);
   const R pt_ = active ? (R)pT[b] : R(0);
   const R mT = sqrt(pt_ * pt_ + (R)(sp.mass * sp.mass));
   R px[kPhi], py[kPhi];
@@ -131,6 +133,10 @@ __global__ void __launch_bounds__(kThreads) cf_sum_kernel(const R* __restrict__ 
   double acc[kPhi];
 #pragma unroll
   for (int j = 0; j < kPhi; ++j) acc[j] = 0.0;
+  // the elements split evenly (in whole tiles) over the gridDim.y chunks,
+  // by the count actually present
+  const long long tiles = (nel + kTile - 1) / kTile;
+  const long long chunk = (tiles + gridDim.y - 1) / gridDim.y * kTile;
   const long long e_begin = (long long)blockIdx.y * chunk;
   long long e_end = e_begin + chunk;
   if (e_end > nel) e_end = nel;
@@ -150,8 +156,12 @@ __global__ void __launch_bounds__(kThreads) cf_sum_kernel(const R* __restrict__ 
     for (int j = 0; j < kPhi; ++j) part[j] = R(0);
     for (int i = 0; i < n; ++i) {
       const R* el = tile + i * kPrep;
-      const R ch = chY * el[0] - shY * el[1];   // cosh(Y - eta)
-      const R sh = shY * el[0] - chY * el[1];   // sinh(Y - eta)
+      // e^(Y - eta) and e^(eta - Y) as products (the addition theorem for
+      // cosh(Y - eta) cancels catastrophically in single precision at large
+      // |Y| and |eta|)
+      const R ep = eY * el[1], em = emY * el[0];
+      const R ch = R(0.5) * (ep + em);          // cosh(Y - eta)
+      const R sh = R(0.5) * (ep - em);          // sinh(Y - eta)
       const R ptau = mT * ch, peta = mT * sh;
       const R base_dS = ptau * el[2] + peta * el[5];
       const R base_u = ptau * el[6] - peta * el[9];
@@ -275,11 +285,11 @@ clv_status cf_run(const clv_cf_params* p, const clv_cf_species* species, int nsp
                                                                      (R)pi_scale, p->viscous != 0, prep);
     const dim3 grid((unsigned)P.gx, (unsigned)P.nchunk, (unsigned)nsp);
     if (p->viscous)
-      cf_sum_kernel<R, true><<<grid, kThreads, 0, st>>>(prep, nel, d_nel, P.chunk, d_Y, nY, d_pT, npt, d_phi, nphi,
-                                                        set, 1.0 / p->Tf, partial);
+      cf_sum_kernel<R, true><<<grid, kThreads, 0, st>>>(prep, nel, d_nel, d_Y, nY, d_pT, npt, d_phi, nphi, set,
+                                                        1.0 / p->Tf, partial);
     else
-      cf_sum_kernel<R, false><<<grid, kThreads, 0, st>>>(prep, nel, d_nel, P.chunk, d_Y, nY, d_pT, npt, d_phi, nphi,
-                                                         set, 1.0 / p->Tf, partial);
+      cf_sum_kernel<R, false><<<grid, kThreads, 0, st>>>(prep, nel, d_nel, d_Y, nY, d_pT, npt, d_phi, nphi, set,
+                                                         1.0 / p->Tf, partial);
   }
   const long long nout = (long long)nsp * P.npts;
   cf_reduce_kernel<<<(unsigned)((nout + 255) / 256), 256, 0, st>>>(partial, P.nchunk, nsp, P.npts, set, d_out);

@@ -521,8 +521,15 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
 // the new T~^{tau mu} and pi~^{tau mu}, solves for (eps, u~) warm-started
 // from the stage velocity, writes P and c_s, zeroes pi~ in vacuum cells, and
 // (STATS) reduces sum T~^{tau tau} and max eps.
+// at least four 256-thread blocks per SM in FP32 (at most 64 registers): the
+// dependent table lookups of the root solve need the occupancy
+template <typename R>
+struct RecoverMinBlocks {
+  static constexpr int value = sizeof(R) == 4 ? 4 : 3;
+};
+
 template <typename R, bool VISC, bool STATS, int GUESS = kGuessPrevious>
-__global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p) {
+__global__ void __launch_bounds__(kBlock, RecoverMinBlocks<R>::value) recover_kernel(const StageParams<R> p) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = c < p.N;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -640,19 +647,29 @@ __global__ void __launch_bounds__(kBlock) recover_kernel(const StageParams<R> p)
   const int w_solved = __reduce_add_sync(full, my_solved);
   const int w_piters = __reduce_add_sync(full, my_polish_iters);
   const unsigned w_maxit = __reduce_max_sync(full, (unsigned)my_iters);   // a warp runs as long as its slowest lane
+  // counters summed per block in shared memory, then one global atomic per
+  // counter and block (per-warp global atomics on one cache line queue up
+  // in a single L2 slice)
+  __shared__ unsigned s_cnt[kBlock / 32][9];
   if (lane == 0) {
-    if (b_res) atomicAdd(p.counters + 0, (unsigned long long)__popc(b_res));
-    if (b_fail) { atomicAdd(p.counters + 1, (unsigned long long)__popc(b_fail)); atomicOr(p.err, 1u); }
-    if (b_pol) atomicAdd(p.counters + 2, (unsigned long long)__popc(b_pol));
-    if (b_nc) atomicAdd(p.counters + 3, (unsigned long long)__popc(b_nc));
-    if (w_iters) atomicAdd(p.counters + 4, (unsigned long long)w_iters);
-    if (w_solved) atomicAdd(p.counters + 5, (unsigned long long)w_solved);
-    if (w_piters) atomicAdd(p.counters + 6, (unsigned long long)w_piters);
-    if (w_maxit) {
-      atomicAdd(p.counters + 7, (unsigned long long)w_maxit);
-      atomicAdd(p.counters + 8, 1ull);
-    }
+    s_cnt[wid][0] = __popc(b_res);
+    s_cnt[wid][1] = __popc(b_fail);
+    s_cnt[wid][2] = __popc(b_pol);
+    s_cnt[wid][3] = __popc(b_nc);
+    s_cnt[wid][4] = (unsigned)w_iters;
+    s_cnt[wid][5] = (unsigned)w_solved;
+    s_cnt[wid][6] = (unsigned)w_piters;
+    s_cnt[wid][7] = w_maxit;
+    s_cnt[wid][8] = w_maxit ? 1u : 0u;
+    if (b_fail) atomicOr(p.err, 1u);
     if (b_nf) atomicOr(p.err, 2u);
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    unsigned long long t = 0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) t += s_cnt[w][threadIdx.x];
+    if (t) atomicAdd(p.counters + threadIdx.x, t);
   }
   if constexpr (STATS) {
     __shared__ double s_sum[kBlock / 32];

@@ -465,3 +465,17 @@ def freezeout_slices(shape=(13, 11, 9), d=(0.3, 0.3, 0.25), tau0=2.0, tau1=2.12,
     e0, f0 = at(tau0)
     e1, f1 = at(tau1)
     return {"tau0": tau0, "tau1": tau1, "d": tuple(d), "eps0": e0, "eps1": e1, "f0": f0, "f1": f1}
+
+
+def spectra_grid(nY=41, npt=15, nphi=48, Y_max=4.0, pT_max=4.0):
+    """The momentum grid of the smooth spectra: nY rapidities uniform in
+    [-Y_max, Y_max], npt transverse momenta at the Gauss-Legendre nodes of
+    [0, pT_max] GeV and nphi azimuths at the Gauss-Legendre nodes of
+    [0, 2 pi] (the paper tabulates 41 x 15 x 48 points with pT and phi at
+    Gauss quadrature nodes).  Returns (Y, pT, w_pT, phi, w_phi)."""
+    Y = np.linspace(-Y_max, Y_max, nY)
+    x, w = np.polynomial.legendre.leggauss(npt)
+    pT, wpT = 0.5 * pT_max * (x + 1), 0.5 * pT_max * w
+    x, w = np.polynomial.legendre.leggauss(nphi)
+    phi, wphi = np.pi * (x + 1), np.pi * w
+    return Y, pT, wpT, phi, wphi

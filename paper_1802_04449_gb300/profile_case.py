@@ -4,11 +4,15 @@ launches).  Usage:
 
     python -m paper_1802_04449_gb300.profile_case [--precision fp32|fp64]
         [--guess previous|cold|learned] [--skip S] [--steps K] [--no-autotune]
+        [--surface]
 
 The tile shape is autotuned first (as bench.py does; its timing launches
 come first), --skip S steps run next (reaching the later, more dilute
 state), then K steps.  --guess learned trains the network briefly (FP64 states of another
-seed of the same workload) before the run.
+seed of the same workload) before the run.  --surface then takes a slice,
+runs 10 more steps, finds the freeze-out surface at T_f = 137 MeV between the
+two slices (clv_fo_find) and computes the pi+, K+ and p spectra on the
+41 x 15 x 48 grid from it (clv_cf_spectra): those launches come last.
 """
 from __future__ import annotations
 
@@ -28,6 +32,7 @@ def main(argv=None):
     ap.add_argument("--skip", type=int, default=0)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--surface", action="store_true")
     a = ap.parse_args(argv)
 
     import torch
@@ -60,6 +65,21 @@ def main(argv=None):
     torch.cuda.synchronize()
     print("profile case done: tau %.3f, newton iters/solve %.3f, polished %d" %
           (st["tau"], st["n_newton_iters"] / max(1, st["n_newton_cells"]), st["n_polished"]))
+    if a.surface:
+        import numpy as np
+        snap = g.fo_snapshot()
+        g.step(10)
+        eos = case.eos
+        lne = eos["lne0"] + eos["dlne"] * np.arange(len(eos["T"]))
+        eps_f = float(np.float32(np.exp(np.interp(0.137, eos["T"], lne))))
+        finder = clv.FreezeoutFinder(g.fo_grid(), stream=g.stream)
+        finder.find(snap, g.fo_current(), eps_f)
+        Y, pT, _, phi, _ = I.spectra_grid()
+        P_f = float(np.interp(np.log(eps_f), lne, eos["P"]))
+        cf = clv.CooperFrye(["pi+", "K+", "p"], Y, pT, phi, 0.137, eps_f + P_f, True, prec, stream=g.stream)
+        cf.spectra(finder.rec, d_nel=finder.count)
+        _, _, n = finder.result()
+        print("surface: %d elements at eps_f = %.4f" % (n, eps_f))
 
 
 if __name__ == "__main__":

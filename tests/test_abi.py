@@ -96,3 +96,33 @@ def test_freezeout_host_checks(lib):
     assert find(s0, s_noeps) == 1 and "eps" in so.clv_last_error(None).decode()
     s_neg = clv.FoSlice(-1.0, p, [p, p, p])
     assert find(s_neg, s1) == 1 and "Milne" in so.clv_last_error(None).decode()
+
+
+def test_cooperfrye_host_checks(lib):
+    """clv_cf_scratch_bytes and the argument checks of clv_cf_spectra run on
+    the host (no launch happens when an argument is bad)."""
+    so = clv.load()
+    p = clv.clv_cf_params()
+    p.Tf, p.ePf, p.viscous, p.precision = 0.137, 0.4, 1, clv.CLV_FP32
+    n = ctypes.c_size_t()
+    assert so.clv_cf_scratch_bytes(ctypes.byref(p), 10000, 3, 41, 15, 48, ctypes.byref(n)) == 0
+    assert n.value >= 10000 * 24 * 4 + 3 * 41 * 15 * 48 * 8
+    assert so.clv_cf_scratch_bytes(ctypes.byref(p), 10000, 33, 41, 15, 48, ctypes.byref(n)) == 1
+    assert "nsp" in so.clv_last_error(None).decode()
+    bad = clv.clv_cf_params()
+    bad.Tf, bad.ePf, bad.viscous, bad.precision = 0.137, 0.0, 1, clv.CLV_FP32
+    assert so.clv_cf_scratch_bytes(ctypes.byref(bad), 10, 1, 4, 4, 4, ctypes.byref(n)) == 1
+    assert "ePf" in so.clv_last_error(None).decode()
+    buf = (ctypes.c_double * 64)()
+    q = ctypes.c_void_p(ctypes.addressof(buf))
+    sp = (clv.clv_cf_species * 1)()
+    sp[0].mass, sp[0].g, sp[0].stat = 0.14, 1.0, -1
+
+    def call(species=sp, rec=q, out=q, scratch=None, nel=4):
+        return so.clv_cf_spectra(ctypes.byref(p), species, 1, rec, nel, None, q, 1, q, 1, q, 1, out, scratch, None)
+    assert call() == 1 and "d_scratch" in so.clv_last_error(None).decode()
+    assert call(rec=None) == 1 and "d_rec" in so.clv_last_error(None).decode()
+    assert call(out=None) == 1 and "d_out" in so.clv_last_error(None).decode()
+    sp2 = (clv.clv_cf_species * 1)()
+    sp2[0].mass, sp2[0].g, sp2[0].stat = 0.14, 1.0, 2
+    assert call(species=sp2) == 1 and "stat" in so.clv_last_error(None).decode()
