@@ -84,13 +84,6 @@ __global__ void cf_prep_kernel(const R* __restrict__ rec, long long cap, const i
   for (int m = 20; m < kPrep; ++m) o[m] = R(0);
 }
 
-template <typename R>
-__device__ __forceinline__ R fast_exp2(R x);
-template <>
-__device__ __forceinline__ float fast_exp2<float>(float x) { return exp2f(x); }
-template <>
-__device__ __forceinline__ double fast_exp2<double>(double x) { return exp2(x); }
-
 template <typename R, bool VISC>
 __global__ void __launch_bounds__(kThreads) cf_sum_kernel(const R* __restrict__ prep, long long cap,
                                                           const int64_t* __restrict__ d_nel,
@@ -173,17 +166,53 @@ __global__ void __launch_bounds__(kThreads) cf_sum_kernel(const R* __restrict__ 
         a1 = peta * el[16] - ptau * el[11];
         a2 = peta * el[18] - ptau * el[12];
       }
-#pragma unroll
-      for (int j = 0; j < kPhi; ++j) {
-        const R pdS = base_dS + px[j] * el[3] + py[j] * el[4];
-        const R pu = base_u - px[j] * el[7] - py[j] * el[8];
-        const R f = R(1) / (fast_exp2<R>(pu * k2 - mu2) + s);
-        R term = pdS * f;
+      if constexpr (sizeof(R) == 4) {
+        // FP32: two phi points per packed FP32x2 instruction (the same
+        // IEEE roundings per lane as the scalar path)
+        const float2 b_dS = make_float2(base_dS, base_dS), b_u = make_float2(base_u, base_u);
+        const float2 e3 = make_float2(el[3], el[3]), e4 = make_float2(el[4], el[4]);
+        const float2 e7 = make_float2(-el[7], -el[7]), e8 = make_float2(-el[8], -el[8]);
+        const float2 k2v = make_float2(k2, k2), mu2v = make_float2(-mu2, -mu2), sv = make_float2(s, s);
+        const float2 one = make_float2(1.f, 1.f), msv = make_float2(-s, -s);
+        float2 e14, e15, e17, a1v, a2v, qtv;
         if (VISC) {
-          const R q = qt + px[j] * (px[j] * el[14] + py[j] * el[15] + a1) + py[j] * (py[j] * el[17] + a2);
-          term = term * (R(1) + (R(1) - s * f) * q);
+          e14 = make_float2(el[14], el[14]);
+          e15 = make_float2(el[15], el[15]);
+          e17 = make_float2(el[17], el[17]);
+          a1v = make_float2(a1, a1);
+          a2v = make_float2(a2, a2);
+          qtv = make_float2(qt, qt);
         }
-        part[j] += term;
+#pragma unroll
+        for (int j = 0; j < kPhi; j += 2) {
+          const float2 X = make_float2(px[j], px[j + 1]), Yv = make_float2(py[j], py[j + 1]);
+          const float2 pdS = __ffma2_rn(Yv, e4, __ffma2_rn(X, e3, b_dS));
+          const float2 pu = __ffma2_rn(Yv, e8, __ffma2_rn(X, e7, b_u));
+          const float2 arg = __ffma2_rn(pu, k2v, mu2v);
+          const float2 den = __fadd2_rn(make_float2(exp2f(arg.x), exp2f(arg.y)), sv);
+          const float2 f = make_float2(1.f / den.x, 1.f / den.y);
+          float2 term = __fmul2_rn(pdS, f);
+          if (VISC) {
+            const float2 qx = __ffma2_rn(X, __ffma2_rn(Yv, e15, __ffma2_rn(X, e14, a1v)), qtv);
+            const float2 q = __ffma2_rn(Yv, __ffma2_rn(Yv, e17, a2v), qx);
+            term = __fmul2_rn(term, __ffma2_rn(__ffma2_rn(msv, f, one), q, one));
+          }
+          part[j] += term.x;
+          part[j + 1] += term.y;
+        }
+      } else {   // FP64
+#pragma unroll
+        for (int j = 0; j < kPhi; ++j) {
+          const R pdS = base_dS + px[j] * el[3] + py[j] * el[4];
+          const R pu = base_u - px[j] * el[7] - py[j] * el[8];
+          const R f = R(1) / (exp2(pu * k2 - mu2) + s);
+          R term = pdS * f;
+          if (VISC) {
+            const R q = qt + px[j] * (px[j] * el[14] + py[j] * el[15] + a1) + py[j] * (py[j] * el[17] + a2);
+            term = term * (R(1) + (R(1) - s * f) * q);
+          }
+          part[j] += term;
+        }
       }
     }
 #pragma unroll
