@@ -202,12 +202,13 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
       P = C(Pe);
       cs2 = C(ce);
     }
-    C den = E + P;
-    const C iden = Ops::div(C(1), den);
-    C f = v - M * iden;
-    if (f > C(0)) hi = v; else lo = v;
-    C fp = C(1) - cs2 * (M * M) * (iden * iden);
-    const C dv = -Ops::div(f, fp);
+    // Newton step on f(v) = v - M/den, den = E + P: with g = v den - M
+    // (the sign of f, den > 0) the step -f/f' is -den g / (den^2 - c_s^2 M^2),
+    // one division
+    const C den = E + P;
+    const C g = v * den - M;
+    if (g > C(0)) hi = v; else lo = v;
+    const C dv = -Ops::div(den * g, den * den - cs2 * (M * M));
     // converged when the Newton step is below tol; otherwise keep the iterate
     // strictly inside the shrinking bracket
     if (fabs(dv) <= tol) { v += dv; ok = true; break; }

@@ -167,7 +167,7 @@ constexpr double kViscEpsMin = 1e-3;   // GeV/fm^3
 // interpolation of P sets the noise floor beyond which more steps gain
 // nothing); an unconverged one gets a full bracketed FP64 solve.  Returns the
 // iterations taken, -1 if the full solve hit its cap.
-constexpr int kPolishSteps = 3;
+constexpr int kPolishSteps = 2;
 template <typename R>
 __device__ __forceinline__ int polish_root(const StageParams<R>& p, R E, R Mx, R My, R Me, R v32, bool converged,
                                            R& en, R& ux, R& uy, R& ue) {
