@@ -129,13 +129,26 @@ __device__ __forceinline__ double refine_sqrt(double x) {
   y = y * fma(-0.5 * x * y, y, 1.5);
   return x * y;
 }
+__device__ __forceinline__ double refine_rsqrt(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  return y;
+}
 template <typename C, typename CE> struct SolveOps {
   static __device__ __forceinline__ C div(C a, C b) { return a / b; }
   static __device__ __forceinline__ C sqrt_(C x) { return sqrt(x); }
+  static __device__ __forceinline__ C rsqrt_(C x) { return C(1) / sqrt(x); }
+};
+template <> struct SolveOps<float, float> {
+  static __device__ __forceinline__ float div(float a, float b) { return a / b; }
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
 };
 template <> struct SolveOps<double, float> {
   static __device__ __forceinline__ double div(double a, double b) { return a * refine_rcp(b); }
   static __device__ __forceinline__ double sqrt_(double x) { return refine_sqrt(x); }
+  static __device__ __forceinline__ double rsqrt_(double x) { return refine_rsqrt(x); }
 };
 
 // C: arithmetic of the solve (E - M v, f, Newton step, gamma); CE: arithmetic
@@ -228,7 +241,7 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
     at_root->P = P + cs2 * (e - e_last);
     at_root->cs2 = cs2;
   }
-  C gam = Ops::div(C(1), Ops::sqrt_(C(1) - v * v));
+  C gam = Ops::rsqrt_(C(1) - v * v);
   C s = Ops::div(gam * v, M);
   ux = s * Mx;
   uy = s * My;

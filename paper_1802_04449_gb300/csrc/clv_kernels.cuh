@@ -540,7 +540,8 @@ __global__ void __launch_bounds__(kBlock, RecoverMinBlocks<R>::value) recover_ke
   R T0v = R(0), E = R(0), Mx = R(0), My = R(0), Me = R(0);
   if (active) {
     T0v = p.Tout[0][c];
-    E = T0v / tn; Mx = p.Tout[1][c] / tn; My = p.Tout[2][c] / tn; Me = p.Tout[3][c] / tn;
+    const R itn = R(1) / tn;
+    E = T0v * itn; Mx = p.Tout[1][c] * itn; My = p.Tout[2][c] * itn; Me = p.Tout[3][c] * itn;
     if constexpr (VISC) {
       E -= p.piout[0][c]; Mx -= p.piout[1][c]; My -= p.piout[2][c]; Me -= p.piout[3][c];
     }
