@@ -98,6 +98,7 @@ def _load(plant: int = 0):
             lib.orc_set_threads.restype = ctypes.c_int
             lib.orc_set_initial.argtypes = [P, D, D, D, D, D]
             lib.orc_set_initial_T.argtypes = [P, D]
+            lib.orc_set_initial_n.argtypes = [P, D]
             lib.orc_step.argtypes = [P, ctypes.c_int]
             lib.orc_get.argtypes = [P, ctypes.c_int, D]
             lib.orc_stats.argtypes = [P, D]
@@ -127,7 +128,7 @@ FIELD_INDEX = {"eps": 0, "ux": 1, "uy": 2, "ueta": 3,
                "Ttt": 4, "Ttx": 5, "Tty": 6, "Tte": 7,
                **{f"pi{k}": 8 + i for i, k in enumerate(
                    ["tt", "tx", "ty", "te", "xx", "xy", "xe", "yy", "ye", "ee"])},
-               "upx": 18, "upy": 19, "upe": 20}
+               "upx": 18, "upy": 19, "upe": 20, "Nt": 21, "n": 22}
 
 
 class Oracle:
@@ -181,6 +182,11 @@ class Oracle:
         a = np.ascontiguousarray(T, dtype=np.float64).reshape((4,) + self.shape)
         if self._lib.orc_set_initial_T(self._h, _dp(a)) != 0:
             raise RuntimeError("root solve hit its iteration cap")
+
+    def set_initial_n(self, n):
+        """Net charge density at tau0 (after set_initial): N~^tau = tau0 n u~^tau."""
+        a = np.ascontiguousarray(n, dtype=np.float64).reshape(self.shape)
+        self._lib.orc_set_initial_n(self._h, _dp(a))
 
     def step(self, n=1):
         return self._lib.orc_step(self._h, int(n))

@@ -54,6 +54,13 @@
  *       - (2/3) Delta^{mu nu} theta with finite-difference gradients.
  *   R17 Boundaries: two ghost cells per side, copies of the edge cell
  *       (zero gradient) or periodic wrap.
+ *   R19 Net charge (Eq. Ntilde with S_N = 0; the paper sets n = 0, so this
+ *       is off unless an initial n is given): N~^tau = tau n u^tau (1 in
+ *       place of tau in Cartesian mode) is conserved with the flux
+ *       v^a N~^tau along each axis, through the same limited reconstruction
+ *       of N~^tau and v^a and the same local speed as the other fields;
+ *       the diffusion current d^mu is 0 (ideal charge transport).  Vacuum
+ *       cells keep their charge.  n = N~^tau / (tau u^tau).
  *   R18 Shear regulator (the paper is silent; without one the dilute,
  *       ultra-relativistic edge of a viscous event runs away): after each
  *       stage update and before the root solve, with eps and P of the
@@ -114,6 +121,7 @@ typedef struct {
   double *pi[NPI];
   double *ed;     /* eps */
   double *u[3];   /* u~^x, u~^y, u~^eta */
+  double *N;      /* N~^tau (R19) */
 } orc_fields;
 
 typedef struct {
@@ -127,6 +135,7 @@ typedef struct {
   double tau;
   long step;
   int viscous;
+  int charge;       /* 1: net charge transported (R19) */
   long n_rescaled, n_rootfail;
   double stats[8];
 } orc_t;
@@ -336,7 +345,7 @@ static void regulate_pi(const orc_t* h, double e, double* pi) {
 }
 
 /* ------------------------- KT (Eqs. kt, flux_out) -------------------- */
-#define NR 17 /* reconstructed: T(4) pi(10) u^tau v^a P */
+#define NR 18 /* reconstructed: T(4) pi(10) u^tau v^a P N~^tau */
 
 static double minmod(double a, double b) {
   if (a > 0.0 && b > 0.0) return a < b ? a : b;
@@ -363,13 +372,14 @@ static void cell_R(const view_t* vw, size_t id, int axis, double R[NR], double* 
   R[14] = u[0];
   R[15] = u[axis] / u[0];
   R[16] = P;
+  R[17] = f->N[id];
   *cs = sqrt(cs2);
 }
 
 /* Flux H at the interface between cells b and c on axis a, from cells a,b,c,d
  * (= i-1, i, i+1, i+2).  Q = (T~^{tau mu}, Q_pi = u~^tau pi~). */
 static void kt_interface(const view_t* vw, int axis, double taus, size_t ia, size_t ib, size_t ic,
-                         size_t id, double H[4 + NPI]) {
+                         size_t id, double H[4 + NPI], double* HN) {
   double Ra[NR], Rb[NR], Rc[NR], Rd[NR], csa, csb, csc, csd;
   cell_R(vw, ia, axis, Ra, &csa);
   cell_R(vw, ib, axis, Rb, &csb);
@@ -405,6 +415,8 @@ static void kt_interface(const view_t* vw, int axis, double taus, size_t ia, siz
   }
   for (int q = 0; q < 4 + NPI; ++q)
     H[q] = 0.5 * (Fl[q] + Fr[q]) - 0.5 * cmax * (Qr[q] - Ql[q]);
+  /* net charge (R19): flux v^a N~^tau */
+  *HN = 0.5 * (vl * L[17] + vr * Rr[17]) - ((PLANT == 16) ? -0.5 : 0.5) * cmax * (Rr[17] - L[17]);
 }
 
 /* -------------------------- ghost cells (R17) ------------------------ */
@@ -424,6 +436,7 @@ static void fill_ghosts_array(const orc_t* h, double* a) {
 }
 
 static void fill_ghosts(const orc_t* h, orc_fields* f) {
+  if (h->charge) fill_ghosts_array(h, f->N);
   for (int m = 0; m < 4; ++m) fill_ghosts_array(h, f->T[m]);
   for (int q = 0; q < NPI; ++q) fill_ghosts_array(h, f->pi[q]);
   fill_ghosts_array(h, f->ed);
@@ -436,12 +449,13 @@ static void fill_ghosts(const orc_t* h, orc_fields* f) {
  * un: velocity at step n (spatial components). */
 static void stage_source(const orc_t* h, const orc_fields* f, int viscous, double tau_s, int i,
                          int j, int k, const double ulate[4], const double un[4],
-                         double S[4 + NPI]) {
+                         double S[4 + NPI], double* SN) {
   view_t vw = {h, f, viscous};
   double taus = tau_scale(h, tau_s);
   double g = geo(h, tau_s);
   double hstep = h->c.dtau;
   for (int q = 0; q < 4 + NPI; ++q) S[q] = 0.0;
+  *SN = 0.0;
   /* KT flux differences along x, y, eta_s (Eq. kt) */
   double dl[3] = {h->c.dx, h->c.dy, ((PLANT == 4) ? 1.0 : taus) * h->c.deta};
   for (int ax = 1; ax <= 3; ++ax) {
@@ -451,11 +465,12 @@ static void stage_source(const orc_t* h, const orc_fields* f, int viscous, doubl
     size_t c0 = IX(h, i, j, k);
     size_t p1 = IX(h, i + di, j + dj, k + dk);
     size_t p2 = IX(h, i + 2 * di, j + 2 * dj, k + 2 * dk);
-    double Hm[4 + NPI], Hp[4 + NPI];
-    kt_interface(&vw, ax, taus, m2, m1, c0, p1, Hm);
-    kt_interface(&vw, ax, taus, m1, c0, p1, p2, Hp);
+    double Hm[4 + NPI], Hp[4 + NPI], HNm, HNp;
+    kt_interface(&vw, ax, taus, m2, m1, c0, p1, Hm, &HNm);
+    kt_interface(&vw, ax, taus, m1, c0, p1, p2, Hp, &HNp);
     int nq = viscous ? 4 + NPI : 4;
     for (int q = 0; q < nq; ++q) S[q] -= (Hp[q] - Hm[q]) / dl[ax - 1];
+    *SN -= (HNp - HNm) / dl[ax - 1];
   }
   /* geometric source S_T (R1) */
   size_t c0 = IX(h, i, j, k);
@@ -526,9 +541,10 @@ static void heun_step(orc_t* h, int viscous) {
         un[0] = sqrt(1.0 + un[1] * un[1] + un[2] * un[2] + un[3] * un[3]);
         for (int b = 1; b < 4; ++b) us[b] = viscous ? 2.0 * un[b] - h->up[b - 1][c] : un[b];
         us[0] = sqrt(1.0 + us[1] * us[1] + us[2] * us[2] + us[3] * us[3]);
-        double S[4 + NPI];
-        stage_source(h, s, viscous, tn, i, j, k, us, un, S);
+        double S[4 + NPI], SN;
+        stage_source(h, s, viscous, tn, i, j, k, us, un, S, &SN);
         for (int m = 0; m < 4; ++m) s1->T[m][c] = s->T[m][c] + hs * S[m];
+        if (h->charge) s1->N[c] = s->N[c] + hs * SN;
         if (viscous) {
           double pv[NPI];
           for (int q = 0; q < NPI; ++q) pv[q] = (un[0] * s->pi[q][c] + hs * S[4 + q]) / us[0];
@@ -551,9 +567,10 @@ static void heun_step(orc_t* h, int viscous) {
         us[0] = sqrt(1.0 + us[1] * us[1] + us[2] * us[2] + us[3] * us[3]);
         u1[1] = s1->u[0][c]; u1[2] = s1->u[1][c]; u1[3] = s1->u[2][c];
         u1[0] = sqrt(1.0 + u1[1] * u1[1] + u1[2] * u1[2] + u1[3] * u1[3]);
-        double S[4 + NPI];
-        stage_source(h, s1, viscous, tn1, i, j, k, u1, un, S);
+        double S[4 + NPI], SN;
+        stage_source(h, s1, viscous, tn1, i, j, k, u1, un, S, &SN);
         for (int m = 0; m < 4; ++m) s->T[m][c] = 0.5 * (s->T[m][c] + s1->T[m][c] + hs * S[m]);
+        if (h->charge) s->N[c] = 0.5 * (s->N[c] + s1->N[c] + hs * SN);
         if (viscous) {
           double pv[NPI];
           for (int q = 0; q < NPI; ++q)
@@ -601,18 +618,21 @@ static void fields_alloc(orc_fields* f, size_t n) {
   for (int q = 0; q < NPI; ++q) f->pi[q] = zalloc(n);
   f->ed = zalloc(n);
   for (int m = 0; m < 3; ++m) f->u[m] = zalloc(n);
+  f->N = zalloc(n);
 }
 static void fields_free(orc_fields* f) {
   for (int m = 0; m < 4; ++m) free(f->T[m]);
   for (int q = 0; q < NPI; ++q) free(f->pi[q]);
   free(f->ed);
   for (int m = 0; m < 3; ++m) free(f->u[m]);
+  free(f->N);
 }
 static void fields_copy(orc_fields* d, const orc_fields* s, size_t n) {
   for (int m = 0; m < 4; ++m) memcpy(d->T[m], s->T[m], n * sizeof(double));
   for (int q = 0; q < NPI; ++q) memcpy(d->pi[q], s->pi[q], n * sizeof(double));
   memcpy(d->ed, s->ed, n * sizeof(double));
   for (int m = 0; m < 3; ++m) memcpy(d->u[m], s->u[m], n * sizeof(double));
+  memcpy(d->N, s->N, n * sizeof(double));
 }
 
 orc_t* orc_create(const orc_config* c) {
@@ -670,6 +690,9 @@ int orc_set_initial(orc_t* h, const double* eps, const double* ux, const double*
   h->tau = h->c.tau0;
   h->step = 0;
   h->n_rescaled = h->n_rootfail = 0;
+  h->charge = 0;
+  memset(h->s.N, 0, h->NG * sizeof(double));
+  memset(h->s1.N, 0, h->NG * sizeof(double));
   for (int i = 0; i < nx; ++i)
     for (int j = 0; j < ny; ++j)
       for (int k = 0; k < ne; ++k) {
@@ -752,6 +775,23 @@ int orc_set_initial_T(orc_t* h, const double* T) {
   return r;
 }
 
+/* Net charge density n at tau0 (R19), after orc_set_initial: N~^tau =
+ * tau0 n u~^tau from the initial velocities. */
+int orc_set_initial_n(orc_t* h, const double* n) {
+  int nx = h->c.nx, ny = h->c.ny, ne = h->c.neta;
+  double taus = tau_scale(h, h->tau);
+  for (int i = 0; i < nx; ++i)
+    for (int j = 0; j < ny; ++j)
+      for (int k = 0; k < ne; ++k) {
+        size_t l = ((size_t)i * ny + j) * ne + k, c = IX(h, i, j, k);
+        double ux = h->s.u[0][c], uy = h->s.u[1][c], ue = h->s.u[2][c];
+        double ut = sqrt(1.0 + ux * ux + uy * uy + ue * ue);
+        h->s.N[c] = ((PLANT == 17) ? 1.0 : taus) * n[l] * ut;
+      }
+  h->charge = 1;
+  return 0;
+}
+
 int orc_step(orc_t* h, int n) {
   for (int s = 0; s < n; ++s) heun_step(h, h->viscous);
   compute_stats(h);
@@ -767,6 +807,19 @@ int orc_get(const orc_t* h, int which, double* out) {
   else if (which <= 7) a = h->s.T[which - 4];
   else if (which <= 17) a = h->s.pi[which - 8];
   else if (which <= 20) a = h->up[which - 18];
+  else if (which == 21) a = h->s.N;
+  else if (which == 22) {
+    /* n = N~^tau / (tau u^tau) (R19) */
+    double taus = tau_scale(h, h->tau);
+    for (int i = 0; i < nx; ++i)
+      for (int j = 0; j < ny; ++j)
+        for (int k = 0; k < ne; ++k) {
+          size_t c = IX(h, i, j, k);
+          double ux = h->s.u[0][c], uy = h->s.u[1][c], ue = h->s.u[2][c];
+          out[((size_t)i * ny + j) * ne + k] = h->s.N[c] / (taus * sqrt(1.0 + ux * ux + uy * uy + ue * ue));
+        }
+    return 0;
+  }
   else return 1;
   for (int i = 0; i < nx; ++i)
     for (int j = 0; j < ny; ++j)

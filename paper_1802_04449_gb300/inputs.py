@@ -479,3 +479,16 @@ def spectra_grid(nY=41, npt=15, nphi=48, Y_max=4.0, pT_max=4.0):
     x, w = np.polynomial.legendre.leggauss(nphi)
     phi, wphi = np.pi * (x + 1), np.pi * w
     return Y, pT, wpT, phi, wphi
+
+
+def gubser_charge(tau, x, y, q=1.0, n_norm=1.0):
+    """Net charge density carried by the ideal Gubser flow of gubser_ideal:
+    n = C 4 q^2 / (tau [1 + 2 q^2 (tau^2 + r^2) + q^4 (tau^2 - r^2)^2]), the
+    solution of d_mu (tau n u^mu) = 0 for that velocity field (n cosh^2 rho
+    tau^3 is constant along the flow).  C is fixed so that n(tau=1 fm, r=0) =
+    n_norm (fm^-3)."""
+    def raw(t, r2):
+        return 4 * q * q / (t * (1 + 2 * q * q * (t * t + r2) + q ** 4 * (t * t - r2) ** 2))
+    C = n_norm / raw(1.0, 0.0)
+    X, Y = np.meshgrid(x, y, indexing="ij")
+    return C * raw(tau, X * X + Y * Y)

@@ -19,12 +19,16 @@ Cooper-Frye spectra (clv_cooperfrye.c):
  13 tau p^eta dSigma_eta multiplied by tau instead of divided -> particle number n u.dSigma
  14 quantum statistics sign flipped       -> Bessel closed form of the boost-invariant surface
  15 sign of the p~^eta u~^eta term of p.u -> particle number n u.dSigma
+Net charge (clv_oracle.c, R19):
+ 16 the local-speed term of the charge flux with the wrong sign -> Gubser charge convergence
+ 17 initial N~^tau without the tau factor -> Bjorken n tau constant
 """
 import numpy as np
 import pytest
 
 import oracle
 import test_oracle_flows as F
+import test_oracle_charge as CH
 import test_oracle_cooperfrye as CF
 import test_oracle_freezeout as FO
 
@@ -44,6 +48,8 @@ CASES = {
     13: CF.check_particle_number,
     14: CF.check_bjorken_bessel,
     15: CF.check_particle_number,
+    16: CH.check_gubser_charge,
+    17: CH.check_bjorken_charge,
 }
 
 
