@@ -81,6 +81,9 @@ typedef struct {
                                 0: no lambda_1 term (the default) */
   int halo_x;                /* 0: the whole grid (default); 2: an x-slab of a larger grid with two halo
                                 planes on each x side, filled by the caller (clv_slab_*) */
+  int charge;                /* 1: also transport a net charge (Eq. Ntilde, S_N = 0, no diffusion
+                                current; the paper runs with n = 0): N~^tau = tau n u~^tau, set by
+                                clv_set_initial_n; single events only (not a batch or an x-slab) */
 } clv_config;
 
 /* Per-run statistics, filled by clv_step / clv_get_stats. */
@@ -145,6 +148,17 @@ clv_status clv_set_initial_device(clv_handle* h, const double* d_eps, const doub
 clv_status clv_set_initial_T(clv_handle* h, const double* T);
 clv_status clv_set_initial_T_device(clv_handle* h, const double* d_T);
 
+/* Net charge density n (fm^-3) at the current tau, for a handle created
+ * with charge = 1, after clv_set_initial(_T): N~^tau = tau n u~^tau from the
+ * current velocities (host array, or device array for _device, of
+ * nx*ny*neta doubles).  From then on each step carries N~^tau with the flux
+ * v^a N~^tau through the same limited reconstruction and local speed as the
+ * other fields (one extra launch per stage).  clv_set_initial(_T) resets
+ * the charge to zero (not transported).  CLV_EINVAL without charge = 1 or
+ * before the initial state. */
+clv_status clv_set_initial_n(clv_handle* h, const double* n);
+clv_status clv_set_initial_n_device(clv_handle* h, const double* d_n);
+
 /* Advance nsteps Heun steps.  If stats is not NULL the call synchronises and
  * fills it; otherwise it only enqueues work and returns.  Returns CLV_EROOT /
  * CLV_ENONFINITE when the device error word is set (checked only when stats
@@ -158,7 +172,8 @@ clv_status clv_get_stats(clv_handle* h, clv_stats* stats);
  *   0 eps, 1 u~^x, 2 u~^y, 3 u~^eta,
  *   4..7 T~^{tau mu} (mu = tau, x, y, eta),
  *   8..17 pi~ (tt tx ty te xx xy xe yy ye ee),
- *   18..20 u~^{x,y,eta} of the previous step.
+ *   18..20 u~^{x,y,eta} of the previous step,
+ *   21 N~^tau and 22 n = N~^tau / (tau u~^tau) (charge = 1 only; CLV_EINVAL otherwise).
  * host_out receives popcount(mask) grids of nx*ny*neta doubles, in
  * increasing field order.  Synchronises. */
 clv_status clv_get_fields(clv_handle* h, uint32_t mask, double* host_out);

@@ -23,7 +23,7 @@ STATUS = {0: "CLV_OK", 1: "CLV_EINVAL", 2: "CLV_ENOMEM", 3: "CLV_ECUDA", 4: "CLV
 
 FIELDS = ["eps", "ux", "uy", "ueta", "Ttt", "Ttx", "Tty", "Tte",
           "pitt", "pitx", "pity", "pite", "pixx", "pixy", "pixe", "piyy", "piye", "piee",
-          "upx", "upy", "upe"]
+          "upx", "upy", "upe", "Nt", "n"]
 FIELD_BIT = {k: i for i, k in enumerate(FIELDS)}
 
 
@@ -41,6 +41,7 @@ class clv_config(ctypes.Structure):
         ("precision", ctypes.c_int), ("cartesian", ctypes.c_int), ("periodic", ctypes.c_int),
         ("eps_cut", ctypes.c_double), ("kernel", ctypes.c_int),
         ("taupi_coef", ctypes.c_double), ("lambda1_hat", ctypes.c_double), ("halo_x", ctypes.c_int),
+        ("charge", ctypes.c_int),
     ]
 
 
@@ -116,7 +117,8 @@ EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initi
             "clv_batch_event_stats", "clv_set_graphs", "clv_slab_halo_bytes", "clv_slab_pack",
             "clv_slab_unpack", "clv_slab_fill_edge", "clv_slab_predictor", "clv_stage",
             "clv_fo_scratch_bytes", "clv_fo_find", "clv_fo_grid_of", "clv_fo_current", "clv_fo_slice_bytes",
-            "clv_fo_snapshot", "clv_cf_scratch_bytes", "clv_cf_spectra"]
+            "clv_fo_snapshot", "clv_cf_scratch_bytes", "clv_cf_spectra", "clv_set_initial_n",
+            "clv_set_initial_n_device"]
 CLV_GUESS_PREVIOUS, CLV_GUESS_COLD, CLV_GUESS_MLP = 0, 1, 2
 MLP_NPARAM = 5124
 
@@ -142,6 +144,8 @@ def load(path: str | None = None):
         lib.clv_set_initial_device.argtypes = [P, V, V, V, V, V]
         lib.clv_set_initial_T.argtypes = [P, D]
         lib.clv_set_initial_T_device.argtypes = [P, V]
+        lib.clv_set_initial_n.argtypes = [P, D]
+        lib.clv_set_initial_n_device.argtypes = [P, V]
         lib.clv_step.argtypes = [P, ctypes.c_int, ctypes.POINTER(clv_stats)]
         lib.clv_get_stats.argtypes = [P, ctypes.POINTER(clv_stats)]
         lib.clv_get_fields.argtypes = [P, ctypes.c_uint32, D]
@@ -349,8 +353,9 @@ def fo_find(grid, s0, s1, eps_f, capacity=None, device=None, stream=None):
 
 def make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
                 precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7, kernel=0,
-                taupi_coef=0.0, lambda1_hat=0.0, halo_x=0):
+                taupi_coef=0.0, lambda1_hat=0.0, halo_x=0, charge=False):
     c = clv_config()
+    c.charge = int(bool(charge))
     c.taupi_coef, c.lambda1_hat = float(taupi_coef), float(lambda1_hat)
     c.halo_x = int(halo_x)
     c.nx, c.ny, c.neta = int(nx), int(ny), int(neta)
@@ -380,14 +385,14 @@ class Hydro:
     def __init__(self, nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
                  precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7,
                  stream=None, device=None, torch_workspace=True, kernel=0, taupi_coef=0.0, lambda1_hat=0.0,
-                 halo_x=0):
+                 halo_x=0, charge=False):
         import torch
         self._lib = load()
         self.torch = torch
         self.device = torch.device(device or "cuda")
         self.cfg, self._keep = make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s, eos,
                                            precision, cartesian, periodic, eps_cut, kernel, taupi_coef,
-                                           lambda1_hat, halo_x)
+                                           lambda1_hat, halo_x, charge)
         self.shape = (int(nx), int(ny), int(neta))
         self.N = int(nx) * int(ny) * int(neta)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -448,6 +453,19 @@ class Hydro:
         else:
             a = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape((4,) + self.shape))
             st = self._lib.clv_set_initial_T(self._h, _dp(a))
+        self._check(st, self._h)
+
+    def set_initial_n(self, n):
+        """Net charge density (handle created with charge=True), after the
+        initial state: host array or CUDA tensor of the grid's shape."""
+        t = self.torch
+        if isinstance(n, t.Tensor) and n.is_cuda:
+            a = n.to(t.float64).contiguous()
+            self._dev_keep = [a]
+            st = self._lib.clv_set_initial_n_device(self._h, ctypes.c_void_p(a.data_ptr()))
+        else:
+            a = np.ascontiguousarray(np.asarray(n, dtype=np.float64).reshape(self.shape))
+            st = self._lib.clv_set_initial_n(self._h, _dp(a))
         self._check(st, self._h)
 
     def set_initial_case(self, case):
@@ -623,7 +641,9 @@ class Hydro:
     def get(self, names=None, out=None):
         """Host copy of the named fields: dict name -> (nx, ny, neta) float64.
         ``out`` may be a preallocated (len(names), N) float64 array (pinned or not)."""
-        names = list(FIELDS if names is None else ([names] if isinstance(names, str) else names))
+        if names is None:
+            names = FIELDS if self.cfg.charge else FIELDS[:21]
+        names = list([names] if isinstance(names, str) else names)
         names = sorted(names, key=lambda k: FIELD_BIT[k])
         buf = out if out is not None else np.empty((len(names), self.N), dtype=np.float64)
         self._check(self._lib.clv_get_fields(self._h, self.mask_of(names), _dp(buf)), self._h)

@@ -18,6 +18,19 @@
 
 using namespace clv;
 
+// clv_charge.cu: the net-charge kernels
+namespace clv {
+template <typename R>
+void launch_charge_stage(const StageParams<R>& p, int stage, const void* Nin, const void* Nn, void* Nout,
+                         cudaStream_t st);
+template <typename R>
+void launch_charge_init(const double* n, const Prim<R>& pr, double taus, void* N, long long nc, int ne, int nep,
+                        cudaStream_t st);
+template <typename R>
+void launch_charge_density(const void* N, const Prim<R>& pr, double taus, double* out, long long nc, int ne, int nep,
+                           cudaStream_t st);
+}  // namespace clv
+
 namespace {
 
 std::string g_create_error;
@@ -60,6 +73,8 @@ struct clv_handle {
   void* T1[4];
   void* PI1[10];
   void* PR[kNumPrimSets][kPrimFields];
+  void* NC[2] = {nullptr, nullptr};   // charge = 1: N~^tau of the state and of the stage
+  bool charge_on = false;             // clv_set_initial_n since the last initial state
   int cur = 0, prev = 1;
   void* eos[3];
   void* mlp = nullptr;            // tensor-core copy of the guess network
@@ -151,6 +166,8 @@ clv_status validate(const clv_config* c) {
   if (c->kernel != 0 && c->kernel != 1) return fail(nullptr, CLV_EINVAL, "unknown kernel variant");
   if (c->halo_x != 0 && c->halo_x != 2) return fail(nullptr, CLV_EINVAL, "halo_x must be 0 or 2");
   if (c->halo_x && (c->nx < 2 || c->kernel != 0)) return fail(nullptr, CLV_EINVAL, "an x-slab needs nx >= 2 and kernel 0");
+  if (c->charge != 0 && c->charge != 1) return fail(nullptr, CLV_EINVAL, "charge must be 0 or 1");
+  if (c->charge && c->halo_x) return fail(nullptr, CLV_EINVAL, "charge transport runs on single events, not x-slabs");
   if (!(c->taupi_coef >= 0) || !std::isfinite(c->lambda1_hat))
     return fail(nullptr, CLV_EINVAL, "taupi_coef must be >= 0 and lambda1_hat finite");
   long long N = (long long)c->nx * c->ny * c->neta;
@@ -290,6 +307,9 @@ size_t layout(const clv_config* c, clv_handle* h) {
   for (int q = 0; q < 10; ++q) oPI1[q] = take(fb);
   for (int s = 0; s < kNumPrimSets; ++s)
     for (int f = 0; f < kPrimFields; ++f) oPR[s][f] = take(fb);
+  size_t oNC[2] = {0, 0};
+  if (c->charge)
+    for (int t = 0; t < 2; ++t) oNC[t] = take(fb);
   const int ne = c->eos_kind == CLV_EOS_TABLE ? c->eos_n : 1;
   oE[0] = take((size_t)4 * ne * rs);  // nodes packed as (P, T, c_s^2, 0)
   oE[1] = oE[2] = oE[0];
@@ -304,6 +324,7 @@ size_t layout(const clv_config* c, clv_handle* h) {
     for (int q = 0; q < 10; ++q) { h->PI0[q] = b + oPI0[q] + hoff; h->PI1[q] = b + oPI1[q] + hoff; }
     for (int s = 0; s < kNumPrimSets; ++s)
       for (int f = 0; f < kPrimFields; ++f) h->PR[s][f] = b + oPR[s][f] + hoff;
+    for (int t = 0; t < 2; ++t) h->NC[t] = c->charge ? b + oNC[t] + hoff : nullptr;
     for (int t = 0; t < 3; ++t) h->eos[t] = b + oE[t];
     h->mlp = b + oMlp;
     h->staging = (double*)(b + oStage);
@@ -479,7 +500,10 @@ void set_tau(clv_handle* h, double tau) {
 template <typename R, bool VISC>
 void launch_half(clv_handle* h, int stage, bool stats, bool timed) {
   if (stage == 1) {
-    launch_stage<R, VISC, 1, false>(h, stage_params<R>(h, 1), timed);
+    const StageParams<R> p1 = stage_params<R>(h, 1);
+    launch_stage<R, VISC, 1, false>(h, p1, timed);
+    // net charge: stage 1 from N^n into the stage buffer, with the stage's input velocities
+    if (h->charge_on) launch_charge_stage<R>(p1, 1, h->NC[0], h->NC[0], h->NC[1], h->stream);
     return;
   }
   const StageParams<R> p2 = stage_params<R>(h, 2);
@@ -489,6 +513,7 @@ void launch_half(clv_handle* h, int stage, bool stats, bool timed) {
   } else {
     launch_stage<R, VISC, 2, false>(h, p2, timed);
   }
+  if (h->charge_on) launch_charge_stage<R>(p2, 2, h->NC[1], h->NC[0], h->NC[0], h->stream);
   advance_tau_kernel<<<1, 1, 0, h->stream>>>(h->tau_dev, h->cfg.dtau);
   std::swap(h->cur, h->prev);
   h->tau = h->tau + h->cfg.dtau;
@@ -732,6 +757,12 @@ template <typename R> clv_status initial_end(clv_handle* h) {
 }
 
 template <typename R> clv_status finish_initial(clv_handle* h) {
+  if (h->cfg.charge) {   // a new initial state carries no charge until clv_set_initial_n
+    if (h->charge_on) invalidate_graphs(h);
+    h->charge_on = false;
+    for (int t = 0; t < 2; ++t)
+      CLV_CUDA(h, cudaMemsetAsync(h->NC[t], 0, (size_t)h->N * h->rsize, h->stream));
+  }
   clv_status s = initial_begin<R>(h);
   if (s != CLV_OK || !h->viscous) return s;
   if (h->cfg.halo_x) {   // an x-slab: the caller drives the predictor with halo exchanges
@@ -753,11 +784,18 @@ clv_status set_initial_impl(clv_handle* h, const double* const in[4], const doub
 // ne of pitch nep) as compact doubles
 template <typename R>
 clv_status export_field(clv_handle* h, int which, double* dst, long long off, long long n, int ne, int nep) {
+  if (which == 22) {   // n = N~^tau / (tau u~^tau)
+    launch_charge_density<R>(h->NC[0], prim_set<R>(h, h->cur), h->cfg.cartesian ? 1.0 : h->tau, dst, n, ne, nep,
+                             h->stream);
+    CLV_CUDA(h, cudaGetLastError());
+    return CLV_OK;
+  }
   const void* src = nullptr;
   if (which <= 3) src = h->PR[h->cur][which];
   else if (which <= 7) src = h->T0[which - 4];
   else if (which <= 17) src = h->PI0[which - 8];
-  else src = h->PR[h->prev][1 + (which - 18)];
+  else if (which <= 20) src = h->PR[h->prev][1 + (which - 18)];
+  else src = h->NC[0];
   export_kernel<R><<<grid_of(n), kBlock, 0, h->stream>>>((const R*)src + off, dst, n, ne, nep);
   CLV_CUDA(h, cudaGetLastError());
   return CLV_OK;
@@ -960,6 +998,31 @@ clv_status clv_set_initial_device(clv_handle* h, const double* d_eps, const doub
   return set_initial_any(h, d_eps, d_ux, d_uy, d_ueta, d_pi, false);
 }
 
+static clv_status set_initial_n_any(clv_handle* h, const double* n, bool host) {
+  if (!h || !n) return CLV_EINVAL;
+  if (!h->cfg.charge) return fail(h, CLV_EINVAL, "the handle was created without charge = 1");
+  if (!h->batch.empty()) return fail(h, CLV_EINVAL, "charge transport runs on single events, not a batch");
+  if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
+  const double* src = n;
+  if (host) {
+    CLV_CUDA(h, cudaMemcpyAsync(h->staging, n, (size_t)h->Nc * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    src = h->staging;
+  }
+  const double taus = h->cfg.cartesian ? 1.0 : h->tau;
+  if (h->rsize == 8)
+    launch_charge_init<double>(src, prim_set<double>(h, h->cur), taus, h->NC[0], h->Nc, h->cfg.neta, h->nep, h->stream);
+  else
+    launch_charge_init<float>(src, prim_set<float>(h, h->cur), taus, h->NC[0], h->Nc, h->cfg.neta, h->nep, h->stream);
+  CLV_CUDA(h, cudaGetLastError());
+  if (host) CLV_CUDA(h, cudaStreamSynchronize(h->stream));   // the staging buffer is reused
+  if (!h->charge_on) invalidate_graphs(h);
+  h->charge_on = true;
+  return CLV_OK;
+}
+
+clv_status clv_set_initial_n(clv_handle* h, const double* n) { return set_initial_n_any(h, n, true); }
+clv_status clv_set_initial_n_device(clv_handle* h, const double* d_n) { return set_initial_n_any(h, d_n, false); }
+
 clv_status clv_step(clv_handle* h, int nsteps, clv_stats* stats) {
   if (!h) return CLV_EINVAL;
   if (h->cfg.halo_x) return fail(h, CLV_EINVAL, "an x-slab steps by clv_stage with halo exchanges in between");
@@ -1004,9 +1067,10 @@ static clv_status get_fields_range(clv_handle* h, uint32_t mask, double* out, bo
                                    long long n, int ne, int nep) {
   if (!h || !out) return CLV_EINVAL;
   if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
-  if (mask >> 21) return fail(h, CLV_EINVAL, "mask selects fields beyond index 20");
+  if (mask >> 23) return fail(h, CLV_EINVAL, "mask selects fields beyond index 22");
+  if ((mask >> 21) && !h->cfg.charge) return fail(h, CLV_EINVAL, "fields 21 and 22 need charge = 1");
   size_t slot = 0;
-  for (int f = 0; f < 21; ++f) {
+  for (int f = 0; f < 23; ++f) {
     if (!(mask >> f & 1u)) continue;
     double* dst = host ? h->staging : out + slot * (size_t)n;
     clv_status s = h->rsize == 8 ? export_field<double>(h, f, dst, off, n, ne, nep)
@@ -1252,7 +1316,7 @@ constexpr uint32_t kStateMagic = 0x53564c43u;  // "CLVS"
 constexpr int kStateFields = 4 + 10 + 2 * kPrimFields;
 
 static size_t state_bytes(const clv_handle* h) {
-  return sizeof(StateHeader) + (size_t)kStateFields * (size_t)h->N * h->rsize;
+  return sizeof(StateHeader) + (size_t)(kStateFields + (h->cfg.charge ? 1 : 0)) * (size_t)h->N * h->rsize;
 }
 
 // device arrays of the state in checkpoint order: T~ (4), pi~ (10), the
@@ -1276,7 +1340,8 @@ clv_status clv_get_state(clv_handle* h, void* buf, size_t bytes) {
   if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
   if (bytes < state_bytes(h)) return fail(h, CLV_EINVAL, "state buffer too small (clv_state_bytes)");
   const clv_config& c = h->cfg;
-  StateHeader hd{kStateMagic, 1u, c.nx, c.ny, c.neta, c.precision, h->viscous ? 1 : 0, 0,
+  // pad: bit 0 = the net charge is being transported (its field follows the others)
+  StateHeader hd{kStateMagic, 1u, c.nx, c.ny, c.neta, c.precision, h->viscous ? 1 : 0, h->charge_on ? 1 : 0,
                  h->tau, c.dx, c.dy, c.deta, c.dtau, c.eta_over_s, h->step};
   std::memcpy(buf, &hd, sizeof(hd));
   void* a[kStateFields];
@@ -1285,6 +1350,8 @@ clv_status clv_get_state(clv_handle* h, void* buf, size_t bytes) {
   const size_t fb = (size_t)h->N * h->rsize;
   for (int k = 0; k < kStateFields; ++k)
     CLV_CUDA(h, cudaMemcpyAsync(dst + k * fb, a[k], fb, cudaMemcpyDeviceToHost, h->stream));
+  if (c.charge)
+    CLV_CUDA(h, cudaMemcpyAsync(dst + kStateFields * fb, h->NC[0], fb, cudaMemcpyDeviceToHost, h->stream));
   CLV_CUDA(h, cudaStreamSynchronize(h->stream));
   return CLV_OK;
 }
@@ -1309,6 +1376,12 @@ clv_status clv_set_state(clv_handle* h, const void* buf, size_t bytes) {
   const size_t fb = (size_t)h->N * h->rsize;
   for (int k = 0; k < kStateFields; ++k)
     CLV_CUDA(h, cudaMemcpyAsync(a[k], src + k * fb, fb, cudaMemcpyHostToDevice, h->stream));
+  if (c.charge) {
+    const bool on = (hd.pad & 1) != 0;
+    if (on != h->charge_on) invalidate_graphs(h);
+    h->charge_on = on;
+    CLV_CUDA(h, cudaMemcpyAsync(h->NC[0], src + kStateFields * fb, fb, cudaMemcpyHostToDevice, h->stream));
+  }
   CLV_CUDA(h, cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream));
   set_tau(h, hd.tau);
   CLV_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1569,6 +1642,7 @@ clv_status clv_create_batch(const clv_config* cfgs, int nevents, void* cuda_stre
          (c.eos_n == c0.eos_n && c.eos_lne0 == c0.eos_lne0 && c.eos_dlne == c0.eos_dlne &&
           std::equal(c.eos_P, c.eos_P + c.eos_n, c0.eos_P) && std::equal(c.eos_T, c.eos_T + c.eos_n, c0.eos_T) &&
           std::equal(c.eos_cs2, c.eos_cs2 + c.eos_n, c0.eos_cs2)));
+    if (c.charge) return fail(nullptr, CLV_EINVAL, "charge transport runs on single events, not a batch");
     if (c.tau0 != c0.tau0 || c.dtau != c0.dtau || c.precision != c0.precision || c.cartesian != c0.cartesian ||
         c.periodic != c0.periodic || c.eps_cut != c0.eps_cut || c.kernel != 0 || !same_eos)
       return fail(nullptr, CLV_EINVAL,

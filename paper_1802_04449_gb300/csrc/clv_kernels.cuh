@@ -759,7 +759,7 @@ __global__ void __launch_bounds__(kBlock) mlp_samples_kernel(const SampleIn<R> a
 
 // Exclusive scan of n block counts (one block of kBlock threads; each thread
 // scans a contiguous chunk), total into *total.
-__global__ void __launch_bounds__(kBlock) scan_counts_kernel(const unsigned* counts, int n,
+static __global__ void __launch_bounds__(kBlock) scan_counts_kernel(const unsigned* counts, int n,
                                                              unsigned long long* offsets, long long* total) {
   __shared__ unsigned long long s_part[kBlock];
   const int per = (n + kBlock - 1) / kBlock;
@@ -841,7 +841,7 @@ __global__ void __launch_bounds__(kBlock) export_kernel(const R* src, double* ds
 }
 
 // Deterministic final sum of the per-block partials (one block).
-__global__ void __launch_bounds__(1024) finalize_sum_kernel(const double* partial, int n, double* out) {
+static __global__ void __launch_bounds__(1024) finalize_sum_kernel(const double* partial, int n, double* out) {
   __shared__ double s[1024];
   double a = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) a += partial[i];

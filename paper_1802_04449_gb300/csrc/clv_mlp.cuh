@@ -206,7 +206,7 @@ __device__ __forceinline__ long long batch_index(unsigned long long seed, int it
   return (long long)(mix64(seed ^ ((unsigned long long)iter << 32) ^ (unsigned long long)j) % (unsigned long long)n);
 }
 
-__global__ void __launch_bounds__(kMlpTrainBlock) mlp_grad_kernel(const float* __restrict__ params,
+static __global__ void __launch_bounds__(kMlpTrainBlock) mlp_grad_kernel(const float* __restrict__ params,
                                                                   const float* __restrict__ X,
                                                                   const float* __restrict__ Y, long long n,
                                                                   long long batch, unsigned long long seed, int iter,
@@ -312,7 +312,7 @@ constexpr size_t mlp_grad_smem_bytes() {
 }
 
 // Adam step (Kingma & Ba 2015) on all parameters; clears the gradient.
-__global__ void mlp_adam_kernel(float* params, float* m, float* v, float* grad, int step, float lr) {
+static __global__ void mlp_adam_kernel(float* params, float* m, float* v, float* grad, int step, float lr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kMlpParams) return;
   const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;

@@ -126,3 +126,22 @@ def test_cooperfrye_host_checks(lib):
     sp2 = (clv.clv_cf_species * 1)()
     sp2[0].mass, sp2[0].g, sp2[0].stat = 0.14, 1.0, 2
     assert call(species=sp2) == 1 and "stat" in so.clv_last_error(None).decode()
+
+
+def test_charge_host_checks(lib):
+    """charge = 1 adds two fields to the workspace; a batch or an x-slab with
+    charge is refused before anything is allocated."""
+    so = clv.load()
+    n0, n1 = ctypes.c_size_t(), ctypes.c_size_t()
+    c0, _ = clv.make_config(33, 31, 21, 0.2, 0.2, 0.2, 0.4, 0.01, 0.08, precision=clv.CLV_FP32)
+    c1, _ = clv.make_config(33, 31, 21, 0.2, 0.2, 0.2, 0.4, 0.01, 0.08, precision=clv.CLV_FP32, charge=True)
+    assert so.clv_workspace_bytes(ctypes.byref(c0), ctypes.byref(n0)) == 0
+    assert so.clv_workspace_bytes(ctypes.byref(c1), ctypes.byref(n1)) == 0
+    assert n1.value - n0.value >= 2 * 33 * 31 * 24 * 4
+    cfgs = (clv.clv_config * 1)(c1)
+    h = ctypes.c_void_p()
+    assert so.clv_create_batch(cfgs, 1, None, ctypes.byref(h)) == 1
+    assert "batch" in so.clv_last_error(None).decode()
+    c2, _ = clv.make_config(33, 31, 21, 0.2, 0.2, 0.2, 0.4, 0.01, 0.08, halo_x=2, charge=True)
+    assert so.clv_workspace_bytes(ctypes.byref(c2), ctypes.byref(n0)) == 1
+    assert "x-slab" in so.clv_last_error(None).decode()
