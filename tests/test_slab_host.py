@@ -64,3 +64,34 @@ def test_exchange_with_three_gloo_ranks(tmp_path):
 def test_combine_stats():
     got = S.combine_stats([(1.0, 0.2, 5.0), (4.0, 0.3, 6.0), (2.0, 0.25, 7.5)])
     assert got == {"eps_max": 4.0, "T_max": 0.3, "E_tot": 18.5}
+
+
+def _leaving_worker(rank, world, port, out):
+    """Rank 1 leaves between steps (exits before the next halo exchange);
+    rank 0 must learn of it from the exchange itself, with an error instead
+    of a hang (short process-group timeout)."""
+    import datetime
+    import sys
+
+    import torch
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=5))
+    lo = torch.full((5,), float(rank))
+    hi = torch.full((5,), float(rank) + 0.5)
+    S.exchange_halos(lo, hi, rank, world)          # one healthy exchange
+    if rank == 1:
+        sys.exit(0)                                # leaves with nothing in flight
+    try:
+        S.exchange_halos(lo, hi, rank, world)
+        result = "no error"
+    except Exception as e:                         # gloo reports the lost peer
+        result = "detected: " + type(e).__name__
+    with open(os.path.join(out, "rank0.txt"), "w") as f:
+        f.write(result)
+
+
+def test_a_rank_that_leaves_is_detected_by_its_neighbour(tmp_path):
+    import torch.multiprocessing as mp
+    mp.start_processes(_leaving_worker, args=(2, _port(), str(tmp_path)), nprocs=2, start_method="spawn")
+    assert (tmp_path / "rank0.txt").read_text().startswith("detected"), (tmp_path / "rank0.txt").read_text()
