@@ -205,6 +205,28 @@ def test_full_size_viscous_event_one_step():
     assert fp32_eps_err(o, g32) <= FP32_TOL
 
 
+def test_largest_event_one_step():
+    """The largest configuration, the 261x261x121 mini-jet event (8.2 M cells,
+    initial state from T^{tau mu}, eta/s = 0.16): one full step, every cell,
+    FP64 to the FP64 bar and FP32 (the benchmark's precision) to the FP32 bar."""
+    case = I.minijet_event()
+    oracle.set_threads(0)
+    o = oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
+                      case.eta_over_s, case.eos, case.cartesian, case.periodic)
+    o.set_initial_T(case.T0)
+    o.step(1)
+    g64 = clv.from_case(case, clv.CLV_FP64)
+    g64.set_initial_case(case)
+    g64.step(1, stats=True)
+    compare_fp64(o, g64, viscous=True, fields=["eps", "ux", "ueta", "Ttt", "Ttx", "pixx", "piee"])
+    g64.close()
+    g32 = clv.from_case(case, clv.CLV_FP32)
+    g32.set_initial_case(case)
+    g32.step(1, stats=True)
+    assert fp32_eps_err(o, g32) <= FP32_TOL
+    g32.close()
+
+
 def test_single_cell_and_degenerate_grids():
     for shape in [(1, 1, 1), (1, 1, 5), (3, 1, 1), (2, 3, 1)]:
         nx, ny, ne = shape
