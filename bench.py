@@ -55,11 +55,11 @@ FO_BYTES_PER_CUBE = 2 * 4
 FO_BYTES_PER_ELEMENT = 22 * 4 + 8 + 2 * 13 * 4
 # Cooper-Frye sum: flops of one (element, momentum) pair with delta f, an FMA
 # counted as 2 and exp2 / reciprocal as 1 each.  What depends on the element
-# and (Y, pT) only is formed once for the 4 phi points of a thread: e^(Y-eta),
+# and (Y, pT) only is formed once for the 8 phi points of a thread: e^(Y-eta),
 # cosh, sinh 8, p^tau and tau p^eta 2, their parts of p.dSigma and p.u 6, of
-# p p pi 14 -> 30 / 4 = 7.5 per pair; per phi point: p.dSigma 4, p.u 4,
+# p p pi 14 -> 30 / 8 = 3.75 per pair; per phi point: p.dSigma 4, p.u 4,
 # exponent 2, exp2 1, f 2, p p pi 10, (1 - s f) q + 1 4, product and sum 3 -> 30
-CF_FLOPS_PER_PAIR = 37.5
+CF_FLOPS_PER_PAIR = 33.75
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 KERNEL_NAMES = {"stage1": "stage_tile_kernel<float,1,viscous>", "recover1": "recover_kernel<float,viscous>",
                 "stage2": "stage_tile_kernel<float,2,viscous>", "recover2": "recover_kernel<float,viscous>"}
@@ -218,11 +218,14 @@ def run_gpu(args):
                "setup_s": time.perf_counter() - t_setup}
     del buf, Xs, Ys, params
 
-    # ---- FP32 + learned guess: the headline value, with per-kernel event timing
+    # ---- FP32 + learned guess: the headline value, with per-kernel event timing.
+    # nvidia-smi samples the clocks from here through the last timed
+    # configuration below (it needs a moment to start; the headline alone
+    # lasts a fraction of a second)
     sampler = ClockSampler(dev.index)
     sampler.start()
+    time.sleep(0.5)
     ms32, kt, st32 = timed_run(clv.CLV_FP32, args.steps, args.warmup, kernel_timing=True, params=params_host)
-    clocks = sampler.stop()
     # ---- FP32 with the previous-step guess, and the FP64 path (fewer steps:
     # it is ALU-bound), on the same grid
     ms32p, _, st32p = timed_run(clv.CLV_FP32, args.steps, args.warmup)
@@ -472,6 +475,10 @@ def run_gpu(args):
                                                         "error")},
                  "stats_fp64": {k: stB64.get(k) for k in ("tau", "eps_max", "n_rootfail", "error_word", "error")}}
         del evs
+
+    clocks = sampler.stop()
+    clocks["covers"] = ("from the headline through the batch: every timed configuration, e2e, freeze-out and "
+                        "Cooper-Frye included")
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

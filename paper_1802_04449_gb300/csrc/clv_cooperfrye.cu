@@ -11,7 +11,7 @@
 //   sum      grid (momentum tiles, element chunks, species): the elements
 //            present (the device count when given) split in whole tiles over
 //            the chunks; each thread owns
-//            one (Y, pT) and kPhi consecutive phi points; the CTA stages tiles
+//            one (Y, pT) and kPhi (8) consecutive phi points; the CTA stages tiles
 //            of prepared elements in shared memory (every thread reads the
 //            same element: broadcast) and each thread accumulates its points
 //            over the tile, then adds the tile sum to FP64 accumulators; the
@@ -34,7 +34,7 @@ namespace {
 
 constexpr int kPrep = 24;          // prepared values per element
 constexpr int kThreads = 128;      // sum CTA
-constexpr int kPhi = 4;            // phi points per thread
+constexpr int kPhi = 8;            // phi points per thread
 constexpr int kTile = 128;         // elements per shared-memory tile
 constexpr double kHbarc = 0.1973269804;
 
