@@ -68,6 +68,7 @@ class _Config(ctypes.Structure):
         ("cartesian", ctypes.c_int), ("periodic", ctypes.c_int),
         ("eps_cut", ctypes.c_double), ("nthreads", ctypes.c_int),
         ("taupi_coef", ctypes.c_double), ("lambda1_hat", ctypes.c_double),
+        ("zeta_over_s", ctypes.c_double),
     ]
 
 
@@ -128,7 +129,7 @@ FIELD_INDEX = {"eps": 0, "ux": 1, "uy": 2, "ueta": 3,
                "Ttt": 4, "Ttx": 5, "Tty": 6, "Tte": 7,
                **{f"pi{k}": 8 + i for i, k in enumerate(
                    ["tt", "tx", "ty", "te", "xx", "xy", "xe", "yy", "ye", "ee"])},
-               "upx": 18, "upy": 19, "upe": 20, "Nt": 21, "n": 22}
+               "upx": 18, "upy": 19, "upe": 20, "Nt": 21, "n": 22, "Pi": 23}
 
 
 class Oracle:
@@ -137,7 +138,7 @@ class Oracle:
 
     def __init__(self, nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
                  cartesian=False, periodic=False, eps_cut=1e-7, nthreads=0, plant=0, taupi_coef=5.0,
-                 lambda1_hat=0.0):
+                 lambda1_hat=0.0, zeta_over_s=0.0):
         self._lib = _load(plant)
         c = _Config()
         c.nx, c.ny, c.neta = int(nx), int(ny), int(neta)
@@ -157,6 +158,7 @@ class Oracle:
         c.cartesian, c.periodic = int(bool(cartesian)), int(bool(periodic))
         c.eps_cut, c.nthreads = float(eps_cut), int(nthreads)
         c.taupi_coef, c.lambda1_hat = float(taupi_coef), float(lambda1_hat)
+        c.zeta_over_s = float(zeta_over_s)
         self.shape = (int(nx), int(ny), int(neta))
         self._h = self._lib.orc_create(ctypes.byref(c))
         if not self._h:

@@ -54,6 +54,20 @@
  *       - (2/3) Delta^{mu nu} theta with finite-difference gradients.
  *   R17 Boundaries: two ghost cells per side, copies of the edge cell
  *       (zero gradient) or periodic wrap.
+ *   R20 Bulk pressure (Eqs. Pi, Pitilde; the paper sets zeta = 0, so this is
+ *       off unless zeta/s > 0, and runs with the shear machinery, eta/s > 0):
+ *       Q_Pi = u~^tau Pi is carried with the flux v^a Q_Pi (the same limited
+ *       reconstruction of u~^tau and Pi as for Q_pi), and Pi adds to the
+ *       pressure everywhere T^{mu nu} appears: the T~ fluxes, S_T and the
+ *       root solve (P(eps) + Pi).  Source, from Eq. (Pi) and the conservative
+ *       form of Eq. (Pitilde):
+ *         S_Pi = -(Pi + zeta theta~)/tau_Pi - Pi theta~/3 - Pi u~^tau/tau,
+ *       theta~ = d~_mu u~^mu + u~^tau/tau; the printed -(Pi - zeta theta~)
+ *       contradicts Eq. (Pi), and the Pi u~^tau/tau term follows from
+ *       nabla_mu (Pi u^mu) as for pi~ (R2).  tau_Pi = 5 zeta/(T s) with
+ *       constant zeta/s, so zeta/tau_Pi = (eps + P)/5.  Update as R15 for pi~.
+ *       Regulator (as R18): Pi = 0 where the stage's input eps < 1e-3, and
+ *       |Pi| <= P there.  Vacuum cells: Pi = 0.
  *   R19 Net charge (Eq. Ntilde with S_N = 0; the paper sets n = 0, so this
  *       is off unless an initial n is given): N~^tau = tau n u^tau (1 in
  *       place of tau in Cartesian mode) is conserved with the flux
@@ -114,6 +128,7 @@ typedef struct {
   int nthreads;
   double taupi_coef;   /* b in tau_pi = b eta_v / (eps + P); 0 -> 5 (reading R10) */
   double lambda1_hat;  /* lambda_1 = lambda1_hat / eps (conformal scaling); 0 -> no lambda_1 term */
+  double zeta_over_s;  /* bulk viscosity over entropy (R20); 0 -> no bulk pressure */
 } orc_config;
 
 typedef struct {
@@ -122,6 +137,7 @@ typedef struct {
   double *ed;     /* eps */
   double *u[3];   /* u~^x, u~^y, u~^eta */
   double *N;      /* N~^tau (R19) */
+  double *Pi;     /* bulk pressure (R20) */
 } orc_fields;
 
 typedef struct {
@@ -136,6 +152,7 @@ typedef struct {
   long step;
   int viscous;
   int charge;       /* 1: net charge transported (R19) */
+  int bulk;         /* 1: bulk pressure evolved (R20) */
   long n_rescaled, n_rootfail;
   double stats[8];
 } orc_t;
@@ -187,7 +204,7 @@ static void eos_eval(const orc_t* h, double e, double* P, double* T, double* cs2
 /* ------------------- primitive recovery (Sec. 3, R13) ---------------- */
 /* Given E = T_ideal^{tau tau}, M = T_ideal^{tau i} (tilde components), find
  * eps and u~.  Returns number of iterations, -1 on iteration cap. */
-static int prim_solve(const orc_t* h, double E, double Mx, double My, double Me,
+static int prim_solve(const orc_t* h, double E, double Mx, double My, double Me, double Pshift,
                       double* eps, double u[4], int* rescaled) {
   *rescaled = 0;
   u[0] = 1.0; u[1] = u[2] = u[3] = 0.0;
@@ -208,11 +225,13 @@ static int prim_solve(const orc_t* h, double E, double Mx, double My, double Me,
   double lo = 0.0, hi = M / E;
   double P, T, cs2;
   eos_eval(h, E, &P, &T, &cs2);
+  P += Pshift;   /* bulk pressure (R20) */
   double v = M / (E + P);
   int it, ok = 0;
   for (it = 1; it <= 100; ++it) {
     double e = (PLANT == 8) ? E : E - M * v;
     eos_eval(h, e, &P, &T, &cs2);
+    P += Pshift;
     double f = v - M / (E + P);
     if (f > 0.0) hi = v; else lo = v;
     double df = 1.0 - M * M * cs2 / ((E + P) * (E + P));
@@ -345,7 +364,17 @@ static void regulate_pi(const orc_t* h, double e, double* pi) {
 }
 
 /* ------------------------- KT (Eqs. kt, flux_out) -------------------- */
-#define NR 18 /* reconstructed: T(4) pi(10) u^tau v^a P N~^tau */
+#define NR 19 /* reconstructed: T(4) pi(10) u^tau v^a P(+Pi) N~^tau Pi */
+
+/* bulk regulator (R20) with eps and P of the stage's input state */
+static double regulate_Pi(const orc_t* h, double e, double Pb) {
+  if (e < VISC_EPS_MIN) return 0.0;
+  double P, T, cs2;
+  eos_eval(h, e, &P, &T, &cs2);
+  if (Pb > P) return P;
+  if (Pb < -P) return -P;
+  return Pb;
+}
 
 static double minmod(double a, double b) {
   if (a > 0.0 && b > 0.0) return a < b ? a : b;
@@ -371,7 +400,8 @@ static void cell_R(const view_t* vw, size_t id, int axis, double R[NR], double* 
   for (int q = 0; q < NPI; ++q) R[4 + q] = vw->viscous ? f->pi[q][id] : 0.0;
   R[14] = u[0];
   R[15] = u[axis] / u[0];
-  R[16] = P;
+  R[18] = (vw->viscous && vw->h->bulk) ? f->Pi[id] : 0.0;
+  R[16] = P + ((PLANT == 21) ? 0.0 : R[18]);   /* the pressure of T^{mu nu} (R20) */
   R[17] = f->N[id];
   *cs = sqrt(cs2);
 }
@@ -379,7 +409,7 @@ static void cell_R(const view_t* vw, size_t id, int axis, double R[NR], double* 
 /* Flux H at the interface between cells b and c on axis a, from cells a,b,c,d
  * (= i-1, i, i+1, i+2).  Q = (T~^{tau mu}, Q_pi = u~^tau pi~). */
 static void kt_interface(const view_t* vw, int axis, double taus, size_t ia, size_t ib, size_t ic,
-                         size_t id, double H[4 + NPI], double* HN) {
+                         size_t id, double H[4 + NPI], double* HN, double* HPi) {
   double Ra[NR], Rb[NR], Rc[NR], Rd[NR], csa, csb, csc, csd;
   cell_R(vw, ia, axis, Ra, &csa);
   cell_R(vw, ib, axis, Rb, &csb);
@@ -417,6 +447,9 @@ static void kt_interface(const view_t* vw, int axis, double taus, size_t ia, siz
     H[q] = 0.5 * (Fl[q] + Fr[q]) - 0.5 * cmax * (Qr[q] - Ql[q]);
   /* net charge (R19): flux v^a N~^tau */
   *HN = 0.5 * (vl * L[17] + vr * Rr[17]) - ((PLANT == 16) ? -0.5 : 0.5) * cmax * (Rr[17] - L[17]);
+  /* bulk (R20): Q_Pi = u~^tau Pi on each side, flux v^a Q_Pi */
+  double QPl = L[14] * L[18], QPr = Rr[14] * Rr[18];
+  *HPi = 0.5 * (vl * QPl + vr * QPr) - 0.5 * cmax * (QPr - QPl);
 }
 
 /* -------------------------- ghost cells (R17) ------------------------ */
@@ -437,6 +470,7 @@ static void fill_ghosts_array(const orc_t* h, double* a) {
 
 static void fill_ghosts(const orc_t* h, orc_fields* f) {
   if (h->charge) fill_ghosts_array(h, f->N);
+  if (h->bulk) fill_ghosts_array(h, f->Pi);
   for (int m = 0; m < 4; ++m) fill_ghosts_array(h, f->T[m]);
   for (int q = 0; q < NPI; ++q) fill_ghosts_array(h, f->pi[q]);
   fill_ghosts_array(h, f->ed);
@@ -449,13 +483,14 @@ static void fill_ghosts(const orc_t* h, orc_fields* f) {
  * un: velocity at step n (spatial components). */
 static void stage_source(const orc_t* h, const orc_fields* f, int viscous, double tau_s, int i,
                          int j, int k, const double ulate[4], const double un[4],
-                         double S[4 + NPI], double* SN) {
+                         double S[4 + NPI], double* SN, double* SPi) {
   view_t vw = {h, f, viscous};
   double taus = tau_scale(h, tau_s);
   double g = geo(h, tau_s);
   double hstep = h->c.dtau;
   for (int q = 0; q < 4 + NPI; ++q) S[q] = 0.0;
   *SN = 0.0;
+  *SPi = 0.0;
   /* KT flux differences along x, y, eta_s (Eq. kt) */
   double dl[3] = {h->c.dx, h->c.dy, ((PLANT == 4) ? 1.0 : taus) * h->c.deta};
   for (int ax = 1; ax <= 3; ++ax) {
@@ -465,12 +500,13 @@ static void stage_source(const orc_t* h, const orc_fields* f, int viscous, doubl
     size_t c0 = IX(h, i, j, k);
     size_t p1 = IX(h, i + di, j + dj, k + dk);
     size_t p2 = IX(h, i + 2 * di, j + 2 * dj, k + 2 * dk);
-    double Hm[4 + NPI], Hp[4 + NPI], HNm, HNp;
-    kt_interface(&vw, ax, taus, m2, m1, c0, p1, Hm, &HNm);
-    kt_interface(&vw, ax, taus, m1, c0, p1, p2, Hp, &HNp);
+    double Hm[4 + NPI], Hp[4 + NPI], HNm, HNp, HPm, HPp;
+    kt_interface(&vw, ax, taus, m2, m1, c0, p1, Hm, &HNm, &HPm);
+    kt_interface(&vw, ax, taus, m1, c0, p1, p2, Hp, &HNp, &HPp);
     int nq = viscous ? 4 + NPI : 4;
     for (int q = 0; q < nq; ++q) S[q] -= (Hp[q] - Hm[q]) / dl[ax - 1];
     *SN -= (HNp - HNm) / dl[ax - 1];
+    *SPi -= (HPp - HPm) / dl[ax - 1];
   }
   /* geometric source S_T (R1) */
   size_t c0 = IX(h, i, j, k);
@@ -480,7 +516,8 @@ static void stage_source(const orc_t* h, const orc_fields* f, int viscous, doubl
   double e = f->ed[c0], P, T, cs2;
   eos_eval(h, e, &P, &T, &cs2);
   double piee = viscous ? f->pi[9][c0] : 0.0;
-  double Tee_over_tau = e * u[3] * u[3] + P * (1.0 + u[3] * u[3]) + piee;
+  double Pb = (viscous && h->bulk) ? f->Pi[c0] : 0.0;   /* R20: the pressure of T^{mu nu} is P + Pi */
+  double Tee_over_tau = e * u[3] * u[3] + (P + Pb) * (1.0 + u[3] * u[3]) + piee;
   S[0] -= ((PLANT == 3) ? -1.0 : 1.0) * (h->c.cartesian ? 0.0 : 1.0) * Tee_over_tau;
   if (PLANT != 7) S[3] -= g * f->T[3][c0];
   if (!viscous) return;
@@ -502,6 +539,14 @@ static void stage_source(const orc_t* h, const orc_fields* f, int viscous, doubl
   for (int q = 0; q < NPI; ++q) pi[q] = f->pi[q][c0];
   source_pi(g, u, du, pi, e, P, T, h->c.eta_over_s, h->c.taupi_coef, h->c.lambda1_hat, Spi);
   for (int q = 0; q < NPI; ++q) S[4 + q] += Spi[q];
+  if (h->bulk) {
+    /* R20: theta~ = d~_mu u~^mu + u~^tau/tau; 1/tau_Pi = T / (5 (zeta/s) hbar c),
+       zeta / tau_Pi = (eps + P)/5 */
+    double theta = du[0] + du[5] + du[10] + du[15] + g * u[0];
+    double inv_tauPi = T / (5.0 * h->c.zeta_over_s * HBARC);
+    *SPi += -Pb * inv_tauPi - ((PLANT == 19) ? -1.0 : 1.0) * (e + P) * theta / 5.0 - Pb * theta / 3.0
+            - ((PLANT == 18) ? 0.0 : 1.0) * g * u[0] * Pb;
+  }
 }
 
 static void recover(orc_t* h, double tau_new, size_t c, orc_fields* out, int viscous,
@@ -514,13 +559,16 @@ static void recover(orc_t* h, double tau_new, size_t c, orc_fields* out, int vis
   double Me = out->T[3][c] / taus - (viscous ? out->pi[3][c] : 0.0);
   double e, u[4];
   int resc;
-  int it = prim_solve(h, E, Mx, My, Me, &e, u, &resc);
+  double Pb = (viscous && h->bulk && PLANT != 20) ? out->Pi[c] : 0.0;
+  int it = prim_solve(h, E, Mx, My, Me, Pb, &e, u, &resc);
   if (it < 0) (*nfail)++;
   if (resc) (*nres)++;
   out->ed[c] = e;
   out->u[0][c] = u[1]; out->u[1][c] = u[2]; out->u[2][c] = u[3];
-  if (viscous && e == 0.0)
+  if (viscous && e == 0.0) {
     for (int q = 0; q < NPI; ++q) out->pi[q][c] = 0.0;
+    if (h->bulk) out->Pi[c] = 0.0;
+  }
 }
 
 static void heun_step(orc_t* h, int viscous) {
@@ -541,8 +589,8 @@ static void heun_step(orc_t* h, int viscous) {
         un[0] = sqrt(1.0 + un[1] * un[1] + un[2] * un[2] + un[3] * un[3]);
         for (int b = 1; b < 4; ++b) us[b] = viscous ? 2.0 * un[b] - h->up[b - 1][c] : un[b];
         us[0] = sqrt(1.0 + us[1] * us[1] + us[2] * us[2] + us[3] * us[3]);
-        double S[4 + NPI], SN;
-        stage_source(h, s, viscous, tn, i, j, k, us, un, S, &SN);
+        double S[4 + NPI], SN, SPi;
+        stage_source(h, s, viscous, tn, i, j, k, us, un, S, &SN, &SPi);
         for (int m = 0; m < 4; ++m) s1->T[m][c] = s->T[m][c] + hs * S[m];
         if (h->charge) s1->N[c] = s->N[c] + hs * SN;
         if (viscous) {
@@ -550,6 +598,7 @@ static void heun_step(orc_t* h, int viscous) {
           for (int q = 0; q < NPI; ++q) pv[q] = (un[0] * s->pi[q][c] + hs * S[4 + q]) / us[0];
           regulate_pi(h, s->ed[c], pv);
           for (int q = 0; q < NPI; ++q) s1->pi[q][c] = pv[q];
+          if (h->bulk) s1->Pi[c] = regulate_Pi(h, s->ed[c], (un[0] * s->Pi[c] + hs * SPi) / us[0]);
         }
         recover(h, tn1, c, s1, viscous, &nres, &nfail);
       }
@@ -567,8 +616,8 @@ static void heun_step(orc_t* h, int viscous) {
         us[0] = sqrt(1.0 + us[1] * us[1] + us[2] * us[2] + us[3] * us[3]);
         u1[1] = s1->u[0][c]; u1[2] = s1->u[1][c]; u1[3] = s1->u[2][c];
         u1[0] = sqrt(1.0 + u1[1] * u1[1] + u1[2] * u1[2] + u1[3] * u1[3]);
-        double S[4 + NPI], SN;
-        stage_source(h, s1, viscous, tn1, i, j, k, u1, un, S, &SN);
+        double S[4 + NPI], SN, SPi;
+        stage_source(h, s1, viscous, tn1, i, j, k, u1, un, S, &SN, &SPi);
         for (int m = 0; m < 4; ++m) s->T[m][c] = 0.5 * (s->T[m][c] + s1->T[m][c] + hs * S[m]);
         if (h->charge) s->N[c] = 0.5 * (s->N[c] + s1->N[c] + hs * SN);
         if (viscous) {
@@ -577,6 +626,8 @@ static void heun_step(orc_t* h, int viscous) {
             pv[q] = 0.5 * (un[0] * s->pi[q][c] + us[0] * s1->pi[q][c] + hs * S[4 + q]) / u1[0];
           regulate_pi(h, s1->ed[c], pv);
           for (int q = 0; q < NPI; ++q) s->pi[q][c] = pv[q];
+          if (h->bulk)
+            s->Pi[c] = regulate_Pi(h, s1->ed[c], 0.5 * (un[0] * s->Pi[c] + us[0] * s1->Pi[c] + hs * SPi) / u1[0]);
         }
         /* keep u^n as u^{n-1} for the next step */
         h->up[0][c] = un[1]; h->up[1][c] = un[2]; h->up[2][c] = un[3];
@@ -619,6 +670,7 @@ static void fields_alloc(orc_fields* f, size_t n) {
   f->ed = zalloc(n);
   for (int m = 0; m < 3; ++m) f->u[m] = zalloc(n);
   f->N = zalloc(n);
+  f->Pi = zalloc(n);
 }
 static void fields_free(orc_fields* f) {
   for (int m = 0; m < 4; ++m) free(f->T[m]);
@@ -626,6 +678,7 @@ static void fields_free(orc_fields* f) {
   free(f->ed);
   for (int m = 0; m < 3; ++m) free(f->u[m]);
   free(f->N);
+  free(f->Pi);
 }
 static void fields_copy(orc_fields* d, const orc_fields* s, size_t n) {
   for (int m = 0; m < 4; ++m) memcpy(d->T[m], s->T[m], n * sizeof(double));
@@ -633,12 +686,14 @@ static void fields_copy(orc_fields* d, const orc_fields* s, size_t n) {
   memcpy(d->ed, s->ed, n * sizeof(double));
   for (int m = 0; m < 3; ++m) memcpy(d->u[m], s->u[m], n * sizeof(double));
   memcpy(d->N, s->N, n * sizeof(double));
+  memcpy(d->Pi, s->Pi, n * sizeof(double));
 }
 
 orc_t* orc_create(const orc_config* c) {
   if (!c || c->nx < 1 || c->ny < 1 || c->neta < 1) return NULL;
   if (!(c->dx > 0 && c->dy > 0 && c->deta > 0 && c->dtau > 0)) return NULL;
   if (!c->cartesian && !(c->tau0 > 0)) return NULL;
+  if (!(c->zeta_over_s >= 0.0) || (c->zeta_over_s > 0.0 && !(c->eta_over_s > 0.0))) return NULL; /* R20 */
   if (c->eos_kind == 1 && (c->eos_n < 2 || !c->eos_P || !c->eos_T || !c->eos_cs2)) return NULL;
   orc_t* h = (orc_t*)calloc(1, sizeof(orc_t));
   h->c = *c;
@@ -656,6 +711,7 @@ orc_t* orc_create(const orc_config* c) {
   for (int m = 0; m < 3; ++m) h->up[m] = zalloc(h->NG);
   h->tau = c->tau0;
   h->viscous = c->eta_over_s > 0.0;
+  h->bulk = h->viscous && c->zeta_over_s > 0.0;
 #ifdef _OPENMP
   if (c->nthreads > 0) omp_set_num_threads(c->nthreads);
 #endif
@@ -693,6 +749,8 @@ int orc_set_initial(orc_t* h, const double* eps, const double* ux, const double*
   h->charge = 0;
   memset(h->s.N, 0, h->NG * sizeof(double));
   memset(h->s1.N, 0, h->NG * sizeof(double));
+  memset(h->s.Pi, 0, h->NG * sizeof(double));   /* Pi = 0 at tau0 (R20) */
+  memset(h->s1.Pi, 0, h->NG * sizeof(double));
   for (int i = 0; i < nx; ++i)
     for (int j = 0; j < ny; ++j)
       for (int k = 0; k < ne; ++k) {
@@ -764,7 +822,7 @@ int orc_set_initial_T(orc_t* h, const double* T) {
   for (size_t l = 0; l < N; ++l) {
     double e, u[4];
     int resc;
-    if (prim_solve(h, T[l], T[N + l], T[2 * N + l], T[3 * N + l], &e, u, &resc) < 0) fail = 1;
+    if (prim_solve(h, T[l], T[N + l], T[2 * N + l], T[3 * N + l], 0.0, &e, u, &resc) < 0) fail = 1;
     a[l] = e;
     a[N + l] = u[1];
     a[2 * N + l] = u[2];
@@ -798,7 +856,8 @@ int orc_step(orc_t* h, int n) {
   return h->n_rootfail ? 4 : 0;
 }
 
-/* which: 0 eps, 1..3 u~^x,y,eta, 4..7 T~^{tau mu}, 8..17 pi~, 18..20 u~^{n-1} */
+/* which: 0 eps, 1..3 u~^x,y,eta, 4..7 T~^{tau mu}, 8..17 pi~, 18..20 u~^{n-1},
+ * 21 N~^tau, 22 n, 23 Pi */
 int orc_get(const orc_t* h, int which, double* out) {
   int nx = h->c.nx, ny = h->c.ny, ne = h->c.neta;
   const double* a;
@@ -808,6 +867,7 @@ int orc_get(const orc_t* h, int which, double* out) {
   else if (which <= 17) a = h->s.pi[which - 8];
   else if (which <= 20) a = h->up[which - 18];
   else if (which == 21) a = h->s.N;
+  else if (which == 23) a = h->s.Pi;
   else if (which == 22) {
     /* n = N~^tau / (tau u^tau) (R19) */
     double taus = tau_scale(h, h->tau);
@@ -835,7 +895,7 @@ void orc_eos(const orc_t* h, double e, double out[3]) { eos_eval(h, e, &out[0], 
 int orc_prim(const orc_t* h, double E, double Mx, double My, double Me, double out[6]) {
   double e, u[4];
   int resc;
-  int it = prim_solve(h, E, Mx, My, Me, &e, u, &resc);
+  int it = prim_solve(h, E, Mx, My, Me, 0.0, &e, u, &resc);
   out[0] = e; out[1] = u[0]; out[2] = u[1]; out[3] = u[2]; out[4] = u[3]; out[5] = it;
   return it;
 }

@@ -22,12 +22,18 @@ Cooper-Frye spectra (clv_cooperfrye.c):
 Net charge (clv_oracle.c, R19):
  16 the local-speed term of the charge flux with the wrong sign -> Gubser charge convergence
  17 initial N~^tau without the tau factor -> Bjorken n tau constant
+Bulk pressure (clv_oracle.c, R20):
+ 18 the -Pi u~^tau/tau term of S_Pi dropped -> Bjorken bulk ODE
+ 19 sign of the zeta theta~ term flipped  -> Bjorken bulk ODE / sound wave
+ 20 root solve without the Pi pressure shift -> decomposition of T^{tau mu}
+ 21 Pi left out of the pressure in the T~ fluxes -> linearised sound wave
 """
 import numpy as np
 import pytest
 
 import oracle
 import test_oracle_flows as F
+import test_oracle_bulk as BU
 import test_oracle_charge as CH
 import test_oracle_cooperfrye as CF
 import test_oracle_freezeout as FO
@@ -50,6 +56,10 @@ CASES = {
     15: CF.check_particle_number,
     16: CH.check_gubser_charge,
     17: CH.check_bjorken_charge,
+    18: BU.check_bjorken_bulk,
+    19: BU.check_bjorken_bulk,
+    20: BU.check_decomposition,
+    21: BU.check_bulk_sound_wave,
 }
 
 
