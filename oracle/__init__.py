@@ -106,6 +106,8 @@ def _load(plant: int = 0):
             lib.orc_eos.argtypes = [P, ctypes.c_double, D]
             lib.orc_prim.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, D]
+            lib.orc_prim_bulk.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, D]
             lib.orc_source_pi.argtypes = [P, ctypes.c_double, D, D, D, ctypes.c_double, D]
             lib.orc_source_T.argtypes = [P, ctypes.c_double, D, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, D]
@@ -216,6 +218,11 @@ class Oracle:
     def prim(self, E, Mx, My, Me):
         out = np.zeros(6)
         self._lib.orc_prim(self._h, float(E), float(Mx), float(My), float(Me), _dp(out))
+        return out
+
+    def prim_bulk(self, E, Mx, My, Me, Pi):
+        out = np.zeros(6)
+        self._lib.orc_prim_bulk(self._h, float(E), float(Mx), float(My), float(Me), float(Pi), _dp(out))
         return out
 
     def source_pi(self, tau, u, du, pi, e):

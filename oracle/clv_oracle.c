@@ -67,7 +67,13 @@
  *       nabla_mu (Pi u^mu) as for pi~ (R2).  tau_Pi = 5 zeta/(T s) with
  *       constant zeta/s, so zeta/tau_Pi = (eps + P)/5.  Update as R15 for pi~.
  *       Regulator (as R18): Pi = 0 where the stage's input eps < 1e-3, and
- *       |Pi| <= P there.  Vacuum cells: Pi = 0.
+ *       |Pi| <= P there.  Vacuum cells: Pi = 0.  The pressure of T^{mu nu} is
+ *       max(P + Pi, 0): the bound uses P of the stage's input, and where eps
+ *       then falls P(eps) + Pi can dip below 0, which leaves the root
+ *       function f(v) of the solve with two roots or none in [0, M/E]; with
+ *       the floor (and d(P + Pi)/d eps = 0 on it) f is increasing and its
+ *       root unique.  A negative total pressure is outside the validity of
+ *       the second-order equations anyway.
  *   R19 Net charge (Eq. Ntilde with S_N = 0; the paper sets n = 0, so this
  *       is off unless an initial n is given): N~^tau = tau n u^tau (1 in
  *       place of tau in Cartesian mode) is conserved with the flux
@@ -225,13 +231,15 @@ static int prim_solve(const orc_t* h, double E, double Mx, double My, double Me,
   double lo = 0.0, hi = M / E;
   double P, T, cs2;
   eos_eval(h, E, &P, &T, &cs2);
-  P += Pshift;   /* bulk pressure (R20) */
+  P += Pshift;   /* bulk pressure, total floored at 0 (R20) */
+  if (P < 0.0) P = 0.0;
   double v = M / (E + P);
   int it, ok = 0;
   for (it = 1; it <= 100; ++it) {
     double e = (PLANT == 8) ? E : E - M * v;
     eos_eval(h, e, &P, &T, &cs2);
     P += Pshift;
+    if (P < 0.0) { P = 0.0; cs2 = 0.0; }
     double f = v - M / (E + P);
     if (f > 0.0) hi = v; else lo = v;
     double df = 1.0 - M * M * cs2 / ((E + P) * (E + P));
@@ -402,6 +410,7 @@ static void cell_R(const view_t* vw, size_t id, int axis, double R[NR], double* 
   R[15] = u[axis] / u[0];
   R[18] = (vw->viscous && vw->h->bulk) ? f->Pi[id] : 0.0;
   R[16] = P + ((PLANT == 21) ? 0.0 : R[18]);   /* the pressure of T^{mu nu} (R20) */
+  if (R[16] < 0.0) R[16] = 0.0;
   R[17] = f->N[id];
   *cs = sqrt(cs2);
 }
@@ -517,7 +526,9 @@ static void stage_source(const orc_t* h, const orc_fields* f, int viscous, doubl
   eos_eval(h, e, &P, &T, &cs2);
   double piee = viscous ? f->pi[9][c0] : 0.0;
   double Pb = (viscous && h->bulk) ? f->Pi[c0] : 0.0;   /* R20: the pressure of T^{mu nu} is P + Pi */
-  double Tee_over_tau = e * u[3] * u[3] + (P + Pb) * (1.0 + u[3] * u[3]) + piee;
+  double Pt = P + Pb;
+  if (Pt < 0.0) Pt = 0.0;
+  double Tee_over_tau = e * u[3] * u[3] + Pt * (1.0 + u[3] * u[3]) + piee;
   S[0] -= ((PLANT == 3) ? -1.0 : 1.0) * (h->c.cartesian ? 0.0 : 1.0) * Tee_over_tau;
   if (PLANT != 7) S[3] -= g * f->T[3][c0];
   if (!viscous) return;
@@ -896,6 +907,15 @@ int orc_prim(const orc_t* h, double E, double Mx, double My, double Me, double o
   double e, u[4];
   int resc;
   int it = prim_solve(h, E, Mx, My, Me, 0.0, &e, u, &resc);
+  out[0] = e; out[1] = u[0]; out[2] = u[1]; out[3] = u[2]; out[4] = u[3]; out[5] = it;
+  return it;
+}
+
+/* The root solve with a bulk pressure Pi added to P (total floored at 0, R20). */
+int orc_prim_bulk(const orc_t* h, double E, double Mx, double My, double Me, double Pi, double out[6]) {
+  double e, u[4];
+  int resc;
+  int it = prim_solve(h, E, Mx, My, Me, Pi, &e, u, &resc);
   out[0] = e; out[1] = u[0]; out[2] = u[1]; out[3] = u[2]; out[4] = u[3]; out[5] = it;
   return it;
 }

@@ -8,8 +8,9 @@ tau_Pi = 5 zeta/(T s)), against solutions the mathematics fixes.
     equations of Pi and pi^{xx} gives a 4 x 4 linear system per Fourier mode,
     solved exactly by a matrix exponential.
   * The decomposition of Eq. (Tmn): after steps of a flowing event, the
-    stored T~^{tau mu} equals (eps + P + Pi) u~^tau u~^mu - (P + Pi) g~^{tau mu}
-    + pi~^{tau mu} of the stored primitives (what the root solve must invert).
+    stored T~^{tau mu} equals (eps + P_t) u~^tau u~^mu - P_t g~^{tau mu}
+    + pi~^{tau mu} of the stored primitives, P_t = max(P + Pi, 0) (what the
+    root solve must invert).
   * Energy-momentum conservation in a periodic box, and zeta/s = 0 leaving
     every bit of the shear-only run unchanged.
 
@@ -134,7 +135,7 @@ def decomposition_err(plant=0, zeta_over_s=0.2, nsteps=12):
     f = o.fields()
     tau = o.stats()["tau"]
     e = f["eps"]
-    P = np.vectorize(lambda x: o.eos(x)[0])(e) + f["Pi"]
+    P = np.maximum(np.vectorize(lambda x: o.eos(x)[0])(e) + f["Pi"], 0.0)
     u = [f["ux"], f["uy"], f["ueta"]]
     ut = np.sqrt(1 + u[0] ** 2 + u[1] ** 2 + u[2] ** 2)
     w = e + P
@@ -155,6 +156,32 @@ def check_decomposition(plant=0):
 
 def test_decomposition_of_T_with_bulk():
     check_decomposition()
+
+
+# ------------------------------------------------- root solve with Pi
+def test_root_solve_with_bulk_pressure_is_the_unique_root():
+    """For random (eps, v, Pi) with |Pi| <= P(eps) and the table EOS, build
+    E = (eps + P_t) gamma^2 - P_t and M = (eps + P_t) gamma^2 v with
+    P_t = max(P(eps) + Pi, 0): the solve returns (eps, v).  Where the total
+    pressure floor binds nearby, f(v) = v - M/(E + P_t(E - M v)) still has a
+    single sign change on [0, M/E] (brute force on 4001 points)."""
+    eos = I.crossover_eos()
+    o = oracle.Oracle(2, 2, 2, 0.3, 0.3, 0.3, 0.6, 0.01, eta_over_s=0.1, zeta_over_s=0.1, eos=eos)
+    rng = np.random.default_rng(4)
+    Pt = lambda x, Pi: max(o.eos(x)[0] + Pi, 0.0)
+    for _ in range(150):
+        e = 10 ** rng.uniform(-2.5, 1.5)
+        v = rng.uniform(0, 0.95)
+        Pi = rng.uniform(-1.05, 1.0) * o.eos(e)[0]   # a little beyond -P: the floor binds
+        w = e + Pt(e, Pi)
+        g2 = 1 / (1 - v * v)
+        E, M = w * g2 - Pt(e, Pi), w * g2 * v
+        out = o.prim_bulk(E, M, 0.0, 0.0, Pi)
+        assert out[5] > 0
+        assert abs(out[0] / e - 1) < 1e-11 and abs(out[2] / out[1] - v) < 1e-11, (e, v, Pi, out)
+        vs = np.linspace(0, M / E, 4001)
+        f = np.array([x - M / (E + Pt(E - M * x, Pi)) for x in vs])
+        assert np.sum(np.diff(np.sign(f)) != 0) == 1
 
 
 # ------------------------------------------------ conservation, limits
