@@ -84,6 +84,12 @@ typedef struct {
   int charge;                /* 1: also transport a net charge (Eq. Ntilde, S_N = 0, no diffusion
                                 current; the paper runs with n = 0): N~^tau = tau n u~^tau, set by
                                 clv_set_initial_n; single events only (not a batch or an x-slab) */
+  double zeta_over_s;        /* bulk viscosity over entropy (Eqs. Pi, Pitilde, tau_Pi = 5 zeta/(T s));
+                                0: no bulk pressure (the paper's setting).  > 0 needs eta_over_s > 0
+                                and a single event (not a batch or an x-slab).  Pi = 0 at tau0; it
+                                relaxes by S_Pi = -(Pi + zeta theta)/tau_Pi - Pi theta/3 - Pi u^tau/tau
+                                (theta = nabla_mu u^mu), is carried by the flux v^a u~^tau Pi and adds
+                                to the pressure of T^{mu nu} (fluxes, S_T, the root solve) */
 } clv_config;
 
 /* Per-run statistics, filled by clv_step / clv_get_stats. */
@@ -173,7 +179,8 @@ clv_status clv_get_stats(clv_handle* h, clv_stats* stats);
  *   4..7 T~^{tau mu} (mu = tau, x, y, eta),
  *   8..17 pi~ (tt tx ty te xx xy xe yy ye ee),
  *   18..20 u~^{x,y,eta} of the previous step,
- *   21 N~^tau and 22 n = N~^tau / (tau u~^tau) (charge = 1 only; CLV_EINVAL otherwise).
+ *   21 N~^tau and 22 n = N~^tau / (tau u~^tau) (charge = 1 only; CLV_EINVAL otherwise),
+ *   23 the bulk pressure Pi (GeV/fm^3; zeta_over_s > 0 only; CLV_EINVAL otherwise).
  * host_out receives popcount(mask) grids of nx*ny*neta doubles, in
  * increasing field order.  Synchronises. */
 clv_status clv_get_fields(clv_handle* h, uint32_t mask, double* host_out);

@@ -23,7 +23,7 @@ STATUS = {0: "CLV_OK", 1: "CLV_EINVAL", 2: "CLV_ENOMEM", 3: "CLV_ECUDA", 4: "CLV
 
 FIELDS = ["eps", "ux", "uy", "ueta", "Ttt", "Ttx", "Tty", "Tte",
           "pitt", "pitx", "pity", "pite", "pixx", "pixy", "pixe", "piyy", "piye", "piee",
-          "upx", "upy", "upe", "Nt", "n"]
+          "upx", "upy", "upe", "Nt", "n", "Pi"]
 FIELD_BIT = {k: i for i, k in enumerate(FIELDS)}
 
 
@@ -42,6 +42,7 @@ class clv_config(ctypes.Structure):
         ("eps_cut", ctypes.c_double), ("kernel", ctypes.c_int),
         ("taupi_coef", ctypes.c_double), ("lambda1_hat", ctypes.c_double), ("halo_x", ctypes.c_int),
         ("charge", ctypes.c_int),
+        ("zeta_over_s", ctypes.c_double),
     ]
 
 
@@ -353,9 +354,10 @@ def fo_find(grid, s0, s1, eps_f, capacity=None, device=None, stream=None):
 
 def make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
                 precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7, kernel=0,
-                taupi_coef=0.0, lambda1_hat=0.0, halo_x=0, charge=False):
+                taupi_coef=0.0, lambda1_hat=0.0, halo_x=0, charge=False, zeta_over_s=0.0):
     c = clv_config()
     c.charge = int(bool(charge))
+    c.zeta_over_s = float(zeta_over_s)
     c.taupi_coef, c.lambda1_hat = float(taupi_coef), float(lambda1_hat)
     c.halo_x = int(halo_x)
     c.nx, c.ny, c.neta = int(nx), int(ny), int(neta)
@@ -385,14 +387,14 @@ class Hydro:
     def __init__(self, nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s=0.0, eos=None,
                  precision=CLV_FP64, cartesian=False, periodic=False, eps_cut=1e-7,
                  stream=None, device=None, torch_workspace=True, kernel=0, taupi_coef=0.0, lambda1_hat=0.0,
-                 halo_x=0, charge=False):
+                 halo_x=0, charge=False, zeta_over_s=0.0):
         import torch
         self._lib = load()
         self.torch = torch
         self.device = torch.device(device or "cuda")
         self.cfg, self._keep = make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s, eos,
                                            precision, cartesian, periodic, eps_cut, kernel, taupi_coef,
-                                           lambda1_hat, halo_x, charge)
+                                           lambda1_hat, halo_x, charge, zeta_over_s)
         self.shape = (int(nx), int(ny), int(neta))
         self.N = int(nx) * int(ny) * int(neta)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -642,7 +644,7 @@ class Hydro:
         """Host copy of the named fields: dict name -> (nx, ny, neta) float64.
         ``out`` may be a preallocated (len(names), N) float64 array (pinned or not)."""
         if names is None:
-            names = FIELDS if self.cfg.charge else FIELDS[:21]
+            names = FIELDS[:21] + (["Nt", "n"] if self.cfg.charge else []) + (["Pi"] if self.cfg.zeta_over_s > 0 else [])
         names = list([names] if isinstance(names, str) else names)
         names = sorted(names, key=lambda k: FIELD_BIT[k])
         buf = out if out is not None else np.empty((len(names), self.N), dtype=np.float64)

@@ -29,6 +29,10 @@ void launch_charge_init(const double* n, const Prim<R>& pr, double taus, void* N
 template <typename R>
 void launch_charge_density(const void* N, const Prim<R>& pr, double taus, double* out, long long nc, int ne, int nep,
                            cudaStream_t st);
+// clv_bulk.cu: the bulk-pressure kernel
+template <typename R>
+void launch_bulk_stage(const StageParams<R>& p, int stage, const void* Pin, const void* Pn, void* Pout,
+                       double zeta_over_s, cudaStream_t st);
 }  // namespace clv
 
 namespace {
@@ -75,6 +79,7 @@ struct clv_handle {
   void* PR[kNumPrimSets][kPrimFields];
   void* NC[2] = {nullptr, nullptr};   // charge = 1: N~^tau of the state and of the stage
   bool charge_on = false;             // clv_set_initial_n since the last initial state
+  void* PB[2] = {nullptr, nullptr};   // zeta_over_s > 0: Pi of the state and of the stage
   int cur = 0, prev = 1;
   void* eos[3];
   void* mlp = nullptr;            // tensor-core copy of the guess network
@@ -168,6 +173,12 @@ clv_status validate(const clv_config* c) {
   if (c->halo_x && (c->nx < 2 || c->kernel != 0)) return fail(nullptr, CLV_EINVAL, "an x-slab needs nx >= 2 and kernel 0");
   if (c->charge != 0 && c->charge != 1) return fail(nullptr, CLV_EINVAL, "charge must be 0 or 1");
   if (c->charge && c->halo_x) return fail(nullptr, CLV_EINVAL, "charge transport runs on single events, not x-slabs");
+  if (!(c->zeta_over_s >= 0) || !std::isfinite(c->zeta_over_s))
+    return fail(nullptr, CLV_EINVAL, "zeta_over_s must be finite and >= 0");
+  if (c->zeta_over_s > 0 && !(c->eta_over_s > 0))
+    return fail(nullptr, CLV_EINVAL, "bulk pressure (zeta_over_s > 0) needs eta_over_s > 0");
+  if (c->zeta_over_s > 0 && c->halo_x)
+    return fail(nullptr, CLV_EINVAL, "bulk pressure runs on single events, not x-slabs");
   if (!(c->taupi_coef >= 0) || !std::isfinite(c->lambda1_hat))
     return fail(nullptr, CLV_EINVAL, "taupi_coef must be >= 0 and lambda1_hat finite");
   long long N = (long long)c->nx * c->ny * c->neta;
@@ -307,9 +318,12 @@ size_t layout(const clv_config* c, clv_handle* h) {
   for (int q = 0; q < 10; ++q) oPI1[q] = take(fb);
   for (int s = 0; s < kNumPrimSets; ++s)
     for (int f = 0; f < kPrimFields; ++f) oPR[s][f] = take(fb);
-  size_t oNC[2] = {0, 0};
+  size_t oNC[2] = {0, 0}, oPB[2] = {0, 0};
   if (c->charge)
     for (int t = 0; t < 2; ++t) oNC[t] = take(fb);
+  const bool bulk = c->zeta_over_s > 0;
+  if (bulk)
+    for (int t = 0; t < 2; ++t) oPB[t] = take(fb);
   const int ne = c->eos_kind == CLV_EOS_TABLE ? c->eos_n : 1;
   oE[0] = take((size_t)4 * ne * rs);  // nodes packed as (P, T, c_s^2, 0)
   oE[1] = oE[2] = oE[0];
@@ -325,6 +339,7 @@ size_t layout(const clv_config* c, clv_handle* h) {
     for (int s = 0; s < kNumPrimSets; ++s)
       for (int f = 0; f < kPrimFields; ++f) h->PR[s][f] = b + oPR[s][f] + hoff;
     for (int t = 0; t < 2; ++t) h->NC[t] = c->charge ? b + oNC[t] + hoff : nullptr;
+    for (int t = 0; t < 2; ++t) h->PB[t] = bulk ? b + oPB[t] + hoff : nullptr;
     for (int t = 0; t < 3; ++t) h->eos[t] = b + oE[t];
     h->mlp = b + oMlp;
     h->staging = (double*)(b + oStage);
@@ -418,6 +433,7 @@ StageParams<R> stage_params(clv_handle* h, int stage) {
   p.fail_cell = &h->dstats->fail_cell;
   p.fail_EM = h->dstats->fail_EM;
   p.mlp = h->mlp;
+  p.Pib = nullptr;   // set by launch_half for viscous stages with bulk pressure
   return p;
 }
 
@@ -500,13 +516,21 @@ void set_tau(clv_handle* h, double tau) {
 template <typename R, bool VISC>
 void launch_half(clv_handle* h, int stage, bool stats, bool timed) {
   if (stage == 1) {
-    const StageParams<R> p1 = stage_params<R>(h, 1);
+    StageParams<R> p1 = stage_params<R>(h, 1);
+    if (VISC && h->PB[0]) {   // bulk: Pi' from Pi^n before the stage (its root solve adds Pi' to P)
+      p1.Pib = (R*)h->PB[1];
+      launch_bulk_stage<R>(p1, 1, h->PB[0], h->PB[0], h->PB[1], h->cfg.zeta_over_s, h->stream);
+    }
     launch_stage<R, VISC, 1, false>(h, p1, timed);
     // net charge: stage 1 from N^n into the stage buffer, with the stage's input velocities
     if (h->charge_on) launch_charge_stage<R>(p1, 1, h->NC[0], h->NC[0], h->NC[1], h->stream);
     return;
   }
-  const StageParams<R> p2 = stage_params<R>(h, 2);
+  StageParams<R> p2 = stage_params<R>(h, 2);
+  if (VISC && h->PB[0]) {   // bulk: Pi^{n+1} from Pi' and Pi^n, in place over Pi^n
+    p2.Pib = (R*)h->PB[0];
+    launch_bulk_stage<R>(p2, 2, h->PB[1], h->PB[0], h->PB[0], h->cfg.zeta_over_s, h->stream);
+  }
   if (stats) {
     launch_stage<R, VISC, 2, true>(h, p2, timed);
     h->stat_blocks = (int)grid_of(h->N);
@@ -763,6 +787,9 @@ template <typename R> clv_status finish_initial(clv_handle* h) {
     for (int t = 0; t < 2; ++t)
       CLV_CUDA(h, cudaMemsetAsync(h->NC[t], 0, (size_t)h->N * h->rsize, h->stream));
   }
+  if (h->PB[0])   // Pi = 0 at tau0
+    for (int t = 0; t < 2; ++t)
+      CLV_CUDA(h, cudaMemsetAsync(h->PB[t], 0, (size_t)h->N * h->rsize, h->stream));
   clv_status s = initial_begin<R>(h);
   if (s != CLV_OK || !h->viscous) return s;
   if (h->cfg.halo_x) {   // an x-slab: the caller drives the predictor with halo exchanges
@@ -795,6 +822,7 @@ clv_status export_field(clv_handle* h, int which, double* dst, long long off, lo
   else if (which <= 7) src = h->T0[which - 4];
   else if (which <= 17) src = h->PI0[which - 8];
   else if (which <= 20) src = h->PR[h->prev][1 + (which - 18)];
+  else if (which == 23) src = h->PB[0];
   else src = h->NC[0];
   export_kernel<R><<<grid_of(n), kBlock, 0, h->stream>>>((const R*)src + off, dst, n, ne, nep);
   CLV_CUDA(h, cudaGetLastError());
@@ -1067,10 +1095,11 @@ static clv_status get_fields_range(clv_handle* h, uint32_t mask, double* out, bo
                                    long long n, int ne, int nep) {
   if (!h || !out) return CLV_EINVAL;
   if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
-  if (mask >> 23) return fail(h, CLV_EINVAL, "mask selects fields beyond index 22");
-  if ((mask >> 21) && !h->cfg.charge) return fail(h, CLV_EINVAL, "fields 21 and 22 need charge = 1");
+  if (mask >> 24) return fail(h, CLV_EINVAL, "mask selects fields beyond index 23");
+  if ((mask >> 21 & 3u) && !h->cfg.charge) return fail(h, CLV_EINVAL, "fields 21 and 22 need charge = 1");
+  if ((mask >> 23 & 1u) && !h->PB[0]) return fail(h, CLV_EINVAL, "field 23 needs zeta_over_s > 0");
   size_t slot = 0;
-  for (int f = 0; f < 23; ++f) {
+  for (int f = 0; f < 24; ++f) {
     if (!(mask >> f & 1u)) continue;
     double* dst = host ? h->staging : out + slot * (size_t)n;
     clv_status s = h->rsize == 8 ? export_field<double>(h, f, dst, off, n, ne, nep)
@@ -1316,7 +1345,8 @@ constexpr uint32_t kStateMagic = 0x53564c43u;  // "CLVS"
 constexpr int kStateFields = 4 + 10 + 2 * kPrimFields;
 
 static size_t state_bytes(const clv_handle* h) {
-  return sizeof(StateHeader) + (size_t)(kStateFields + (h->cfg.charge ? 1 : 0)) * (size_t)h->N * h->rsize;
+  return sizeof(StateHeader) +
+         (size_t)(kStateFields + (h->cfg.charge ? 1 : 0) + (h->PB[0] ? 1 : 0)) * (size_t)h->N * h->rsize;
 }
 
 // device arrays of the state in checkpoint order: T~ (4), pi~ (10), the
@@ -1340,8 +1370,10 @@ clv_status clv_get_state(clv_handle* h, void* buf, size_t bytes) {
   if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
   if (bytes < state_bytes(h)) return fail(h, CLV_EINVAL, "state buffer too small (clv_state_bytes)");
   const clv_config& c = h->cfg;
-  // pad: bit 0 = the net charge is being transported (its field follows the others)
-  StateHeader hd{kStateMagic, 1u, c.nx, c.ny, c.neta, c.precision, h->viscous ? 1 : 0, h->charge_on ? 1 : 0,
+  // pad: bit 0 = the net charge is being transported (its field follows the others),
+  // bit 1 = the state carries the bulk pressure (its field comes last)
+  StateHeader hd{kStateMagic, 1u, c.nx, c.ny, c.neta, c.precision, h->viscous ? 1 : 0,
+                 (h->charge_on ? 1 : 0) | (h->PB[0] ? 2 : 0),
                  h->tau, c.dx, c.dy, c.deta, c.dtau, c.eta_over_s, h->step};
   std::memcpy(buf, &hd, sizeof(hd));
   void* a[kStateFields];
@@ -1352,6 +1384,9 @@ clv_status clv_get_state(clv_handle* h, void* buf, size_t bytes) {
     CLV_CUDA(h, cudaMemcpyAsync(dst + k * fb, a[k], fb, cudaMemcpyDeviceToHost, h->stream));
   if (c.charge)
     CLV_CUDA(h, cudaMemcpyAsync(dst + kStateFields * fb, h->NC[0], fb, cudaMemcpyDeviceToHost, h->stream));
+  if (h->PB[0])   // the bulk pressure follows (after the charge field, if any)
+    CLV_CUDA(h, cudaMemcpyAsync(dst + (kStateFields + (c.charge ? 1 : 0)) * fb, h->PB[0], fb,
+                                cudaMemcpyDeviceToHost, h->stream));
   CLV_CUDA(h, cudaStreamSynchronize(h->stream));
   return CLV_OK;
 }
@@ -1365,7 +1400,7 @@ clv_status clv_set_state(clv_handle* h, const void* buf, size_t bytes) {
   if (hd.magic != kStateMagic || hd.version != 1u) return fail(h, CLV_EINVAL, "not a checkpoint of this library");
   if (hd.nx != c.nx || hd.ny != c.ny || hd.neta != c.neta || hd.precision != c.precision ||
       hd.viscous != (h->viscous ? 1 : 0) || hd.dx != c.dx || hd.dy != c.dy || hd.deta != c.deta ||
-      hd.dtau != c.dtau || hd.eta_over_s != c.eta_over_s)
+      hd.dtau != c.dtau || hd.eta_over_s != c.eta_over_s || ((hd.pad >> 1) & 1) != (h->PB[0] ? 1 : 0))
     return fail(h, CLV_EINVAL, "checkpoint of a different configuration");
   if (bytes < state_bytes(h)) return fail(h, CLV_EINVAL, "state buffer too small (clv_state_bytes)");
   h->cur = 0;
@@ -1382,6 +1417,9 @@ clv_status clv_set_state(clv_handle* h, const void* buf, size_t bytes) {
     h->charge_on = on;
     CLV_CUDA(h, cudaMemcpyAsync(h->NC[0], src + kStateFields * fb, fb, cudaMemcpyHostToDevice, h->stream));
   }
+  if (h->PB[0])
+    CLV_CUDA(h, cudaMemcpyAsync(h->PB[0], src + (kStateFields + (c.charge ? 1 : 0)) * fb, fb, cudaMemcpyHostToDevice,
+                                h->stream));
   CLV_CUDA(h, cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream));
   set_tau(h, hd.tau);
   CLV_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1643,6 +1681,7 @@ clv_status clv_create_batch(const clv_config* cfgs, int nevents, void* cuda_stre
           std::equal(c.eos_P, c.eos_P + c.eos_n, c0.eos_P) && std::equal(c.eos_T, c.eos_T + c.eos_n, c0.eos_T) &&
           std::equal(c.eos_cs2, c.eos_cs2 + c.eos_n, c0.eos_cs2)));
     if (c.charge) return fail(nullptr, CLV_EINVAL, "charge transport runs on single events, not a batch");
+    if (c.zeta_over_s > 0) return fail(nullptr, CLV_EINVAL, "bulk pressure runs on single events, not a batch");
     if (c.tau0 != c0.tau0 || c.dtau != c0.dtau || c.precision != c0.precision || c.cartesian != c0.cartesian ||
         c.periodic != c0.periodic || c.eps_cut != c0.eps_cut || c.kernel != 0 || !same_eos)
       return fail(nullptr, CLV_EINVAL,

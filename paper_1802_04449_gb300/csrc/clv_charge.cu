@@ -48,7 +48,7 @@ __device__ __forceinline__ R charge_flux(const ChargeCell<R>& a, const ChargeCel
 
 template <typename R, int STAGE>
 __global__ void __launch_bounds__(kBlock) charge_stage_kernel(const StageParams<R> p, const R* __restrict__ Nin,
-                                                              const R* __restrict__ Nn, R* __restrict__ Nout) {
+                                                              const R* Nn, R* Nout) {   // Nn == Nout in stage 2
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= p.N) return;
   const int k = (int)(c % p.nep);

@@ -161,6 +161,10 @@ template <> struct SolveOps<double, float> {
 // P and c_s^2 at the root, from the last iteration's table lookup (at
 // e_last) moved to the final eps to first order: P + c_s^2 (eps - e_last).
 // valid = false when no iteration ran (vacuum, M = 0).
+// Pshift is added to the table's P wherever the solve uses the pressure: the
+// bulk pressure Pi, for which T^{mu nu} carries P + Pi floored at 0 (0
+// without bulk, where P >= 0 leaves the floor inactive).  On the floor dP/de
+// is 0, f(v) stays increasing and its root on [0, M/E] unique.
 template <typename C> struct EosAtRoot {
   bool valid;
   C P, cs2;
@@ -170,7 +174,7 @@ template <typename C, typename R, typename CE = C, bool FIXED = false>
 __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps_cut, C E, C Mx,
                                                       C My, C Me, C tol, int maxit, C& eps,
                                                       C& ux, C& uy, C& ue, C* vguess = nullptr,
-                                                      EosAtRoot<C>* at_root = nullptr) {
+                                                      EosAtRoot<C>* at_root = nullptr, C Pshift = C(0)) {
   if (at_root) at_root->valid = false;
   using Ops = SolveOps<C, CE>;
   RootResult rr{0, 0};
@@ -191,7 +195,7 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
     return rr;
   }
   C lo = C(0), hi = Ops::div(M, E);
-  C P, cs2;
+  C P, cs2, dPde;   // dPde: d(P + Pshift)/d eps, 0 on the floor (cs2 keeps the table's value)
   C v;
   bool fixed = FIXED;
   if (vguess && *vguess > lo && *vguess < hi) {
@@ -200,7 +204,8 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
     if (FIXED) { fixed = false; maxit = 100; }  // no usable start: solve in full
     CE Pe, Te, ce;
     eos_eval<CE, R>(q, CE(E), Pe, Te, ce);
-    P = C(Pe);
+    P = C(Pe) + Pshift;
+    if (P < C(0)) P = C(0);
     v = Ops::div(M, E + P);
   }
   int it = 1;
@@ -212,8 +217,10 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
     {
       CE Pe, Te, ce;
       eos_eval<CE, R>(q, CE(e), Pe, Te, ce);
-      P = C(Pe);
+      P = C(Pe) + Pshift;
       cs2 = C(ce);
+      dPde = cs2;
+      if (P < C(0)) { P = C(0); dPde = C(0); }
     }
     // Newton step on f(v) = v - M/den, den = E + P: with g = v den - M
     // (the sign of f, den > 0) the step -f/f' is -den g / (den^2 - c_s^2 M^2),
@@ -221,7 +228,7 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
     const C den = E + P;
     const C g = v * den - M;
     if (g > C(0)) hi = v; else lo = v;
-    const C dv = -Ops::div(den * g, den * den - cs2 * (M * M));
+    const C dv = -Ops::div(den * g, den * den - dPde * (M * M));
     // converged when the Newton step is below tol; otherwise keep the iterate
     // strictly inside the shrinking bracket
     if (fabs(dv) <= tol) { v += dv; ok = true; break; }
@@ -238,7 +245,7 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
   eps = e;
   if (at_root) {
     at_root->valid = true;
-    at_root->P = P + cs2 * (e - e_last);
+    at_root->P = P + dPde * (e - e_last);
     at_root->cs2 = cs2;
   }
   C gam = Ops::rsqrt_(C(1) - v * v);

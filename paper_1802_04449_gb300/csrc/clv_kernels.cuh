@@ -71,6 +71,10 @@ template <typename R> struct StageParams {
   unsigned long long* fail_cell; // first failing cell + 1 (0: none)
   double* fail_EM;               // E and |M| of that cell
   const void* mlp;               // tensor-core copy of the guess network (BF16 W1|W2|W3, FP32 biases)
+  // bulk pressure Pi of the stage's output (written before the stage by the
+  // bulk kernel; the recovery solves with P + Pi, stores P + Pi as the cell's
+  // pressure and sets Pi = 0 in vacuum cells); nullptr without bulk
+  R* Pib;
 };
 
 enum GuessMode { kGuessPrevious = 0, kGuessCold = 1, kGuessMlp = 2 };
@@ -170,15 +174,15 @@ constexpr double kViscEpsMin = 1e-3;   // GeV/fm^3
 constexpr int kPolishSteps = 2;
 template <typename R>
 __device__ __forceinline__ int polish_root(const StageParams<R>& p, R E, R Mx, R My, R Me, R v32, bool converged,
-                                           R& en, R& ux, R& uy, R& ue) {
+                                           R& en, R& ux, R& uy, R& ue, R Pb) {
   double dv = converged ? (double)v32 : -1.0, de, dux, duy, due;
   RootResult r2;
   if (converged)
     r2 = solve_primitive<double, R, float, true>(p.eos, p.eps_cut_d, (double)E, (double)Mx, (double)My, (double)Me,
-                                                 1e-13, kPolishSteps, de, dux, duy, due, &dv);
+                                                 1e-13, kPolishSteps, de, dux, duy, due, &dv, nullptr, (double)Pb);
   else
     r2 = solve_primitive<double, R, float>(p.eos, p.eps_cut_d, (double)E, (double)Mx, (double)My, (double)Me, 1e-13,
-                                           100, de, dux, duy, due, &dv);
+                                           100, de, dux, duy, due, &dv, nullptr, (double)Pb);
   en = R(de); ux = R(dux); uy = R(duy); ue = R(due);
   return r2.iters;
 }
@@ -354,7 +358,8 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
     }
     // ---------------- own-cell state ----------------
     const R e = p.pr.e[c];
-    const R Pc = p.pr.P[c];
+    const R Pc = p.pr.P[c];   // the pressure of T^{mu nu}: P(eps) + Pi
+    R Pe = Pc;                // the EOS pressure P(eps) (shear source and regulator)
     R u[4];
     u[1] = p.pr.u[0][c]; u[2] = p.pr.u[1][c]; u[3] = p.pr.u[2][c];
     u[0] = sqrt(R(1) + u[1] * u[1] + u[2] * u[2] + u[3] * u[3]);
@@ -402,11 +407,11 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
 #pragma unroll
         for (int b = 0; b < 4; ++b) du[a][b] = (unb[a - 1][1][b] - unb[a - 1][0][b]) * half_inv;
       }
-      R Pdummy, Tc, c2dummy;
-      eos_eval<R, R>(p.eos, e, Pdummy, Tc, c2dummy);
+      R Tc, c2dummy;
+      eos_eval<R, R>(p.eos, e, Pe, Tc, c2dummy);
       const R inv_taupi = Tc * p.is.inv_b_etas_hbarc;
       R Spi[10];
-      shear_source<R>(ts.geo, u, du, pic, e, Pc, inv_taupi, p.is, Spi);
+      shear_source<R>(ts.geo, u, du, pic, e, Pe, inv_taupi, p.is, Spi);
 #pragma unroll
       for (int q = 0; q < 10; ++q) S[4 + q] += Spi[q];
     }
@@ -420,7 +425,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
         const R inv = R(1) / ustar0;
 #pragma unroll
         for (int q = 0; q < 10; ++q) pinew[q] = (un[0] * pic[q] + h * S[4 + q]) * inv;
-        regulate_shear<R>(e, Pc, pinew);
+        regulate_shear<R>(e, Pe, pinew);
       }
     } else {
 #pragma unroll
@@ -429,7 +434,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
         const R inv = R(0.5) / u[0];
 #pragma unroll
         for (int q = 0; q < 10; ++q) pinew[q] = (un[0] * p.pin[q][c] + ustar0 * pic[q] + h * S[4 + q]) * inv;
-        regulate_shear<R>(e, Pc, pinew);
+        regulate_shear<R>(e, Pe, pinew);
       }
     }
     // ---------------- primitive recovery from T_ideal = T - pi ----------------
@@ -439,12 +444,13 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       E -= pinew[0]; Mx -= pinew[1]; My -= pinew[2]; Me -= pinew[3];
     }
     R en = R(0), ux = R(0), uy = R(0), ue = R(0);
+    R Pb = p.Pib ? p.Pib[c] : R(0);   // bulk pressure of the stage's output
     if (!(isfinite(E) && isfinite(Mx) && isfinite(My) && isfinite(Me))) {
       f_nonfinite = true;
     } else {
       R vg = R(-1);
       RootResult rr = solve_primitive<R, R>(p.eos, p.eps_cut, E, Mx, My, Me, SolveTraits<R>::tol,
-                                            SolveTraits<R>::maxit, en, ux, uy, ue, &vg);
+                                            SolveTraits<R>::maxit, en, ux, uy, ue, &vg, nullptr, Pb);
       f_rescaled = rr.rescaled;
       if constexpr (sizeof(R) == 4) {
         // FP64 Newton near the vacuum, at high velocity, and wherever the
@@ -453,7 +459,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
         f_nonconv = rr.iters < 0;
         const bool near_cut = en < p.polish_E;
         if (E >= p.eps_cut && M > R(0) && (near_cut || M > p.polish_v * E || rr.iters < 0)) {
-          rr.iters = polish_root<R>(p, E, Mx, My, Me, vg, rr.iters >= 0, en, ux, uy, ue);
+          rr.iters = polish_root<R>(p, E, Mx, My, Me, vg, rr.iters >= 0, en, ux, uy, ue, Pb);
           f_polished = true;
         }
       }
@@ -471,7 +477,10 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       const bool vac = !(en > R(0));
 #pragma unroll
       for (int q = 0; q < 10; ++q) p.piout[q][c] = vac ? R(0) : pinew[q];
+      if (p.Pib && vac) { Pb = R(0); p.Pib[c] = R(0); }
     }
+    Pn += Pb;
+    if (Pn < R(0)) Pn = R(0);   // the pressure of T^{mu nu}, floored at 0
     p.prout.e[c] = en;
     p.prout.u[0][c] = ux;
     p.prout.u[1][c] = uy;
@@ -582,12 +591,13 @@ __global__ void __launch_bounds__(kBlock, RecoverMinBlocks<R>::value) recover_ke
   }
   if (active) {
     R en = R(0), ux = R(0), uy = R(0), ue = R(0);
+    R Pb = p.Pib ? p.Pib[c] : R(0);   // bulk pressure of the stage's output
     EosAtRoot<R> at_root{false, R(0), R(0)};
     if (!(isfinite(E) && isfinite(Mx) && isfinite(My) && isfinite(Me))) {
       f_nonfinite = true;
     } else {
       RootResult rr = solve_primitive<R, R>(p.eos, p.eps_cut, E, Mx, My, Me, SolveTraits<R>::tol,
-                                            SolveTraits<R>::maxit, en, ux, uy, ue, &vg, &at_root);
+                                            SolveTraits<R>::maxit, en, ux, uy, ue, &vg, &at_root, Pb);
       f_rescaled = rr.rescaled;
       my_iters = rr.iters > 0 ? rr.iters : 0;
       my_solved = rr.iters > 0 ? 1 : 0;
@@ -601,7 +611,7 @@ __global__ void __launch_bounds__(kBlock, RecoverMinBlocks<R>::value) recover_ke
         f_nonconv = rr.iters < 0;
         const bool near_cut = en < p.polish_E;
         if (E >= p.eps_cut && M > R(0) && (near_cut || M > p.polish_v * E || rr.iters < 0)) {
-          rr.iters = polish_root<R>(p, E, Mx, My, Me, vg, rr.iters >= 0, en, ux, uy, ue);
+          rr.iters = polish_root<R>(p, E, Mx, My, Me, vg, rr.iters >= 0, en, ux, uy, ue, Pb);
           my_polish_iters = rr.iters > 0 ? rr.iters : 0;
           f_polished = true;
           at_root.valid = false;   // the refined root: evaluate the table afresh
@@ -614,14 +624,18 @@ __global__ void __launch_bounds__(kBlock, RecoverMinBlocks<R>::value) recover_ke
       }
     }
     R Pn, c2n;
+    if (p.Pib && !(en > R(0))) { Pb = R(0); p.Pib[c] = R(0); }   // vacuum: no bulk pressure
     if (at_root.valid && en > R(0)) {
       // the last Newton iteration looked the table up within the tolerance of
-      // the root: move its P to the root to first order instead of a new lookup
+      // the root: move its P (P + Pi with bulk) to the root to first order
+      // instead of a new lookup
       Pn = at_root.P;
       c2n = at_root.cs2;
     } else {
       R Tn_;
       eos_eval<R, R>(p.eos, en, Pn, Tn_, c2n);
+      Pn += Pb;
+      if (Pn < R(0)) Pn = R(0);   // the pressure of T^{mu nu}, floored at 0
     }
     p.prout.e[c] = en;
     p.prout.u[0][c] = ux;

@@ -344,7 +344,8 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
 #pragma unroll
             for (int q = 0; q < NQ; ++q) S[q] = pd[q * ncell + cid] - (H[q] - Hprev[q]) * inv_dx;
             const R e = cb[CI::E * ncell];
-            const R Pc = W0[L::P];
+            const R Pc = W0[L::P];   // the pressure of T^{mu nu}: P(eps) + Pi
+            R Pe = Pc;               // the EOS pressure P(eps) (shear source and regulator)
             R u[4];
             u[0] = W0[L::UT];
             u[1] = mul_rn(u[0], W0[L::V]);
@@ -392,13 +393,13 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
                 du[2][b2] = pd[(NQ + b2) * ncell + cid];
                 du[3][b2] = pd[(NQ + 4 + b2) * ncell + cid];
               }
-              R Pd, Tc, c2d;
-              eos_eval<R, R>(p.eos, e, Pd, Tc, c2d);
+              R Tc, c2d;
+              eos_eval<R, R>(p.eos, e, Pe, Tc, c2d);
               const R inv_taupi = Tc * ev.is.inv_b_etas_hbarc;
               R pic[10], Spi[10];
 #pragma unroll
               for (int r = 0; r < 10; ++r) pic[r] = W0[4 + r];
-              shear_source<R>(ts.geo, u, du, pic, e, Pc, inv_taupi, ev.is, Spi);
+              shear_source<R>(ts.geo, u, du, pic, e, Pe, inv_taupi, ev.is, Spi);
 #pragma unroll
               for (int r = 0; r < 10; ++r) S[4 + r] += Spi[r];
             }
@@ -412,7 +413,7 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
                 const R inv = R(1) / ustar0;
 #pragma unroll
                 for (int r = 0; r < 10; ++r) pinew[r] = (un[0] * W0[4 + r] + hh * S[4 + r]) * inv;
-                regulate_shear<R>(e, Pc, pinew);
+                regulate_shear<R>(e, Pe, pinew);
               }
             } else {
 #pragma unroll
@@ -422,7 +423,7 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
 #pragma unroll
                 for (int r = 0; r < 10; ++r)
                   pinew[r] = (un[0] * cb[(CI::PIN + r) * ncell] + ustar0 * W0[4 + r] + hh * S[4 + r]) * inv;
-                regulate_shear<R>(e, Pc, pinew);
+                regulate_shear<R>(e, Pe, pinew);
               }
             }
             // conserved quantities of the stage; the primitive recovery runs in

@@ -145,3 +145,25 @@ def test_charge_host_checks(lib):
     c2, _ = clv.make_config(33, 31, 21, 0.2, 0.2, 0.2, 0.4, 0.01, 0.08, halo_x=2, charge=True)
     assert so.clv_workspace_bytes(ctypes.byref(c2), ctypes.byref(n0)) == 1
     assert "x-slab" in so.clv_last_error(None).decode()
+
+
+def test_bulk_host_checks(lib):
+    """zeta_over_s > 0 adds two fields to the workspace; it needs eta_over_s > 0,
+    a finite non-negative ratio and a single event (no batch, no x-slab)."""
+    so = clv.load()
+    n0, n1 = ctypes.c_size_t(), ctypes.c_size_t()
+    c0, _ = clv.make_config(33, 31, 21, 0.2, 0.2, 0.2, 0.4, 0.01, 0.08, precision=clv.CLV_FP32)
+    c1, _ = clv.make_config(33, 31, 21, 0.2, 0.2, 0.2, 0.4, 0.01, 0.08, precision=clv.CLV_FP32, zeta_over_s=0.05)
+    assert so.clv_workspace_bytes(ctypes.byref(c0), ctypes.byref(n0)) == 0
+    assert so.clv_workspace_bytes(ctypes.byref(c1), ctypes.byref(n1)) == 0
+    assert n1.value - n0.value >= 2 * 33 * 31 * 24 * 4
+    for kw, word in [({"eta_over_s": 0.0}, "eta_over_s"), ({"zeta_over_s": -0.1}, "zeta_over_s"),
+                     ({"zeta_over_s": float("nan")}, "zeta_over_s"), ({"halo_x": 2}, "x-slab")]:
+        args = {"eta_over_s": 0.08, "zeta_over_s": 0.05, **kw}
+        c, _ = clv.make_config(33, 31, 21, 0.2, 0.2, 0.2, 0.4, 0.01, **args)
+        assert so.clv_workspace_bytes(ctypes.byref(c), ctypes.byref(n0)) == 1, kw
+        assert word in so.clv_last_error(None).decode(), kw
+    cfgs = (clv.clv_config * 1)(c1)
+    h = ctypes.c_void_p()
+    assert so.clv_create_batch(cfgs, 1, None, ctypes.byref(h)) == 1
+    assert "batch" in so.clv_last_error(None).decode()
