@@ -172,6 +172,8 @@ constexpr double kViscEpsMin = 1e-3;   // GeV/fm^3
 // nothing); an unconverged one gets a full bracketed FP64 solve.  Returns the
 // iterations taken, -1 if the full solve hit its cap.
 constexpr int kPolishSteps = 2;
+// Below this fraction of eps_cut an FP32 eps is vacuum for certain (no refinement).
+constexpr double kVacuumSure = 0.999;
 template <typename R>
 __device__ __forceinline__ int polish_root(const StageParams<R>& p, R E, R Mx, R My, R Me, R v32, bool converged,
                                            R& en, R& ux, R& uy, R& ue, R Pb) {
@@ -454,10 +456,11 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       f_rescaled = rr.rescaled;
       if constexpr (sizeof(R) == 4) {
         // FP64 Newton near the vacuum, at high velocity, and wherever the
-        // FP32 solve did not converge
+        // FP32 solve did not converge (near_cut: see recover_kernel)
         const R M = sqrt(Mx * Mx + My * My + Me * Me);
         f_nonconv = rr.iters < 0;
-        const bool near_cut = en < p.polish_E;
+        const R eraw = E - M * vg;   // the FP32 eps before the vacuum decision
+        const bool near_cut = eraw < p.polish_E && eraw > R(kVacuumSure) * p.eps_cut;
         if (E >= p.eps_cut && M > R(0) && (near_cut || M > p.polish_v * E || rr.iters < 0)) {
           rr.iters = polish_root<R>(p, E, Mx, My, Me, vg, rr.iters >= 0, en, ux, uy, ue, Pb);
           f_polished = true;
@@ -609,7 +612,13 @@ __global__ void __launch_bounds__(kBlock, RecoverMinBlocks<R>::value) recover_ke
         // tail outweighing the divergence it removes)
         const R M = sqrt(Mx * Mx + My * My + Me * Me);
         f_nonconv = rr.iters < 0;
-        const bool near_cut = en < p.polish_E;
+        // near the cut: the FP32 eps = E - M v before the vacuum decision lies
+        // in [kVacuumSure, polish_E/eps_cut) x eps_cut.  With M <= polish_v E
+        // (faster cells are refined anyway) its relative error is below 3e-5,
+        // so under kVacuumSure eps_cut the cell is vacuum in FP64 too and the
+        // refinement could not change it (eps = 0, u = 0)
+        const R eraw = E - M * vg;
+        const bool near_cut = eraw < p.polish_E && eraw > R(kVacuumSure) * p.eps_cut;
         if (E >= p.eps_cut && M > R(0) && (near_cut || M > p.polish_v * E || rr.iters < 0)) {
           rr.iters = polish_root<R>(p, E, Mx, My, Me, vg, rr.iters >= 0, en, ux, uy, ue, Pb);
           my_polish_iters = rr.iters > 0 ? rr.iters : 0;
