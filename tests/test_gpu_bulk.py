@@ -63,6 +63,23 @@ def test_hotspot_bulk_fp32():
     g.close()
 
 
+def test_hotspot_bulk_fp32_learned_guess():
+    """The learned guess seeds the shifted root solve (the network sees no Pi;
+    an untrained one only changes the starting point): same bars as above."""
+    from paper_1802_04449_gb300 import learned as L
+    case = I.hotspot_event(nx=21, ny=19, neta=11, n_spots=30, seed=11, eta_over_s=0.08)
+    o, g = _pair(case, 0, clv.CLV_FP32, 0.1)
+    g.set_mlp(L.init_params(0))
+    g.set_guess(clv.CLV_GUESS_MLP)
+    o.step(20)
+    st = g.step(20, stats=True)
+    assert st["error_word"] == 0 and st["n_rootfail"] == 0
+    assert fp32_eps_err(o, g) <= 1e-4
+    ref, got = o.get("Pi"), g.get(["Pi"])["Pi"]
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max()
+    g.close()
+
+
 def test_bjorken_bulk_on_the_gpu():
     """Uniform Bjorken flow with shear and bulk: the GPU equals the oracle (and
     both follow the three-ODE solution the oracle is pinned to)."""
