@@ -199,8 +199,8 @@ clv_status clv_get_time(const clv_handle* h, double* tau, int64_t* step);
  * kernel, 3 stage-2 recovery kernel (1 and 3 stay 0 with kernel = 1, whose
  * stage kernel includes the recovery).  With zeta_over_s > 0 the bulk kernel
  * of a stage is counted in that stage's stage-kernel slot; with charge = 1 the
- * charge kernel of stage 1 falls in slot 2 and that of stage 2 in the next
- * step's slot 0. */
+ * charge kernel of stage 1 falls in slot 2, and that of stage 2, like the tau
+ * advance, in none. */
 clv_status clv_enable_kernel_timing(clv_handle* h, int enable);
 clv_status clv_get_kernel_times(clv_handle* h, double ms[4], int64_t launches[4]);
 
