@@ -61,6 +61,7 @@ FO_BYTES_PER_ELEMENT = 22 * 4 + 8 + 2 * 13 * 4
 # exponent 2, exp2 1, f 2, p p pi 10, (1 - s f) q + 1 4, product and sum 3 -> 30
 CF_FLOPS_PER_PAIR = 33.75
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+HBM_NOMINAL_GBS = 7900.0   # GB300 HBM3e, nominal (context beside the measured copy peak)
 KERNEL_NAMES = {"stage1": "stage_tile_kernel<float,1,viscous>", "recover1": "recover_kernel<float,viscous>",
                 "stage2": "stage_tile_kernel<float,2,viscous>", "recover2": "recover_kernel<float,viscous>"}
 
@@ -294,6 +295,7 @@ def run_gpu(args):
     achieved = alg / (avg_ms[dom] / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved,
             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "nominal_peak": HBM_NOMINAL_GBS, "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
             "traffic": load_traffic(dom, st32.get("tile") if dom.startswith("stage") else None),
             "algorithmic_bytes_per_launch": alg,
             "kernel_ms_avg": avg_ms,
