@@ -38,7 +38,8 @@
  *       derivative: (u_late - u^n)/h, u_late = u* in stage 1, u' in stage 2.
  *   R8  First step: u^{-1} := 2u^0 - u^1_ideal, where u^1_ideal comes from one
  *       pi-free Heun step, so that u* = u^1_ideal.
- *   R9  lambda_1..3 = 0; bulk and net-baryon parts off (the paper sets them to 0).
+ *   R9  lambda_1..3 = 0; bulk and net-baryon parts off unless asked for (the
+ *       paper sets them to 0; R19, R20).
  *   R10 tau_pi = 5 eta_v/(eps + P) = 5 (eta/s) hbar c / T.
  *   R11 Conformal EOS: P = eps/3, eps = 3 g pi^2 T^4 / (90 (hbar c)^3), g = 47.5.
  *   R12 Tabulated EOS: nodes uniform in ln eps; P, T, c_s^2 linear in ln eps;
@@ -54,6 +55,22 @@
  *       - (2/3) Delta^{mu nu} theta with finite-difference gradients.
  *   R17 Boundaries: two ghost cells per side, copies of the edge cell
  *       (zero gradient) or periodic wrap.
+ *   R18 Shear regulator (the paper is silent; without one the dilute,
+ *       ultra-relativistic edge of a viscous event runs away): after each
+ *       stage update and before the root solve, with eps and P of the
+ *       stage's input state of the cell,
+ *         - pi~ = 0 where that eps < 1e-3 GeV/fm^3 (ideal flow far below
+ *           freeze-out densities);
+ *         - otherwise pi~ is scaled by rho_max / rho wherever
+ *           rho = sqrt(|pi~_{mu nu} pi~^{mu nu}|) / sqrt(eps^2 + 3 P^2)
+ *           exceeds rho_max = 1.
+ *   R19 Net charge (Eq. Ntilde with S_N = 0; the paper sets n = 0, so this
+ *       is off unless an initial n is given): N~^tau = tau n u^tau (1 in
+ *       place of tau in Cartesian mode) is conserved with the flux
+ *       v^a N~^tau along each axis, through the same limited reconstruction
+ *       of N~^tau and v^a and the same local speed as the other fields;
+ *       the diffusion current d^mu is 0 (ideal charge transport).  Vacuum
+ *       cells keep their charge.  n = N~^tau / (tau u^tau).
  *   R20 Bulk pressure (Eqs. Pi, Pitilde; the paper sets zeta = 0, so this is
  *       off unless zeta/s > 0, and runs with the shear machinery, eta/s > 0):
  *       Q_Pi = u~^tau Pi is carried with the flux v^a Q_Pi (the same limited
@@ -74,22 +91,6 @@
  *       the floor (and d(P + Pi)/d eps = 0 on it) f is increasing and its
  *       root unique.  A negative total pressure is outside the validity of
  *       the second-order equations anyway.
- *   R19 Net charge (Eq. Ntilde with S_N = 0; the paper sets n = 0, so this
- *       is off unless an initial n is given): N~^tau = tau n u^tau (1 in
- *       place of tau in Cartesian mode) is conserved with the flux
- *       v^a N~^tau along each axis, through the same limited reconstruction
- *       of N~^tau and v^a and the same local speed as the other fields;
- *       the diffusion current d^mu is 0 (ideal charge transport).  Vacuum
- *       cells keep their charge.  n = N~^tau / (tau u^tau).
- *   R18 Shear regulator (the paper is silent; without one the dilute,
- *       ultra-relativistic edge of a viscous event runs away): after each
- *       stage update and before the root solve, with eps and P of the
- *       stage's input state of the cell,
- *         - pi~ = 0 where that eps < 1e-3 GeV/fm^3 (ideal flow far below
- *           freeze-out densities);
- *         - otherwise pi~ is scaled by rho_max / rho wherever
- *           rho = sqrt(|pi~_{mu nu} pi~^{mu nu}|) / sqrt(eps^2 + 3 P^2)
- *           exceeds rho_max = 1.
  *
  * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC.
  * Parity: bit-level determinism across thread counts (each cell is computed
