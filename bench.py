@@ -429,6 +429,7 @@ def run_gpu(args):
                 bt.set_mlp(params)
                 bt.set_guess(clv.CLV_GUESS_MLP)
             bt.step(warmup)
+            tuned = bt.autotune(max_candidates=8, reps=2)   # tiling policy of the batch (untimed setup)
             torch.cuda.synchronize()
             bt.enable_kernel_timing(True)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -445,12 +446,12 @@ def run_gpu(args):
             except clv.ClvError as ex:
                 st = {"error": str(ex)}
             bt.close()
-            return e0.elapsed_time(e1), kt, st
+            return e0.elapsed_time(e1), kt, st, tuned
 
         sB = max(3, args.steps // 8)
-        msB, ktB, stB = timed_batch(clv.CLV_FP32, sB, 2, params_host)
+        msB, ktB, stB, tunedB = timed_batch(clv.CLV_FP32, sB, 2, params_host)
         sB64 = max(2, sB // 10)
-        msB64, _, stB64 = timed_batch(clv.CLV_FP64, sB64, 1)
+        msB64, _, stB64, tunedB64 = timed_batch(clv.CLV_FP64, sB64, 1)
         tb = torch.tensor([msB, msB64], dtype=torch.float64, device=dev)
         if ws > 1:
             dist.all_reduce(tb, op=dist.ReduceOp.MAX)
@@ -465,6 +466,12 @@ def run_gpu(args):
                  "events": len(evs), "cells": NB, "steps": sB, "value": valB, "unit": UNIT,
                  "ms_per_step": msB_max / sB, "launch": "one persistent stage launch per stage (a CTA per SM, "
                                                           "work items most expensive first) + one root-solve launch",
+                 "schedule": {"fp32": {"max_threads": tunedB["TJ"], "chunk_planes": tunedB["CX"],
+                                       "stage1_ms": tunedB["ms"]},
+                              "fp64": {"max_threads": tunedB64["TJ"], "chunk_planes": tunedB64["CX"],
+                                       "stage1_ms": tunedB64["ms"]},
+                              "how": "clv_autotune on the started batch: thread cap x x-chunk policies, "
+                                     "stage-1 launches timed, untimed setup"},
                  "fp64": {"value": ws * NB * sB64 / (msB64_max / 1e3), "steps": sB64,
                           "ms_per_step": msB64_max / sB64},
                  "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[domB].replace("stage_tile_kernel",

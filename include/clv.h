@@ -264,9 +264,18 @@ clv_status clv_mlp_train(float* d_params, float* d_work, const float* d_X, const
  * (kernel 0); they may differ in nx, ny, neta, dx, dy, deta and eta/s.
  * clv_step, the guess calls, clv_get_stats (E_tot = 0: per event below),
  * clv_get_state / clv_set_state and clv_get_fields (all events back to back)
- * take a batch handle; clv_set_initial(_T), clv_set_tile and clv_autotune do
- * not (CLV_EINVAL).  The batch starts (first-step predictor) at the first
- * clv_step, after every event's initial state was set. */
+ * take a batch handle; clv_set_initial(_T) and clv_set_tile do not
+ * (CLV_EINVAL).  The batch starts (first-step predictor) at the first
+ * clv_step, after every event's initial state was set.
+ * Each event's tile follows a tiling policy shared by the batch: at most
+ * max_threads threads per CTA (TJ as large as that allows, TK from neta, at
+ * most 32 columns) and x chunks of about `chunk` planes; the default is 256
+ * (128 in FP64) threads and 32 planes.  clv_autotune on a started batch
+ * times the current policy and up to max_candidates others (thread caps of
+ * 1, 3/4 and 1/2 of the limit, chunks of 16-64 planes; reps stage-1 launches
+ * each, which leave the state unchanged), keeps the fastest (the current
+ * unless another is at least 2% faster) and reports it in clv_tile_info as
+ * TJ = max_threads, TK = 0, CX = chunk.  The policy changes no result. */
 clv_status clv_create_batch(const clv_config* cfgs, int nevents, void* cuda_stream, clv_handle** out);
 
 /* Number of events and total cells of a batch (0 events for a single event). */
@@ -283,6 +292,12 @@ clv_status clv_batch_get_fields(clv_handle* h, int event, uint32_t which_mask, d
 /* eps_max, T_max and E_tot of one event (the counters are the batch's).
  * Synchronises the stream. */
 clv_status clv_batch_event_stats(clv_handle* h, int event, clv_stats* out);
+
+/* Explicit tiling policy of a batch (see above): max_threads in [32, 256]
+ * (capped at 128 in FP64), chunk in [1, 4096] planes.  CLV_EINVAL if out of
+ * range, not a batch, or if a tile would exceed the shared memory of a CTA.
+ * Synchronises the stream. */
+clv_status clv_batch_set_schedule(clv_handle* h, int max_threads, int chunk);
 
 /* ---------------- x-slab of a larger grid (halo_x = 2) ----------------
  * One event split into slabs along x (one per GPU): each handle owns nx

@@ -119,7 +119,7 @@ EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initi
             "clv_slab_unpack", "clv_slab_fill_edge", "clv_slab_predictor", "clv_stage",
             "clv_fo_scratch_bytes", "clv_fo_find", "clv_fo_grid_of", "clv_fo_current", "clv_fo_slice_bytes",
             "clv_fo_snapshot", "clv_cf_scratch_bytes", "clv_cf_spectra", "clv_set_initial_n",
-            "clv_set_initial_n_device"]
+            "clv_set_initial_n_device", "clv_batch_set_schedule"]
 CLV_GUESS_PREVIOUS, CLV_GUESS_COLD, CLV_GUESS_MLP = 0, 1, 2
 MLP_NPARAM = 5124
 
@@ -175,6 +175,7 @@ def load(path: str | None = None):
         lib.clv_batch_set_initial.argtypes = [P, ctypes.c_int, D, D, D, D, D]
         lib.clv_batch_get_fields.argtypes = [P, ctypes.c_int, ctypes.c_uint32, D]
         lib.clv_batch_event_stats.argtypes = [P, ctypes.c_int, ctypes.POINTER(clv_stats)]
+        lib.clv_batch_set_schedule.argtypes = [P, ctypes.c_int, ctypes.c_int]
         lib.clv_state_bytes.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
         lib.clv_get_state.argtypes = [P, V, ctypes.c_size_t]
         lib.clv_set_state.argtypes = [P, V, ctypes.c_size_t]
@@ -722,6 +723,10 @@ class Batch(Hydro):
         s = clv_stats()
         self._check(self._lib.clv_batch_event_stats(self._h, int(e), ctypes.byref(s)), self._h)
         return s.as_dict()
+
+    def set_schedule(self, max_threads, chunk):
+        """Tiling policy of the batch: thread cap per CTA, planes per x chunk."""
+        self._check(self._lib.clv_batch_set_schedule(self._h, int(max_threads), int(chunk)), self._h)
 
 
 def mlp_loss_grad(params, X, Y, stream=None):

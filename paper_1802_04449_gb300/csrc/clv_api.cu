@@ -127,6 +127,7 @@ struct clv_handle {
   int batch_nitems = 0, batch_threads = 0;
   unsigned batch_blocks = 0;
   size_t batch_smem = 0;
+  int batch_maxthr = 0, batch_chunk = 0;   // tiling policy of the batch (thread cap per CTA, x chunk)
 };
 
 namespace {
@@ -1290,6 +1291,16 @@ clv_status clv_mlp_train(float* d_params, float* d_work, const float* d_X, const
 }  // extern "C"
 
 static void tile_info(const clv_handle* h, double ms, clv_tile_info* out) {
+  if (!h->batch.empty()) {   // a batch: its tiling policy (thread cap, x chunk) and launch shape
+    out->TJ = h->batch_maxthr;
+    out->TK = 0;
+    out->CX = h->batch_chunk;
+    out->threads = h->batch_threads;
+    out->blocks = (int)h->batch_blocks;
+    out->smem_bytes = (int)h->batch_smem;
+    out->ms = ms;
+    return;
+  }
   out->TJ = h->tile.TJ;
   out->TK = h->tile.TK;
   out->CX = h->tile.CX;
@@ -1315,6 +1326,28 @@ static cudaError_t apply_tile(clv_handle* h, const TileGeom& g) {
 // Mean time of `reps` stage-1 tile launches on the current state (stage 1
 // reads the state and writes only the stage buffers, so repeating it leaves
 // the evolution unchanged).
+static cudaError_t batch_schedule(clv_handle* h, int maxthr, int chunk, int sms, size_t smem_max);
+
+template <typename R, bool VISC>
+static cudaError_t time_stage1_batch(clv_handle* h, int reps, cudaEvent_t e0, cudaEvent_t e1, double* ms) {
+  const StageParams<R> p = stage_params<R>(h, 1);
+  auto launch = [&]() {
+    cudaMemsetAsync(h->batch_ctr, 0, sizeof(int), h->stream);
+    stage_batch_kernel<R, 1, VISC><<<h->batch_blocks, h->batch_threads, h->batch_smem, h->stream>>>(
+        p, (const EventGeom<R>*)h->batch_geom, h->batch_tiles, h->batch_items, h->batch_nitems, h->batch_ctr);
+  };
+  launch();
+  cudaEventRecord(e0, h->stream);
+  for (int r = 0; r < reps; ++r) launch();
+  cudaEventRecord(e1, h->stream);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  *ms = (double)t / reps;
+  return e;
+}
+
 template <typename R, bool VISC>
 static cudaError_t time_stage1(clv_handle* h, int reps, cudaEvent_t e0, cudaEvent_t e1, double* ms) {
   const StageParams<R> p = stage_params<R>(h, 1);
@@ -1576,9 +1609,51 @@ clv_status clv_set_tile(clv_handle* h, int TJ, int TK, int CX) {
   return CLV_OK;
 }
 
+static clv_status autotune_batch(clv_handle* h, int max_candidates, int reps, clv_tile_info* best) {
+  if (!h->initialized) return fail(h, CLV_EINVAL, "the batch is initialised by its first clv_step; autotune after it");
+  size_t smem_max = 0;
+  const int sms = device_sms(&smem_max);
+  // candidate policies: thread cap per CTA x planes per x chunk, the current first
+  const int tmax = h->rsize == 8 ? std::min(CLV_TILE_MAX_THREADS, kBlock / 2) : CLV_TILE_MAX_THREADS;
+  std::vector<std::pair<int, int>> cand = {{h->batch_maxthr, h->batch_chunk}};
+  for (int thr : {tmax, tmax * 3 / 4, tmax / 2})
+    for (int chunk : {32, 16, 24, 48, 64})
+      if (std::make_pair(thr, chunk) != cand[0] && (int)cand.size() <= max_candidates) cand.push_back({thr, chunk});
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CLV_CUDA(h, cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(h, CLV_ECUDA, "cudaEventCreate"); }
+  double best_ms = 1e300, cur_ms = 1e300;
+  size_t best_i = 0;
+  cudaError_t err = cudaSuccess;
+  for (size_t i = 0; i < cand.size() && err == cudaSuccess; ++i) {
+    cudaError_t es = batch_schedule(h, cand[i].first, cand[i].second, sms, smem_max);
+    if (es == cudaErrorInvalidValue) continue;   // beyond the shared memory of a CTA: not a candidate
+    err = es;
+    double ms = 0.0;
+    if (err == cudaSuccess) {
+      if (h->rsize == 8)
+        err = h->viscous ? time_stage1_batch<double, true>(h, reps, e0, e1, &ms)
+                         : time_stage1_batch<double, false>(h, reps, e0, e1, &ms);
+      else
+        err = h->viscous ? time_stage1_batch<float, true>(h, reps, e0, e1, &ms)
+                         : time_stage1_batch<float, false>(h, reps, e0, e1, &ms);
+    }
+    if (err == cudaSuccess && i == 0) cur_ms = ms;
+    if (err == cudaSuccess && ms < best_ms) { best_ms = ms; best_i = i; }
+  }
+  // keep the current policy unless a candidate is clearly (2%) faster
+  if (best_i != 0 && best_ms > 0.98 * cur_ms) { best_i = 0; best_ms = cur_ms; }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return fail(h, CLV_ECUDA, std::string("autotune: ") + cudaGetErrorString(err));
+  CLV_CUDA(h, batch_schedule(h, cand[best_i].first, cand[best_i].second, sms, smem_max));
+  if (best) tile_info(h, best_ms, best);
+  return CLV_OK;
+}
+
 clv_status clv_autotune(clv_handle* h, int max_candidates, int reps, clv_tile_info* best) {
   if (!h || max_candidates < 1 || reps < 1) return CLV_EINVAL;
-  if (!h->batch.empty()) return fail(h, CLV_EINVAL, "the autotuner tunes single-event handles");
+  if (!h->batch.empty()) return autotune_batch(h, max_candidates, reps, best);
   if (!h->initialized) return fail(h, CLV_EINVAL, "clv_set_initial was not called");
   if (h->cfg.kernel != 0) return fail(h, CLV_EINVAL, "the autotuner tunes the tiled stage kernel");
   size_t smem_max = 0;
@@ -1621,15 +1696,16 @@ clv_status clv_autotune(clv_handle* h, int max_candidates, int reps, clv_tile_in
 // ---------------- batch of events ----------------
 }  // extern "C"
 
-// Tile of one event of a batch: TK from the eta_s extent (at most 32 columns),
-// TJ as large as the thread limit allows, x chunks of about 32 planes.
-static TileArgs batch_tile(const clv_config& c) {
+// Tile of one event of a batch under a tiling policy: TK from the eta_s
+// extent (at most 32 columns), TJ as large as the thread cap allows (at most
+// maxthr threads per CTA), x chunks of about `chunk` planes.
+static TileArgs batch_tile(const clv_config& c, int maxthr_cap, int chunk) {
   TileArgs t;
-  const int maxthr = tile_max_threads(&c);
+  const int maxthr = std::min(tile_max_threads(&c), maxthr_cap);
   const int nk = (c.neta + 31) / 32;
   t.TK = (c.neta + nk - 1) / nk;
   t.TJ = std::max(1, std::min(c.ny, maxthr / (t.TK + 1) - 1));
-  const int nch = (c.nx + 31) / 32;
+  const int nch = (c.nx + chunk - 1) / chunk;
   t.CX = (c.nx + nch - 1) / nch;
   t.ntj = (c.ny + t.TJ - 1) / t.TJ;
   t.ntk = (c.neta + t.TK - 1) / t.TK;
@@ -1650,16 +1726,75 @@ template <typename R> static cudaError_t batch_upload(clv_handle* h) {
   cudaError_t err = cudaMalloc(&h->batch_geom, ne * sizeof(EventGeom<R>));
   if (err == cudaSuccess) err = cudaMemcpy(h->batch_geom, g.data(), ne * sizeof(EventGeom<R>), cudaMemcpyHostToDevice);
   if (err == cudaSuccess) err = cudaMalloc((void**)&h->batch_tiles, ne * sizeof(TileArgs));
-  if (err == cudaSuccess) err = cudaMemcpy(h->batch_tiles, t.data(), ne * sizeof(TileArgs), cudaMemcpyHostToDevice);
+  (void)t;
+  return err;
+}
+
+template <typename R> static cudaError_t batch_attributes(size_t smem) {
+  cudaError_t err = cudaSuccess;
   auto attr = [&](const void* f) {
-    if (err == cudaSuccess)
-      err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->batch_smem);
+    if (err == cudaSuccess) err = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   };
   attr((const void*)stage_batch_kernel<R, 1, false>);
   attr((const void*)stage_batch_kernel<R, 2, false>);
   attr((const void*)stage_batch_kernel<R, 1, true>);
   attr((const void*)stage_batch_kernel<R, 2, true>);
   return err;
+}
+
+// (Re)builds the events' tiles and the work-item list (event, tile-chunk),
+// most expensive first, for one tiling policy, and uploads them on the
+// handle's stream.  Nothing changes (and cudaErrorInvalidValue is returned)
+// if a tile would exceed the shared memory of a CTA.
+static cudaError_t batch_schedule(clv_handle* h, int maxthr, int chunk, int sms, size_t smem_max) {
+  maxthr = std::min(maxthr, h->rsize == 8 ? std::min(CLV_TILE_MAX_THREADS, kBlock / 2) : CLV_TILE_MAX_THREADS);
+  const size_t ne = h->batch.size();
+  std::vector<TileArgs> tiles(ne);
+  std::vector<std::pair<double, int2>> items;
+  size_t smem = 0;
+  int thr = 0;
+  for (size_t e = 0; e < ne; ++e) {
+    const auto& ev = h->batch[e];
+    const TileArgs t = batch_tile(ev.cfg, maxthr, chunk);
+    tiles[e] = t;
+    const size_t sm = ev.viscous ? tile_smem_bytes<true>(t.TJ, t.TK, h->rsize) : tile_smem_bytes<false>(t.TJ, t.TK, h->rsize);
+    smem = std::max(smem, sm);
+    thr = std::max(thr, (t.TJ + 1) * (t.TK + 1));
+    const int nch = (ev.cfg.nx + t.CX - 1) / t.CX;
+    const int nb = t.ntj * t.ntk * nch;
+    for (int b = 0; b < nb; ++b) {
+      const int ch = b / (t.ntj * t.ntk);
+      const int planes = std::min(t.CX, ev.cfg.nx - ch * t.CX);
+      const double cost = (planes + 4.0) * (t.TJ + 4.0) * (t.TK + 4.0) * (ev.viscous ? 2.0 : 1.0);
+      items.push_back({cost, make_int2((int)e, b)});
+    }
+  }
+  if (smem > smem_max) return cudaErrorInvalidValue;
+  std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  std::vector<int2> it(items.size());
+  for (size_t i = 0; i < items.size(); ++i) it[i] = items[i].second;
+  cudaError_t err = cudaStreamSynchronize(h->stream);   // no launch of the old schedule is in flight
+  if (err == cudaSuccess) err = h->rsize == 8 ? batch_attributes<double>(smem) : batch_attributes<float>(smem);
+  if (err == cudaSuccess && it.size() > (size_t)h->batch_nitems) {
+    cudaFree(h->batch_items);
+    h->batch_items = nullptr;
+    err = cudaMalloc((void**)&h->batch_items, it.size() * sizeof(int2));
+  }
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(h->batch_items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice, h->stream);
+  if (err == cudaSuccess)
+    err = cudaMemcpyAsync(h->batch_tiles, tiles.data(), ne * sizeof(TileArgs), cudaMemcpyHostToDevice, h->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);   // host vectors die here
+  if (err != cudaSuccess) return err;
+  for (size_t e = 0; e < ne; ++e) h->batch[e].tile = tiles[e];
+  h->batch_smem = smem;
+  h->batch_threads = thr;
+  h->batch_nitems = (int)it.size();
+  h->batch_blocks = (unsigned)std::min<long long>((long long)sms * CLV_TILE_MIN_BLOCKS, h->batch_nitems);
+  h->batch_maxthr = maxthr;
+  h->batch_chunk = chunk;
+  invalidate_graphs(h);   // captured steps hold the old launch shape and item list
+  return cudaSuccess;
 }
 
 extern "C" {
@@ -1703,7 +1838,6 @@ clv_status clv_create_batch(const clv_config* cfgs, int nevents, void* cuda_stre
   clv_handle* h = *out;
   size_t smem_max = 0;
   const int sms = device_sms(&smem_max);
-  std::vector<std::pair<double, int2>> items;
   long long off = 0;
   h->batch.resize(nevents);
   for (int e = 0; e < nevents; ++e) {
@@ -1715,30 +1849,11 @@ clv_status clv_create_batch(const clv_config* cfgs, int nevents, void* cuda_stre
     ev.N = (long long)ev.cfg.nx * ev.cfg.ny * ev.nep;
     ev.Nc = (long long)ev.cfg.nx * ev.cfg.ny * ev.cfg.neta;
     ev.viscous = ev.cfg.eta_over_s > 0.0;
-    ev.tile = batch_tile(ev.cfg);
     off += ev.N;
-    const TileArgs& t = ev.tile;
-    const size_t sm = ev.viscous ? tile_smem_bytes<true>(t.TJ, t.TK, h->rsize) : tile_smem_bytes<false>(t.TJ, t.TK, h->rsize);
-    h->batch_smem = std::max(h->batch_smem, sm);
-    h->batch_threads = std::max(h->batch_threads, (t.TJ + 1) * (t.TK + 1));
-    const int nch = (ev.cfg.nx + t.CX - 1) / t.CX;
-    const int nb = t.ntj * t.ntk * nch;
-    for (int b = 0; b < nb; ++b) {
-      const int ch = b / (t.ntj * t.ntk);
-      const int planes = std::min(t.CX, ev.cfg.nx - ch * t.CX);
-      const double cost = (planes + 4.0) * (t.TJ + 4.0) * (t.TK + 4.0) * (ev.viscous ? 2.0 : 1.0);
-      items.push_back({cost, make_int2(e, b)});
-    }
   }
-  std::stable_sort(items.begin(), items.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
-  std::vector<int2> it(items.size());
-  for (size_t i = 0; i < items.size(); ++i) it[i] = items[i].second;
-  h->batch_nitems = (int)it.size();
-  h->batch_blocks = (unsigned)std::min<long long>((long long)sms * CLV_TILE_MIN_BLOCKS, h->batch_nitems);
-  cudaError_t err = h->batch_smem > smem_max ? cudaErrorInvalidValue : cudaSuccess;
-  if (err == cudaSuccess) err = h->rsize == 8 ? batch_upload<double>(h) : batch_upload<float>(h);
-  if (err == cudaSuccess) err = cudaMalloc((void**)&h->batch_items, it.size() * sizeof(int2));
-  if (err == cudaSuccess) err = cudaMemcpy(h->batch_items, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  // default policy: the largest tiles the thread limit allows, x chunks of about 32 planes
+  cudaError_t err = h->rsize == 8 ? batch_upload<double>(h) : batch_upload<float>(h);
+  if (err == cudaSuccess) err = batch_schedule(h, CLV_TILE_MAX_THREADS, 32, sms, smem_max);
   if (err == cudaSuccess) err = cudaMalloc((void**)&h->batch_ctr, 2 * sizeof(int));
   if (err != cudaSuccess) {
     clv_destroy(h);
@@ -1781,6 +1896,19 @@ clv_status clv_batch_get_fields(clv_handle* h, int event, uint32_t mask, double*
   if (event < 0 || event >= (int)h->batch.size()) return fail(h, CLV_EINVAL, "event index out of range");
   const auto& ev = h->batch[event];
   return get_fields_range(h, mask, host_out, true, ev.off, ev.Nc, ev.cfg.neta, ev.nep);
+}
+
+clv_status clv_batch_set_schedule(clv_handle* h, int max_threads, int chunk) {
+  if (!h) return CLV_EINVAL;
+  if (h->batch.empty()) return fail(h, CLV_EINVAL, "not a batch (clv_create_batch)");
+  if (max_threads < 32 || max_threads > CLV_TILE_MAX_THREADS || chunk < 1 || chunk > 4096)
+    return fail(h, CLV_EINVAL, "max_threads must be in [32, 256] and chunk in [1, 4096]");
+  size_t smem_max = 0;
+  const int sms = device_sms(&smem_max);
+  const cudaError_t e = batch_schedule(h, max_threads, chunk, sms, smem_max);
+  if (e == cudaErrorInvalidValue) return fail(h, CLV_EINVAL, "a tile of this policy exceeds the shared memory of a CTA");
+  CLV_CUDA(h, e);
+  return CLV_OK;
 }
 
 clv_status clv_batch_event_stats(clv_handle* h, int event, clv_stats* out) {

@@ -419,9 +419,49 @@ def test_batch_of_uneven_events_equals_single_events(prec):
     with pytest.raises(clv.ClvError):
         b.set_initial(flat, flat, flat, flat)
     with pytest.raises(clv.ClvError):
-        b.autotune()
+        b.set_tile(4, 4, 4)
     with pytest.raises(clv.ClvError):
         b.set_event(0, cases[0].eps, cases[0].ux, cases[0].uy, cases[0].ueta)   # already started
+
+
+@pytest.mark.parametrize("prec", [clv.CLV_FP64, clv.CLV_FP32])
+def test_batch_schedules_and_autotuner_leave_results_unchanged(prec):
+    """Tiling policies of a batch (thread cap, x chunk), explicit or picked by
+    the autotuner between steps, give bit-identical fields."""
+    cases = [
+        I.hotspot_event(nx=23, ny=21, neta=13, n_spots=60, seed=41, eta_over_s=0.08),
+        I.hotspot_event(nx=17, ny=25, neta=7, dx=0.25, deta=0.25, n_spots=40, seed=42, eta_over_s=0.0),
+        I.hotspot_event(nx=31, ny=19, neta=41, dx=0.15, deta=0.15, n_spots=80, seed=43, eta_over_s=0.16),
+    ]
+    names = ["eps", "ux", "ueta", "Ttt", "pixx", "piee"]
+    runs = []
+    for sched in (None, (128, 8), (64, 48), "tune"):
+        b = clv.Batch(cases, prec)
+        for e, c in enumerate(cases):
+            b.set_event(e, c.eps, c.ux, c.uy, c.ueta)
+        if sched == "tune":
+            with pytest.raises(clv.ClvError):
+                b.autotune()                     # the batch starts at its first step
+        elif sched is not None:
+            b.set_schedule(*sched)
+        b.step(3)
+        if sched == "tune":
+            info = b.autotune(max_candidates=8, reps=2)
+            assert info["TK"] == 0 and info["TJ"] >= 32 and info["CX"] >= 1 and info["ms"] > 0
+            assert b.tile() == {**info, "ms": 0.0}
+        b.step(3)
+        runs.append([b.get_event(e, names) for e in range(len(cases))])
+        b.close()
+    for r in runs[1:]:
+        for e in range(len(cases)):
+            for k in names:
+                np.testing.assert_array_equal(r[e][k], runs[0][e][k])
+    b = clv.Batch(cases[:1], prec)
+    with pytest.raises(clv.ClvError):
+        b.set_schedule(16, 32)                   # thread cap below a warp
+    with pytest.raises(clv.ClvError):
+        b.set_schedule(256, 0)
+    b.close()
 
 
 def test_batch_needs_every_event_and_a_common_setup():
