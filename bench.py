@@ -489,6 +489,35 @@ def run_gpu(args):
     clocks["covers"] = ("from the headline through the batch: every timed configuration, e2e, freeze-out and "
                         "Cooper-Frye included")
 
+    # ---- accuracy of the FP32 + learned-guess path on the headline event,
+    # against the FP64 GPU path on the same grid (which the parity tests hold
+    # to 1e-10 of the FP64 oracle): at the parity tests' 40-step horizon and
+    # at the end of the headline run's span (warm-up + timed steps); untimed
+    accuracy = None
+    if args.accuracy:
+        span = args.warmup + args.steps
+        g32 = clv.from_case(case, clv.CLV_FP32)
+        g32.set_initial_case(case)
+        g32.set_mlp(params_host)
+        g32.set_guess(clv.CLV_GUESS_MLP)
+        g64 = clv.from_case(case, clv.CLV_FP64)
+        g64.set_initial_case(case)
+        marks, done = sorted({min(40, span), span}), 0
+        acc = {}
+        for m in marks:
+            g32.step(m - done)
+            g64.step(m - done)
+            done = m
+            e32, e64 = g32.get(["eps"])["eps"], g64.get(["eps"])["eps"]
+            live = e64 > 1e-3
+            acc[str(m)] = {"tau": g64.time()[0], "cells_compared": int(live.sum()),
+                           "eps_linf_rel_where_eps_gt_1e-3": float(np.max(np.abs(e32[live] / e64[live] - 1))),
+                           "eps_l1_rel": float(np.abs(e32 - e64).sum() / np.abs(e64).sum())}
+        g32.close()
+        g64.close()
+        accuracy = {"vs": "the FP64 GPU path on the same grid (held to 1e-10 of the FP64 oracle by the parity tests)",
+                    "after_steps": acc}
+
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32_max / args.steps, "higher_is_better": True,
@@ -507,6 +536,7 @@ def run_gpu(args):
         "fp32_cold_guess": {"value": value32c, "unit": UNIT, "steps": args.steps,
                             "ms_per_step": ms32c_max / args.steps},
         "learned_guess": learned,
+        "accuracy": accuracy,
         "large_event": large,
         "batch": batch,
         "freezeout": freezeout,
@@ -628,6 +658,8 @@ def main():
                     help="skip the 261x261x121 mini-jet event measured beside the headline")
     ap.add_argument("--no-freezeout", dest="freezeout", action="store_false",
                     help="skip the freeze-out surface measured beside the headline")
+    ap.add_argument("--no-accuracy", dest="accuracy", action="store_false",
+                    help="skip the FP32-vs-FP64 accuracy check of the headline event")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default tile shape instead of timing candidates (setup, untimed)")
     ap.add_argument("--train-events", type=int, default=2, help="FP64 events whose states train the guess")
