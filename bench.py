@@ -61,6 +61,12 @@ FO_BYTES_PER_ELEMENT = 22 * 4 + 8 + 2 * 13 * 4
 # exponent 2, exp2 1, f 2, p p pi 10, (1 - s f) q + 1 4, product and sum 3 -> 30
 CF_FLOPS_PER_PAIR = 33.75
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# algorithmic words per cell of one launch of the optional kernels: bulk reads
+# eps, u~ (3), c_s and Pi of the stage's input, Pi^n, u~^n (3) and u~^{n-1} (3),
+# writes Pi (15); charge reads N~ of the stage's input, u~ (3), c_s and N~^n,
+# writes N~ (7)
+BULK_WORDS = 15
+CHARGE_WORDS = 7
 HBM_NOMINAL_GBS = 7900.0   # GB300 HBM3e, nominal (context beside the measured copy peak)
 KERNEL_NAMES = {"stage1": "stage_tile_kernel<float,1,viscous>", "recover1": "recover_kernel<float,viscous>",
                 "stage2": "stage_tile_kernel<float,2,viscous>", "recover2": "recover_kernel<float,viscous>"}
@@ -161,10 +167,13 @@ def run_gpu(args):
         if ws > 1:
             dist.barrier()
 
-    def timed_run(precision, steps, warmup, kernel_timing=False, params=None, guess=None, ev=None, flush_l2=True):
+    def timed_run(precision, steps, warmup, kernel_timing=False, params=None, guess=None, ev=None, flush_l2=True,
+                  n0=None, **hkw):
         ev = case if ev is None else ev
-        g = clv.from_case(ev, precision)
+        g = clv.from_case(ev, precision, **hkw)
         g.set_initial_case(ev)
+        if n0 is not None:
+            g.set_initial_n(n0)
         if params is not None:
             g.set_mlp(params)
             g.set_guess(clv.CLV_GUESS_MLP)
@@ -485,9 +494,46 @@ def run_gpu(args):
                  "stats_fp64": {k: stB64.get(k) for k in ("tau", "eps_max", "n_rootfail", "error_word", "error")}}
         del evs
 
+    # ---- the optional fields on the headline event (FP32 + learned guess):
+    # bulk pressure (zeta/s = 0.1) and net charge.  Their kernels run inside the
+    # stage-kernel timing slots (bulk: both stages; charge: stage 1 in slot 2,
+    # stage 2 in none), so each kernel's time is the slot's growth over the
+    # headline run, and its bandwidth the algorithmic bytes over that time
+    options = None
+    if args.options:
+        so = max(20, args.steps // 4)
+        msBk, ktBk, stBk = timed_run(clv.CLV_FP32, so, args.warmup, kernel_timing=True, params=params_host,
+                                     zeta_over_s=0.1)
+        n0 = 0.2 + 0.05 * np.cos(np.linspace(0.0, 6.283, N)).reshape(case.eps.shape)
+        msCh, ktCh, stCh = timed_run(clv.CLV_FP32, so, args.warmup, kernel_timing=True, params=params_host,
+                                     charge=True, n0=n0)
+        avg = lambda kt_: {k: (ms / n if n else 0.0) for k, (ms, n) in kt_.items()}
+        a0, aB, aC = avg(kt), avg(ktBk), avg(ktCh)
+        t_bulk = 0.5 * ((aB["stage1"] - a0["stage1"]) + (aB["stage2"] - a0["stage2"]))
+        t_charge = aC["stage2"] - a0["stage2"]
+        ach_b = BULK_WORDS * 4 * N / (t_bulk / 1e3) / 1e9 if t_bulk > 0 else None
+        ach_c = CHARGE_WORDS * 4 * N / (t_charge / 1e3) / 1e9 if t_charge > 0 else None
+        options = {"workload": "the headline event, FP32 + learned guess, L2 flushed between steps",
+                   "steps": so,
+                   "bulk": {"zeta_over_s": 0.1, "value": N * so / (msBk / 1e3), "unit": UNIT,
+                            "ms_per_step": msBk / so, "step_overhead": (msBk / so) / (ms32 / args.steps) - 1.0,
+                            "launches_per_step": 7,
+                            "roofline": {"bound": "hbm", "kernel": "bulk_stage_kernel<float>", "ms_avg": t_bulk,
+                                         "achieved": ach_b, "peak": peak, "unit": "GB/s",
+                                         "frac": (ach_b / peak) if ach_b else None,
+                                         "algorithmic_bytes_per_launch": BULK_WORDS * 4 * N},
+                            "error_word": stBk.get("error_word")},
+                   "charge": {"value": N * so / (msCh / 1e3), "unit": UNIT, "ms_per_step": msCh / so,
+                              "step_overhead": (msCh / so) / (ms32 / args.steps) - 1.0, "launches_per_step": 7,
+                              "roofline": {"bound": "hbm", "kernel": "charge_stage_kernel<float>", "ms_avg": t_charge,
+                                           "achieved": ach_c, "peak": peak, "unit": "GB/s",
+                                           "frac": (ach_c / peak) if ach_c else None,
+                                           "algorithmic_bytes_per_launch": CHARGE_WORDS * 4 * N},
+                              "error_word": stCh.get("error_word")}}
+
     clocks = sampler.stop()
-    clocks["covers"] = ("from the headline through the batch: every timed configuration, e2e, freeze-out and "
-                        "Cooper-Frye included")
+    clocks["covers"] = ("from the headline through the batch: every timed configuration, e2e, freeze-out, "
+                        "Cooper-Frye and the bulk and charge runs included")
 
     # ---- accuracy of the FP32 + learned-guess path on the headline event,
     # against the FP64 GPU path on the same grid (which the parity tests hold
@@ -537,6 +583,7 @@ def run_gpu(args):
                             "ms_per_step": ms32c_max / args.steps},
         "learned_guess": learned,
         "accuracy": accuracy,
+        "options": options,
         "large_event": large,
         "batch": batch,
         "freezeout": freezeout,
@@ -658,6 +705,8 @@ def main():
                     help="skip the 261x261x121 mini-jet event measured beside the headline")
     ap.add_argument("--no-freezeout", dest="freezeout", action="store_false",
                     help="skip the freeze-out surface measured beside the headline")
+    ap.add_argument("--no-options", dest="options", action="store_false",
+                    help="skip the bulk-pressure and net-charge runs of the headline event")
     ap.add_argument("--no-accuracy", dest="accuracy", action="store_false",
                     help="skip the FP32-vs-FP64 accuracy check of the headline event")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
