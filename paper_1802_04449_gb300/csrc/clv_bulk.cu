@@ -77,12 +77,15 @@ __global__ void __launch_bounds__(kBlock) bulk_stage_kernel(const StageParams<R>
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
     BulkCell<R> q[5];
+    // interior cells: neighbours at a fixed stride; within two cells of an
+    // edge: clamped (zero gradient) or wrapped (periodic) indices
+    const int pos = ax == 0 ? i : (ax == 1 ? j : k), n = ax == 0 ? p.nx : (ax == 1 ? p.ny : p.ne);
+    const long long stride = ax == 0 ? (long long)p.ny * p.nep : (ax == 1 ? (long long)p.nep : 1ll);
 #pragma unroll
     for (int o = -2; o <= 2; ++o) {
-      const int ii = ax == 0 ? wrap_index(i + o, p.nx, p.periodic) : i;
-      const int jj = ax == 1 ? wrap_index(j + o, p.ny, p.periodic) : j;
-      const int kk = ax == 2 ? wrap_index(k + o, p.ne, p.periodic) : k;
-      q[o + 2] = bulk_cell(p, Pin, ((long long)ii * p.ny + jj) * p.nep + kk, ax);
+      long long s = c + o * stride;
+      if (pos < 2 || pos >= n - 2) s = c + (long long)(wrap_index(pos + o, n, p.periodic) - pos) * stride;
+      q[o + 2] = bulk_cell(p, Pin, s, ax);
     }
     const R Hm = bulk_flux(q[0], q[1], q[2], q[3]);
     const R Hp = bulk_flux(q[1], q[2], q[3], q[4]);

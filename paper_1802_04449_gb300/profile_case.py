@@ -4,7 +4,7 @@ launches).  Usage:
 
     python -m paper_1802_04449_gb300.profile_case [--precision fp32|fp64]
         [--guess previous|cold|learned] [--skip S] [--steps K] [--no-autotune]
-        [--surface]
+        [--surface] [--zeta-over-s Z] [--charge]
 
 The tile shape is autotuned first (as bench.py does; its timing launches
 come first), --skip S steps run next (reaching the later, more dilute
@@ -13,6 +13,8 @@ seed of the same workload) before the run.  --surface then takes a slice,
 runs 10 more steps, finds the freeze-out surface at T_f = 137 MeV between the
 two slices (clv_fo_find) and computes the pi+, K+ and p spectra on the
 41 x 15 x 48 grid from it (clv_cf_spectra): those launches come last.
+--zeta-over-s Z > 0 evolves the bulk pressure too, --charge a smooth net
+charge (their kernels run once per stage).
 """
 from __future__ import annotations
 
@@ -33,6 +35,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--surface", action="store_true")
+    ap.add_argument("--zeta-over-s", type=float, default=0.0)
+    ap.add_argument("--charge", action="store_true")
     a = ap.parse_args(argv)
 
     import torch
@@ -51,8 +55,11 @@ def main(argv=None):
         p, _ = L.train(X, Y, iters=1000, batch=32768, lr=2e-3, seed=7)
         params = p.cpu().numpy()
         h.close()
-    g = clv.from_case(case, prec)
+    g = clv.from_case(case, prec, zeta_over_s=a.zeta_over_s, charge=a.charge)
     g.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    if a.charge:
+        import numpy as np
+        g.set_initial_n(0.2 + 0.05 * np.cos(np.linspace(0.0, 6.283, case.eps.size)).reshape(case.eps.shape))
     if params is not None:
         g.set_mlp(params)
     g.set_guess({"previous": clv.CLV_GUESS_PREVIOUS, "cold": clv.CLV_GUESS_COLD,
