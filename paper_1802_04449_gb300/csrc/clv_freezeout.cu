@@ -270,8 +270,11 @@ __device__ __forceinline__ R warp_sum(R x) {
   return x;
 }
 
+// At least four CTAs per SM (at most 64 registers, a 4-byte spill in FP32):
+// the warps are latency-bound, and 32 resident warps per SM instead of 24
+// (78 registers) made a find 5% faster.
 template <typename R>
-__global__ void __launch_bounds__(kElemThreads) fo_elements_kernel(FoArgs<R> a, const int* __restrict__ list,
+__global__ void __launch_bounds__(kElemThreads, 4) fo_elements_kernel(FoArgs<R> a, const int* __restrict__ list,
                                                                    const long long* __restrict__ total,
                                                                    long long capacity, R* __restrict__ rec,
                                                                    int64_t* __restrict__ cube_out) {
