@@ -176,3 +176,25 @@ def test_checkpoint_graphs_and_reset_with_bulk():
     with pytest.raises(clv.ClvError):
         h.set_state(state)
     h.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 1, 5), (3, 1, 1), (2, 3, 1), (4, 5, 3)])
+def test_degenerate_grids_with_bulk_and_charge(shape):
+    """Axes of 1 to 5 cells: every neighbour of the bulk and charge stencils
+    is clamped (no interior fast path on short axes); FP64 against the oracle."""
+    nx, ny, ne = shape
+    rng = np.random.default_rng(sum(shape))
+    e = 4.0 + rng.uniform(0, 2, shape)
+    z = np.zeros(shape)
+    n0 = 0.2 + 0.05 * rng.uniform(-1, 1, shape)
+    case = I.HydroCase("tiny", nx, ny, ne, 0.3, 0.3, 0.3, 0.6, 0.02, 0.1, None, e, z, z, z, 5)
+    o = oracle.Oracle(nx, ny, ne, 0.3, 0.3, 0.3, 0.6, 0.02, 0.1, zeta_over_s=0.2)
+    o.set_initial(e, z, z, z)
+    o.set_initial_n(n0)
+    o.step(6)
+    g = clv.from_case(case, clv.CLV_FP64, zeta_over_s=0.2, charge=True)
+    g.set_initial(e, z, z, z)
+    g.set_initial_n(n0)
+    g.step(6)
+    compare_fp64(o, g, True, ALL + ["Nt", "n"])
+    g.close()
