@@ -46,7 +46,14 @@
  *       below the first node P, c_s^2 of the first node scaled as described in
  *       eos_eval; above the last node conformal continuation.
  *   R13 Root solve on v in [0, M/E]: f(v) = v - M/(E + P(E - M v)).  E below the
- *       cutoff -> vacuum.  M > (1 - 1e-6) E -> M rescaled to (1 - 1e-6) E.
+ *       cutoff -> vacuum.  M > (1 - 1e-3) E -> M rescaled to (1 - 1e-3) E,
+ *       which bounds the flow's Lorentz factor near 22.  The bound only acts
+ *       in the dilute, ultra-relativistic fringe of an expanding event (the
+ *       paper's analytic flows stay far below it).  There E/eps grows as
+ *       gamma^2, so the rest-frame density eps = E - M v is ill-conditioned
+ *       in the stored T~; a looser bound (1 - 1e-6, gamma up to ~700) let
+ *       rounding-level differences of T~ grow into percent-level differences
+ *       of eps near 1e-3 GeV/fm^3 after a few hundred steps.
  *   R14 Vacuum cells (eps < cutoff): eps = 0, u~ = (1, 0, 0, 0), pi~ = 0.
  *   R15 pi~ stage update: Q* = u~^{tau,n} pi~^n + h S1, pi~' = Q* / u~*^tau;
  *       Q^{n+1} = (u~^{tau,n} pi~^n + u~*^tau pi~' + h S2)/2,
@@ -59,9 +66,13 @@
  *       ultra-relativistic edge of a viscous event runs away): after each
  *       stage update and before the root solve, with eps and P of the
  *       stage's input state of the cell,
- *         - pi~ = 0 where that eps < 1e-3 GeV/fm^3 (ideal flow far below
- *           freeze-out densities);
- *         - otherwise pi~ is scaled by rho_max / rho wherever
+ *         - pi~ is scaled by the ramp r(eps) = min(max(eps/eps_0 - 1, 0), 1)
+ *           with eps_0 = 1e-3 GeV/fm^3: zero below eps_0 (ideal flow far
+ *           below freeze-out densities), full above 2 eps_0, linear in
+ *           between.  The ramp is continuous, so a rounding-level change of
+ *           eps changes pi~ at the rounding level (a step at eps_0 switched
+ *           a cell's whole pi~ on or off);
+ *         - then pi~ is scaled by rho_max / rho wherever
  *           rho = sqrt(|pi~_{mu nu} pi~^{mu nu}|) / sqrt(eps^2 + 3 P^2)
  *           exceeds rho_max = 1.
  *   R19 Net charge (Eq. Ntilde with S_N = 0; the paper sets n = 0, so this
@@ -83,8 +94,8 @@
  *       contradicts Eq. (Pi), and the Pi u~^tau/tau term follows from
  *       nabla_mu (Pi u^mu) as for pi~ (R2).  tau_Pi = 5 zeta/(T s) with
  *       constant zeta/s, so zeta/tau_Pi = (eps + P)/5.  Update as R15 for pi~.
- *       Regulator (as R18): Pi = 0 where the stage's input eps < 1e-3, and
- *       |Pi| <= P there.  Vacuum cells: Pi = 0.  The pressure of T^{mu nu} is
+ *       Regulator (as R18): Pi is scaled by the ramp r(eps) of the stage's
+ *       input eps, then |Pi| <= P of that eps.  Vacuum cells: Pi = 0.  The pressure of T^{mu nu} is
  *       max(P + Pi, 0): the bound uses P of the stage's input, and where eps
  *       then falls P(eps) + Pi can dip below 0, which leaves the root
  *       function f(v) of the solve with two roots or none in [0, M/E]; with
@@ -217,7 +228,7 @@ static int prim_solve(const orc_t* h, double E, double Mx, double My, double Me,
   u[0] = 1.0; u[1] = u[2] = u[3] = 0.0;
   if (!(E >= h->c.eps_cut)) { *eps = 0.0; return 0; }
   double M = sqrt(Mx * Mx + My * My + Me * Me);
-  double Mmax = (1.0 - 1e-6) * E;
+  double Mmax = (1.0 - 1e-3) * E;
   if (M > Mmax) {
     double s = Mmax / M;
     Mx *= s; My *= s; Me *= s;
@@ -347,15 +358,19 @@ static void source_pi(double g, const double u[4], const double du[16], const do
   S[9] -= 2.0 * g * ue * pi[3];
 }
 
-/* Shear regulator R18: pi = 0 below VISC_EPS_MIN, otherwise
+/* Shear regulator R18: pi scaled by the ramp r(eps) (0 below VISC_EPS_MIN,
+ * 1 above twice it, linear between), then
  * |pi_{mu nu} pi^{mu nu}| <= rho_max^2 (eps^2 + 3 P^2). */
 #define RHO_MAX 1.0
 #define VISC_EPS_MIN 1e-3
+static double visc_ramp(double e) {
+  double r = e / VISC_EPS_MIN - 1.0;
+  return r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
+}
 static void regulate_pi(const orc_t* h, double e, double* pi) {
-  if (e < VISC_EPS_MIN) {
-    for (int q = 0; q < NPI; ++q) pi[q] = 0.0;
-    return;
-  }
+  double r = visc_ramp(e);
+  for (int q = 0; q < NPI; ++q) pi[q] *= r;
+  if (r == 0.0) return;
   double P, T, cs2;
   eos_eval(h, e, &P, &T, &cs2);
   double pp = 0.0;
@@ -377,7 +392,8 @@ static void regulate_pi(const orc_t* h, double e, double* pi) {
 
 /* bulk regulator (R20) with eps and P of the stage's input state */
 static double regulate_Pi(const orc_t* h, double e, double Pb) {
-  if (e < VISC_EPS_MIN) return 0.0;
+  Pb *= visc_ramp(e);
+  if (Pb == 0.0) return 0.0;
   double P, T, cs2;
   eos_eval(h, e, &P, &T, &cs2);
   if (Pb > P) return P;

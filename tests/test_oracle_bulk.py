@@ -23,6 +23,7 @@ from scipy.integrate import solve_ivp
 from scipy.linalg import expm
 
 import oracle
+from conftest import assert_regulator_inactive
 from paper_1802_04449_gb300 import inputs as I
 
 HBARC = 0.1973269804
@@ -67,6 +68,8 @@ def check_bjorken_bulk(plant=0):
     errs = []
     for dtau in (0.02, 0.01):
         f, (e_ex, phi_ex, Pi_ex) = bjorken_bulk_run(dtau, plant=plant)
+        if plant == 0:
+            assert_regulator_inactive(f, f["eps"] / 3, f["Pi"])
         for k in ("eps", "Pi", "piee"):
             assert np.ptp(f[k]) == 0.0          # uniform stays exactly uniform
         assert Pi_ex < 0                        # expansion lowers the pressure
@@ -97,6 +100,9 @@ def sound_wave_err(nx, plant=0, amp=1e-4, L=4.0, t1=2.0, e0=10.0, eta_over_s=0.1
     z = np.zeros(sh)
     o.set_initial((e0 * (1 + amp * np.cos(k * x))).reshape(sh), z, z, z)
     o.step(int(round(t1 / dt)))
+    if plant == 0:
+        f = o.fields()
+        assert_regulator_inactive(f, f["eps"] / 3, f["Pi"])
     t = o.stats()["tau"]
     c, s = np.cos(k * x), np.sin(k * x)
     got = np.array([2 * np.mean(o.get("eps")[:, 0, 0] * c), 2 * np.mean(o.get("ux")[:, 0, 0] * s),

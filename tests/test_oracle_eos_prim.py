@@ -75,6 +75,10 @@ def test_crossover_table_is_thermodynamically_consistent(eos_table):
     assert np.max(np.abs(s_fd[mid] / s[mid] - 1)) < 2e-3
 
 
+# reading R13: M above (1 - 1e-3) E is rescaled to (1 - 1e-3) E before the solve
+M_CAP = 1.0 - 1e-3
+
+
 def rand_EM(rng, n):
     E = 10 ** rng.uniform(-5, 3, n)
     frac = np.concatenate([rng.uniform(0, 1, n - 20), 1 - 10 ** rng.uniform(-5, -1.5, 20)])
@@ -89,7 +93,7 @@ def test_prim_solve_conformal_closed_form():
     rng = np.random.default_rng(7)
     E, Mv = rand_EM(rng, 3000)
     for Ei, Mi in zip(E, Mv):
-        M = np.linalg.norm(Mi)
+        M = min(np.linalg.norm(Mi), M_CAP * Ei)
         out = o.prim(Ei, *Mi)
         eps_exact = math.sqrt(4 * Ei * Ei - 3 * M * M) - Ei
         if eps_exact < 1e-7:   # below the vacuum cutoff of Sec. 5
@@ -99,7 +103,7 @@ def test_prim_solve_conformal_closed_form():
         v_exact = M / (Ei + eps_exact / 3)
         ut = 1 / math.sqrt(1 - v_exact ** 2)
         assert out[1] == pytest.approx(ut, rel=1e-11)
-        np.testing.assert_allclose(out[2:5], ut * v_exact * Mi / M, rtol=1e-10, atol=1e-14)
+        np.testing.assert_allclose(out[2:5], ut * v_exact * Mi / np.linalg.norm(Mi), rtol=1e-10, atol=1e-14)
         assert 0 <= out[5] <= 100
 
 
@@ -119,7 +123,7 @@ def test_prim_solve_table_bruteforce_bisection(eos_table):
     o = make(eos_table)
     rng = np.random.default_rng(11)
     E, Mv = rand_EM(rng, 10000)
-    M = np.linalg.norm(Mv, axis=1)
+    M = np.minimum(np.linalg.norm(Mv, axis=1), M_CAP * E)
     lne_nodes = eos_table["lne0"] + eos_table["dlne"] * np.arange(len(eos_table["P"]))
     P_of = lambda e: np.interp(np.log(e), lne_nodes, eos_table["P"])
     v = _bisect(E, M, P_of)
@@ -140,7 +144,7 @@ def test_prim_solve_table_bruteforce_bisection(eos_table):
     np.testing.assert_allclose((got[:, 0] + Pg) * got[:, 1] ** 2 - Pg, E, rtol=1e-11)
     np.testing.assert_allclose((got[:, 0] + Pg) * got[:, 1] * gv, M, rtol=1e-11)
     # u~ points along M
-    np.testing.assert_allclose(got[:, 2:5] / gv[:, None], Mv / M[:, None], atol=1e-12)
+    np.testing.assert_allclose(got[:, 2:5] / gv[:, None], Mv / np.linalg.norm(Mv, axis=1)[:, None], atol=1e-12)
     assert got[:, 5].max() <= 100
 
 
@@ -151,8 +155,13 @@ def test_prim_solve_edge_cases(eos_table):
         assert out[0] == 5.0 and out[1] == 1.0 and np.all(out[2:5] == 0)
         out = o.prim(5e-8, 1e-8, 0, 0)            # below the vacuum cutoff
         assert out[0] == 0.0 and out[1] == 1.0
-        out = o.prim(2.0, 3.0, 0.0, 0.0)          # M > E: rescaled to (1-1e-6) E
+        out = o.prim(2.0, 3.0, 0.0, 0.0)          # M > E: rescaled to (1-1e-3) E
         assert np.isfinite(out).all() and out[0] > 0 and out[2] > 0
         o2 = make(eos)
-        ref = o2.prim(2.0, 2.0 * (1 - 1e-6), 0.0, 0.0)
+        ref = o2.prim(2.0, 2.0 * M_CAP, 0.0, 0.0)
         np.testing.assert_allclose(out[:5], ref[:5], rtol=1e-13)
+        # just below the bound nothing is rescaled; just above, M is moved onto it
+        below = o2.prim(2.0, 2.0 * M_CAP * (1 - 1e-9), 0.0, 0.0)
+        above = o2.prim(2.0, 2.0 * M_CAP * (1 + 1e-9), 0.0, 0.0)
+        np.testing.assert_allclose(above[:5], ref[:5], rtol=1e-13)
+        assert below[0] > ref[0] and abs(below[0] / ref[0] - 1) < 1e-5

@@ -12,6 +12,7 @@ import pytest
 from scipy.integrate import solve_ivp
 
 import oracle
+from conftest import assert_regulator_inactive
 from paper_1802_04449_gb300 import inputs as I
 
 HBARC = 0.1973269804
@@ -89,6 +90,8 @@ def check_bjorken_viscous(plant=0):
     errs = []
     for dtau in (0.02, 0.01):
         f, e_ex, phi_ex = bjorken_viscous_run(dtau, plant=plant)
+        if plant == 0:
+            assert_regulator_inactive(f, f["eps"] / 3)
         phi = -f["piee"][0, 0, 0]
         errs.append((f["eps"][0, 0, 0] / e_ex - 1, phi / phi_ex - 1))
         # symmetry and tracelessness of Bjorken flow: pi^xx = pi^yy = phi/2, pi^tt = 0
@@ -289,3 +292,29 @@ def test_shear_regulator_caps_oversized_pi():
     assert np.all(np.sqrt(pp) <= 1.05 * bound(1.1 * f["eps"]))
     assert np.all(np.sqrt(pp) >= 0.95 * bound(e0))
     assert np.all(np.isfinite(f["eps"])) and np.all(f["eps"] > 0)
+
+
+def test_shear_regulator_ramp_static_box():
+    """Reading R18's ramp r(eps) = clamp(eps/1e-3 - 1, 0, 1).  In a static,
+    uniform Cartesian box every gradient vanishes, T~ and eps stay put, and
+    the IS equation reduces to d pi/dt = -pi/tau_pi.  One Heun step with the
+    regulator after each stage then gives, with k = 1 - h/tau_pi,
+    pi' = r k pi and pi^{n+1} = r (pi + pi' k)/2 = r (1 + r k^2) pi / 2.
+    Cells at eps = 0.9e-3, 1.4e-3 and 2.5e-3 span the three branches; pi~^{xy}
+    is small, so the cap of R18 stays inactive."""
+    n, h, a = 2, 0.01, 1e-7
+    for e0, r in ((0.9e-3, 0.0), (1.4e-3, 0.4), (2.5e-3, 1.0)):
+        e = np.full((n, n, n), e0)
+        z = np.zeros_like(e)
+        pi = np.zeros((10, n, n, n))
+        pi[5] = a
+        o = oracle.Oracle(n, n, n, 0.3, 0.3, 0.3, 1.0, h, eta_over_s=0.16, cartesian=True, periodic=True)
+        o.set_initial(e, z, z, z, pi)
+        o.step(1)
+        f = o.fields()
+        _, T, _ = o.eos(e0)
+        k = 1.0 - h * T / (5 * 0.16 * HBARC)
+        want = 0.5 * r * (1.0 + r * k * k) * a
+        np.testing.assert_allclose(f["pixy"], want, rtol=1e-12, atol=1e-30)
+        np.testing.assert_allclose(f["eps"], e0, rtol=1e-14)
+        assert np.all(f["pitt"] == 0) and np.all(f["pixx"] == 0)

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from conftest import assert_regulator_inactive
 from paper_1802_04449_gb300 import inputs as I
 
 HBARC = 0.1973269804
@@ -76,6 +77,9 @@ def _gubser_error(dx, lambda1_oracle, b=None, tau1=1.5):
                       case.eta_over_s, None, taupi_coef=b or case.taupi_coef, lambda1_hat=lambda1_oracle)
     o.set_initial(case.eps, case.ux, case.uy, case.ueta, case.pi0)
     o.step(case.nsteps)
+    if lambda1_oracle == -10.0 and b is None:
+        f = o.fields()
+        assert_regulator_inactive(f, f["eps"] / 3)
     x = I.cell_coords(nx, dx)
     e, ux, uy, pi = I.gubser_viscous(tau1, x, x, 2.0, -10.0)
     X, Y = np.meshgrid(x, x, indexing="ij")
