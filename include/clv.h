@@ -69,8 +69,11 @@ typedef struct {
   const double* eos_P;       /* host, eos_n values; copied */
   const double* eos_T;       /* host, eos_n values (GeV); copied */
   const double* eos_cs2;     /* host, eos_n values; copied */
-  int precision;             /* CLV_FP64 or CLV_FP32 (FP32 stencil; FP64 root polish near
-                                vacuum and at high velocity; FP64 reductions) */
+  int precision;             /* CLV_FP64 or CLV_FP32 (FP32 stencil, sources, pi~ and primitives; the
+                                conserved T~^{tau mu} as float-float pairs, ~48 bits, accumulated
+                                exactly and read by the root solve unrounded; float-float Newton
+                                correction of every root, FP64 root polish near vacuum and at high
+                                velocity; FP64 reductions) */
   int cartesian;             /* 1: Christoffel terms off and tau factors 1 (t, x, y, z) */
   int periodic;              /* 1: periodic boundaries; 0: zero-gradient (outflow) */
   double eps_cut;            /* vacuum cutoff, GeV/fm^3 (the paper uses 1e-7) */
@@ -241,16 +244,22 @@ clv_status clv_mlp_forward(clv_handle* h, const float* d_X, int64_t n, float* d_
 /* Loss (mean over samples of the squared error summed over the 4 outputs)
  * and its gradient with respect to the packed parameters, over n device
  * samples, in FP32.  d_grad: CLV_MLP_NPARAM floats, d_loss: 1 float
- * (both overwritten).  Enqueued on cuda_stream. */
+ * (both overwritten).  d_work: CLV_MLP_PARTIAL_FLOATS floats of device
+ * scratch (per-block partial sums, added in a fixed order, so the result is
+ * bitwise reproducible).  Enqueued on cuda_stream. */
+#define CLV_MLP_PARTIAL_FLOATS (256 * (CLV_MLP_NPARAM + 1))
 clv_status clv_mlp_loss_grad(const float* d_params, const float* d_X, const float* d_Y, int64_t n,
-                             void* cuda_stream, float* d_grad, float* d_loss);
+                             void* cuda_stream, float* d_grad, float* d_loss, float* d_work);
 
 /* iters Adam steps (lr, beta 0.9/0.999) on mini-batches of `batch` samples
  * drawn from the n device samples by a counter-based generator (seed != 0).
- * d_params is updated in place; d_work holds 3 x CLV_MLP_NPARAM floats (Adam
- * moments and the gradient; zero before the first call); step0 continues the
- * Adam step count; d_loss[i] receives the mini-batch loss of step i (must be
- * zero on entry).  Enqueued on cuda_stream. */
+ * d_params is updated in place; d_work holds CLV_MLP_TRAIN_WORK_FLOATS floats:
+ * the Adam moments (zero before the first call, kept between calls), the
+ * gradient and the per-block partial sums of the deterministic gradient
+ * reduction; step0 continues the Adam step count; d_loss[i] receives the
+ * mini-batch loss of step i.  The same inputs give the same parameters bit
+ * for bit.  Enqueued on cuda_stream. */
+#define CLV_MLP_TRAIN_WORK_FLOATS (3 * CLV_MLP_NPARAM + CLV_MLP_PARTIAL_FLOATS)
 clv_status clv_mlp_train(float* d_params, float* d_work, const float* d_X, const float* d_Y, int64_t n,
                          int iters, int batch, float lr, uint64_t seed, int step0, void* cuda_stream,
                          float* d_loss);
@@ -307,7 +316,8 @@ clv_status clv_batch_set_schedule(clv_handle* h, int max_threads, int chunk);
  * the ends of the global grid, by clv_slab_fill_edge (zero gradient).
  * set 1 = the inputs of stage 1 (T~, pi~, u~, P, c_s of the step), set 2 =
  * those of stage 2 (the stage-1 results).  side 0 = low x, 1 = high x.  A
- * packed side (the two boundary planes of every field of the set) holds
+ * packed side (the two boundary planes of every field of the set, in the
+ * working precision; FP32: the low parts of T~ too) holds
  * clv_slab_halo_bytes bytes of device memory; pack(side 1) of the left
  * neighbour fills unpack(side 0) here and vice versa.  Stepping:
  *   after clv_set_initial, viscous runs:  for s in 1, 2: fill set s; clv_slab_predictor(s)
@@ -324,9 +334,10 @@ clv_status clv_slab_predictor(clv_handle* h, int stage);
 clv_status clv_stage(clv_handle* h, int stage, clv_stats* stats);
 
 /* ---------------- checkpoint ----------------
- * The complete evolution state: T~^{tau mu}, pi~^{mu nu} and the primitives
- * (eps, u~, P, c_s) of the current and the previous step in the working
- * precision, with tau, the step count and the configuration it belongs to.
+ * The complete evolution state: T~^{tau mu} (FP32: its float-float pairs),
+ * pi~^{mu nu} and the primitives (eps, u~, P, c_s) of the current and the
+ * previous step in the working precision, with tau, the step count and the
+ * configuration it belongs to.
  * Restoring it into a handle of the same configuration continues the run
  * bit for bit.  Buffers are host memory of clv_state_bytes bytes, owned by
  * the caller; both calls synchronise the stream.  clv_set_state returns
@@ -385,9 +396,13 @@ clv_status clv_autotune(clv_handle* h, int max_candidates, int reps, clv_tile_in
  * larger n returns CLV_EINVAL with a message in clv_last_error(NULL).
  * The first call on each device looks up the device address of the scratch
  * array (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the scratch array: calls that
- * overlap on the GPU (other streams or host threads on the same device) race
- * and must be serialised by the caller. */
+ * before any stream capture.  That address is cached per device for the life
+ * of the process: do not call this entry point on a device after
+ * cudaDeviceReset on it.  An error already pending in the CUDA runtime when
+ * the call starts returns CLV_ECUDA without launching anything (and stays
+ * pending).  Every call shares the scratch array: calls that overlap on the
+ * GPU (other streams or host threads on the same device) race and must be
+ * serialised by the caller. */
 clv_status clv_field_stats_noalloc(const double* d_eps, const double* d_Ttt, int64_t n, double cell_volume,
                                    void* cuda_stream, double* d_out);
 

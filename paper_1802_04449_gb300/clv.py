@@ -122,6 +122,8 @@ EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initi
             "clv_set_initial_n_device", "clv_batch_set_schedule"]
 CLV_GUESS_PREVIOUS, CLV_GUESS_COLD, CLV_GUESS_MLP = 0, 1, 2
 MLP_NPARAM = 5124
+MLP_PARTIAL_FLOATS = 256 * (MLP_NPARAM + 1)          # CLV_MLP_PARTIAL_FLOATS
+MLP_TRAIN_WORK_FLOATS = 3 * MLP_NPARAM + MLP_PARTIAL_FLOATS   # CLV_MLP_TRAIN_WORK_FLOATS
 
 
 def load(path: str | None = None):
@@ -160,7 +162,7 @@ def load(path: str | None = None):
         lib.clv_set_mlp.argtypes = [P, F]
         lib.clv_mlp_samples.argtypes = [P, V, V, V]
         lib.clv_mlp_forward.argtypes = [P, V, ctypes.c_int64, V]
-        lib.clv_mlp_loss_grad.argtypes = [V, V, V, ctypes.c_int64, V, V, V]
+        lib.clv_mlp_loss_grad.argtypes = [V, V, V, ctypes.c_int64, V, V, V, V]
         lib.clv_mlp_train.argtypes = [V, V, V, V, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                                       ctypes.c_uint64, ctypes.c_int, V, V]
         lib.clv_set_graphs.argtypes = [P, ctypes.c_int]
@@ -663,14 +665,26 @@ class Hydro:
 
 def field_stats_noalloc(d_eps, d_Ttt, cell_volume, d_out, stream=None):
     """E_tot and max eps of device float64 tensors into the device tensor
-    ``d_out`` (2 values) without any allocation; see clv_field_stats_noalloc."""
+    ``d_out`` (2 values) without any allocation; see clv_field_stats_noalloc.
+    The three tensors must be contiguous float64 CUDA tensors on one device,
+    d_Ttt as long as d_eps and d_out at least 2 values long (CLV_EINVAL
+    otherwise: the C entry point trusts the sizes it is given)."""
     import torch
     lib = load()
+    ts = (d_eps, d_Ttt, d_out)
+    if not all(isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+               for x in ts):
+        raise ClvError(1, "d_eps, d_Ttt and d_out must be contiguous float64 CUDA tensors")
+    if not (d_eps.device == d_Ttt.device == d_out.device):
+        raise ClvError(1, "d_eps, d_Ttt and d_out must be on one device")
+    if d_Ttt.numel() != d_eps.numel() or d_out.numel() < 2:
+        raise ClvError(1, "d_Ttt must have as many values as d_eps, and d_out at least 2")
     n = d_eps.numel()
-    st = stream if stream is not None else torch.cuda.current_stream(d_eps.device)
-    status = lib.clv_field_stats_noalloc(ctypes.c_void_p(d_eps.data_ptr()), ctypes.c_void_p(d_Ttt.data_ptr()),
-                                         int(n), float(cell_volume), ctypes.c_void_p(st.cuda_stream),
-                                         ctypes.c_void_p(d_out.data_ptr()))
+    with torch.cuda.device(d_eps.device):   # the scratch address is looked up on the current device
+        st = stream if stream is not None else torch.cuda.current_stream(d_eps.device)
+        status = lib.clv_field_stats_noalloc(ctypes.c_void_p(d_eps.data_ptr()), ctypes.c_void_p(d_Ttt.data_ptr()),
+                                             int(n), float(cell_volume), ctypes.c_void_p(st.cuda_stream),
+                                             ctypes.c_void_p(d_out.data_ptr()))
     if status != 0:
         raise ClvError(status, lib.clv_last_error(None).decode())
 
@@ -736,9 +750,11 @@ def mlp_loss_grad(params, X, Y, stream=None):
     st = stream if stream is not None else torch.cuda.current_stream(params.device)
     g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=params.device)
     loss = torch.empty(1, dtype=torch.float32, device=params.device)
+    work = torch.empty(MLP_PARTIAL_FLOATS, dtype=torch.float32, device=params.device)
     status = lib.clv_mlp_loss_grad(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(X.data_ptr()),
                                    ctypes.c_void_p(Y.data_ptr()), X.shape[0], ctypes.c_void_p(st.cuda_stream),
-                                   ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(loss.data_ptr()))
+                                   ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(loss.data_ptr()),
+                                   ctypes.c_void_p(work.data_ptr()))
     if status != 0:
         raise ClvError(status, lib.clv_last_error(None).decode())
     return loss, g
@@ -746,7 +762,9 @@ def mlp_loss_grad(params, X, Y, stream=None):
 
 def mlp_train(params, work, X, Y, iters, batch=8192, lr=1e-3, seed=1, step0=0, stream=None):
     """Adam training of the guess network on the GPU (params/work updated in
-    place); returns the per-step mini-batch losses (device tensor)."""
+    place; work: MLP_TRAIN_WORK_FLOATS floats, zero before the first call);
+    returns the per-step mini-batch losses (device tensor).  Deterministic:
+    the same inputs give the same parameters bit for bit."""
     import torch
     lib = load()
     st = stream if stream is not None else torch.cuda.current_stream(params.device)

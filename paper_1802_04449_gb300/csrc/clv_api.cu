@@ -40,6 +40,7 @@ namespace {
 std::string g_create_error;
 
 constexpr int kNumPrimSets = 3;
+constexpr int kEosXkEntries = 254;   // frexp exponents -125..128 of positive normal floats
 constexpr int kPrimFields = 6;  // e, ux, uy, ueta, P, cs
 
 struct DevStats {
@@ -72,10 +73,12 @@ struct clv_handle {
   bool viscous = false;
   int nblocks = 0;
   // device arrays (typed at use)
-  void* T0[4];
+  void* T0[4];                    // T~ (FP32 path: high parts of the float-float pairs)
   void* PI0[10];
   void* T1[4];
   void* PI1[10];
+  void* TL0[4] = {nullptr, nullptr, nullptr, nullptr};   // FP32 path: low parts of T~ (state)
+  void* TL1[4] = {nullptr, nullptr, nullptr, nullptr};   // and of the stage-1 result
   void* PR[kNumPrimSets][kPrimFields];
   void* NC[2] = {nullptr, nullptr};   // charge = 1: N~^tau of the state and of the stage
   bool charge_on = false;             // clv_set_initial_n since the last initial state
@@ -90,6 +93,7 @@ struct clv_handle {
   DevStats* dstats = nullptr;
   int sms = 148;                  // multiprocessors of the device
   double* tau_dev = nullptr;      // tau of the step on the device (the kernels read it)
+  float* itau_dev = nullptr;      // 1/tau at the end of the step as a float-float pair (FP32 recovery)
   double tau = 0.0;               // host copy, advanced by the same additions
   long long step = 0;
   bool initialized = false;
@@ -187,6 +191,9 @@ clv_status validate(const clv_config* c) {
   return CLV_OK;
 }
 
+// shared memory a block may opt in to on sm_100 / sm_103 (227 KiB)
+constexpr size_t kSmemOptinMax = 232448;
+
 struct TileGeom {
   TileArgs t;
   int threads;
@@ -201,10 +208,16 @@ TileGeom tile_geometry(const clv_config* c, int sms) {
   const int rsize = c->precision == CLV_FP64 ? 8 : 4;
   const int maxthr = rsize == 4 ? CLV_TILE_MAX_THREADS : std::min(CLV_TILE_MAX_THREADS, kBlock / 2);
   const int nk = (c->neta + 31) / 32;
+  const bool visc = c->eta_over_s > 0.0;
   TileGeom g;
   TileArgs& t = g.t;
   t.TK = (c->neta + nk - 1) / nk;
   t.TJ = std::max(1, std::min(c->ny, maxthr / (t.TK + 1) - 1));
+  // fewer rows while the CTA's shared memory exceeds the opt-in limit of a block
+  auto smem_of = [&](int TJ) {
+    return visc ? tile_smem_bytes<true>(TJ, t.TK, rsize) : tile_smem_bytes<false>(TJ, t.TK, rsize);
+  };
+  while (t.TJ > 1 && smem_of(t.TJ) > kSmemOptinMax) --t.TJ;
   t.ntj = (c->ny + t.TJ - 1) / t.TJ;
   t.ntk = (c->neta + t.TK - 1) / t.TK;
   // CLV_TILE_MIN_BLOCKS CTAs per SM: pick the chunking that minimises
@@ -224,8 +237,7 @@ TileGeom tile_geometry(const clv_config* c, int sms) {
   const long long nch = (c->nx + t.CX - 1) / t.CX;
   g.threads = (t.TJ + 1) * (t.TK + 1);
   g.blocks = (unsigned)(tiles * nch);
-  const bool visc = c->eta_over_s > 0.0;
-  g.smem = visc ? tile_smem_bytes<true>(t.TJ, t.TK, rsize) : tile_smem_bytes<false>(t.TJ, t.TK, rsize);
+  g.smem = smem_of(t.TJ);
   return g;
 }
 
@@ -307,6 +319,8 @@ size_t layout(const clv_config* c, clv_handle* h) {
   // field pointers below point at plane 0, so [0, N) is the interior
   const size_t hoff = (size_t)c->halo_x * c->ny * nep * rs;
   const size_t fb = align_up((size_t)N * rs + 2 * hoff, 256);
+  // FP32 path: T~ as float-float pairs (StageParams), the low parts in 2 x 4 more arrays
+  const bool ffT = c->precision != CLV_FP64;
   // block partials of the stats reduction: enough for the direct grid and for
   // the tiled grid on any device (at most 1024 SMs)
   const int nblocks = (int)std::max<long long>((N + kBlock - 1) / kBlock, tile_geometry(c, 1024).blocks);
@@ -319,6 +333,9 @@ size_t layout(const clv_config* c, clv_handle* h) {
   for (int q = 0; q < 10; ++q) oPI1[q] = take(fb);
   for (int s = 0; s < kNumPrimSets; ++s)
     for (int f = 0; f < kPrimFields; ++f) oPR[s][f] = take(fb);
+  size_t oTL0[4] = {0, 0, 0, 0}, oTL1[4] = {0, 0, 0, 0};
+  if (ffT)
+    for (int m = 0; m < 4; ++m) { oTL0[m] = take(fb); oTL1[m] = take(fb); }
   size_t oNC[2] = {0, 0}, oPB[2] = {0, 0};
   if (c->charge)
     for (int t = 0; t < 2; ++t) oNC[t] = take(fb);
@@ -326,16 +343,20 @@ size_t layout(const clv_config* c, clv_handle* h) {
   if (bulk)
     for (int t = 0; t < 2; ++t) oPB[t] = take(fb);
   const int ne = c->eos_kind == CLV_EOS_TABLE ? c->eos_n : 1;
-  oE[0] = take((size_t)4 * ne * rs);  // nodes packed as (P, T, c_s^2, 0)
+  oE[0] = take((size_t)4 * ne * rs + kEosXkEntries * sizeof(float2));  // nodes packed as (P, T, c_s^2, Plo), then xk
   oE[1] = oE[2] = oE[0];
   size_t oMlp = take(kMlpDeviceBytes);
   size_t oStage = take(std::max((size_t)N * 8, (size_t)256));  // also scratch of clv_mlp_samples
   size_t oBlock = take((size_t)nblocks * 8);
   size_t oStats = take(sizeof(DevStats));
-  size_t oTau = take(sizeof(double));
+  size_t oTau = take(4 * sizeof(double));   // tau (double), then 1/tau as two floats
   if (h) {
     char* b = h->ws;
     for (int m = 0; m < 4; ++m) { h->T0[m] = b + oT0[m] + hoff; h->T1[m] = b + oT1[m] + hoff; }
+    for (int m = 0; m < 4; ++m) {
+      h->TL0[m] = ffT ? b + oTL0[m] + hoff : nullptr;
+      h->TL1[m] = ffT ? b + oTL1[m] + hoff : nullptr;
+    }
     for (int q = 0; q < 10; ++q) { h->PI0[q] = b + oPI0[q] + hoff; h->PI1[q] = b + oPI1[q] + hoff; }
     for (int s = 0; s < kNumPrimSets; ++s)
       for (int f = 0; f < kPrimFields; ++f) h->PR[s][f] = b + oPR[s][f] + hoff;
@@ -347,6 +368,7 @@ size_t layout(const clv_config* c, clv_handle* h) {
     h->block_sum = (double*)(b + oBlock);
     h->dstats = (DevStats*)(b + oStats);
     h->tau_dev = (double*)(b + oTau);
+    h->itau_dev = (float*)(b + oTau + 2 * sizeof(double));
     h->nblocks = nblocks;
     h->N = N;
     h->Nc = (long long)c->nx * c->ny * c->neta;
@@ -354,6 +376,13 @@ size_t layout(const clv_config* c, clv_handle* h) {
     h->rsize = (int)rs;
   }
   return off;
+}
+
+// four T~ arrays (or their low parts; nullptr stays nullptr) as a Ptr10
+template <typename R> Ptr10<R> t_arrays(void* const a[4]) {
+  Ptr10<R> t{};
+  for (int m = 0; m < 4; ++m) t.p[m] = (R*)a[m];
+  return t;
 }
 
 template <typename R> Prim<R> prim_set(clv_handle* h, int s) {
@@ -378,6 +407,7 @@ template <typename R> EosView<R> eos_view(const clv_handle* h) {
   const double pi = 3.14159265358979323846;
   v.t_coef = (R)(30.0 * kHbarC * kHbarC * kHbarC / (kDofConformal * pi * pi));
   v.node = (const R*)h->eos[0];
+  v.xk = (const float2*)((const char*)h->eos[0] + (size_t)4 * v.n * sizeof(R));
   return v;
 }
 
@@ -399,6 +429,9 @@ StageParams<R> stage_params(clv_handle* h, int stage) {
     p.T[m] = (const R*)(s1 ? h->T0[m] : h->T1[m]);
     p.Tn[m] = (const R*)h->T0[m];
     p.Tout[m] = (R*)(s1 ? h->T1[m] : h->T0[m]);
+    p.Tl[m] = (const R*)(s1 ? h->TL0[m] : h->TL1[m]);
+    p.Tnl[m] = (const R*)h->TL0[m];
+    p.Toutl[m] = (R*)(s1 ? h->TL1[m] : h->TL0[m]);
   }
   for (int q = 0; q < 10; ++q) {
     p.pi[q] = (const R*)(s1 ? h->PI0[q] : h->PI1[q]);
@@ -414,6 +447,7 @@ StageParams<R> stage_params(clv_handle* h, int stage) {
   p.xhalo = c.halo_x > 0 ? 1 : 0;
   p.N = h->N;
   p.tau_dev = h->tau_dev;
+  p.itau = h->itau_dev;
   p.dtau_d = c.dtau;
   p.cartesian = c.cartesian;
   p.h = (R)c.dtau;
@@ -426,7 +460,7 @@ StageParams<R> stage_params(clv_handle* h, int stage) {
   p.deta_d = c.deta;
   p.is = is_coef<R>(c);
   p.polish_E = (R)(1.01 * c.eps_cut);
-  p.polish_v = (R)0.999;
+  p.polish_v = (R)0.99;   // gamma above ~7: E/eps > ~65, the FP32 eps = E - M v loses digits
   p.block_sum = h->block_sum;
   p.emax_bits = &h->dstats->emax_bits;
   p.counters = h->dstats->counters;
@@ -504,12 +538,27 @@ void launch_stage(clv_handle* h, const StageParams<R>& p, bool timed) {
   if (timed) timing_event(h);
 }
 
-__global__ void set_tau_kernel(double* tau_dev, double tau) { *tau_dev = tau; }
-__global__ void advance_tau_kernel(double* tau_dev, double dtau) { *tau_dev = *tau_dev + dtau; }
+// tau of the step, and 1/tau of the end of the step (tau + dtau; 1 in
+// Cartesian mode) as a float-float pair for the FP32 recovery
+__device__ __forceinline__ void store_itau(float* itau, double tau, double dtau, int cartesian) {
+  const double x = cartesian ? 1.0 : 1.0 / (tau + dtau);
+  const float hi = (float)x;
+  itau[0] = hi;
+  itau[1] = (float)(x - (double)hi);
+}
+__global__ void set_tau_kernel(double* tau_dev, float* itau, double tau, double dtau, int cartesian) {
+  *tau_dev = tau;
+  store_itau(itau, tau, dtau, cartesian);
+}
+__global__ void advance_tau_kernel(double* tau_dev, float* itau, double dtau, int cartesian) {
+  const double t = *tau_dev + dtau;
+  *tau_dev = t;
+  store_itau(itau, t, dtau, cartesian);
+}
 
 void set_tau(clv_handle* h, double tau) {
   h->tau = tau;
-  set_tau_kernel<<<1, 1, 0, h->stream>>>(h->tau_dev, tau);
+  set_tau_kernel<<<1, 1, 0, h->stream>>>(h->tau_dev, h->itau_dev, tau, h->cfg.dtau, h->cfg.cartesian);
 }
 
 // Half of a Heun step: stage 1, or stage 2 with the end-of-step bookkeeping
@@ -539,7 +588,7 @@ void launch_half(clv_handle* h, int stage, bool stats, bool timed) {
     launch_stage<R, VISC, 2, false>(h, p2, timed);
   }
   if (h->charge_on) launch_charge_stage<R>(p2, 2, h->NC[1], h->NC[0], h->NC[0], h->stream);
-  advance_tau_kernel<<<1, 1, 0, h->stream>>>(h->tau_dev, h->cfg.dtau);
+  advance_tau_kernel<<<1, 1, 0, h->stream>>>(h->tau_dev, h->itau_dev, h->cfg.dtau, h->cfg.cartesian);
   std::swap(h->cur, h->prev);
   h->tau = h->tau + h->cfg.dtau;
   h->step += 1;
@@ -609,12 +658,13 @@ cudaGraphExec_t step_pair_graph(clv_handle* h) {
   return ex;
 }
 
-template <typename R> __global__ void stats_scan_kernel(const R* e, const R* T0, long long N, double* block_sum,
-                                                        unsigned long long* emax_bits) {
+// T0l: the low parts of the float-float T~ (FP32 path) or nullptr
+template <typename R> __global__ void stats_scan_kernel(const R* e, const R* T0, const R* T0l, long long N,
+                                                        double* block_sum, unsigned long long* emax_bits) {
   __shared__ double s_sum[kBlock / 32], s_max[kBlock / 32];
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double a = 0.0, b = 0.0;
-  if (c < N) { a = (double)T0[c]; b = (double)e[c]; }
+  if (c < N) { a = (double)T0[c] + (T0l ? (double)T0l[c] : 0.0); b = (double)e[c]; }
   for (int o = 16; o > 0; o >>= 1) {
     a += __shfl_down_sync(0xffffffffu, a, o);
     b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
@@ -643,7 +693,8 @@ template <typename R> clv_status reduce_stats(clv_handle* h, bool scan, clv_stat
   if (scan) {
     CLV_CUDA(h, cudaMemsetAsync(&h->dstats->emax_bits, 0, sizeof(unsigned long long), h->stream));
     stats_scan_kernel<R><<<grid_of(h->N), kBlock, 0, h->stream>>>(
-        (const R*)h->PR[h->cur][0], (const R*)h->T0[0], h->N, h->block_sum, &h->dstats->emax_bits);
+        (const R*)h->PR[h->cur][0], (const R*)h->T0[0], (const R*)h->TL0[0], h->N, h->block_sum,
+        &h->dstats->emax_bits);
     h->stat_blocks = (int)grid_of(h->N);
   }
   finalize_sum_kernel<<<1, 1024, 0, h->stream>>>(h->block_sum, h->stat_blocks, &h->dstats->esum);
@@ -750,8 +801,8 @@ template <typename R> clv_status initial_begin(clv_handle* h) {
   const double taus0 = c.cartesian ? 1.0 : c.tau0;
   set_tau(h, c.tau0);
   h->step = 0;
-  tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(pc, pi0, false, (R*)h->T0[0], (R*)h->T0[1], (R*)h->T0[2],
-                                                 (R*)h->T0[3], taus0, N);
+  tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(pc, pi0, false, t_arrays<R>(h->T0), t_arrays<R>(h->TL0),
+                                                 h->TL0[0] != nullptr, taus0, N);
   if (!h->viscous) {
     CLV_CUDA(h, cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream));
     h->initialized = true;
@@ -772,8 +823,9 @@ template <typename R> clv_status initial_end(clv_handle* h) {
   extrapolate_prev_kernel<R><<<g, kBlock, 0, h->stream>>>(prim_set<R>(h, h->cur), prim_set<R>(h, h->prev), N);
   set_tau(h, c.tau0);
   h->step = 0;
-  tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(prim_set<R>(h, h->cur), pi0, true, (R*)h->T0[0], (R*)h->T0[1],
-                                                 (R*)h->T0[2], (R*)h->T0[3], c.cartesian ? 1.0 : c.tau0, N);
+  tilde_T_kernel<R><<<g, kBlock, 0, h->stream>>>(prim_set<R>(h, h->cur), pi0, true, t_arrays<R>(h->T0),
+                                                 t_arrays<R>(h->TL0), h->TL0[0] != nullptr,
+                                                 c.cartesian ? 1.0 : c.tau0, N);
   CLV_CUDA(h, cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream));
   CLV_CUDA(h, cudaGetLastError());
   h->predictor_pending = false;
@@ -825,7 +877,11 @@ clv_status export_field(clv_handle* h, int which, double* dst, long long off, lo
   else if (which <= 20) src = h->PR[h->prev][1 + (which - 18)];
   else if (which == 23) src = h->PB[0];
   else src = h->NC[0];
-  export_kernel<R><<<grid_of(n), kBlock, 0, h->stream>>>((const R*)src + off, dst, n, ne, nep);
+  if (which >= 4 && which <= 7 && h->TL0[0])   // FP32 path: T~ = high + low parts
+    export_pair_kernel<R><<<grid_of(n), kBlock, 0, h->stream>>>((const R*)src + off,
+                                                                (const R*)h->TL0[which - 4] + off, dst, n, ne, nep);
+  else
+    export_kernel<R><<<grid_of(n), kBlock, 0, h->stream>>>((const R*)src + off, dst, n, ne, nep);
   CLV_CUDA(h, cudaGetLastError());
   return CLV_OK;
 }
@@ -880,7 +936,7 @@ clv_status create_common(const clv_config* cfg, void* stream, void* ws, size_t w
       return fail(nullptr, CLV_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     }
   }
-  // EOS table in the working precision, nodes packed as (P, T, c_s^2, 0)
+  // EOS table in the working precision, nodes packed as (P, T, c_s^2, Plo); Plo = 0 in FP64
   if (cfg->eos_kind == CLV_EOS_TABLE) {
     const int n = cfg->eos_n;
     cudaError_t e;
@@ -894,9 +950,21 @@ clv_status create_common(const clv_config* cfg, void* stream, void* ws, size_t w
       std::vector<float> pk((size_t)4 * n);
       for (int i = 0; i < n; ++i) {
         pk[4 * i] = (float)cfg->eos_P[i]; pk[4 * i + 1] = (float)cfg->eos_T[i];
-        pk[4 * i + 2] = (float)cfg->eos_cs2[i]; pk[4 * i + 3] = 0.f;
+        pk[4 * i + 2] = (float)cfg->eos_cs2[i];
+        pk[4 * i + 3] = (float)(cfg->eos_P[i] - (double)pk[4 * i]);   // the rest of P (EosView)
       }
       e = cudaMemcpy(h->eos[0], pk.data(), pk.size() * 4, cudaMemcpyHostToDevice);
+    }
+    // table positions of the powers of two for the FP32 lookups (EosView::xk)
+    if (e == cudaSuccess) {
+      std::vector<float2> xk(kEosXkEntries);
+      for (int i = 0; i < kEosXkEntries; ++i) {
+        const double x = ((i - 125) * std::log(2.0) - cfg->eos_lne0) / cfg->eos_dlne;
+        const double ip = std::floor(x);
+        xk[i] = make_float2((float)ip, (float)(x - ip));
+      }
+      e = cudaMemcpy((char*)h->eos[0] + (size_t)4 * n * h->rsize, xk.data(), xk.size() * sizeof(float2),
+                     cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) { clv_destroy(h); return fail(nullptr, CLV_ECUDA, cudaGetErrorString(e)); }
   }
@@ -1179,7 +1247,7 @@ clv_status clv_set_mlp(clv_handle* h, const float* params) {
 
 template <typename R> static clv_status mlp_samples_impl(clv_handle* h, float* X, float* Y, int64_t* count) {
   SampleIn<R> a;
-  for (int m = 0; m < 4; ++m) a.T4.p[m] = (R*)h->T0[m];
+  for (int m = 0; m < 4; ++m) { a.T4.p[m] = (R*)h->T0[m]; a.T4l[m] = (const R*)h->TL0[m]; }
   for (int q = 0; q < 10; ++q) a.pi.p[q] = (R*)h->PI0[q];
   a.pr = prim_set<R>(h, h->cur);
   a.viscous = h->viscous;
@@ -1252,19 +1320,22 @@ static clv_status mlp_grad_attr() {
   return CLV_OK;
 }
 
+// blocks of a deterministic gradient launch over `batch` samples
+static int mlp_grad_blocks(long long batch) {
+  return (int)std::min<long long>(kMlpGradBlocks, (batch + kMlpTrainBlock - 1) / kMlpTrainBlock);
+}
+
 clv_status clv_mlp_loss_grad(const float* d_params, const float* d_X, const float* d_Y, int64_t n, void* stream,
-                             float* d_grad, float* d_loss) {
-  if (!d_params || !d_X || !d_Y || !d_grad || !d_loss || n < 1) return fail(nullptr, CLV_EINVAL, "bad arguments");
+                             float* d_grad, float* d_loss, float* d_work) {
+  if (!d_params || !d_X || !d_Y || !d_grad || !d_loss || !d_work || n < 1)
+    return fail(nullptr, CLV_EINVAL, "bad arguments");
   clv_status s = mlp_grad_attr();
   if (s != CLV_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e = cudaMemsetAsync(d_grad, 0, kMlpParams * sizeof(float), st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_loss, 0, sizeof(float), st);
-  if (e != cudaSuccess) return fail(nullptr, CLV_ECUDA, cudaGetErrorString(e));
-  const unsigned blocks = (unsigned)((n + kMlpTrainBlock - 1) / kMlpTrainBlock);
-  mlp_grad_kernel<<<blocks, kMlpTrainBlock, mlp_grad_smem_bytes(), st>>>(d_params, d_X, d_Y, n, n, 0ull, 0, d_grad,
-                                                                        d_loss);
-  e = cudaGetLastError();
+  const int blocks = mlp_grad_blocks(n);
+  mlp_grad_kernel<<<blocks, kMlpTrainBlock, mlp_grad_smem_bytes(), st>>>(d_params, d_X, d_Y, n, n, 0ull, 0, d_work);
+  mlp_reduce_kernel<<<(kMlpPartialRow + 255) / 256, 256, 0, st>>>(d_work, blocks, d_grad, d_loss);
+  cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? CLV_OK : fail(nullptr, CLV_ECUDA, cudaGetErrorString(e));
 }
 
@@ -1278,10 +1349,12 @@ clv_status clv_mlp_train(float* d_params, float* d_work, const float* d_X, const
   float* m = d_work;
   float* v = d_work + kMlpParams;
   float* g = d_work + 2 * kMlpParams;
-  const unsigned blocks = (unsigned)((batch + kMlpTrainBlock - 1) / kMlpTrainBlock);
+  float* partial = d_work + 3 * kMlpParams;
+  const int blocks = mlp_grad_blocks(batch);
   for (int it = 0; it < iters; ++it) {
     mlp_grad_kernel<<<blocks, kMlpTrainBlock, mlp_grad_smem_bytes(), st>>>(d_params, d_X, d_Y, n, batch, seed,
-                                                                          step0 + it, g, d_loss + it);
+                                                                          step0 + it, partial);
+    mlp_reduce_kernel<<<(kMlpPartialRow + 255) / 256, 256, 0, st>>>(partial, blocks, g, d_loss + it);
     mlp_adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(d_params, m, v, g, step0 + it + 1, lr);
   }
   cudaError_t e = cudaGetLastError();
@@ -1375,18 +1448,25 @@ struct StateHeader {
   int64_t step;
 };
 constexpr uint32_t kStateMagic = 0x53564c43u;  // "CLVS"
-constexpr int kStateFields = 4 + 10 + 2 * kPrimFields;
+constexpr uint32_t kStateVersion = 2u;          // 2: the FP32 path's T~ as float-float pairs
+constexpr int kStateFieldsMax = 4 + 4 + 10 + 2 * kPrimFields;
+
+// fields of the checkpoint (FP32 path: the low parts of T~ follow T~)
+static int state_fields(const clv_handle* h) { return kStateFieldsMax - (h->TL0[0] ? 0 : 4); }
 
 static size_t state_bytes(const clv_handle* h) {
-  return sizeof(StateHeader) +
-         (size_t)(kStateFields + (h->cfg.charge ? 1 : 0) + (h->PB[0] ? 1 : 0)) * (size_t)h->N * h->rsize;
+  return sizeof(StateHeader) + (size_t)(state_fields(h) + (h->cfg.charge ? 1 : 0) + (h->PB[0] ? 1 : 0)) *
+                                   (size_t)h->N * h->rsize;
 }
 
-// device arrays of the state in checkpoint order: T~ (4), pi~ (10), the
-// primitives of the current step (6) and of the previous step (6)
-static void state_arrays(clv_handle* h, void* a[kStateFields]) {
+// device arrays of the state in checkpoint order: T~ (4; FP32 path: then its
+// low parts, 4), pi~ (10), the primitives of the current step (6) and of the
+// previous step (6)
+static void state_arrays(clv_handle* h, void* a[kStateFieldsMax]) {
   int k = 0;
   for (int m = 0; m < 4; ++m) a[k++] = h->T0[m];
+  if (h->TL0[0])
+    for (int m = 0; m < 4; ++m) a[k++] = h->TL0[m];
   for (int q = 0; q < 10; ++q) a[k++] = h->PI0[q];
   for (int f = 0; f < kPrimFields; ++f) a[k++] = h->PR[h->cur][f];
   for (int f = 0; f < kPrimFields; ++f) a[k++] = h->PR[h->prev][f];
@@ -1405,21 +1485,24 @@ clv_status clv_get_state(clv_handle* h, void* buf, size_t bytes) {
   const clv_config& c = h->cfg;
   // pad: bit 0 = the net charge is being transported (its field follows the others),
   // bit 1 = the state carries the bulk pressure (its field comes last)
-  StateHeader hd{kStateMagic, 1u, c.nx, c.ny, c.neta, c.precision, h->viscous ? 1 : 0,
+  StateHeader hd{kStateMagic, kStateVersion, c.nx, c.ny, c.neta, c.precision, h->viscous ? 1 : 0,
                  (h->charge_on ? 1 : 0) | (h->PB[0] ? 2 : 0),
                  h->tau, c.dx, c.dy, c.deta, c.dtau, c.eta_over_s, h->step};
   std::memcpy(buf, &hd, sizeof(hd));
-  void* a[kStateFields];
+  void* a[kStateFieldsMax];
   state_arrays(h, a);
   char* dst = static_cast<char*>(buf) + sizeof(hd);
   const size_t fb = (size_t)h->N * h->rsize;
-  for (int k = 0; k < kStateFields; ++k)
-    CLV_CUDA(h, cudaMemcpyAsync(dst + k * fb, a[k], fb, cudaMemcpyDeviceToHost, h->stream));
-  if (c.charge)
-    CLV_CUDA(h, cudaMemcpyAsync(dst + kStateFields * fb, h->NC[0], fb, cudaMemcpyDeviceToHost, h->stream));
+  for (int k = 0; k < state_fields(h); ++k) {
+    CLV_CUDA(h, cudaMemcpyAsync(dst, a[k], fb, cudaMemcpyDeviceToHost, h->stream));
+    dst += fb;
+  }
+  if (c.charge) {
+    CLV_CUDA(h, cudaMemcpyAsync(dst, h->NC[0], fb, cudaMemcpyDeviceToHost, h->stream));
+    dst += fb;
+  }
   if (h->PB[0])   // the bulk pressure follows (after the charge field, if any)
-    CLV_CUDA(h, cudaMemcpyAsync(dst + (kStateFields + (c.charge ? 1 : 0)) * fb, h->PB[0], fb,
-                                cudaMemcpyDeviceToHost, h->stream));
+    CLV_CUDA(h, cudaMemcpyAsync(dst, h->PB[0], fb, cudaMemcpyDeviceToHost, h->stream));
   CLV_CUDA(h, cudaStreamSynchronize(h->stream));
   return CLV_OK;
 }
@@ -1430,7 +1513,8 @@ clv_status clv_set_state(clv_handle* h, const void* buf, size_t bytes) {
   StateHeader hd;
   std::memcpy(&hd, buf, sizeof(hd));
   const clv_config& c = h->cfg;
-  if (hd.magic != kStateMagic || hd.version != 1u) return fail(h, CLV_EINVAL, "not a checkpoint of this library");
+  if (hd.magic != kStateMagic || hd.version != kStateVersion)
+    return fail(h, CLV_EINVAL, "not a checkpoint of this library version");
   if (hd.nx != c.nx || hd.ny != c.ny || hd.neta != c.neta || hd.precision != c.precision ||
       hd.viscous != (h->viscous ? 1 : 0) || hd.dx != c.dx || hd.dy != c.dy || hd.deta != c.deta ||
       hd.dtau != c.dtau || hd.eta_over_s != c.eta_over_s || ((hd.pad >> 1) & 1) != (h->PB[0] ? 1 : 0))
@@ -1438,21 +1522,22 @@ clv_status clv_set_state(clv_handle* h, const void* buf, size_t bytes) {
   if (bytes < state_bytes(h)) return fail(h, CLV_EINVAL, "state buffer too small (clv_state_bytes)");
   h->cur = 0;
   h->prev = 1;
-  void* a[kStateFields];
+  void* a[kStateFieldsMax];
   state_arrays(h, a);
   const char* src = static_cast<const char*>(buf) + sizeof(hd);
   const size_t fb = (size_t)h->N * h->rsize;
-  for (int k = 0; k < kStateFields; ++k)
-    CLV_CUDA(h, cudaMemcpyAsync(a[k], src + k * fb, fb, cudaMemcpyHostToDevice, h->stream));
+  for (int k = 0; k < state_fields(h); ++k) {
+    CLV_CUDA(h, cudaMemcpyAsync(a[k], src, fb, cudaMemcpyHostToDevice, h->stream));
+    src += fb;
+  }
   if (c.charge) {
     const bool on = (hd.pad & 1) != 0;
     if (on != h->charge_on) invalidate_graphs(h);
     h->charge_on = on;
-    CLV_CUDA(h, cudaMemcpyAsync(h->NC[0], src + kStateFields * fb, fb, cudaMemcpyHostToDevice, h->stream));
+    CLV_CUDA(h, cudaMemcpyAsync(h->NC[0], src, fb, cudaMemcpyHostToDevice, h->stream));
+    src += fb;
   }
-  if (h->PB[0])
-    CLV_CUDA(h, cudaMemcpyAsync(h->PB[0], src + (kStateFields + (c.charge ? 1 : 0)) * fb, fb, cudaMemcpyHostToDevice,
-                                h->stream));
+  if (h->PB[0]) CLV_CUDA(h, cudaMemcpyAsync(h->PB[0], src, fb, cudaMemcpyHostToDevice, h->stream));
   CLV_CUDA(h, cudaMemsetAsync(h->dstats, 0, sizeof(DevStats), h->stream));
   set_tau(h, hd.tau);
   CLV_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -1464,13 +1549,13 @@ clv_status clv_set_state(clv_handle* h, const void* buf, size_t bytes) {
 // ---------------- x-slab: halo planes and stage-level stepping ----------------
 }  // extern "C"
 
-template <typename R> struct Ptr19 { R* p[19]; };
+template <typename R> struct Ptr23 { R* p[23]; };
 
 // mode 0: pack planes src, src + 1 of every field into buf [field][2][plane];
 // mode 1: unpack buf into planes dst, dst + 1; mode 2: copy plane src into
 // planes dst, dst + 1 (zero-gradient edge).
 template <typename R>
-__global__ void __launch_bounds__(kBlock) slab_planes_kernel(Ptr19<R> f, int nf, long long plane, long long src,
+__global__ void __launch_bounds__(kBlock) slab_planes_kernel(Ptr23<R> f, int nf, long long plane, long long src,
                                                              long long dst, R* buf, int mode) {
   const long long per = 2 * plane;
   const long long total = per * nf;
@@ -1485,12 +1570,18 @@ __global__ void __launch_bounds__(kBlock) slab_planes_kernel(Ptr19<R> f, int nf,
   }
 }
 
-// The fields a stage reads from its x-neighbours: set 1 (stage 1) T~, pi~ and
-// the current primitives u~, P, c_s; set 2 (stage 2) the stage-1 results.
-template <typename R> static int slab_fields(clv_handle* h, int set, Ptr19<R>& f) {
+// The fields a stage reads from its x-neighbours: set 1 (stage 1) T~ (FP32
+// path: high and low parts), pi~ and the current primitives u~, P, c_s; set 2
+// (stage 2) the stage-1 results.
+static int slab_nfields(const clv_handle* h) {
+  return 4 + (h->TL0[0] ? 4 : 0) + (h->viscous ? 10 : 0) + (kPrimFields - 1);
+}
+template <typename R> static int slab_fields(clv_handle* h, int set, Ptr23<R>& f) {
   int n = 0;
   const int st = 3 - h->cur - h->prev;
   for (int m = 0; m < 4; ++m) f.p[n++] = (R*)(set == 1 ? h->T0[m] : h->T1[m]);
+  if (h->TL0[0])
+    for (int m = 0; m < 4; ++m) f.p[n++] = (R*)(set == 1 ? h->TL0[m] : h->TL1[m]);
   if (h->viscous)
     for (int q = 0; q < 10; ++q) f.p[n++] = (R*)(set == 1 ? h->PI0[q] : h->PI1[q]);
   const int ps = set == 1 ? h->cur : st;
@@ -1499,7 +1590,7 @@ template <typename R> static int slab_fields(clv_handle* h, int set, Ptr19<R>& f
 }
 
 template <typename R> static clv_status slab_op(clv_handle* h, int set, int side, R* buf, int mode) {
-  Ptr19<R> f;
+  Ptr23<R> f;
   const int nf = slab_fields<R>(h, set, f);
   const long long plane = (long long)h->cfg.ny * h->nep;
   const long long nx = h->cfg.nx;
@@ -1525,8 +1616,7 @@ extern "C" {
 
 clv_status clv_slab_halo_bytes(const clv_handle* h, size_t* bytes) {
   if (!h || !bytes) return CLV_EINVAL;
-  const int nf = 4 + (h->viscous ? 10 : 0) + (kPrimFields - 1);
-  *bytes = (size_t)2 * h->cfg.ny * h->nep * nf * h->rsize;
+  *bytes = (size_t)2 * h->cfg.ny * h->nep * slab_nfields(h) * h->rsize;
   return CLV_OK;
 }
 
@@ -1705,6 +1795,11 @@ static TileArgs batch_tile(const clv_config& c, int maxthr_cap, int chunk) {
   const int nk = (c.neta + 31) / 32;
   t.TK = (c.neta + nk - 1) / nk;
   t.TJ = std::max(1, std::min(c.ny, maxthr / (t.TK + 1) - 1));
+  const size_t rsize = c.precision == CLV_FP64 ? 8 : 4;
+  auto smem_of = [&](int TJ) {
+    return c.eta_over_s > 0 ? tile_smem_bytes<true>(TJ, t.TK, rsize) : tile_smem_bytes<false>(TJ, t.TK, rsize);
+  };
+  while (t.TJ > 1 && smem_of(t.TJ) > kSmemOptinMax) --t.TJ;
   const int nch = (c.nx + chunk - 1) / chunk;
   t.CX = (c.nx + nch - 1) / nch;
   t.ntj = (c.ny + t.TJ - 1) / t.TJ;
@@ -1921,11 +2016,12 @@ clv_status clv_batch_event_stats(clv_handle* h, int event, clv_stats* out) {
   CLV_CUDA(h, cudaMemsetAsync(&h->dstats->emax_bits, 0, sizeof(unsigned long long), h->stream));
   if (h->rsize == 8) {
     stats_scan_kernel<double><<<g, kBlock, 0, h->stream>>>((const double*)h->PR[h->cur][0] + ev.off,
-                                                           (const double*)h->T0[0] + ev.off, ev.N, h->block_sum,
-                                                           &h->dstats->emax_bits);
+                                                           (const double*)h->T0[0] + ev.off, nullptr, ev.N,
+                                                           h->block_sum, &h->dstats->emax_bits);
   } else {
     stats_scan_kernel<float><<<g, kBlock, 0, h->stream>>>((const float*)h->PR[h->cur][0] + ev.off,
-                                                          (const float*)h->T0[0] + ev.off, ev.N, h->block_sum,
+                                                          (const float*)h->T0[0] + ev.off,
+                                                          (const float*)h->TL0[0] + ev.off, ev.N, h->block_sum,
                                                           &h->dstats->emax_bits);
   }
   h->stat_blocks = (int)g;

@@ -107,9 +107,10 @@ __global__ void __launch_bounds__(kBlock) bulk_stage_kernel(const StageParams<R>
   const R Pc = Pin[c];
   S += -Pc * (T * inv_5zs_hbarc) - (e + P) * theta * R(0.2) - Pc * theta * (R(1) / R(3)) - ts.geo * ut * Pc;
   R Pnew = STAGE == 1 ? (utn * Pn[c] + p.h * S) / uts : R(0.5) * (utn * Pn[c] + uts * Pc + p.h * S) / ut;
-  // regulator (eps and P of the stage's input)
-  if (e < R(kViscEpsMin)) Pnew = R(0);
-  else if (Pnew > P) Pnew = P;
+  // regulator (eps and P of the stage's input): the ramp of the shear
+  // regulator, then |Pi| <= P
+  Pnew *= visc_ramp(e);
+  if (Pnew > P) Pnew = P;
   else if (Pnew < -P) Pnew = -P;
   Pout[c] = Pnew;
 }

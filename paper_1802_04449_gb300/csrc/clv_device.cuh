@@ -49,18 +49,25 @@ template <typename R> struct EosView {
   R e0, e_top;             // eps of node 0 and of the last node
   R t_coef;                // conformal: T^4 = t_coef * e
   R top;                   // n - 1 as R
-  const R* node;           // table nodes packed as (P, T, c_s^2, 0), 4 values per node
+  const R* node;           // table nodes packed as (P, T, c_s^2, Plo), 4 values per node (Node)
+  // FP32 table lookups: for e = m 2^ex (frexp, m in [0.5, 1)), entry ex + 125
+  // holds (ex ln 2 - lne0)/dlne, formed in FP64 on the host and split into its
+  // integer part and its fraction (ex in [-125, 128]: every positive normal float)
+  const float2* xk;
 };
 
-template <typename R> struct Node { R P, T, c2; };
+// Node k: P, T, c_s^2 and, in the FP32 table, Plo = P - (float)P (the rest of
+// the FP64 pressure, so that the interpolated P carries no rounding of the
+// node values: P enters every flux and the root solve); 0 in FP64.
+template <typename R> struct Node { R P, T, c2, Plo; };
 __device__ __forceinline__ Node<float> load_node(const float* base, int k) {
   const float4 v = __ldg(reinterpret_cast<const float4*>(base) + k);
-  return {v.x, v.y, v.z};
+  return {v.x, v.y, v.z, v.w};
 }
 __device__ __forceinline__ Node<double> load_node(const double* base, int k) {
   const double2 a = __ldg(reinterpret_cast<const double2*>(base) + 2 * k);
   const double2 b = __ldg(reinterpret_cast<const double2*>(base) + 2 * k + 1);
-  return {a.x, a.y, b.x};
+  return {a.x, a.y, b.x, 0.0};
 }
 
 // Evaluate in arithmetic type C (C may be wider than the table type R).
@@ -78,8 +85,35 @@ __device__ __forceinline__ void eos_eval(const EosView<R>& q, C e, C& P, C& T, C
     cs2 = C(load_node(q.node, 0).c2);
     return;
   }
-  C x = (Fast<C>::log(e) - C(q.lne0)) * C(q.inv_dlne);
-  if (x < C(0)) {
+  int k;
+  C w;
+  if constexpr (sizeof(C) == 4 && sizeof(R) == 4) {
+    // The table position x = (ln e - lne0)/dlne runs up to n - 1 (4095), where
+    // an FP32 x keeps only ~2e-4 of a node interval: P would carry ~1e-6
+    // relative noise from the lookup alone.  So x is never formed as one
+    // float: x = xk[ex] + ln(m)/dlne with ln(m) in (-0.7, 0] to ~1e-7, and the
+    // fraction of the sum is exact to ~1e-5 of a node interval.
+    int ex;
+    const float m = frexpf(e, &ex);
+    if (ex < -125) {
+      k = -1;
+      w = C(0);
+    } else if (ex > 128) {
+      k = q.n;
+      w = C(0);
+    } else {
+      const float2 tk = __ldg(q.xk + (ex + 125));
+      const float s = tk.y + logf(m) * q.inv_dlne;
+      const float fs = floorf(s);
+      k = (int)tk.x + (int)fs;
+      w = s - fs;
+    }
+  } else {
+    const C x = (Fast<C>::log(e) - C(q.lne0)) * C(q.inv_dlne);
+    k = x < C(0) ? -1 : (int)x;
+    w = x - C(k);
+  }
+  if (k < 0) {
     const Node<R> a = load_node(q.node, 0);
     C r = e / C(q.e0);
     P = C(a.P) * r;
@@ -87,18 +121,16 @@ __device__ __forceinline__ void eos_eval(const EosView<R>& q, C e, C& P, C& T, C
     cs2 = C(a.c2);
     return;
   }
-  if (x >= C(q.top)) {
+  if (k >= q.n - 1) {
     const Node<R> a = load_node(q.node, q.n - 1);
     P = C(a.P) + (e - C(q.e_top)) * C(1.0 / 3.0);
     T = C(a.T) * sqrt(sqrt(e / C(q.e_top)));
     cs2 = C(1.0 / 3.0);
     return;
   }
-  int k = (int)x;
-  if (k > q.n - 2) k = q.n - 2;
-  C w = x - C(k);
   const Node<R> a = load_node(q.node, k), b = load_node(q.node, k + 1);
   P = C(a.P) + w * (C(b.P) - C(a.P));
+  if constexpr (sizeof(R) == 4) P += C(a.Plo) + w * (C(b.Plo) - C(a.Plo));
   T = C(a.T) + w * (C(b.T) - C(a.T));
   cs2 = C(a.c2) + w * (C(b.c2) - C(a.c2));
 }
@@ -108,9 +140,15 @@ __device__ __forceinline__ void eos_eval(const EosView<R>& q, C e, C& P, C& T, C
 // f(v) = v - M/(E + P(E - M v)) on [0, M/E] by Newton steps kept inside a
 // shrinking bracket (bisection when a step leaves it).
 // ---------------------------------------------------------------------------
+// M above (1 - kMaxMoverE) E is rescaled onto that bound before the solve, so
+// the flow's Lorentz factor stays below ~22.  The bound only acts in the
+// dilute, ultra-relativistic fringe of an expanding event, where E/eps grows
+// as gamma^2 and eps = E - M v is ill-conditioned.
+constexpr double kMaxMoverE = 1e-3;
+
 struct RootResult {
   int iters;      // -1: cap reached
-  int rescaled;   // |M| > (1-1e-6) E was rescaled
+  int rescaled;   // |M| > (1 - kMaxMoverE) E was rescaled
 };
 
 // Division and square root for the FP64 refinement of the FP32 path: an FP32
@@ -183,7 +221,7 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
   if (!(E >= eps_cut)) return rr;
   C M2 = Mx * Mx + My * My + Me * Me;
   C M = Ops::sqrt_(M2);
-  C Mcap = C(1.0 - 1e-6) * E;
+  C Mcap = C(1.0 - kMaxMoverE) * E;
   if (M > Mcap) {
     C s = Ops::div(Mcap, M);
     Mx *= s; My *= s; Me *= s;
@@ -255,6 +293,62 @@ __device__ __forceinline__ RootResult solve_primitive(const EosView<R>& q, C eps
   ue = s * Me;
   return rr;
 }
+
+// ---------------------------------------------------------------------------
+// Float-float ("double-single") arithmetic: a value held as hi + lo with
+// |lo| <= ulp(hi)/2, about 48 significant bits, computed on the FP32 pipes
+// (GB300's FP64 rate is a small fraction of its FP32 rate).  Error-free
+// transformations: Knuth's two-sum, Dekker's fast two-sum (|a| >= |b|) and
+// the FMA-based exact product.  Sums and products are written so that the
+// compiler cannot fuse them (explicit fmaf and __fmul_rn where it matters).
+// ---------------------------------------------------------------------------
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ ff ff_fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// (a.hi + a.lo) + b
+__device__ __forceinline__ ff ff_add(ff a, float b) {
+  ff s = ff_two_sum(a.hi, b);
+  return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  ff s = ff_two_sum(a.hi, b.hi);
+  return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_mul(ff a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = fmaf(a.lo, b, fmaf(a.hi, b, -p));
+  return ff_fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+  if (!(a.hi > 0.f)) return {0.f, 0.f};
+  const float s = sqrtf(a.hi);
+  // one Newton correction: s + (a - s^2)/(2 s), the residual exact by FMA
+  const float r = __fadd_rn(fmaf(-s, s, a.hi), a.lo);
+  return ff_fast_two_sum(s, r / (2.f * s));
+}
+__device__ __forceinline__ ff ff_of(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return (double)a.hi + (double)a.lo; }
 
 // Asynchronous global -> shared copies (cp.async, 4 or 8 bytes per element).
 __device__ __forceinline__ void cp_async_elem(float* smem, const float* gmem) {

@@ -29,18 +29,31 @@ template <typename R> struct IsCoef {
   R lambda1_hat;
 };
 
+// T~^{tau mu} keeps ~48 significant bits on the FP32 path: a float-float pair
+// T~ = T + Tl (high parts T, low parts Tl, both float arrays).  It is the
+// conserved energy-momentum that every stage accumulates into; in the dilute,
+// fast-moving edge of an event the rest-frame density eps = E - M v is a
+// small difference of its components (E/eps ~ gamma^2), so plain FP32
+// storage of T~ turned its rounding into percent-level errors of eps there
+// after a few hundred steps.  The stencil reads the high parts (fluxes and
+// sources stay FP32); the update adds the FP32 increment to the pair exactly,
+// and the recovery forms E and M from the pair.  The FP64 path stores T~ in
+// T and leaves Tl unused.
 template <typename R> struct StageParams {
   // fields of the stage being differentiated (stage 1: step n, stage 2: stage-1 result)
   const R* T[4];
+  const R* Tl[4];
   const R* pi[10];
   Prim<R> pr;
   // own-cell inputs: T~ and pi~ at step n, u~ at n and n-1
   const R* Tn[4];
+  const R* Tnl[4];
   const R* pin[10];
   const R* un[3];
   const R* up[3];
   // outputs (stage 2 writes T and pi in place over Tn/pin, prim over the n-1 set)
   R* Tout[4];
+  R* Toutl[4];
   R* piout[10];
   Prim<R> prout;
   EosView<R> eos;
@@ -52,6 +65,7 @@ template <typename R> struct StageParams {
   // step), so the launches of a step do not depend on it and a captured step
   // replays unchanged; tau_scalars() forms the stage's tau factors from it
   const double* tau_dev;
+  const float* itau;   // FP32 path: 1/tau at the end of the step (Cartesian: 1) as a float-float pair
   double dtau_d;
   int cartesian;
   // scalars in the working precision
@@ -160,11 +174,16 @@ __device__ __forceinline__ void interface_flux(const R* L, const R* Rr, R csl, R
 
 // Shear regulator (the paper is silent; without a bound the dilute,
 // ultra-relativistic edge of a viscous event runs away).  With eps and P of
-// the stage's input state of the cell: pi~ = 0 where eps < kViscEpsMin (ideal
-// flow far below freeze-out densities); otherwise pi~ is scaled so that
+// the stage's input state of the cell: pi~ is scaled by the ramp
+// r(eps) = clamp(eps/kViscEpsMin - 1, 0, 1) (zero below kViscEpsMin, ideal
+// flow far below freeze-out densities; continuous, so that rounding-level
+// changes of eps change pi~ at the rounding level), then so that
 // |pi_{mu nu} pi^{mu nu}| <= kRhoMax^2 (eps^2 + 3 P^2).
 constexpr double kRhoMax = 1.0;
 constexpr double kViscEpsMin = 1e-3;   // GeV/fm^3
+template <typename R> __device__ __forceinline__ R visc_ramp(R e) {
+  return fmin(fmax(e * R(1.0 / kViscEpsMin) - R(1), R(0)), R(1));
+}
 // FP64 refinement of the FP32 root solve (E - M v, the Newton step and gamma
 // in FP64 around the FP32 table lookup).  A converged FP32 root starts
 // kPolishSteps FP64 Newton steps (it lies in the quadratic basin; the FP32
@@ -174,28 +193,107 @@ constexpr double kViscEpsMin = 1e-3;   // GeV/fm^3
 constexpr int kPolishSteps = 2;
 // Below this fraction of eps_cut an FP32 eps is vacuum for certain (no refinement).
 constexpr double kVacuumSure = 0.999;
+// E and M come in FP64 (formed from the FP64 T~), so the refined root sees
+// no FP32 rounding of its inputs.
 template <typename R>
-__device__ __forceinline__ int polish_root(const StageParams<R>& p, R E, R Mx, R My, R Me, R v32, bool converged,
-                                           R& en, R& ux, R& uy, R& ue, R Pb) {
+__device__ __forceinline__ int polish_root(const StageParams<R>& p, double E, double Mx, double My, double Me, R v32,
+                                           bool converged, R& en, R& ux, R& uy, R& ue, R Pb) {
   double dv = converged ? (double)v32 : -1.0, de, dux, duy, due;
   RootResult r2;
   if (converged)
-    r2 = solve_primitive<double, R, float, true>(p.eos, p.eps_cut_d, (double)E, (double)Mx, (double)My, (double)Me,
-                                                 1e-13, kPolishSteps, de, dux, duy, due, &dv, nullptr, (double)Pb);
+    r2 = solve_primitive<double, R, float, true>(p.eos, p.eps_cut_d, E, Mx, My, Me, 1e-13, kPolishSteps, de, dux, duy,
+                                                 due, &dv, nullptr, (double)Pb);
   else
-    r2 = solve_primitive<double, R, float>(p.eos, p.eps_cut_d, (double)E, (double)Mx, (double)My, (double)Me, 1e-13,
-                                           100, de, dux, duy, due, &dv, nullptr, (double)Pb);
+    r2 = solve_primitive<double, R, float>(p.eos, p.eps_cut_d, E, Mx, My, Me, 1e-13, 100, de, dux, duy, due, &dv,
+                                           nullptr, (double)Pb);
   en = R(de); ux = R(dux); uy = R(duy); ue = R(due);
   return r2.iters;
 }
 
+// Ideal part of the stage's T~ for the root solve (Sec. 3): E = T~^{tau tau}/tau
+// - pi~^{tau tau}, M^i = T~^{tau i}/tau - pi~^{tau i}.  FP32 path: from the
+// float-floats T~ and 1/tau as float-float pairs (E, M unrounded for the
+// correction step, their high parts for the FP32 solve); FP64 path: in R.
+template <typename R, bool VISC> struct IdealPart {
+  ff E, M[3];     // FP32 path
+  R e, m[3];      // rounded to R (the FP64 path's values)
+};
+template <typename R, bool VISC>
+__device__ __forceinline__ IdealPart<R, VISC> ideal_part(const StageParams<R>& p, const R Tv[4], const R Tlv[4],
+                                                        const R pi4[4], R tn) {
+  IdealPart<R, VISC> a;
+  if constexpr (sizeof(R) == 4) {
+    const ff itn{p.itau[0], p.itau[1]};
+    a.E = ff_mul(ff{Tv[0], Tlv[0]}, itn);
+    if constexpr (VISC) a.E = ff_add(a.E, -pi4[0]);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      a.M[i] = ff_mul(ff{Tv[1 + i], Tlv[1 + i]}, itn);
+      if constexpr (VISC) a.M[i] = ff_add(a.M[i], -pi4[1 + i]);
+    }
+    a.e = a.E.hi;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) a.m[i] = a.M[i].hi;
+  } else {
+    const R itn = R(1) / tn;
+    a.e = Tv[0] * itn;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) a.m[i] = Tv[1 + i] * itn;
+    if constexpr (VISC) {
+      a.e -= pi4[0];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) a.m[i] -= pi4[1 + i];
+    }
+  }
+  return a;
+}
+
+// One Newton step of the root solve from a converged FP32 root in
+// float-float arithmetic (FP32 path; cells below the FP64 refinement's
+// velocity threshold, so M < (1 - kMaxMoverE) E and no rescaling applies).
+// In the FP32 solve E, M and the residual v (E + P) - M carry FP32 rounding,
+// which leaves eps = E - M v with a relative error of ~1e-7 E/eps (E/eps
+// grows as gamma^2).  Here E and M come unrounded from the float-float T~,
+// eps = E - M v and the residual are formed in float-float around the FP32
+// table lookup, and only the correction itself is divided in FP32.  Returns
+// false (outputs untouched) if the corrected eps falls below the cut, which
+// the refinement window near the cut would have caught first.
+__device__ __forceinline__ bool correct_root(const EosView<float>& eos, const ff& E, const ff Mc[3], float v32,
+                                             float Pb, float eps_cut, float& en, float& ux, float& uy, float& ue,
+                                             EosAtRoot<float>& at) {
+  const ff M2 = ff_add(ff_add(ff_mul(Mc[0], Mc[0]), ff_mul(Mc[1], Mc[1])), ff_mul(Mc[2], Mc[2]));
+  const ff M = ff_sqrt(M2);
+  const ff e0 = ff_add(E, ff_neg(ff_mul(M, v32)));
+  float P, T, cs2;
+  eos_eval<float, float>(eos, e0.hi, P, T, cs2);
+  float dPde = cs2;
+  P += Pb;
+  if (P < 0.f) { P = 0.f; dPde = 0.f; }
+  const ff den = ff_add(E, P);
+  const ff g = ff_add(ff_mul(den, v32), ff_neg(M));
+  const float dv = -(den.hi * g.hi) / (den.hi * den.hi - dPde * M2.hi);
+  const ff v = ff_fast_two_sum(v32, dv);
+  const ff e = ff_add(E, ff_neg(ff_mul(M, v)));
+  const float ef = __fadd_rn(e.hi, e.lo);
+  if (!(ef >= eps_cut)) return false;
+  const ff w = ff_add(ff_neg(ff_mul(v, v)), 1.f);   // 1 - v^2
+  const float s = v.hi / (sqrtf(__fadd_rn(w.hi, w.lo)) * M.hi);   // gamma v / M
+  en = ef;
+  ux = s * Mc[0].hi;
+  uy = s * Mc[1].hi;
+  ue = s * Mc[2].hi;
+  at.valid = true;
+  at.P = P + dPde * ff_add(e, ff_neg(e0)).hi;
+  at.cs2 = cs2;
+  return true;
+}
+
 template <typename R>
 __device__ __forceinline__ void regulate_shear(R e, R P, R* pi) {
-  if (e < R(kViscEpsMin)) {
+  const R r = visc_ramp(e);
 #pragma unroll
-    for (int q = 0; q < 10; ++q) pi[q] = R(0);
-    return;
-  }
+  for (int q = 0; q < 10; ++q) pi[q] *= r;
+  if (r == R(0)) return;
   const R pp = pi[0] * pi[0] - R(2) * (pi[1] * pi[1] + pi[2] * pi[2] + pi[3] * pi[3]) + pi[4] * pi[4] +
                pi[7] * pi[7] + pi[9] * pi[9] + R(2) * (pi[5] * pi[5] + pi[6] * pi[6] + pi[8] * pi[8]);
   const R bound2 = R(kRhoMax * kRhoMax) * (e * e + R(3) * P * P);
@@ -418,11 +516,21 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       for (int q = 0; q < 10; ++q) S[4 + q] += Spi[q];
     }
     // ---------------- stage update (Sec. 3) ----------------
+    // FP32 path: the increment h S added exactly to the float-float T~
+    // (Tnl: the new low parts)
     const R h = p.h;
-    R Tnew[4], pinew[10];
+    R Tnew[4], Tnl[4], pinew[10];
     if constexpr (STAGE == 1) {
 #pragma unroll
-      for (int m = 0; m < 4; ++m) Tnew[m] = p.T[m][c] + h * S[m];
+      for (int m = 0; m < 4; ++m) {
+        if constexpr (sizeof(R) == 4) {
+          const ff s = ff_add(ff{p.T[m][c], p.Tl[m][c]}, mul_rn(h, S[m]));
+          Tnew[m] = s.hi;
+          Tnl[m] = s.lo;
+        } else {
+          Tnew[m] = p.T[m][c] + h * S[m];
+        }
+      }
       if constexpr (VISC) {
         const R inv = R(1) / ustar0;
 #pragma unroll
@@ -431,7 +539,15 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       }
     } else {
 #pragma unroll
-      for (int m = 0; m < 4; ++m) Tnew[m] = R(0.5) * (p.Tn[m][c] + p.T[m][c] + h * S[m]);
+      for (int m = 0; m < 4; ++m) {
+        if constexpr (sizeof(R) == 4) {
+          const ff s = ff_add(ff_add(ff{p.Tn[m][c], p.Tnl[m][c]}, ff{p.T[m][c], p.Tl[m][c]}), mul_rn(h, S[m]));
+          Tnew[m] = 0.5f * s.hi;
+          Tnl[m] = 0.5f * s.lo;
+        } else {
+          Tnew[m] = R(0.5) * (p.Tn[m][c] + p.T[m][c] + h * S[m]);
+        }
+      }
       if constexpr (VISC) {
         const R inv = R(0.5) / u[0];
 #pragma unroll
@@ -440,11 +556,13 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
       }
     }
     // ---------------- primitive recovery from T_ideal = T - pi ----------------
-    const R tn = tau_scalars(p, 1).taus_new;
-    R E = Tnew[0] / tn, Mx = Tnew[1] / tn, My = Tnew[2] / tn, Me = Tnew[3] / tn;
+    R pi4[4] = {R(0), R(0), R(0), R(0)};
     if constexpr (VISC) {
-      E -= pinew[0]; Mx -= pinew[1]; My -= pinew[2]; Me -= pinew[3];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) pi4[m] = pinew[m];
     }
+    const IdealPart<R, VISC> ip = ideal_part<R, VISC>(p, Tnew, Tnl, pi4, tau_scalars(p, 1).taus_new);
+    const R E = ip.e, Mx = ip.m[0], My = ip.m[1], Me = ip.m[2];
     R en = R(0), ux = R(0), uy = R(0), ue = R(0);
     R Pb = p.Pib ? p.Pib[c] : R(0);   // bulk pressure of the stage's output
     if (!(isfinite(E) && isfinite(Mx) && isfinite(My) && isfinite(Me))) {
@@ -462,8 +580,12 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
         const R eraw = E - M * vg;   // the FP32 eps before the vacuum decision
         const bool near_cut = eraw < p.polish_E && eraw > R(kVacuumSure) * p.eps_cut;
         if (E >= p.eps_cut && M > R(0) && (near_cut || M > p.polish_v * E || rr.iters < 0)) {
-          rr.iters = polish_root<R>(p, E, Mx, My, Me, vg, rr.iters >= 0, en, ux, uy, ue, Pb);
+          rr.iters = polish_root<R>(p, ff_to_double(ip.E), ff_to_double(ip.M[0]), ff_to_double(ip.M[1]),
+                                    ff_to_double(ip.M[2]), vg, rr.iters >= 0, en, ux, uy, ue, Pb);
           f_polished = true;
+        } else if (en > R(0) && M > R(0)) {   // every other moving cell: one float-float Newton step
+          EosAtRoot<R> unused{false, R(0), R(0)};
+          correct_root(p.eos, ip.E, ip.M, vg, Pb, p.eps_cut, en, ux, uy, ue, unused);
         }
       }
       f_fail = rr.iters < 0;
@@ -476,6 +598,10 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
     eos_eval<R, R>(p.eos, en, Pn, Tn_, c2n);
 #pragma unroll
     for (int m = 0; m < 4; ++m) p.Tout[m][c] = Tnew[m];
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) p.Toutl[m][c] = Tnl[m];
+    }
     if constexpr (VISC) {
       const bool vac = !(en > R(0));
 #pragma unroll
@@ -490,7 +616,7 @@ __global__ void __launch_bounds__(kBlock) stage_kernel(const StageParams<R> p) {
     p.prout.u[2][c] = ue;
     p.prout.P[c] = Pn;
     p.prout.cs[c] = sqrt(c2n);
-    my_T0 = (double)Tnew[0];
+    my_T0 = (double)Tnew[0] + (sizeof(R) == 4 ? (double)Tnl[0] : 0.0);
     my_e = (double)en;
   }
   // ---------------- counters and reductions ----------------
@@ -549,15 +675,26 @@ __global__ void __launch_bounds__(kBlock, RecoverMinBlocks<R>::value) recover_ke
   int my_iters = 0, my_solved = 0, my_polish_iters = 0;
   bool f_rescaled = false, f_fail = false, f_polished = false, f_nonfinite = false, f_nonconv = false;
   const R tn = tau_scalars(p, 1).taus_new;
-  R T0v = R(0), E = R(0), Mx = R(0), My = R(0), Me = R(0);
+  // the ideal part E, M of the new T~ (FP32 path: unrounded float-floats for
+  // the correction step, their high parts for the FP32 solve)
+  double T0v = 0.0;
+  IdealPart<R, VISC> ip{};
   if (active) {
-    T0v = p.Tout[0][c];
-    const R itn = R(1) / tn;
-    E = T0v * itn; Mx = p.Tout[1][c] * itn; My = p.Tout[2][c] * itn; Me = p.Tout[3][c] * itn;
-    if constexpr (VISC) {
-      E -= p.piout[0][c]; Mx -= p.piout[1][c]; My -= p.piout[2][c]; Me -= p.piout[3][c];
+    R Tv[4], Tlv[4] = {R(0), R(0), R(0), R(0)}, pi4[4] = {R(0), R(0), R(0), R(0)};
+#pragma unroll
+    for (int m = 0; m < 4; ++m) Tv[m] = p.Tout[m][c];
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) Tlv[m] = p.Toutl[m][c];
     }
+    if constexpr (VISC) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) pi4[m] = p.piout[m][c];
+    }
+    T0v = (double)Tv[0] + (double)Tlv[0];
+    ip = ideal_part<R, VISC>(p, Tv, Tlv, pi4, tn);
   }
+  const R E = ip.e, Mx = ip.m[0], My = ip.m[1], Me = ip.m[2];
   // initial guess for |v|
   R vg = R(-1);
   if constexpr (GUESS == kGuessMlp && sizeof(R) == 4) {
@@ -620,10 +757,13 @@ __global__ void __launch_bounds__(kBlock, RecoverMinBlocks<R>::value) recover_ke
         const R eraw = E - M * vg;
         const bool near_cut = eraw < p.polish_E && eraw > R(kVacuumSure) * p.eps_cut;
         if (E >= p.eps_cut && M > R(0) && (near_cut || M > p.polish_v * E || rr.iters < 0)) {
-          rr.iters = polish_root<R>(p, E, Mx, My, Me, vg, rr.iters >= 0, en, ux, uy, ue, Pb);
+          rr.iters = polish_root<R>(p, ff_to_double(ip.E), ff_to_double(ip.M[0]), ff_to_double(ip.M[1]),
+                                    ff_to_double(ip.M[2]), vg, rr.iters >= 0, en, ux, uy, ue, Pb);
           my_polish_iters = rr.iters > 0 ? rr.iters : 0;
           f_polished = true;
           at_root.valid = false;   // the refined root: evaluate the table afresh
+        } else if (en > R(0) && M > R(0)) {   // every other moving cell: one float-float Newton step
+          correct_root(p.eos, ip.E, ip.M, vg, Pb, p.eps_cut, en, ux, uy, ue, at_root);
         }
       }
       f_fail = rr.iters < 0;
@@ -658,7 +798,7 @@ __global__ void __launch_bounds__(kBlock, RecoverMinBlocks<R>::value) recover_ke
         for (int q = 0; q < 10; ++q) p.piout[q][c] = R(0);
       }
     }
-    my_T0 = (double)T0v;
+    my_T0 = T0v;
     my_e = (double)en;
   }
   const unsigned full = 0xffffffffu;
@@ -720,7 +860,9 @@ __global__ void __launch_bounds__(kBlock, RecoverMinBlocks<R>::value) recover_ke
 // compacted in cell order.  WRITE = false counts the rows of each block into
 // counts[blockIdx]; WRITE = true writes them from the exclusive offsets.
 template <typename R> struct SampleIn {
-  Ptr10<R> T4, pi;
+  Ptr10<R> T4;    // T~ (FP32 path: high parts)
+  const R* T4l[4];   // FP32 path: low parts of T~ (nullptr in FP64)
+  Ptr10<R> pi;
   Prim<R> pr;
   bool viscous;
   R taus, eps_cut;
@@ -729,7 +871,10 @@ template <typename R> struct SampleIn {
 
 template <typename R>
 __device__ __forceinline__ bool sample_of(const SampleIn<R>& a, long long c, float* x, float* y) {
-  R E = a.T4.p[0][c] / a.taus, Mx = a.T4.p[1][c] / a.taus, My = a.T4.p[2][c] / a.taus, Me = a.T4.p[3][c] / a.taus;
+  R Tv[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) Tv[m] = a.T4.p[m][c] + (a.T4l[m] ? a.T4l[m][c] : R(0));
+  R E = Tv[0] / a.taus, Mx = Tv[1] / a.taus, My = Tv[2] / a.taus, Me = Tv[3] / a.taus;
   R pij[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
   if (a.viscous) {
     E -= a.pi.p[0][c]; Mx -= a.pi.p[1][c]; My -= a.pi.p[2][c]; Me -= a.pi.p[3][c];
@@ -801,20 +946,27 @@ static __global__ void __launch_bounds__(kBlock) scan_counts_kernel(const unsign
   for (int i = lo; i < hi; ++i) { offsets[i] = run; run += counts[i]; }
 }
 
-// T~^{tau mu} = tau [(e + P) u^tau u^mu - P g~^{tau mu} + pi~^{tau mu}]
+// T~^{tau mu} = tau [(e + P) u^tau u^mu - P g~^{tau mu} + pi~^{tau mu}], in
+// FP64 from the stored primitives; written as R, and (FP32 path, lo != null)
+// as float-float pairs: high parts T, low parts lo
 template <typename R>
-__global__ void __launch_bounds__(kBlock) tilde_T_kernel(Prim<R> pr, Ptr10<R> pi, bool with_pi, R* T0,
-                                                         R* T1, R* T2, R* T3, double taus, long long N) {
+__global__ void __launch_bounds__(kBlock) tilde_T_kernel(Prim<R> pr, Ptr10<R> pi, bool with_pi, Ptr10<R> T,
+                                                         Ptr10<R> lo, bool with_lo, double taus, long long N) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
-  const R e = pr.e[c], P = pr.P[c];
-  const R u1 = pr.u[0][c], u2 = pr.u[1][c], u3 = pr.u[2][c];
-  const R u0 = sqrt(R(1) + u1 * u1 + u2 * u2 + u3 * u3);
-  const R w = (e + P) * u0;
-  R a0 = w * u0 - P, a1 = w * u1, a2 = w * u2, a3 = w * u3;
-  if (with_pi) { a0 += pi.p[0][c]; a1 += pi.p[1][c]; a2 += pi.p[2][c]; a3 += pi.p[3][c]; }
-  const R ts = R(taus);
-  T0[c] = ts * a0; T1[c] = ts * a1; T2[c] = ts * a2; T3[c] = ts * a3;
+  const double e = pr.e[c], P = pr.P[c];
+  const double u1 = pr.u[0][c], u2 = pr.u[1][c], u3 = pr.u[2][c];
+  const double u0 = sqrt(1.0 + u1 * u1 + u2 * u2 + u3 * u3);
+  const double w = (e + P) * u0;
+  double a0 = w * u0 - P, a1 = w * u1, a2 = w * u2, a3 = w * u3;
+  if (with_pi) { a0 += (double)pi.p[0][c]; a1 += (double)pi.p[1][c]; a2 += (double)pi.p[2][c]; a3 += (double)pi.p[3][c]; }
+  const double v[4] = {taus * a0, taus * a1, taus * a2, taus * a3};
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const R hi = (R)v[m];
+    T.p[m][c] = hi;
+    if (with_lo) lo.p[m][c] = (R)(v[m] - (double)hi);
+  }
 }
 
 // Initial primitives (already converted to R in pr.e and pr.u): vacuum below
@@ -861,6 +1013,17 @@ template <typename R>
 __global__ void __launch_bounds__(kBlock) export_kernel(const R* src, double* dst, long long N, int ne, int nep) {
   const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c < N) dst[c] = (double)src[padded_index(c, ne, nep)];
+}
+
+// a float-float field (high and low parts) as compact doubles
+template <typename R>
+__global__ void __launch_bounds__(kBlock) export_pair_kernel(const R* hi, const R* lo, double* dst, long long N, int ne,
+                                                             int nep) {
+  const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < N) {
+    const long long k = padded_index(c, ne, nep);
+    dst[c] = (double)hi[k] + (double)lo[k];
+  }
 }
 
 // Deterministic final sum of the per-block partials (one block).

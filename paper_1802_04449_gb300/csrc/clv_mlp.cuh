@@ -206,11 +206,20 @@ __device__ __forceinline__ long long batch_index(unsigned long long seed, int it
   return (long long)(mix64(seed ^ ((unsigned long long)iter << 32) ^ (unsigned long long)j) % (unsigned long long)n);
 }
 
+// Gradient of the loss over a batch, deterministically: the launch has a
+// fixed number of blocks (at most kMlpGradBlocks); block b takes the chunks
+// of kMlpTrainBlock samples b, b + gridDim.x, ... in order and sums their
+// parameter gradients and loss into its own row of `partial`
+// ([gridDim.x][kMlpParams + 1], loss last), which mlp_reduce_kernel adds up
+// in block order.  No atomics: the same inputs give the same bits.
+constexpr int kMlpGradBlocks = 256;
+constexpr int kMlpPartialRow = kMlpParams + 1;
+
 static __global__ void __launch_bounds__(kMlpTrainBlock) mlp_grad_kernel(const float* __restrict__ params,
                                                                   const float* __restrict__ X,
                                                                   const float* __restrict__ Y, long long n,
                                                                   long long batch, unsigned long long seed, int iter,
-                                                                  float* grad, float* loss) {
+                                                                  float* partial) {
   extern __shared__ float sm[];
   float* P = sm;                                   // kMlpParams
   float* sX = P + kMlpParams;                      // [10][B]
@@ -222,8 +231,11 @@ static __global__ void __launch_bounds__(kMlpTrainBlock) mlp_grad_kernel(const f
   __shared__ float s_loss[kMlpTrainBlock / 32];
   const int tid = threadIdx.x;
   for (int i = tid; i < kMlpParams; i += kMlpTrainBlock) P[i] = params[i];
+  float* row = partial + (size_t)blockIdx.x * kMlpPartialRow;
+  for (int i = tid; i < kMlpPartialRow; i += kMlpTrainBlock) row[i] = 0.0f;
   __syncthreads();
-  const long long j = (long long)blockIdx.x * kMlpTrainBlock + tid;
+  for (long long chunk = blockIdx.x; chunk * kMlpTrainBlock < batch; chunk += gridDim.x) {
+  const long long j = chunk * kMlpTrainBlock + tid;
   const bool valid = j < batch;
   float l = 0.0f;
   {
@@ -288,10 +300,11 @@ static __global__ void __launch_bounds__(kMlpTrainBlock) mlp_grad_kernel(const f
   if (tid == 0) {
     float a = 0.0f;
     for (int w = 0; w < kMlpTrainBlock / 32; ++w) a += s_loss[w];
-    atomicAdd(loss, a / (float)batch);
+    row[kMlpParams] += a / (float)batch;
   }
-  // parameter gradients: sums over the block's samples
-  const int nb = (int)min((long long)kMlpTrainBlock, batch - (long long)blockIdx.x * kMlpTrainBlock);
+  // parameter gradients: sums over the chunk's samples, added to the block's
+  // row (each entry belongs to one thread)
+  const int nb = (int)min((long long)kMlpTrainBlock, batch - chunk * kMlpTrainBlock);
   for (int pidx = tid; pidx < kMlpParams; pidx += kMlpTrainBlock) {
     const float *u, *v;
     if (pidx < kOffB1) { u = sD1 + (pidx / kMlpIn) * kMlpTrainBlock; v = sX + (pidx % kMlpIn) * kMlpTrainBlock; }
@@ -303,15 +316,27 @@ static __global__ void __launch_bounds__(kMlpTrainBlock) mlp_grad_kernel(const f
     float a = 0.0f;
     if (v) { for (int s = 0; s < nb; ++s) a = fmaf(u[s], v[s], a); }
     else { for (int s = 0; s < nb; ++s) a += u[s]; }
-    atomicAdd(grad + pidx, a);
+    row[pidx] += a;
   }
+  __syncthreads();   // the next chunk overwrites the activations
+  }
+}
+
+// grad = sum of the partial rows in block order (loss likewise)
+static __global__ void mlp_reduce_kernel(const float* __restrict__ partial, int nblocks, float* grad, float* loss) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= kMlpPartialRow) return;
+  float a = 0.0f;
+  for (int b = 0; b < nblocks; ++b) a += partial[(size_t)b * kMlpPartialRow + p];
+  if (p < kMlpParams) grad[p] = a;
+  else *loss = a;
 }
 
 constexpr size_t mlp_grad_smem_bytes() {
   return (size_t)(kMlpParams + (kMlpIn + 4 * kMlpHid + kMlpOut) * kMlpTrainBlock) * sizeof(float);
 }
 
-// Adam step (Kingma & Ba 2015) on all parameters; clears the gradient.
+// Adam step (Kingma & Ba 2015) on all parameters.
 static __global__ void mlp_adam_kernel(float* params, float* m, float* v, float* grad, int step, float lr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kMlpParams) return;
@@ -324,7 +349,6 @@ static __global__ void mlp_adam_kernel(float* params, float* m, float* v, float*
   const float mh = mi / (1.0f - powf(b1, (float)step));
   const float vh = vi / (1.0f - powf(b2, (float)step));
   params[i] -= lr * mh / (sqrtf(vh) + eps);
-  grad[i] = 0.0f;
 }
 
 }  // namespace clv

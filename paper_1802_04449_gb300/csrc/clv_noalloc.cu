@@ -17,6 +17,7 @@
 
 #include <cstdint>
 #include <mutex>
+#include <string>
 
 #include "clv.h"
 
@@ -90,6 +91,9 @@ __global__ void __launch_bounds__(1024) noalloc_final_kernel(const double* scrat
 
 // Device address of the scratch array on the current device, looked up once
 // per device (the array's name is only a host-side stand-in in host code).
+// The cached address belongs to the device's primary context: after
+// cudaDeviceReset the module is loaded anew and the address may change, so
+// a process that resets a device must not call this entry point on it again.
 cudaError_t scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -129,11 +133,18 @@ clv_status clv_field_stats_noalloc(const double* d_eps, const double* d_Ttt, int
   if (e != cudaSuccess) return noalloc_fail(CLV_ECUDA, cudaGetErrorString(e));
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int nparts = (int)((n + kBlock - 1) / kBlock);
+  // an error left pending by earlier, unrelated work is not this call's: it
+  // is reported as such and left pending (cudaPeekAtLastError does not clear it)
+  e = cudaPeekAtLastError();
+  if (e != cudaSuccess)
+    return noalloc_fail(CLV_ECUDA, (std::string("error pending before the call: ") + cudaGetErrorString(e)).c_str());
+  // each launch checked on its own (a launch error is this call's and is cleared)
   noalloc_clear_kernel<<<1, 32, 0, st>>>(scratch);
+  if ((e = cudaGetLastError()) != cudaSuccess) return noalloc_fail(CLV_ECUDA, cudaGetErrorString(e));
   noalloc_partials_kernel<<<nparts, kBlock, 0, st>>>(d_eps, d_Ttt, (long long)n, scratch);
+  if ((e = cudaGetLastError()) != cudaSuccess) return noalloc_fail(CLV_ECUDA, cudaGetErrorString(e));
   noalloc_final_kernel<<<1, 1024, 0, st>>>(scratch, nparts, cell_volume, d_out);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return noalloc_fail(CLV_ECUDA, cudaGetErrorString(e));
+  if ((e = cudaGetLastError()) != cudaSuccess) return noalloc_fail(CLV_ECUDA, cudaGetErrorString(e));
   return CLV_OK;
 }
 

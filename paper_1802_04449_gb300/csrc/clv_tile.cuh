@@ -51,14 +51,18 @@ template <typename R> struct EventGeom {
 
 // Per-cell inputs of the output cell that are not staged with the planes
 // (eps, u~^{n-1}; in stage 2 also u~^n, T~^n, pi~^n), prefetched one plane
-// ahead into a per-thread double buffer.
-template <int STAGE, bool VISC> struct CellIn {
+// ahead into a per-thread double buffer.  FF (the FP32 path, whose T~ is a
+// float-float pair): also the low parts of the stage's input T~ and, in stage
+// 2, of T~^n (the staged planes carry the high parts only).
+template <int STAGE, bool VISC, bool FF> struct CellIn {
   static constexpr int E = 0;
   static constexpr int UP = 1;                       // u~^{n-1} (VISC)
   static constexpr int UN = VISC ? 4 : 1;            // u~^n (stage 2)
-  static constexpr int TN = UN + 3;                  // T~^n (stage 2)
+  static constexpr int TN = UN + 3;                  // T~^n (stage 2; FF: high parts)
   static constexpr int PIN = TN + 4;                 // pi~^n (stage 2, VISC)
-  static constexpr int n = STAGE == 1 ? (VISC ? 4 : 1) : (VISC ? PIN + 10 : TN + 4);
+  static constexpr int TL = STAGE == 1 ? (VISC ? 4 : 1) : (VISC ? PIN + 10 : TN + 4);   // FF: low parts of T~
+  static constexpr int TNL = TL + 4;                 // FF, stage 2: low parts of T~^n
+  static constexpr int n = TL + (FF ? (STAGE == 1 ? 4 : 8) : 0);
 };
 
 // Row width of the staged box (in cells): the tile's TK columns with a
@@ -74,8 +78,9 @@ template <bool VISC> inline size_t tile_smem_bytes(int TJ, int TK, size_t rsize)
   using L = Box<VISC>;
   const size_t NB = (size_t)(TJ + 4) * box_width(TK);
   const size_t ncell = (size_t)TJ * TK;
+  const size_t nin = rsize == 4 ? CellIn<2, VISC, true>::n : CellIn<2, VISC, false>::n;
   const size_t elems = 2 * L::NF * NB + (size_t)L::NQ * ((TJ + 1) * TK + TJ * (TK + 1)) + 2 * (size_t)L::NPEND * ncell +
-                       2 * (size_t)CellIn<2, VISC>::n * ncell;
+                       2 * nin * ncell;
   return elems * rsize + 16 + NB * sizeof(int);   // vector table (NB / 4 int4) after up to 15 bytes of alignment
 }
 
@@ -133,8 +138,16 @@ __device__ __forceinline__ void stage_plane_async(const StageParams<R>& p, R* bo
 // Prefetch of the per-cell inputs of global cell gc into slot cb (stride ncell).
 template <typename R, int STAGE, bool VISC>
 __device__ __forceinline__ void prefetch_cell(const StageParams<R>& p, R* cb, int ncell, long long gc) {
-  using C = CellIn<STAGE, VISC>;
+  using C = CellIn<STAGE, VISC, sizeof(R) == 4>;
   cp_async_elem(cb + C::E * ncell, p.pr.e + gc);
+  if constexpr (sizeof(R) == 4) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) cp_async_elem(cb + (C::TL + m) * ncell, p.Tl[m] + gc);
+    if constexpr (STAGE == 2) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) cp_async_elem(cb + (C::TNL + m) * ncell, p.Tnl[m] + gc);
+    }
+  }
   if constexpr (VISC) {
 #pragma unroll
     for (int m = 0; m < 3; ++m) cp_async_elem(cb + (C::UP + m) * ncell, p.up[m] + gc);
@@ -204,11 +217,12 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
   R* Hy = boxbuf + 2 * NF * NB;  // [NQ][TJ+1][TK]
   R* Hk = Hy + NQ * NHY;       // [NQ][TJ][TK+1]
   R* pend = Hk + NQ * NHK;     // [2][NPEND][ncell]
-  using CI = CellIn<STAGE, VISC>;
+  using CI = CellIn<STAGE, VISC, sizeof(R) == 4>;
   R* cellbuf = pend + 2 * NPEND * ncell;             // [2][CI::n][ncell]
   // [NV] vector table, 16-byte aligned (int4 accesses)
   int4* voff = reinterpret_cast<int4*>(
-      (reinterpret_cast<uintptr_t>(cellbuf + 2 * CellIn<2, VISC>::n * ncell) + 15) & ~static_cast<uintptr_t>(15));
+      (reinterpret_cast<uintptr_t>(cellbuf + 2 * CellIn<2, VISC, sizeof(R) == 4>::n * ncell) + 15) &
+      ~static_cast<uintptr_t>(15));
 
   const int nthr = (t.TJ + 1) * (t.TK + 1);
   const bool worker = threadIdx.x < nthr;
@@ -403,12 +417,22 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
 #pragma unroll
               for (int r = 0; r < 10; ++r) S[4 + r] += Spi[r];
             }
-            // ---- stage update (Sec. 3)
+            // ---- stage update (Sec. 3).  FP32 path: T~ is a float-float
+            // pair (high part staged in W0, low part prefetched) and the
+            // increment h S is added to it exactly (Tnl: the new low parts)
             const R hh = p.h;
-            R Tnew[4], pinew[10];
+            R Tnew[4], Tnl[4], pinew[10];
             if constexpr (STAGE == 1) {
 #pragma unroll
-              for (int m = 0; m < 4; ++m) Tnew[m] = W0[m] + hh * S[m];
+              for (int m = 0; m < 4; ++m) {
+                if constexpr (sizeof(R) == 4) {
+                  const ff s = ff_add(ff{W0[m], cb[(CI::TL + m) * ncell]}, mul_rn(hh, S[m]));
+                  Tnew[m] = s.hi;
+                  Tnl[m] = s.lo;
+                } else {
+                  Tnew[m] = W0[m] + hh * S[m];
+                }
+              }
               if constexpr (VISC) {
                 const R inv = R(1) / ustar0;
 #pragma unroll
@@ -417,7 +441,17 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
               }
             } else {
 #pragma unroll
-              for (int m = 0; m < 4; ++m) Tnew[m] = R(0.5) * (cb[(CI::TN + m) * ncell] + W0[m] + hh * S[m]);
+              for (int m = 0; m < 4; ++m) {
+                if constexpr (sizeof(R) == 4) {
+                  const ff s = ff_add(ff_add(ff{cb[(CI::TN + m) * ncell], cb[(CI::TNL + m) * ncell]},
+                                             ff{W0[m], cb[(CI::TL + m) * ncell]}),
+                                      mul_rn(hh, S[m]));
+                  Tnew[m] = 0.5f * s.hi;   // halving is exact
+                  Tnl[m] = 0.5f * s.lo;
+                } else {
+                  Tnew[m] = R(0.5) * (cb[(CI::TN + m) * ncell] + W0[m] + hh * S[m]);
+                }
+              }
               if constexpr (VISC) {
                 const R inv = R(0.5) / u[0];
 #pragma unroll
@@ -430,6 +464,10 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
             // recover_kernel (high occupancy hides its dependent table lookups)
 #pragma unroll
             for (int m = 0; m < 4; ++m) p.Tout[m][gc] = Tnew[m];
+            if constexpr (sizeof(R) == 4) {
+#pragma unroll
+              for (int m = 0; m < 4; ++m) p.Toutl[m][gc] = Tnl[m];
+            }
             if constexpr (VISC) {
 #pragma unroll
               for (int r = 0; r < 10; ++r) p.piout[r][gc] = pinew[r];

@@ -70,7 +70,7 @@ def train(X, Y, iters, batch=32768, lr=2e-3, seed=1, params=None, lr_final=None,
     dev = X.device
     p = torch.as_tensor(init_params(seed) if params is None else np.asarray(params, np.float32),
                         device=dev).contiguous()
-    work = torch.zeros(3 * clv.MLP_NPARAM, dtype=torch.float32, device=dev)
+    work = torch.zeros(clv.MLP_TRAIN_WORK_FLOATS, dtype=torch.float32, device=dev)
     n2 = int(iters * final_frac)
     n1 = iters - n2
     l1 = clv.mlp_train(p, work, X, Y, n1, batch, lr, seed, 0)

@@ -175,6 +175,25 @@ def test_training_reduces_the_loss(trained):
     assert float(loss.item()) == pytest.approx(ref, rel=1e-4)
 
 
+def test_training_is_bitwise_deterministic(trained):
+    """The gradient kernel sums per-block partials in a fixed order (no
+    atomics), so two trainings from the same start, data and seed give the
+    same parameters bit for bit, and so do two full-batch gradients."""
+    torch = _torch()
+    _, _, X, Y = trained
+    Xs, Ys = X[:40000].contiguous(), Y[:40000].contiguous()
+    runs = []
+    for _ in range(2):
+        p, losses = L.train(Xs, Ys, iters=150, batch=8192, lr=3e-3, seed=9)
+        torch.cuda.synchronize()
+        runs.append((p.cpu().numpy(), losses.cpu().numpy()))
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    g = [clv.mlp_loss_grad(torch.tensor(runs[0][0], device="cuda"), Xs, Ys) for _ in range(2)]
+    torch.cuda.synchronize()
+    assert np.array_equal(g[0][1].cpu().numpy(), g[1][1].cpu().numpy())
+    assert g[0][0].item() == g[1][0].item()
+
+
 def _run_mode(case, mode, params):
     """SKIP steps with the default guess, then RUN steps with `mode`; returns
     the handle and the RUN steps' (iterations per solve, warp-max iterations
@@ -220,3 +239,40 @@ def test_learned_guess_gains_and_keeps_parity(trained):
     # deterministic
     h2, _ = _run_mode(case, clv.CLV_GUESS_MLP, params)
     assert np.array_equal(h2.get(["eps"])["eps"], res["mlp"][0].get(["eps"])["eps"])
+
+
+LONG_STEPS = 420   # tau 0.4 -> 4.6 fm: the headline run's span (20 warm-up + 400 timed steps)
+
+
+@pytest.fixture(scope="module")
+def long_oracle():
+    """The FP64 oracle's eps of the 97x97x41 hot-spot event after LONG_STEPS
+    steps (about a minute on the host's cores)."""
+    case = I.hotspot_event()
+    o = oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
+                      case.eta_over_s, case.eos)
+    o.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    o.step(LONG_STEPS)
+    return case, o.get("eps")
+
+
+@pytest.mark.parametrize("guess", ["learned", "previous"])
+def test_fp32_matches_the_oracle_over_the_headline_span(trained, long_oracle, guess):
+    """The FP32 path, with the learned guess (the headline configuration) and
+    with the previous-step guess, over the whole 420-step span of the
+    benchmark run of the 97x97x41 viscous hot-spot event (Sec. 3 update
+    equations): eps within 1e-4 relative L-inf of the FP64 oracle wherever
+    eps > 1e-3 GeV/fm^3, and no error bit raised."""
+    case, e_o = long_oracle
+    h = clv.from_case(case, clv.CLV_FP32)
+    h.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    if guess == "learned":
+        h.set_mlp(trained[0].cpu().numpy())
+        h.set_guess(clv.CLV_GUESS_MLP)
+    st = h.step(LONG_STEPS, stats=True)
+    assert st["error_word"] == 0 and st["n_rootfail"] == 0
+    e_g = h.get(["eps"])["eps"]
+    m = e_o > EPS_FLOOR
+    err = float(np.max(np.abs(e_g[m] / e_o[m] - 1)))
+    print(f"FP32 ({guess} guess) vs oracle after {LONG_STEPS} steps: L-inf {err:.3e} over {int(m.sum())} cells")
+    assert err <= 1e-4

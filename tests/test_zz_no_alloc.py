@@ -52,3 +52,21 @@ def test_noalloc_limit_and_arguments():
     e_tot, eps_max = out.tolist()
     assert e_tot == pytest.approx(0.5 * b[:n_max].sum().item(), rel=1e-12)
     assert eps_max == a[:n_max].max().item()
+
+
+def test_noalloc_wrapper_refuses_bad_tensors():
+    """The C entry point trusts the sizes it is given, so the binding checks
+    dtype, contiguity, lengths and device before it calls it."""
+    import torch
+    a = torch.rand(1000, dtype=torch.float64, device="cuda")
+    b = torch.rand(1000, dtype=torch.float64, device="cuda")
+    out = torch.zeros(2, dtype=torch.float64, device="cuda")
+    bad = [(a.float(), b, out), (a, b[:999], out), (a, b, out[:1]), (a, b.cpu(), out),
+           (a[::2], b[::2].contiguous(), out)]
+    for x, y, o in bad:
+        with pytest.raises(clv.ClvError) as ei:
+            clv.field_stats_noalloc(x, y, 1.0, o)
+        assert ei.value.status == 1
+    clv.field_stats_noalloc(a, b, 1.0, out)   # the good call still works afterwards
+    torch.cuda.synchronize()
+    assert out[1].item() == a.max().item()
