@@ -48,6 +48,17 @@ KERNEL_WORDS = {
     "recover2": 15,  # read T~^{tau mu} 4, pi~^{tau mu} 4, u~' 3; write eps, u~ 4
 }
 LEDGER_WORDS = 92    # the method's per-cell-update ledger for a fused step (each field once per stage)
+KERNEL_READ_WORDS = {"stage1": 21, "recover1": 11, "stage2": 38, "recover2": 11}
+# Words each FP32 kernel actually moves per cell (each field once): beyond
+# the ledger, the stage kernels read the stored P and c_s of their input, and
+# T~ is a float-float pair (the low parts of every T~ read and written); the
+# recovery also writes P and c_s
+KERNEL_MOVED_WORDS = {
+    "stage1": 45,    # read T~ 4+4, pi~ 10, u~ 3, P, c_s, eps, u~^{n-1} 3; write T~' 4+4, pi~' 10
+    "recover1": 21,  # read T~' 4+4, pi~'^{tau mu} 4, u~ 3; write eps', u~' 3, P', c_s'
+    "stage2": 66,    # read T~' 8, pi~' 10, u~' 3, P', c_s', eps', T~^n 8, pi~^n 10, u~^n 3, u~^{n-1} 3; write 18
+    "recover2": 21,
+}
 # Freeze-out surface finder (FP32): algorithmic bytes per hypercube (eps of
 # both slices, each cell once) and per element (the 22-value record and its
 # hypercube index written, u~ and pi~ of one cell of each slice read)
@@ -252,6 +263,12 @@ def run_gpu(args):
     value32c = ws * N * args.steps / (ms32c_max / 1e3)
     value64 = ws * N * steps64 / (ms64_max / 1e3)
 
+    # FMA rates of this GPU (the ALU-roofline peaks), measured after the
+    # timed runs above
+    fma64 = clv.fma_rate(clv.CLV_FP64)
+    fma32 = clv.fma_rate(clv.CLV_FP32)
+    f64_flops = load_fp64_flops()
+
     def per(a, b):
         return (a / b) if (a is not None and b) else None
 
@@ -302,11 +319,17 @@ def run_gpu(args):
     dom = max(tot_ms, key=tot_ms.get)
     alg = KERNEL_WORDS[dom] * word * N
     achieved = alg / (avg_ms[dom] / 1e3) / 1e9
+    tr = load_traffic(dom, st32.get("tile") if dom.startswith("stage") else None)
     roof = {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": achieved,
             "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
             "nominal_peak": HBM_NOMINAL_GBS, "frac_of_nominal": achieved / HBM_NOMINAL_GBS,
-            "traffic": load_traffic(dom, st32.get("tile") if dom.startswith("stage") else None),
+            "traffic": (tr[0] + tr[1]) if tr else None,
+            "read_traffic_ratio": (tr[0] / (KERNEL_READ_WORDS[dom] * word * N)) if tr else None,
+            "l2_resident": "the 71 MB FP32 state of this event stays in L2 within a step (L2 is flushed "
+                           "between steps); the HBM-bound fractions are those of the large event and the batch "
+                           "(hbm_resident_frac)",
             "algorithmic_bytes_per_launch": alg,
+            "moved_bytes_per_launch": KERNEL_MOVED_WORDS[dom] * word * N,
             "kernel_ms_avg": avg_ms,
             "kernel_share": {k: v / sum(tot_ms.values()) for k, v in tot_ms.items()},
             "ledger_bytes_per_cell_update": LEDGER_WORDS * word,
@@ -347,6 +370,65 @@ def run_gpu(args):
                                                         "error_word", "error", "tile")},
                  "stats_fp64": {k: stL64.get(k) for k in ("tau", "eps_max", "n_rootfail", "error_word", "error",
                                                           "tile")}}
+
+    # ---- the large event over its whole lifetime (tau0 until max T < 137
+    # MeV, the paper's stopping temperature): FP32 + learned guess, the
+    # stopping rule read every CHUNK steps from the device reduction, timed
+    # as a whole with events; then the FP64 path over the same number of
+    # steps, and eps of the two compared at the end
+    lifetime = None
+    if args.lifetime:
+        from paper_1802_04449_gb300 import inputs as I
+        lc = I.minijet_event(seed=2024 + rank)
+        T_F, CHUNK, MAXSTEPS = 0.137, 50, 2400
+
+        def run_life(prec, nsteps=None):
+            g = clv.from_case(lc, prec)
+            g.set_initial_case(lc)
+            if prec == clv.CLV_FP32:
+                g.set_mlp(params_host)
+                g.set_guess(clv.CLV_GUESS_MLP)
+            if args.autotune:
+                g.autotune(max_candidates=12, reps=3)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(g.stream)
+            done, st, err = 0, None, None
+            while done < (nsteps or MAXSTEPS):
+                k = CHUNK if nsteps is None else min(CHUNK, nsteps - done)
+                try:
+                    st = g.step(k, stats=True)
+                except clv.ClvError as e:   # reported in the JSON line, not hidden
+                    err = str(e)
+                    break
+                done += k
+                if nsteps is None and st["T_max"] < T_F:
+                    break
+            e1.record(g.stream)
+            torch.cuda.synchronize()
+            eps = g.get(["eps"])["eps"]
+            g.close()
+            return done, e0.elapsed_time(e1), st, err, eps
+
+        n32, ms_l32, st_l32, err32, eps32 = run_life(clv.CLV_FP32)
+        n64, ms_l64, st_l64, err64, eps64 = run_life(clv.CLV_FP64, n32)
+        live = eps64 > 1e-3
+        lifetime = {
+            "workload": "the 261x261x121 mini-jet event from tau0 = 0.4 fm until max T < 137 MeV",
+            "steps": n32, "tau_end": st_l32["tau"] if st_l32 else None,
+            "T_max_end": st_l32["T_max"] if st_l32 else None,
+            "value": ws * lc.ncells * n32 / (ms_l32 / 1e3), "unit": UNIT, "seconds": ms_l32 / 1e3,
+            "stopping_rule": f"T_max from the device reduction every {CHUNK} steps (a stats step)",
+            "error_word": st_l32["error_word"] if st_l32 else None, "error": err32,
+            "n_rootfail": st_l32["n_rootfail"] if st_l32 else None,
+            "fp64": {"steps": n64, "value": ws * lc.ncells * n64 / (ms_l64 / 1e3), "seconds": ms_l64 / 1e3,
+                     "error_word": st_l64["error_word"] if st_l64 else None, "error": err64},
+            "accuracy_vs_fp64": {"cells_compared": int(live.sum()),
+                                 "eps_linf_rel_where_eps_gt_1e-3":
+                                     float(np.max(np.abs(eps32[live] / eps64[live] - 1))) if live.any() else None,
+                                 "eps_l1_rel": float(np.abs(eps32 - eps64).sum() / np.abs(eps64).sum())},
+        }
+        del eps32, eps64
 
     # ---- freeze-out surface of the same event: T_f = 137 MeV (the paper's
     # stopping temperature) through the EOS table, between the slices at
@@ -412,7 +494,8 @@ def run_gpu(args):
                       "roofline": {"bound": "alu", "kernel": "cf_sum_kernel<float, viscous>",
                                    "achieved": cf_ach, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
                                    "frac": cf_ach / FP32_ALU_TFLOPS, "flops_per_pair": CF_FLOPS_PER_PAIR,
-                                   "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"}}
+                                   "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz",
+                                   "frac_of_measured_fma_rate": cf_ach / fma32}}
         freezeout = {"workload": "the same event at tau = 2.4 -> 2.5 fm (10 steps apart), T_f = 137 MeV",
                      "eps_f": eps_f, "hypercubes": ncube, "elements": nel, "ms_per_find": fms,
                      "value": ncube / (fms / 1e3), "unit": "hypercubes/s", "launches_per_find": 4,
@@ -576,7 +659,15 @@ def run_gpu(args):
                                 "fp64 reductions",
                    "l2": "flushed between timed steps (512 MiB write, untimed)",
                    "parallelism": f"independent events, {ws} rank(s)"},
-        "fp64": {"value": value64, "unit": UNIT, "steps": steps64, "ms_per_step": ms64_max / steps64},
+        "fp64": {"value": value64, "unit": UNIT, "steps": steps64, "ms_per_step": ms64_max / steps64,
+                 "roofline": {"bound": "alu", "kernel": "FP64 step (stage and recovery kernels)",
+                              "achieved": (f64_flops * value64 / ws / 1e12) if f64_flops else None,
+                              "peak": fma64, "unit": "TFLOP/s",
+                              "frac": (f64_flops * value64 / ws / 1e12 / fma64) if f64_flops else None,
+                              "flops_per_cell_update": f64_flops,
+                              "peak_kind": "measured: clv_fma_rate, independent FP64 FMA chains on every SM",
+                              "hbm_frac": value64 / ws * LEDGER_WORDS * 8 / 1e9 / peak}},
+        "alu_peaks_tflops": {"fp64_measured": fma64, "fp32_measured": fma32, "fp32_derived": FP32_ALU_TFLOPS},
         "fp32_previous_guess": {"value": value32p, "unit": UNIT, "steps": args.steps,
                                 "ms_per_step": ms32p_max / args.steps},
         "fp32_cold_guess": {"value": value32c, "unit": UNIT, "steps": args.steps,
@@ -585,6 +676,7 @@ def run_gpu(args):
         "accuracy": accuracy,
         "options": options,
         "large_event": large,
+        "large_event_lifetime": lifetime,
         "batch": batch,
         "freezeout": freezeout,
         "cooperfrye": cooperfrye,
@@ -598,6 +690,8 @@ def run_gpu(args):
         "stats_fp64": {k: st64.get(k) for k in ("tau", "eps_max", "E_tot", "n_rootfail", "error_word", "error",
                                                 "tile")},
     }
+    roof["hbm_resident_frac"] = {"large_event": large["roofline"]["frac"] if large else None,
+                                 "batch": batch["roofline"]["frac"] if batch else None}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -607,11 +701,12 @@ def run_gpu(args):
 
 
 def load_traffic(dom, tile):
-    """DRAM bytes per launch of kernel slot ``dom`` (read + write) from the
-    committed ncu summary: lines ``traffic <slot> <bytes> <kernel-source-hash>
-    <TJxTKxCX>`` in profiles/traffic.txt.  Returns None when absent, when the
-    kernel sources changed since the counters were taken, or (stage slots)
-    when the run used another tile shape."""
+    """DRAM bytes per launch of kernel slot ``dom`` from the committed ncu
+    summary: lines ``traffic <slot> <read bytes> <write bytes>
+    <kernel-source-hash> <TJxTKxCX>`` in profiles/traffic.txt.  Returns
+    (read, write), or None when absent, when the kernel sources changed since
+    the counters were taken, or (stage slots) when the run used another tile
+    shape."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
@@ -620,9 +715,25 @@ def load_traffic(dom, tile):
     with open(p) as f:
         for line in f:
             parts = line.split()
-            if (len(parts) == 5 and parts[0] == "traffic" and parts[1] == dom and parts[3] == want
-                    and (parts[4] == "-" or parts[4] == shape)):
-                return float(parts[2])
+            if (len(parts) == 6 and parts[0] == "traffic" and parts[1] == dom and parts[4] == want
+                    and (parts[5] == "-" or parts[5] == shape)):
+                return float(parts[2]), float(parts[3])
+    return None
+
+
+def load_fp64_flops():
+    """FP64 flops per cell-update of the FP64 step (an FMA counts as 2) from
+    the ncu instruction counts in profiles/fp64_flops.txt (a line ``flops
+    <per cell-update> <kernel-source-hash>``); None once the kernels changed."""
+    p = os.path.join(ROOT, "profiles", "fp64_flops.txt")
+    if not os.path.exists(p):
+        return None
+    want = kernel_source_hash()
+    with open(p) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) == 3 and parts[0] == "flops" and parts[2] == want:
+                return float(parts[1])
     return None
 
 
@@ -690,6 +801,72 @@ def run_reference(args):
     }))
 
 
+def profile_case(args):
+    """A short run through the C ABI for capture under a profiler: the
+    kernels of interest are the last launches.  The event (--case: the
+    97x97x41 hot-spot event, or the 261x261x121 mini-jet event) has its tile
+    shape set by --tile or autotuned first (those timing launches come
+    first), --skip steps
+    run next (reaching a later, more dilute state), then --steps steps.
+    --guess learned / learned-all trains the network briefly on FP64 states
+    of another seed first.  --surface then takes a slice, runs 10 more steps,
+    finds the freeze-out surface at T_f = 137 MeV between the two slices and
+    computes the pi+, K+ and p spectra on the 41 x 15 x 48 grid from it: those
+    launches come last.  --zeta-over-s Z > 0 evolves the bulk pressure too,
+    --charge a smooth net charge."""
+    import torch
+    from paper_1802_04449_gb300 import clv
+    from paper_1802_04449_gb300 import inputs as I
+    from paper_1802_04449_gb300 import learned as L
+
+    mk = I.minijet_event if args.case == "minijet" else I.hotspot_event
+    case = mk()
+    prec = clv.CLV_FP32 if args.precision == "fp32" else clv.CLV_FP64
+    params = None
+    if args.guess.startswith("learned"):
+        tc = mk(seed=1000)
+        h = clv.from_case(tc, clv.CLV_FP64)
+        h.set_initial_case(tc)
+        X, Y = L.collect_samples(h, max(args.skip + args.steps, 40), 20).data()
+        p, _ = L.train(X, Y, iters=1000, batch=32768, lr=2e-3, seed=7)
+        params = p.cpu().numpy()
+        h.close()
+        del X, Y
+    g = clv.from_case(case, prec, zeta_over_s=args.zeta_over_s, charge=args.charge)
+    g.set_initial_case(case)
+    if args.charge:
+        g.set_initial_n(0.2 + 0.05 * np.cos(np.linspace(0.0, 6.283, case.ncells)).reshape(case.eps.shape))
+    if params is not None:
+        g.set_mlp(params)
+    g.set_guess({"previous": clv.CLV_GUESS_PREVIOUS, "cold": clv.CLV_GUESS_COLD, "learned": clv.CLV_GUESS_MLP,
+                 "learned-all": clv.CLV_GUESS_MLP_ALL}[args.guess])
+    if args.tile:
+        g.set_tile(*(int(x) for x in args.tile.split(",")))
+        print("tile:", g.tile())
+    elif args.autotune:
+        print("tile:", g.autotune(max_candidates=12, reps=3))
+    if args.skip:
+        g.step(args.skip)
+    st = g.step(args.steps, stats=True)
+    torch.cuda.synchronize()
+    print("profile case done: tau %.3f, newton iters/solve %.3f, polished %d" %
+          (st["tau"], st["n_newton_iters"] / max(1, st["n_newton_cells"]), st["n_polished"]))
+    if args.surface:
+        snap = g.fo_snapshot()
+        g.step(10)
+        eos = case.eos
+        lne = eos["lne0"] + eos["dlne"] * np.arange(len(eos["T"]))
+        eps_f = float(np.float32(np.exp(np.interp(0.137, eos["T"], lne))))
+        finder = clv.FreezeoutFinder(g.fo_grid(), stream=g.stream)
+        finder.find(snap, g.fo_current(), eps_f)
+        Y, pT, _, phi, _ = I.spectra_grid()
+        P_f = float(np.interp(np.log(eps_f), lne, eos["P"]))
+        cf = clv.CooperFrye(["pi+", "K+", "p"], Y, pT, phi, 0.137, eps_f + P_f, True, prec, stream=g.stream)
+        cf.spectra(finder.rec, d_nel=finder.count)
+        _, _, n = finder.result()
+        print("surface: %d elements at eps_f = %.4f" % (n, eps_f))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -703,6 +880,8 @@ def main():
                     help="events of the event-by-event batch measured beside the headline (0: skip)")
     ap.add_argument("--no-large", dest="large", action="store_false",
                     help="skip the 261x261x121 mini-jet event measured beside the headline")
+    ap.add_argument("--no-lifetime", dest="lifetime", action="store_false",
+                    help="skip the 261x261x121 event's run to max T < 137 MeV (FP32 + learned, then FP64)")
     ap.add_argument("--no-freezeout", dest="freezeout", action="store_false",
                     help="skip the freeze-out surface measured beside the headline")
     ap.add_argument("--no-options", dest="options", action="store_false",
@@ -714,7 +893,20 @@ def main():
     ap.add_argument("--train-events", type=int, default=2, help="FP64 events whose states train the guess")
     ap.add_argument("--train-every", type=int, default=20, help="steps between sample dumps")
     ap.add_argument("--train-iters", type=int, default=4000, help="Adam iterations")
+    pc = ap.add_argument_group("profile case (--profile-case: a short run for a profiler, no JSON line)")
+    pc.add_argument("--profile-case", action="store_true")
+    pc.add_argument("--case", default="hotspot", choices=["hotspot", "minijet"])
+    pc.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    pc.add_argument("--guess", default="previous", choices=["previous", "cold", "learned", "learned-all"])
+    pc.add_argument("--skip", type=int, default=0, help="steps before the profiled ones")
+    pc.add_argument("--tile", default="", help="TJ,TK,CX of the stage kernel instead of autotuning")
+    pc.add_argument("--surface", action="store_true")
+    pc.add_argument("--zeta-over-s", type=float, default=0.0)
+    pc.add_argument("--charge", action="store_true")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -207,6 +207,16 @@ clv_status clv_get_time(const clv_handle* h, double* tau, int64_t* step);
 clv_status clv_enable_kernel_timing(clv_handle* h, int enable);
 clv_status clv_get_kernel_times(clv_handle* h, double ms[4], int64_t launches[4]);
 
+/* Measurement (no counterpart in the paper): the fused multiply-add rate of
+ * the current device in TFLOP/s (an FMA counts as 2 flops) for precision
+ * CLV_FP64 or CLV_FP32, from independent FMA chains on 8 CTAs of 256
+ * threads per SM, the best of three timed launches after a warm-up one.  It
+ * is the peak of the ALU rooflines (the FP64 path, the Cooper-Frye sum).
+ * Allocates and frees a small device buffer; runs on the legacy default
+ * stream and synchronises.  CLV_EINVAL for another precision or a NULL
+ * tflops, CLV_ECUDA on a CUDA error. */
+clv_status clv_fma_rate(int precision, double* tflops);
+
 /* ---------------- learned initial guess of the root solve ----------------
  * Not in the paper (which notes that the varying iteration counts of the
  * root finding make warps diverge): a 10 -> 64 -> 64 -> 4 SiLU network maps
@@ -217,12 +227,17 @@ clv_status clv_get_kernel_times(clv_handle* h, double ms[4], int64_t launches[4]
  * pi~^{tau mu} the root solve starts from.  Parameters: 5124 floats packed
  * W1 (64x10, row-major) | b1 (64) | W2 (64x64) | b2 (64) | W3 (4x64) | b3 (4).
  * Inference: BF16 weights on the tensor cores, FP32 accumulation. */
-enum { CLV_GUESS_PREVIOUS = 0, CLV_GUESS_COLD = 1, CLV_GUESS_MLP = 2 };
+enum { CLV_GUESS_PREVIOUS = 0, CLV_GUESS_COLD = 1, CLV_GUESS_MLP = 2, CLV_GUESS_MLP_ALL = 3 };
 #define CLV_MLP_NPARAM 5124
 
-/* Initial guess of the root solve: CLV_GUESS_PREVIOUS (|v| of the cell's
- * stage velocity; the default), CLV_GUESS_COLD (v = M/(E + P(E))) or
- * CLV_GUESS_MLP (needs clv_set_mlp and the FP32 path). */
+/* Initial guess of the root solve (Sec. 3 primitive recovery; the guess only
+ * sets where Newton starts, the root is solved to the same tolerance):
+ * CLV_GUESS_PREVIOUS (|v| of the cell's stage velocity; the default),
+ * CLV_GUESS_COLD (v = M/(E + P(E))), CLV_GUESS_MLP (the network for cells
+ * that were vacuum in the stage's input, whose stage velocity is the
+ * vacuum's 0; the stage velocity elsewhere) or CLV_GUESS_MLP_ALL (the network
+ * for every cell).  The two network modes need clv_set_mlp and the FP32 path;
+ * other modes or precisions return CLV_EINVAL. */
 clv_status clv_set_guess(clv_handle* h, int mode);
 
 /* Load the network (host array of CLV_MLP_NPARAM floats; converted to BF16). */

@@ -11,7 +11,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libclv.so")
-SOURCES = ["clv_api.cu", "clv_noalloc.cu", "clv_freezeout.cu", "clv_cooperfrye.cu", "clv_charge.cu", "clv_bulk.cu"]
+SOURCES = ["clv_api.cu", "clv_noalloc.cu", "clv_freezeout.cu", "clv_cooperfrye.cu", "clv_charge.cu", "clv_bulk.cu",
+           "clv_measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # -prec-div/-prec-sqrt=false: approximate FP32 division and square root (FP64 unaffected)
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-prec-div=false", "-prec-sqrt=false",

@@ -119,8 +119,8 @@ EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initi
             "clv_slab_unpack", "clv_slab_fill_edge", "clv_slab_predictor", "clv_stage",
             "clv_fo_scratch_bytes", "clv_fo_find", "clv_fo_grid_of", "clv_fo_current", "clv_fo_slice_bytes",
             "clv_fo_snapshot", "clv_cf_scratch_bytes", "clv_cf_spectra", "clv_set_initial_n",
-            "clv_set_initial_n_device", "clv_batch_set_schedule"]
-CLV_GUESS_PREVIOUS, CLV_GUESS_COLD, CLV_GUESS_MLP = 0, 1, 2
+            "clv_set_initial_n_device", "clv_batch_set_schedule", "clv_fma_rate"]
+CLV_GUESS_PREVIOUS, CLV_GUESS_COLD, CLV_GUESS_MLP, CLV_GUESS_MLP_ALL = 0, 1, 2, 3
 MLP_NPARAM = 5124
 MLP_PARTIAL_FLOATS = 256 * (MLP_NPARAM + 1)          # CLV_MLP_PARTIAL_FLOATS
 MLP_TRAIN_WORK_FLOATS = 3 * MLP_NPARAM + MLP_PARTIAL_FLOATS   # CLV_MLP_TRAIN_WORK_FLOATS
@@ -202,6 +202,7 @@ def load(path: str | None = None):
         lib.clv_last_error.argtypes = [P]
         lib.clv_last_error.restype = ctypes.c_char_p
         lib.clv_version.restype = ctypes.c_char_p
+        lib.clv_fma_rate.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
         for name in EXPORTED:
             if name not in ("clv_destroy", "clv_last_error", "clv_version"):
                 getattr(lib, name).restype = ctypes.c_int
@@ -211,6 +212,14 @@ def load(path: str | None = None):
 
 def _dp(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def fma_rate(precision):
+    """FMA rate of the current device in TFLOP/s (clv_fma_rate)."""
+    lib = load()
+    out = ctypes.c_double()
+    _raise(lib, lib.clv_fma_rate(int(precision), ctypes.byref(out)))
+    return out.value
 
 
 def _raise(lib, st):

@@ -201,48 +201,68 @@ struct TileGeom {
   size_t smem;
 };
 
-// Tile shape: TK columns fit neta in ceil(neta/32) tiles; the block has
-// (TJ+1) x (TK+1) threads, at most 256 (FP32) or 128 (FP64); x is cut into
-// chunks of CX planes (see below).
-TileGeom tile_geometry(const clv_config* c, int sms) {
-  const int rsize = c->precision == CLV_FP64 ? 8 : 4;
-  const int maxthr = rsize == 4 ? CLV_TILE_MAX_THREADS : std::min(CLV_TILE_MAX_THREADS, kBlock / 2);
-  const int nk = (c->neta + 31) / 32;
+// CTAs of a stage kernel resident on one SM at `threads` threads and `smem`
+// bytes of dynamic shared memory, from the device's occupancy calculator
+// (registers, shared memory and warps); 1 when it cannot tell.
+int kernel_occupancy(const void* f, int threads, size_t smem) {
+  int n = 0;
+  if (smem > kSmemOptinMax) return 1;
+  if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemOptinMax) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, threads, smem) != cudaSuccess) {
+    cudaGetLastError();   // a failed query leaves no error behind
+    return 1;
+  }
+  return std::max(1, n);
+}
+
+int tile_occupancy(const clv_config* c, int threads, size_t smem) {
   const bool visc = c->eta_over_s > 0.0;
-  TileGeom g;
-  TileArgs& t = g.t;
-  t.TK = (c->neta + nk - 1) / nk;
-  t.TJ = std::max(1, std::min(c->ny, maxthr / (t.TK + 1) - 1));
-  // fewer rows while the CTA's shared memory exceeds the opt-in limit of a block
-  auto smem_of = [&](int TJ) {
-    return visc ? tile_smem_bytes<true>(TJ, t.TK, rsize) : tile_smem_bytes<false>(TJ, t.TK, rsize);
-  };
-  while (t.TJ > 1 && smem_of(t.TJ) > kSmemOptinMax) --t.TJ;
-  t.ntj = (c->ny + t.TJ - 1) / t.TJ;
-  t.ntk = (c->neta + t.TK - 1) / t.TK;
-  // CLV_TILE_MIN_BLOCKS CTAs per SM: pick the chunking that minimises
-  // waves x (planes per chunk + the 4 halo planes each chunk also stages)
-  const long long tiles = (long long)t.ntj * t.ntk;
+  if (c->precision == CLV_FP64)
+    return kernel_occupancy(visc ? (const void*)stage_tile_kernel<double, 2, true> : (const void*)stage_tile_kernel<double, 2, false>,
+                            threads, smem);
+  return kernel_occupancy(visc ? (const void*)stage_tile_kernel<float, 2, true> : (const void*)stage_tile_kernel<float, 2, false>,
+                          threads, smem);
+}
+
+// x chunking of a tile grid: the number of chunks that minimises waves x
+// (planes per chunk + the 4 halo planes each chunk also stages), with `slots`
+// CTAs resident on the device at a time
+int chunk_planes(int nx, long long tiles, long long slots) {
   long long best_nch = 1;
   double best = 1e300;
-  for (long long nch = 1; nch <= std::min<long long>(c->nx, 8LL * sms * CLV_TILE_MIN_BLOCKS); ++nch) {
-    const long long cx = (c->nx + nch - 1) / nch;
-    const long long used = (c->nx + cx - 1) / cx;
-    const long long slots = (long long)sms * CLV_TILE_MIN_BLOCKS;
+  for (long long nch = 1; nch <= std::min<long long>(nx, 8LL * slots); ++nch) {
+    const long long cx = (nx + nch - 1) / nch;
+    const long long used = (nx + cx - 1) / cx;
     const long long waves = (tiles * used + slots - 1) / slots;
     const double cost = (double)waves * (double)(cx + 4);
     if (cost < best - 1e-9) { best = cost; best_nch = used; }
   }
-  t.CX = (int)((c->nx + best_nch - 1) / best_nch);
-  const long long nch = (c->nx + t.CX - 1) / t.CX;
-  g.threads = (t.TJ + 1) * (t.TK + 1);
-  g.blocks = (unsigned)(tiles * nch);
-  g.smem = smem_of(t.TJ);
-  return g;
+  return (int)((nx + best_nch - 1) / best_nch);
+}
+
+TileGeom tile_geometry_of(const clv_config* c, int sms, int TJ, int TK, int cx);
+
+// Tile shape: TK columns fit neta in ceil(neta/32) tiles; the block has
+// (TJ+1) x (TK+1) threads, at most CLV_TILE_MAX_THREADS (FP32) or 128 (FP64),
+// and fewer rows while its shared memory exceeds the opt-in limit of a block;
+// x is cut into chunks of CX planes by the makespan rule of chunk_planes.
+TileGeom tile_geometry(const clv_config* c, int sms) {
+  const int rsize = c->precision == CLV_FP64 ? 8 : 4;
+  const int maxthr = rsize == 4 ? CLV_TILE_MAX_THREADS : std::min(CLV_TILE_MAX_THREADS, kBlock / 2);
+  const int nk = (c->neta + 31) / 32;
+  const int TK = (c->neta + nk - 1) / nk;
+  const bool visc = c->eta_over_s > 0.0;
+  int TJ = std::max(1, std::min(c->ny, maxthr / (TK + 1) - 1));
+  auto smem_of = [&](int tj) {
+    return visc ? tile_smem_bytes<true>(tj, TK, rsize) : tile_smem_bytes<false>(tj, TK, rsize);
+  };
+  while (TJ > 1 && smem_of(TJ) > kSmemOptinMax) --TJ;
+  return tile_geometry_of(c, sms, TJ, TK, 0);
 }
 
 // Geometry of an explicit (TJ, TK) tile shape; CX from the makespan rule of
-// tile_geometry when cx <= 0.
+// chunk_planes when cx <= 0, with as many CTAs per SM as the device keeps
+// resident at this shape.
 TileGeom tile_geometry_of(const clv_config* c, int sms, int TJ, int TK, int cx) {
   const int rsize = c->precision == CLV_FP64 ? 8 : 4;
   TileGeom g;
@@ -251,26 +271,14 @@ TileGeom tile_geometry_of(const clv_config* c, int sms, int TJ, int TK, int cx) 
   t.TK = TK;
   t.ntj = (c->ny + TJ - 1) / TJ;
   t.ntk = (c->neta + TK - 1) / TK;
+  const bool visc = c->eta_over_s > 0.0;
+  g.threads = (TJ + 1) * (TK + 1);
+  g.smem = visc ? tile_smem_bytes<true>(TJ, TK, rsize) : tile_smem_bytes<false>(TJ, TK, rsize);
   const long long tiles = (long long)t.ntj * t.ntk;
-  if (cx <= 0) {
-    long long best_nch = 1;
-    double best = 1e300;
-    for (long long nch = 1; nch <= std::min<long long>(c->nx, 8LL * sms * CLV_TILE_MIN_BLOCKS); ++nch) {
-      const long long cxx = (c->nx + nch - 1) / nch;
-      const long long used = (c->nx + cxx - 1) / cxx;
-      const long long slots = (long long)sms * CLV_TILE_MIN_BLOCKS;
-      const long long waves = (tiles * used + slots - 1) / slots;
-      const double cost = (double)waves * (double)(cxx + 4);
-      if (cost < best - 1e-9) { best = cost; best_nch = used; }
-    }
-    cx = (int)((c->nx + best_nch - 1) / best_nch);
-  }
+  if (cx <= 0) cx = chunk_planes(c->nx, tiles, (long long)sms * tile_occupancy(c, g.threads, g.smem));
   t.CX = cx;
   const long long nch = (c->nx + t.CX - 1) / t.CX;
-  g.threads = (TJ + 1) * (TK + 1);
   g.blocks = (unsigned)(tiles * nch);
-  const bool visc = c->eta_over_s > 0.0;
-  g.smem = visc ? tile_smem_bytes<true>(TJ, TK, rsize) : tile_smem_bytes<false>(TJ, TK, rsize);
   return g;
 }
 
@@ -281,7 +289,9 @@ inline int tile_max_threads(const clv_config* c) {
 // Candidate tile shapes for the autotuner, best modelled makespan first:
 // eta_s split into 1..4 columns of tiles, y tiles from the largest that fits
 // the thread limit down to a third of it, the x chunking of each by the
-// makespan rule.  Model: waves x (planes + 4 halo planes) x staged box cells.
+// makespan rule.  Model: waves x (planes + 4 halo planes) x staged box cells
+// x CTAs sharing an SM, over the SM's issue efficiency (resident warps, up to
+// 16, over 16).
 std::vector<TileGeom> tile_candidates(const clv_config* c, int sms, size_t smem_max) {
   std::vector<std::pair<double, TileGeom>> v;
   const int maxthr = tile_max_threads(c);
@@ -295,9 +305,11 @@ std::vector<TileGeom> tile_candidates(const clv_config* c, int sms, size_t smem_
     for (int TJ = maxTJ; TJ >= std::max(1, maxTJ / 3); --TJ) {
       TileGeom g = tile_geometry_of(c, sms, TJ, TK, 0);
       if (g.smem > smem_max) continue;
-      const long long slots = (long long)sms * CLV_TILE_MIN_BLOCKS;
+      const int occ = tile_occupancy(c, g.threads, g.smem);
+      const long long slots = (long long)sms * occ;
       const long long waves = ((long long)g.blocks + slots - 1) / slots;
-      const double cost = (double)waves * (g.t.CX + 4) * (double)((TJ + 4) * (TK + 4));
+      const double eff = std::min(1.0, occ * ((g.threads + 31) / 32) / 16.0);
+      const double cost = (double)waves * (g.t.CX + 4) * (double)((TJ + 4) * (TK + 4)) * occ / eff;
       v.push_back({cost, g});
     }
   }
@@ -512,6 +524,8 @@ template <typename R, bool VISC, bool STATS> void launch_recover(clv_handle* h, 
   const unsigned g = grid_of(h->N);
   if (sizeof(R) == 4 && h->guess == kGuessMlp)
     recover_kernel<R, VISC, STATS, sizeof(R) == 4 ? kGuessMlp : kGuessPrevious><<<g, kBlock, 0, h->stream>>>(p);
+  else if (sizeof(R) == 4 && h->guess == kGuessMlpAll)
+    recover_kernel<R, VISC, STATS, sizeof(R) == 4 ? kGuessMlpAll : kGuessPrevious><<<g, kBlock, 0, h->stream>>>(p);
   else if (h->guess == kGuessCold) recover_kernel<R, VISC, STATS, kGuessCold><<<g, kBlock, 0, h->stream>>>(p);
   else recover_kernel<R, VISC, STATS, kGuessPrevious><<<g, kBlock, 0, h->stream>>>(p);
 }
@@ -1206,9 +1220,10 @@ clv_status clv_get_time(const clv_handle* h, double* tau, int64_t* step) {
 
 clv_status clv_set_guess(clv_handle* h, int mode) {
   if (!h) return CLV_EINVAL;
-  if (mode < kGuessPrevious || mode > kGuessMlp) return fail(h, CLV_EINVAL, "unknown guess mode");
-  if (mode == kGuessMlp && !h->mlp_loaded) return fail(h, CLV_EINVAL, "no network loaded (clv_set_mlp)");
-  if (mode == kGuessMlp && h->rsize != 4) return fail(h, CLV_EINVAL, "the learned guess runs on the FP32 path");
+  if (mode < kGuessPrevious || mode > kGuessMlpAll) return fail(h, CLV_EINVAL, "unknown guess mode");
+  const bool net = mode == kGuessMlp || mode == kGuessMlpAll;
+  if (net && !h->mlp_loaded) return fail(h, CLV_EINVAL, "no network loaded (clv_set_mlp)");
+  if (net && h->rsize != 4) return fail(h, CLV_EINVAL, "the learned guess runs on the FP32 path");
   if (h->guess != mode) invalidate_graphs(h);
   h->guess = mode;
   return CLV_OK;
@@ -1885,7 +1900,8 @@ static cudaError_t batch_schedule(clv_handle* h, int maxthr, int chunk, int sms,
   h->batch_smem = smem;
   h->batch_threads = thr;
   h->batch_nitems = (int)it.size();
-  h->batch_blocks = (unsigned)std::min<long long>((long long)sms * CLV_TILE_MIN_BLOCKS, h->batch_nitems);
+  const void* bk = h->rsize == 8 ? (const void*)stage_batch_kernel<double, 2, true> : (const void*)stage_batch_kernel<float, 2, true>;
+  h->batch_blocks = (unsigned)std::min<long long>((long long)sms * kernel_occupancy(bk, thr, smem), h->batch_nitems);
   h->batch_maxthr = maxthr;
   h->batch_chunk = chunk;
   invalidate_graphs(h);   // captured steps hold the old launch shape and item list

@@ -361,6 +361,9 @@ __device__ __forceinline__ void cp_async_elem(double* smem, const double* gmem) 
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// this thread's groups complete in commit order: wait for all but the most
+// recently committed one
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // Product rounded on its own (never fused into a neighbouring add), so that
 // differences of equal products cancel exactly.

@@ -91,7 +91,10 @@ template <typename R> struct StageParams {
   R* Pib;
 };
 
-enum GuessMode { kGuessPrevious = 0, kGuessCold = 1, kGuessMlp = 2 };
+// kGuessMlp: the network seeds the cells that were vacuum in the stage's
+// input (no velocity to start from), the stage velocity every other cell;
+// kGuessMlpAll: the network seeds every cell.
+enum GuessMode { kGuessPrevious = 0, kGuessCold = 1, kGuessMlp = 2, kGuessMlpAll = 3 };
 
 __device__ __forceinline__ int wrap_index(int i, int n, int periodic) {
   if (periodic) {
@@ -697,31 +700,51 @@ __global__ void __launch_bounds__(kBlock, RecoverMinBlocks<R>::value) recover_ke
   const R E = ip.e, Mx = ip.m[0], My = ip.m[1], Me = ip.m[2];
   // initial guess for |v|
   R vg = R(-1);
-  if constexpr (GUESS == kGuessMlp && sizeof(R) == 4) {
-    // learned guess: features -> BF16 tensor-core MLP, 32 cells per warp
-    __shared__ __align__(16) __nv_bfloat16 s_w[kMlpSmemW];
-    __shared__ float s_b[kMlpBiasElems];
-    __shared__ __align__(16) __nv_bfloat16 s_x[kBlock / 32][32][kMlpSX];
-    __shared__ float s_y[kBlock / 32][32][4];
-    mlp_load_smem(p.mlp, s_w, s_b);
-    float x[kMlpIn];
-    R pij[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-    if constexpr (VISC) {
+  if constexpr ((GUESS == kGuessMlp || GUESS == kGuessMlpAll) && sizeof(R) == 4) {
+    // learned guess: features -> BF16 tensor-core MLP, 32 cells per warp.
+    // kGuessMlp runs it only for warps holding a cell that leaves vacuum in
+    // this stage (its stage velocity is the vacuum's 0, far from the root of
+    // a cell at the fast edge of the flow), and only blocks holding such a
+    // warp load the weights; every other cell starts from its stage velocity,
+    // which is closer to the root than the network's guess
+    bool want = active;
+    if constexpr (GUESS == kGuessMlp) {
       if (active) {
-        pij[0] = p.piout[4][c]; pij[1] = p.piout[5][c]; pij[2] = p.piout[6][c];
-        pij[3] = p.piout[7][c]; pij[4] = p.piout[8][c]; pij[5] = p.piout[9][c];
+        const R a = p.pr.u[0][c], b = p.pr.u[1][c], d = p.pr.u[2][c];
+        const R w2 = a * a + b * b + d * d;
+        vg = sqrt(w2 / (R(1) + w2));
+        want = E >= p.eps_cut && !(p.pr.e[c] > R(0));
       }
     }
-    mlp_features<R>(active && E > R(0) ? E : R(1), Mx, My, Me, pij, x);
+    if (__syncthreads_or(want)) {
+      __shared__ __align__(16) __nv_bfloat16 s_w[kMlpSmemW];
+      __shared__ float s_b[kMlpBiasElems];
+      __shared__ __align__(16) __nv_bfloat16 s_x[kBlock / 32][32][kMlpSX];
+      __shared__ float s_y[kBlock / 32][32][4];
+      mlp_load_smem(p.mlp, s_w, s_b);
+      float x[kMlpIn];
+      R pij[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+      if constexpr (VISC) {
+        if (active) {
+          pij[0] = p.piout[4][c]; pij[1] = p.piout[5][c]; pij[2] = p.piout[6][c];
+          pij[3] = p.piout[7][c]; pij[4] = p.piout[8][c]; pij[5] = p.piout[9][c];
+        }
+      }
+      mlp_features<R>(active && E > R(0) ? E : R(1), Mx, My, Me, pij, x);
 #pragma unroll
-    for (int k = 0; k < 16; k += 2)
-      *reinterpret_cast<unsigned*>(&s_x[wid][lane][k]) = pack_bf16(k < kMlpIn ? x[k] : 0.f, k + 1 < kMlpIn ? x[k + 1] : 0.f);
-    __syncthreads();
-    mlp_tile16(&s_x[wid][0][0], s_w, s_b, &s_y[wid][0][0], lane);
-    mlp_tile16(&s_x[wid][16][0], s_w, s_b, &s_y[wid][16][0], lane);
-    __syncwarp();
-    const float vx = s_y[wid][lane][1], vy = s_y[wid][lane][2], ve = s_y[wid][lane][3];
-    vg = R(sqrtf(vx * vx + vy * vy + ve * ve));
+      for (int k = 0; k < 16; k += 2)
+        *reinterpret_cast<unsigned*>(&s_x[wid][lane][k]) = pack_bf16(k < kMlpIn ? x[k] : 0.f, k + 1 < kMlpIn ? x[k + 1] : 0.f);
+      __syncthreads();
+      if (__any_sync(0xffffffffu, want)) {   // warp-uniform: the MMA takes the whole warp
+        mlp_tile16(&s_x[wid][0][0], s_w, s_b, &s_y[wid][0][0], lane);
+        mlp_tile16(&s_x[wid][16][0], s_w, s_b, &s_y[wid][16][0], lane);
+        __syncwarp();
+        if (want) {
+          const float vx = s_y[wid][lane][1], vy = s_y[wid][lane][2], ve = s_y[wid][lane][3];
+          vg = R(sqrtf(vx * vx + vy * vy + ve * ve));
+        }
+      }
+    }
   } else if constexpr (GUESS == kGuessPrevious) {
     if (active) {
       const R a = p.pr.u[0][c], b = p.pr.u[1][c], d = p.pr.u[2][c];

