@@ -354,6 +354,7 @@ def run_gpu(args):
         avgL = {k: (ms / n if n else 0.0) for k, (ms, n) in ktL.items()}
         domL = max(avgL, key=avgL.get)
         achL = KERNEL_WORDS[domL] * 4 * NL / (avgL[domL] / 1e3) / 1e9
+        trL = load_traffic("large_" + domL, stL.get("tile") if domL.startswith("stage") else None)
         valL = ws * NL * sL / (msL_max / 1e3)
         large = {"workload": "hot-spot event with mini-jet initial flow 261x261x121, dx=dy=0.08, deta=0.1, "
                              "dtau=0.005 fm, eta/s=0.16, 8000 spots (p_T exponential, mean 1.5 GeV), "
@@ -364,6 +365,10 @@ def run_gpu(args):
                           "ms_per_step": msL64_max / sL64},
                  "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[domL], "achieved": achL, "peak": peak,
                               "unit": "GB/s", "frac": achL / peak, "kernel_ms_avg": avgL,
+                              "traffic": (trL[0] + trL[1]) if trL else None,
+                              "read_traffic_ratio": (trL[0] / (KERNEL_READ_WORDS[domL] * 4 * NL)) if trL else None,
+                              "algorithmic_bytes_per_launch": KERNEL_WORDS[domL] * 4 * NL,
+                              "moved_bytes_per_launch": KERNEL_MOVED_WORDS[domL] * 4 * NL,
                               "step_frac_of_peak": (valL / ws) * LEDGER_WORDS * 4 / 1e9 / peak},
                  "newton_iters_per_solve": per(stL.get("n_newton_iters"), stL.get("n_newton_cells")),
                  "stats_fp32": {k: stL.get(k) for k in ("tau", "eps_max", "T_max", "n_polished", "n_rootfail",
@@ -413,6 +418,11 @@ def run_gpu(args):
         n32, ms_l32, st_l32, err32, eps32 = run_life(clv.CLV_FP32)
         n64, ms_l64, st_l64, err64, eps64 = run_life(clv.CLV_FP64, n32)
         live = eps64 > 1e-3
+        rel = np.zeros_like(eps64)
+        rel[live] = np.abs(eps32[live] / eps64[live] - 1)
+        imax = np.unravel_index(int(np.argmax(rel)), rel.shape)
+        edge = min(min(i, n - 1 - i) for i, n in zip(imax, rel.shape))
+        dense = eps64 > 0.1
         lifetime = {
             "workload": "the 261x261x121 mini-jet event from tau0 = 0.4 fm until max T < 137 MeV",
             "steps": n32, "tau_end": st_l32["tau"] if st_l32 else None,
@@ -426,13 +436,17 @@ def run_gpu(args):
             "accuracy_vs_fp64": {"cells_compared": int(live.sum()),
                                  "eps_linf_rel_where_eps_gt_1e-3":
                                      float(np.max(np.abs(eps32[live] / eps64[live] - 1))) if live.any() else None,
-                                 "eps_l1_rel": float(np.abs(eps32 - eps64).sum() / np.abs(eps64).sum())},
+                                 "eps_l1_rel": float(np.abs(eps32 - eps64).sum() / np.abs(eps64).sum()),
+                                 "eps_linf_rel_where_eps_gt_0.1": float(rel[dense].max()) if dense.any() else None,
+                                 "worst_cell": {"index": [int(i) for i in imax], "eps_fp64": float(eps64[imax]),
+                                                "cells_from_grid_edge": int(edge)},
+                                 "cells_over_1e-4": int((rel > 1e-4).sum())},
         }
         del eps32, eps64
 
     # ---- freeze-out surface of the same event: T_f = 137 MeV (the paper's
     # stopping temperature) through the EOS table, between the slices at
-    # tau = 2.4 and 2.5 fm; the four launches of clv_fo_find timed with
+    # tau = 2.4 and 2.5 fm; the three launches of clv_fo_find timed with
     # events on the handle's stream, L2 flushed between calls (untimed)
     freezeout = cooperfrye = None
     if args.freezeout:
@@ -498,9 +512,10 @@ def run_gpu(args):
                                    "frac_of_measured_fma_rate": cf_ach / fma32}}
         freezeout = {"workload": "the same event at tau = 2.4 -> 2.5 fm (10 steps apart), T_f = 137 MeV",
                      "eps_f": eps_f, "hypercubes": ncube, "elements": nel, "ms_per_find": fms,
-                     "value": ncube / (fms / 1e3), "unit": "hypercubes/s", "launches_per_find": 4,
+                     "value": ncube / (fms / 1e3), "unit": "hypercubes/s", "launches_per_find": 3,
+                     "memsets_per_find": 1,
                      "l2": "flushed between calls (512 MiB write, untimed)",
-                     "roofline": {"bound": "hbm", "kernel": "clv_fo_find (classify, scan, compact, elements)",
+                     "roofline": {"bound": "hbm", "kernel": "clv_fo_find (classify with the last-CTA scan, compact, elements)",
                                   "achieved": fo_ach, "peak": peak, "unit": "GB/s", "frac": fo_ach / peak,
                                   "algorithmic_bytes_per_find": fo_alg}}
         g.close()
@@ -801,6 +816,60 @@ def run_reference(args):
     }))
 
 
+def run_slab(args):
+    """--slab: one 261x261x121 mini-jet event split in x over the N ranks
+    (x-slabs with halo exchange before every stage, NCCL point-to-point
+    between neighbours; the stats are combined over the slabs in FP64).
+    Strong scaling: the event is fixed, N GPUs share it.  FP32, previous-step
+    guess; K timed steps after W warm-up steps, max over ranks."""
+    import socket
+    import torch
+    import torch.distributed as dist
+    from paper_1802_04449_gb300 import clv
+    from paper_1802_04449_gb300 import inputs as I
+    from paper_1802_04449_gb300 import slab as S
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local if ws > 1 else 0)
+    if not dist.is_initialized():
+        if ws == 1:   # a single-rank group: the same code path, no neighbour to exchange with
+            sk = socket.socket()
+            sk.bind(("127.0.0.1", 0))
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", str(sk.getsockname()[1]))
+            sk.close()
+            dist.init_process_group("nccl", rank=0, world_size=1)
+        else:
+            dist.init_process_group("nccl")
+    case = I.minijet_event()
+    sl = S.DistSlab(case, rank, ws, clv.CLV_FP32)
+    sl.step(args.warmup)
+    torch.cuda.synchronize()
+    dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = sl.h.stream
+    e0.record(stream)
+    sl.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = t.item()
+    st = sl.step(1, stats=True)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": case.ncells * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "mode": "slab",
+            "config": {"workload": "hot-spot event with mini-jet initial flow 261x261x121 split in x over the ranks",
+                       "cells_per_event": case.ncells, "slab_planes": [n for _, n in S.partition(case.nx, ws)],
+                       "parallelism": f"x-slabs over {ws} rank(s), halo exchange before every stage",
+                       "guess": "previous-step"},
+            "stats": {k: st.get(k) for k in ("tau", "eps_max", "T_max", "E_tot", "error_word")}}))
+    dist.destroy_process_group()
+
+
 def profile_case(args):
     """A short run through the C ABI for capture under a profiler: the
     kernels of interest are the last launches.  The event (--case: the
@@ -903,7 +972,14 @@ def main():
     pc.add_argument("--surface", action="store_true")
     pc.add_argument("--zeta-over-s", type=float, default=0.0)
     pc.add_argument("--charge", action="store_true")
+    ap.add_argument("--slab", action="store_true",
+                    help="one 261x261x121 event split in x over the ranks (strong scaling) instead of the default")
     args = ap.parse_args()
+    if args.slab:
+        if args.warmup < 3:
+            args.warmup = 3
+        run_slab(args)
+        return
     if args.profile_case:
         profile_case(args)
         return

@@ -371,13 +371,14 @@ __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, 
 __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 // minmod(a, b): 0 unless a and b share a sign, else the one of smaller
-// magnitude.  Branch-free: with s the sign bit of a, min(|a|, s*b) is the
-// smaller magnitude when the signs agree and negative when they differ;
+// magnitude (the value is a, b or 0 exactly).  FP32: b clamped to the
+// interval between 0 and a, four min/max operations on the ALU pipe.  FP64:
+// min/max run on GB300's narrow FP64 pipe, so two of them with the signs
+// handled by integer operations: with s the sign bit of a, min(|a|, s*b) is
+// the smaller magnitude when the signs agree and negative when they differ;
 // clamp at 0 and give it the sign of a.
 __device__ __forceinline__ float minmod(float a, float b) {
-  const unsigned sa = __float_as_uint(a) & 0x80000000u;
-  const float t = fmaxf(fminf(fabsf(a), __uint_as_float(__float_as_uint(b) ^ sa)), 0.0f);
-  return __uint_as_float(__float_as_uint(t) | sa);
+  return fminf(fmaxf(b, fminf(a, 0.0f)), fmaxf(a, 0.0f));
 }
 __device__ __forceinline__ double minmod(double a, double b) {
   const unsigned long long sa = (unsigned long long)__double_as_longlong(a) & 0x8000000000000000ull;

@@ -702,18 +702,19 @@ __global__ void __launch_bounds__(kBlock, RecoverMinBlocks<R>::value) recover_ke
   R vg = R(-1);
   if constexpr ((GUESS == kGuessMlp || GUESS == kGuessMlpAll) && sizeof(R) == 4) {
     // learned guess: features -> BF16 tensor-core MLP, 32 cells per warp.
-    // kGuessMlp runs it only for warps holding a cell that leaves vacuum in
-    // this stage (its stage velocity is the vacuum's 0, far from the root of
-    // a cell at the fast edge of the flow), and only blocks holding such a
-    // warp load the weights; every other cell starts from its stage velocity,
-    // which is closer to the root than the network's guess
+    // kGuessMlp runs it only for warps holding a moving cell whose stage
+    // velocity is exactly 0 -- a cell leaving vacuum (vacuum cells store
+    // u~ = 0), whose root at the fast edge of the flow is far from 0 -- and
+    // only blocks holding such a warp load the weights; every other cell
+    // starts from its stage velocity, which is closer to the root than the
+    // network's guess
     bool want = active;
     if constexpr (GUESS == kGuessMlp) {
       if (active) {
         const R a = p.pr.u[0][c], b = p.pr.u[1][c], d = p.pr.u[2][c];
         const R w2 = a * a + b * b + d * d;
         vg = sqrt(w2 / (R(1) + w2));
-        want = E >= p.eps_cut && !(p.pr.e[c] > R(0));
+        want = E >= p.eps_cut && w2 == R(0) && (Mx != R(0) || My != R(0) || Me != R(0));
       }
     }
     if (__syncthreads_or(want)) {

@@ -89,13 +89,16 @@ def _new_slab(case, precision, **kw):
 
 class DistSlab:
     """This rank's slab of an event (torch.distributed initialised, one rank
-    per slab, slabs in rank order along x)."""
+    per slab, slabs in rank order along x).  ``make(sub_case, precision,
+    **kw)`` builds the slab's handle (an x-slab clv.Hydro by default; any
+    object with the same slab calls works, which lets the stage loop and the
+    exchange be tested on CPU)."""
 
-    def __init__(self, case, rank, world, precision=clv.CLV_FP64, group=None, **kw):
+    def __init__(self, case, rank, world, precision=clv.CLV_FP64, group=None, make=None, **kw):
         import torch
         self.rank, self.world, self.group = rank, world, group
         self.x_begin, self.nx = partition(case.nx, world)[rank]
-        self.h = _new_slab(slab_case(case, self.x_begin, self.nx), precision, **kw)
+        self.h = (make or _new_slab)(slab_case(case, self.x_begin, self.nx), precision, **kw)
         n = self.h.halo_bytes()
         self._send = [torch.empty(n, dtype=torch.uint8, device=self.h.device) for _ in range(2)]
         if self.h.viscous_pending():

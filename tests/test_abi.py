@@ -69,6 +69,7 @@ def test_freezeout_host_checks(lib):
     n = ctypes.c_size_t()
     assert so.clv_fo_scratch_bytes(ctypes.byref(g), ctypes.byref(n)) == 0
     ncube = 96 * 96 * 40
+    # a flag byte and a list entry per hypercube, a count and an offset per 256-hypercube block
     assert 5 * ncube <= n.value <= 5 * ncube + 16 * (ncube // 256 + 1) + 128
     assert so.clv_fo_scratch_bytes(ctypes.byref(clv.fo_grid((1, 4, 4), 0.2, 0.2, 0.2)), ctypes.byref(n)) == 1
     assert ">= 2" in so.clv_last_error(None).decode()

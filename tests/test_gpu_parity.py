@@ -205,24 +205,30 @@ def test_full_size_viscous_event_one_step():
     assert fp32_eps_err(o, g32) <= FP32_TOL
 
 
-def test_largest_event_one_step():
+LARGEST_STEPS = 24
+
+
+def test_largest_event_24_steps():
     """The largest configuration, the 261x261x121 mini-jet event (8.2 M cells,
-    initial state from T^{tau mu}, eta/s = 0.16): one full step, every cell,
-    FP64 to the FP64 bar and FP32 (the benchmark's precision) to the FP32 bar."""
+    initial state from T^{tau mu}, eta/s = 0.16): 24 full steps (about a
+    minute of oracle time on the host's cores), every cell, FP64 to the FP64
+    bar and FP32 (the benchmark's precision) to the FP32 bar."""
     case = I.minijet_event()
     oracle.set_threads(0)
     o = oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
                       case.eta_over_s, case.eos, case.cartesian, case.periodic)
     o.set_initial_T(case.T0)
-    o.step(1)
+    o.step(LARGEST_STEPS)
     g64 = clv.from_case(case, clv.CLV_FP64)
     g64.set_initial_case(case)
-    g64.step(1, stats=True)
+    st = g64.step(LARGEST_STEPS, stats=True)
+    assert st["error_word"] == 0
     compare_fp64(o, g64, viscous=True, fields=["eps", "ux", "ueta", "Ttt", "Ttx", "pixx", "piee"])
     g64.close()
     g32 = clv.from_case(case, clv.CLV_FP32)
     g32.set_initial_case(case)
-    g32.step(1, stats=True)
+    st = g32.step(LARGEST_STEPS, stats=True)
+    assert st["error_word"] == 0
     assert fp32_eps_err(o, g32) <= FP32_TOL
     g32.close()
 
@@ -573,3 +579,35 @@ def test_x_slab_mini_jet_initial_state():
     sl.step(4)
     for k in ("eps", "ux", "pixy"):
         assert np.array_equal(sl.get([k])[k], g.get([k])[k]), k
+
+
+def test_dist_slab_on_one_rank_equals_the_single_domain():
+    """The path bench.py --slab times: DistSlab on a one-rank NCCL group (no
+    neighbour, zero-gradient edges, the stats combined by all_gather) gives
+    the single domain's fields bit for bit, FP32 and FP64."""
+    import os
+    import socket
+
+    import torch
+    import torch.distributed as dist
+    from paper_1802_04449_gb300 import slab as S
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(sk.getsockname()[1])
+    sk.close()
+    torch.cuda.set_device(0)
+    dist.init_process_group("nccl", rank=0, world_size=1)
+    try:
+        case = small_hotspot(seed=12, nx=15, ny=13, neta=9, eta_over_s=0.08)
+        for prec in (clv.CLV_FP64, clv.CLV_FP32):
+            sl = S.DistSlab(case, 0, 1, prec)
+            st = sl.step(5, stats=True)
+            g = clv.from_case(case, prec)
+            g.set_initial(case.eps, case.ux, case.uy, case.ueta)
+            sg = g.step(5, stats=True)
+            for k in ("eps", "ux", "ueta", "pixx", "piee"):
+                assert np.array_equal(sl.h.get([k])[k], g.get([k])[k]), (prec, k)
+            assert st["eps_max"] == sg["eps_max"] and st["E_tot"] == pytest.approx(sg["E_tot"], rel=1e-12)
+    finally:
+        dist.destroy_process_group()
