@@ -4,12 +4,11 @@
 // (cooper_frye), from the piecewise-linear interpolant over the Freudenthal
 // triangulation of each space-time hypercube.
 //
-// Three kernel launches on the caller's stream (after a 4-byte memset):
-//   classify  one thread per hypercube (a CTA covers 256, eta fastest across
-//             the warp): crossed or not from the 16 corner values; a flag
-//             byte per hypercube and a count per CTA.  The CTA that finishes
-//             last (a ticket counter, no CTA waits for another) turns the
-//             counts into CTA offsets and the element count;
+// Four launches on the caller's stream:
+//   classify  one thread per hypercube: crossed or not (16 corner loads, eta
+//             fastest across the warp); a flag byte and a count per CTA;
+//   scan      one CTA: exclusive prefix of the CTA counts -> CTA offsets and
+//             the element count;
 //   compact   one thread per hypercube: the crossed hypercubes' indices in
 //             increasing order (CTA offset + rank in the CTA);
 //   elements  persistent, one warp per element: lane s < 24 takes simplex s
@@ -28,9 +27,8 @@ void clv_set_global_error(const char* msg);
 
 namespace {
 
-constexpr int kThreads = 256;      // classify CTAs
-constexpr int kCubesPerThread = 1;
-constexpr int kBlockCubes = kThreads * kCubesPerThread;   // hypercubes per classify block
+constexpr int kThreads = 256;      // classify / compact CTAs
+constexpr int kScanThreads = 1024;
 constexpr int kElemThreads = 256;  // 8 warps per CTA
 constexpr int kNF = 13;            // interpolated fields: u~ (3), pi~ (10)
 constexpr unsigned kFull = 0xffffffffu;
@@ -62,73 +60,59 @@ __device__ __forceinline__ void decode_cube(long long c, int cy, int ce, int& i,
   i = (int)(t / cy);
 }
 
-// exclusive prefix of x over the CTA (kThreads threads); *sum receives the total
-__device__ __forceinline__ int block_exclusive_scan(int x, int* s_warp, int* sum) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  int incl = x;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int y = __shfl_up_sync(kFull, incl, d);
-    if (lane >= d) incl += y;
-  }
-  __syncthreads();   // s_warp is free
-  if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  int before = 0, all = 0;
-#pragma unroll
-  for (int w = 0; w < kThreads / 32; ++w) {
-    const int t = s_warp[w];
-    before += w < warp ? t : 0;
-    all += t;
-  }
-  *sum = all;
-  return before + incl - x;
-}
-
 template <typename R>
 __global__ void __launch_bounds__(kThreads) fo_classify_kernel(FoArgs<R> a, unsigned char* __restrict__ flags,
-                                                               int* __restrict__ counts, unsigned* __restrict__ ticket,
+                                                               int* __restrict__ counts) {
+  const long long c = (long long)blockIdx.x * kThreads + threadIdx.x;
+  int crossed = 0;
+  if (c < a.ncube) {
+    int i, j, k;
+    decode_cube(c, a.cy, a.ce, i, j, k);
+    int nin = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) nin += a.e[q & 1][corner_offset(a, i, j, k, q)] >= a.ef;
+    crossed = nin > 0 && nin < 16;
+    flags[c] = (unsigned char)crossed;
+  }
+  const int n = __syncthreads_count(crossed);
+  if (threadIdx.x == 0) counts[blockIdx.x] = n;
+}
+
+__global__ void __launch_bounds__(kScanThreads) fo_scan_kernel(const int* __restrict__ counts, int nblk,
                                                                long long* __restrict__ offsets,
                                                                long long* __restrict__ total,
-                                                               int64_t* __restrict__ d_count, int nblk) {
-  __shared__ int s_warp[kThreads / 32];
-  __shared__ int s_last;
-  const long long base = (long long)blockIdx.x * kBlockCubes;
-  int mine = 0;
-#pragma unroll 2
-  for (int q = 0; q < kCubesPerThread; ++q) {
-    const long long c = base + q * kThreads + threadIdx.x;
-    if (c < a.ncube) {
-      int i, j, k;
-      decode_cube(c, a.cy, a.ce, i, j, k);
-      int nin = 0;
-#pragma unroll
-      for (int v = 0; v < 16; ++v) nin += a.e[v & 1][corner_offset(a, i, j, k, v)] >= a.ef;
-      const int crossed = nin > 0 && nin < 16;
-      flags[c] = (unsigned char)crossed;
-      mine += crossed;
-    }
-  }
-  int n = 0;
-  block_exclusive_scan(mine, s_warp, &n);
-  if (threadIdx.x == 0) {
-    counts[blockIdx.x] = n;
-    __threadfence();   // the count is visible before the ticket is taken
-    s_last = atomicAdd(ticket, 1u) == (unsigned)(nblk - 1);
-  }
+                                                               int64_t* __restrict__ d_count) {
+  __shared__ long long warp_sum[kScanThreads / 32];
+  __shared__ long long carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
   __syncthreads();
-  if (!s_last) return;
-  // the last CTA: every other CTA's count is written; exclusive prefix in
-  // chunks of kThreads, reading through L2 (__ldcg)
-  __threadfence();
-  long long carry = 0;
-  for (int b0 = 0; b0 < nblk; b0 += kThreads) {
-    const int b = b0 + threadIdx.x;
-    const int v = b < nblk ? __ldcg(counts + b) : 0;
-    int chunk = 0;
-    const int ex = block_exclusive_scan(v, s_warp, &chunk);
-    if (b < nblk) offsets[b] = carry + ex;
-    carry += chunk;
+  for (int base = 0; base < nblk; base += kScanThreads) {
+    const int b = base + threadIdx.x;
+    const long long v = b < nblk ? counts[b] : 0;
+    long long x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const long long y = __shfl_up_sync(kFull, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      long long w = warp_sum[lane];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const long long y = __shfl_up_sync(kFull, w, d);
+        if (lane >= d) w += y;
+      }
+      warp_sum[lane] = w;
+    }
+    __syncthreads();
+    const long long excl = carry + (warp > 0 ? warp_sum[warp - 1] : 0) + x - v;
+    if (b < nblk) offsets[b] = excl;
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) carry = excl + v;
+    __syncthreads();
   }
   if (threadIdx.x == 0) {
     *total = carry;
@@ -402,7 +386,7 @@ __global__ void __launch_bounds__(kElemThreads, 4) fo_elements_kernel(FoArgs<R> 
 }
 
 struct ScratchLayout {
-  size_t total, ticket, counts, offsets, flags, list, bytes;
+  size_t total, counts, offsets, flags, list, bytes;
   long long ncube;
   int nblk;
 };
@@ -412,12 +396,10 @@ size_t align16(size_t x) { return (x + 15) / 16 * 16; }
 ScratchLayout scratch_layout(const clv_fo_grid* g) {
   ScratchLayout L{};
   L.ncube = (long long)(g->nx - 1) * (g->ny - 1) * (g->neta - 1);
-  L.nblk = (int)((L.ncube + kBlockCubes - 1) / kBlockCubes);
+  L.nblk = (int)((L.ncube + kThreads - 1) / kThreads);
   size_t o = 0;
   L.total = o;
   o = align16(o + 8);
-  L.ticket = o;
-  o = align16(o + 4);
   L.counts = o;
   o = align16(o + (size_t)L.nblk * 4);
   L.offsets = o;
@@ -492,23 +474,20 @@ clv_status fo_run(const clv_fo_grid* g, const clv_fo_slice* s0, const clv_fo_sli
   int* counts = reinterpret_cast<int*>(sc + L.counts);
   long long* offsets = reinterpret_cast<long long*>(sc + L.offsets);
   unsigned char* flags = reinterpret_cast<unsigned char*>(sc + L.flags);
-  unsigned* ticket = reinterpret_cast<unsigned*>(sc + L.ticket);
   int* list = reinterpret_cast<int*>(sc + L.list);
-  cudaError_t err = cudaMemsetAsync(ticket, 0, sizeof(unsigned), st);
-  if (err == cudaSuccess) {
-    fo_classify_kernel<R><<<L.nblk, kThreads, 0, st>>>(a, flags, counts, ticket, offsets, total, d_count, L.nblk);
-    fo_compact_kernel<<<L.nblk, kThreads, 0, st>>>(flags, L.ncube, offsets, list);
-    int dev = 0, sms = 1, per_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fo_elements_kernel<R>, kElemThreads, 0);
-    const long long need = (L.ncube + kElemThreads / 32 - 1) / (kElemThreads / 32);
-    long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    if (blocks > need) blocks = need;
-    fo_elements_kernel<R><<<(unsigned)blocks, kElemThreads, 0, st>>>(a, list, total, (long long)capacity,
-                                                                     static_cast<R*>(d_rec), d_cube);
-    err = cudaGetLastError();
-  }
+  fo_classify_kernel<R><<<L.nblk, kThreads, 0, st>>>(a, flags, counts);
+  fo_scan_kernel<<<1, kScanThreads, 0, st>>>(counts, L.nblk, offsets, total, d_count);
+  fo_compact_kernel<<<L.nblk, kThreads, 0, st>>>(flags, L.ncube, offsets, list);
+  int dev = 0, sms = 1, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fo_elements_kernel<R>, kElemThreads, 0);
+  const long long need = (L.ncube + kElemThreads / 32 - 1) / (kElemThreads / 32);
+  long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
+  if (blocks > need) blocks = need;
+  fo_elements_kernel<R><<<(unsigned)blocks, kElemThreads, 0, st>>>(a, list, total, (long long)capacity,
+                                                                   static_cast<R*>(d_rec), d_cube);
+  const cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) {
     clv_set_global_error((std::string("clv_fo_find: ") + cudaGetErrorString(err)).c_str());
     return CLV_ECUDA;

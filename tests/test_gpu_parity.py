@@ -611,3 +611,16 @@ def test_dist_slab_on_one_rank_equals_the_single_domain():
             assert st["eps_max"] == sg["eps_max"] and st["E_tot"] == pytest.approx(sg["E_tot"], rel=1e-12)
     finally:
         dist.destroy_process_group()
+
+
+def test_fma_rate_is_a_plausible_peak():
+    """clv_fma_rate (the ALU-roofline denominator) measures the FMA rate of
+    this GPU: FP32 far above FP64, both within a factor of two of the
+    GB300's nominal rates (FP32 152 SMs x 128 lanes x 2 x ~2 GHz = 80
+    TFLOP/s, FP64 1.25 TFLOP/s); other precisions are refused."""
+    f64 = clv.fma_rate(clv.CLV_FP64)
+    f32 = clv.fma_rate(clv.CLV_FP32)
+    assert 0.6 < f64 < 2.5, f64
+    assert 40.0 < f32 < 160.0, f32
+    with pytest.raises(clv.ClvError):
+        clv.fma_rate(7)
