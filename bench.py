@@ -440,7 +440,13 @@ def run_gpu(args):
                                  "eps_linf_rel_where_eps_gt_0.1": float(rel[dense].max()) if dense.any() else None,
                                  "worst_cell": {"index": [int(i) for i in imax], "eps_fp64": float(eps64[imax]),
                                                 "cells_from_grid_edge": int(edge)},
-                                 "cells_over_1e-4": int((rel > 1e-4).sum())},
+                                 "cells_over_1e-4": int((rel > 1e-4).sum()),
+                                 "by_eps_band": {f"[{lo:g},{hi:g})": {
+                                     "cells": int(((eps64 >= lo) & (eps64 < hi)).sum()),
+                                     "linf": float(rel[(eps64 >= lo) & (eps64 < hi)].max())
+                                     if ((eps64 >= lo) & (eps64 < hi)).any() else None,
+                                     "over_1e-4": int((rel[(eps64 >= lo) & (eps64 < hi)] > 1e-4).sum())}
+                                     for lo, hi in ((1e-3, 2e-3), (2e-3, 1e-2), (1e-2, 0.1), (0.1, 1e9))}},
         }
         del eps32, eps64
 

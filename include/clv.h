@@ -293,8 +293,10 @@ clv_status clv_mlp_train(float* d_params, float* d_work, const float* d_X, const
  * clv_step, after every event's initial state was set.
  * Each event's tile follows a tiling policy shared by the batch: at most
  * max_threads threads per CTA (TJ as large as that allows, TK from neta, at
- * most 32 columns) and x chunks of about `chunk` planes; the default is 256
- * (128 in FP64) threads and 32 planes.  clv_autotune on a started batch
+ * most 32 columns) and x chunks of about `chunk` planes; the default is 384
+ * (128 in FP64) threads and 32 planes.  The persistent stage launch holds as
+ * many CTAs per SM as the device's occupancy calculator allows for the
+ * policy's largest tile.  clv_autotune on a started batch
  * times the current policy and up to max_candidates others (thread caps of
  * 1, 3/4 and 1/2 of the limit, chunks of 16-64 planes; reps stage-1 launches
  * each, which leave the state unchanged), keeps the fastest (the current
@@ -317,7 +319,7 @@ clv_status clv_batch_get_fields(clv_handle* h, int event, uint32_t which_mask, d
  * Synchronises the stream. */
 clv_status clv_batch_event_stats(clv_handle* h, int event, clv_stats* out);
 
-/* Explicit tiling policy of a batch (see above): max_threads in [32, 256]
+/* Explicit tiling policy of a batch (see above): max_threads in [32, 384]
  * (capped at 128 in FP64), chunk in [1, 4096] planes.  CLV_EINVAL if out of
  * range, not a batch, or if a tile would exceed the shared memory of a CTA.
  * Synchronises the stream. */
@@ -382,8 +384,10 @@ typedef struct {
 
 clv_status clv_get_tile(clv_handle* h, clv_tile_info* out);
 
-/* Explicit shape; CX = 0 picks the x chunking by the makespan rule.
- * CLV_EINVAL if out of range or beyond the thread / shared-memory limits. */
+/* Explicit shape; CX = 0 picks the x chunking by the makespan rule (with as
+ * many CTAs per SM as the occupancy calculator allows at this shape).
+ * CLV_EINVAL if out of range or beyond the thread limit ((TJ + 1)(TK + 1) <=
+ * 384 in FP32, 128 in FP64) or the 227 KiB shared-memory limit of a CTA. */
 clv_status clv_set_tile(clv_handle* h, int TJ, int TK, int CX);
 
 /* Autotuner: times the current shape and up to max_candidates modelled-best

@@ -373,18 +373,20 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 // minmod(a, b): 0 unless a and b share a sign, else the one of smaller
 // magnitude (the value is a, b or 0 exactly).  FP32: b clamped to the
 // interval between 0 and a, four min/max operations on the ALU pipe.  FP64:
-// min/max run on GB300's narrow FP64 pipe, so two of them with the signs
-// handled by integer operations: with s the sign bit of a, min(|a|, s*b) is
-// the smaller magnitude when the signs agree and negative when they differ;
-// clamp at 0 and give it the sign of a.
+// min/max and comparisons would run on GB300's narrow FP64 pipe, so the
+// choice is made on the bit patterns with integer operations: for finite
+// IEEE values the magnitudes order like their bits without the sign; equal
+// magnitudes give a.
 __device__ __forceinline__ float minmod(float a, float b) {
   return fminf(fmaxf(b, fminf(a, 0.0f)), fmaxf(a, 0.0f));
 }
 __device__ __forceinline__ double minmod(double a, double b) {
-  const unsigned long long sa = (unsigned long long)__double_as_longlong(a) & 0x8000000000000000ull;
-  const double t =
-      fmax(fmin(fabs(a), __longlong_as_double((long long)((unsigned long long)__double_as_longlong(b) ^ sa))), 0.0);
-  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(t) | sa));
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+  const unsigned long long mag = 0x7fffffffffffffffull;
+  const bool same = ((ua ^ ub) >> 63) == 0ull;
+  const unsigned long long pick = (ub & mag) < (ua & mag) ? ub : ua;
+  return __longlong_as_double((long long)(same ? pick : 0ull));
 }
 
 }  // namespace clv
