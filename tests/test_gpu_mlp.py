@@ -219,9 +219,9 @@ def test_learned_guess_gains_and_keeps_parity(trained):
     Newton iterations than the solver's cold start, mean and warp maximum.
     Where a stage velocity exists it is closer to the root than the network,
     so the learned mode seeds only the cells leaving vacuum (stage velocity
-    0): it needs fewer iterations than the previous-step guess alone, whose
-    start for those cells is v = 0.  Every evolution matches the FP64 oracle
-    within 1e-4 where eps > 1e-3 GeV/fm^3."""
+    0); its iteration count stays within 1% of the previous-step guess alone
+    (it gains on some events and loses on others).  Every evolution matches
+    the FP64 oracle within 1e-4 where eps > 1e-3 GeV/fm^3."""
     p, _, _, _ = trained
     case = _gain_case(31)
     params = p.cpu().numpy()
@@ -237,13 +237,19 @@ def test_learned_guess_gains_and_keeps_parity(trained):
     # this late state has filled the grid: no cell leaves vacuum, and the
     # learned mode is the previous-step guess
     assert res["mlp"][1] == res["previous"][1]
-    # a peripheral event (b = 11 fm, 20 spots) expanding into vacuum: the
-    # cells it reaches start from the network instead of v = 0
-    edge = I.hotspot_event(nx=41, ny=41, neta=11, n_spots=20, seed=5, b=11.0)
-    e_prev = _run_mode(edge, clv.CLV_GUESS_PREVIOUS, None, skip=2, run=60)[1]
-    e_mlp = _run_mode(edge, clv.CLV_GUESS_MLP, params, skip=2, run=60)[1]
-    print("expanding into vacuum, previous / learned:", e_prev, e_mlp)
-    assert e_mlp[0] < e_prev[0] and e_mlp[1] <= e_prev[1]
+    # peripheral events expanding into vacuum: the cells they reach start from
+    # the network instead of v = 0.  Measured, that is no reliable gain: a
+    # little fewer iterations for one event (b = 11 fm, 20 spots), a little
+    # more for another (b = 11.5 fm, 3 spots, a quarter of the grid vacuum at
+    # first).  Asserted: the learned mode stays within 1% of the previous-step
+    # guess alone
+    for kw in (dict(nx=41, ny=41, neta=11, n_spots=20, seed=5, b=11.0),
+               dict(nx=49, ny=49, neta=9, n_spots=3, seed=3, b=11.5)):
+        edge = I.hotspot_event(**kw)
+        e_prev = _run_mode(edge, clv.CLV_GUESS_PREVIOUS, None, skip=2, run=60)[1]
+        e_mlp = _run_mode(edge, clv.CLV_GUESS_MLP, params, skip=2, run=60)[1]
+        print("expanding into vacuum", kw, "previous / learned:", e_prev, e_mlp)
+        assert abs(e_mlp[0] - e_prev[0]) <= 0.01 * e_prev[0] and abs(e_mlp[1] - e_prev[1]) <= 0.01 * e_prev[1]
     o = oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
                       case.eta_over_s, case.eos)
     o.set_initial(case.eps, case.ux, case.uy, case.ueta)
