@@ -658,7 +658,7 @@ static void heun_step(orc_t* h, int viscous) {
             s->Pi[c] = regulate_Pi(h, s1->ed[c], 0.5 * (un[0] * s->Pi[c] + us[0] * s1->Pi[c] + hs * SPi) / u1[0]);
         }
         /* keep u^n as u^{n-1} for the next step */
-        h->up[0][c] = un[1]; h->up[1][c] = un[2]; h->up[2][c] = un[3];
+        if (PLANT != 23) { h->up[0][c] = un[1]; h->up[1][c] = un[2]; h->up[2][c] = un[3]; }
         recover(h, tn1, c, s, viscous, &nres, &nfail);
       }
   h->tau = tn1;
@@ -802,7 +802,7 @@ int orc_set_initial(orc_t* h, const double* eps, const double* ux, const double*
         h->s.u[0][c] = u[1]; h->s.u[1][c] = u[2]; h->s.u[2][c] = u[3];
         h->up[0][c] = u[1]; h->up[1][c] = u[2]; h->up[2][c] = u[3];
       }
-  if (h->viscous) {
+  if (h->viscous && PLANT != 22) {
     /* R8: one pi-free Heun step gives u^1_ideal; u^{-1} = 2 u^0 - u^1_ideal */
     orc_fields save;
     fields_alloc(&save, h->NG);

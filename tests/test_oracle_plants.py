@@ -27,6 +27,9 @@ Bulk pressure (clv_oracle.c, R20):
  19 sign of the zeta theta~ term flipped  -> Bjorken bulk ODE / sound wave
  20 root solve without the Pi pressure shift -> decomposition of T^{tau mu}
  21 Pi left out of the pressure in the T~ fluxes -> linearised sound wave
+Velocity predictor (clv_oracle.c, R8 and the u* extrapolation of Sec. 3):
+ 22 first step without the pi-free step (u^{-1} = u^0) -> first-step predictor
+ 23 u^{n-1} never updated after a step    -> velocity history / second-order extrapolation
 """
 import numpy as np
 import pytest
@@ -37,6 +40,7 @@ import test_oracle_bulk as BU
 import test_oracle_charge as CH
 import test_oracle_cooperfrye as CF
 import test_oracle_freezeout as FO
+import test_oracle_predictor as PR
 
 CASES = {
     1: F.check_transversality,
@@ -60,6 +64,8 @@ CASES = {
     19: BU.check_bjorken_bulk,
     20: BU.check_decomposition,
     21: BU.check_bulk_sound_wave,
+    22: PR.check_first_step_predictor,
+    23: PR.check_velocity_history,
 }
 
 
