@@ -105,6 +105,16 @@ class ClvError(RuntimeError):
         self.status = status
 
 
+def check_device_arg(numel, device_index, want_numel, want_index, what, at_least=False):
+    """Refuse (CLV_EINVAL) a device array argument that has the wrong number
+    of values or lies on another device than the handle's: the C entry
+    points take plain pointers and trust the sizes they imply."""
+    if (numel < want_numel) if at_least else (numel != want_numel):
+        raise ClvError(1, f"{what} has {numel} values, {'at least ' if at_least else ''}{want_numel} expected")
+    if device_index != want_index:
+        raise ClvError(1, f"{what} is on device {device_index}, the handle on device {want_index}")
+
+
 _lock = threading.Lock()
 _lib = None
 EXPORTED = ["clv_workspace_bytes", "clv_create", "clv_create_ws", "clv_set_initial",
@@ -404,6 +414,8 @@ class Hydro:
         self._lib = load()
         self.torch = torch
         self.device = torch.device(device or "cuda")
+        self._dev_index = self.device.index if self.device.index is not None else torch.cuda.current_device()
+        self.device = torch.device("cuda", self._dev_index)
         self.cfg, self._keep = make_config(nx, ny, neta, dx, dy, deta, tau0, dtau, eta_over_s, eos,
                                            precision, cartesian, periodic, eps_cut, kernel, taupi_coef,
                                            lambda1_hat, halo_x, charge, zeta_over_s)
@@ -440,11 +452,18 @@ class Hydro:
 
     __del__ = close
 
+    def _device_arg(self, a, count, what, dtype=None):
+        """A CUDA tensor argument as a contiguous tensor of ``count`` values
+        (float64 unless ``dtype``) on the handle's device; CLV_EINVAL otherwise."""
+        check_device_arg(a.numel(), a.device.index, count, self._dev_index, what)
+        return a.to(dtype or self.torch.float64).contiguous()
+
     def set_initial(self, eps, ux, uy, ueta, pi=None):
         t = self.torch
         if isinstance(eps, t.Tensor) and eps.is_cuda:
-            arrs = [a.to(t.float64).contiguous() for a in (eps, ux, uy, ueta)]
-            pi_t = pi.to(t.float64).contiguous() if pi is not None else None
+            arrs = [self._device_arg(a, self.N, name) for a, name in ((eps, "eps"), (ux, "ux"), (uy, "uy"),
+                                                                       (ueta, "ueta"))]
+            pi_t = self._device_arg(pi, 10 * self.N, "pi") if pi is not None else None
             self._dev_keep = arrs + ([pi_t] if pi_t is not None else [])
             st = self._lib.clv_set_initial_device(self._h, *(ctypes.c_void_p(a.data_ptr()) for a in arrs),
                                                   ctypes.c_void_p(pi_t.data_ptr()) if pi_t is not None else None)
@@ -461,7 +480,7 @@ class Hydro:
         T^{tau y}, tau T^{tau eta}; pi = 0): host array or CUDA tensor."""
         t = self.torch
         if isinstance(T, t.Tensor) and T.is_cuda:
-            a = T.to(t.float64).contiguous()
+            a = self._device_arg(T, 4 * self.N, "T")
             self._dev_keep = [a]
             st = self._lib.clv_set_initial_T_device(self._h, ctypes.c_void_p(a.data_ptr()))
         else:
@@ -474,7 +493,7 @@ class Hydro:
         initial state: host array or CUDA tensor of the grid's shape."""
         t = self.torch
         if isinstance(n, t.Tensor) and n.is_cuda:
-            a = n.to(t.float64).contiguous()
+            a = self._device_arg(n, self.N, "n")
             self._dev_keep = [a]
             st = self._lib.clv_set_initial_n_device(self._h, ctypes.c_void_p(a.data_ptr()))
         else:
@@ -512,12 +531,19 @@ class Hydro:
         self._check(self._lib.clv_slab_halo_bytes(self._h, ctypes.byref(n)), self._h)
         return n.value
 
+    def _halo_buffer(self, buf):
+        if not (isinstance(buf, self.torch.Tensor) and buf.is_cuda and buf.dtype == self.torch.uint8
+                and buf.is_contiguous()):
+            raise ClvError(1, "a halo buffer is a contiguous uint8 CUDA tensor")
+        check_device_arg(buf.numel(), buf.device.index, self.halo_bytes(), self._dev_index, "halo buffer",
+                         at_least=True)
+        return ctypes.c_void_p(buf.data_ptr())
+
     def slab_pack(self, set_, side, buf):
-        self._check(self._lib.clv_slab_pack(self._h, int(set_), int(side), ctypes.c_void_p(buf.data_ptr())), self._h)
+        self._check(self._lib.clv_slab_pack(self._h, int(set_), int(side), self._halo_buffer(buf)), self._h)
 
     def slab_unpack(self, set_, side, buf):
-        self._check(self._lib.clv_slab_unpack(self._h, int(set_), int(side), ctypes.c_void_p(buf.data_ptr())),
-                    self._h)
+        self._check(self._lib.clv_slab_unpack(self._h, int(set_), int(side), self._halo_buffer(buf)), self._h)
 
     def slab_fill_edge(self, set_, side):
         self._check(self._lib.clv_slab_fill_edge(self._h, int(set_), int(side)), self._h)
@@ -584,6 +610,11 @@ class Hydro:
             Y = t.empty((self.N, 4), dtype=t.float32, device=self.device)
         if X.shape[0] < self.N or Y.shape[0] < self.N or not (X.is_contiguous() and Y.is_contiguous()):
             raise ValueError("sample buffers need N contiguous rows")
+        if X.dtype != t.float32 or Y.dtype != t.float32 or X.dim() != 2 or X.shape[1] != 10 or Y.dim() != 2 \
+                or Y.shape[1] != 4:
+            raise ClvError(1, "sample buffers are float32 (rows, 10) and (rows, 4)")
+        check_device_arg(X.numel(), X.device.index, X.numel(), self._dev_index, "X")
+        check_device_arg(Y.numel(), Y.device.index, Y.numel(), self._dev_index, "Y")
         n = t.zeros(1, dtype=t.int64, device=self.device)
         self._check(self._lib.clv_mlp_samples(self._h, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
                                               ctypes.c_void_p(n.data_ptr())), self._h)
@@ -593,7 +624,9 @@ class Hydro:
 
     def mlp_forward(self, X):
         t = self.torch
-        X = X.to(t.float32).contiguous()
+        if X.dim() != 2 or X.shape[1] != 10:
+            raise ClvError(1, f"features are (rows, 10), got {tuple(X.shape)}")
+        X = self._device_arg(X, X.numel(), "X", t.float32)
         Y = t.empty((X.shape[0], 4), dtype=t.float32, device=self.device)
         self._check(self._lib.clv_mlp_forward(self._h, ctypes.c_void_p(X.data_ptr()), X.shape[0],
                                               ctypes.c_void_p(Y.data_ptr())), self._h)

@@ -279,6 +279,29 @@ def test_error_paths():
     assert ei.value.status == 5
 
 
+def test_device_arguments_are_checked():
+    """CUDA tensors of the wrong size, or in host memory, are refused before
+    the C call (CLV_EINVAL); tensors of the right size still work."""
+    import torch
+    g = clv.Hydro(4, 4, 4, 0.1, 0.1, 0.1, 1.0, 0.01, eta_over_s=0.1)
+    ok = torch.full((4, 4, 4), 5.0, dtype=torch.float64, device=g.device)
+    z = torch.zeros_like(ok)
+    for bad in ((ok[:3], z, z, z), (ok, z, z, z.flatten()[:63])):
+        with pytest.raises(clv.ClvError) as ei:
+            g.set_initial(*bad)
+        assert ei.value.status == 1
+    with pytest.raises(clv.ClvError):
+        g.set_initial(ok, z, z, z, torch.zeros(9 * 64, dtype=torch.float64, device=g.device))   # pi: 10 x 64
+    with pytest.raises(clv.ClvError):
+        g.set_initial_T(torch.zeros(3 * 64, dtype=torch.float64, device=g.device))
+    g.set_initial(ok, z, z, z, torch.zeros(10 * 64, dtype=torch.float64, device=g.device))
+    assert g.step(1, stats=True)["error_word"] == 0
+    with pytest.raises(clv.ClvError):
+        g.mlp_forward(torch.zeros((5, 9), device=g.device))
+    with pytest.raises(clv.ClvError):
+        g.mlp_forward(torch.zeros((5, 10)))                  # host memory
+
+
 def test_tile_shapes_and_autotuner_leave_results_unchanged():
     """The tile shape is a schedule, not arithmetic: explicit shapes and the
     autotuner's choice give bit-identical fields to the default shape."""
