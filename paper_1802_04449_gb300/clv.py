@@ -242,7 +242,7 @@ class FoSlice:
     """A time slice for the freeze-out finder: the clv_fo_slice struct and
     the device memory it points into (kept alive here)."""
 
-    def __init__(self, tau, eps, u, pi=None, keep=()):
+    def __init__(self, tau, eps, u, pi=None, keep=(), extent=None):
         self.s = clv_fo_slice()
         self.s.tau = float(tau)
         self.s.eps = eps
@@ -251,6 +251,8 @@ class FoSlice:
         for q in range(10):
             self.s.pi[q] = pi[q] if pi is not None else None
         self.keep = list(keep)
+        # (values per array, device index, dtype) of a slice made from tensors; None for a handle's slice
+        self.extent = extent
 
     @classmethod
     def from_tensors(cls, tau, eps, u, pi=None):
@@ -260,8 +262,11 @@ class FoSlice:
         for t in ts:
             if not (t.is_cuda and t.is_contiguous() and t.dtype == eps.dtype and t.shape == eps.shape):
                 raise ValueError("slice arrays must be contiguous CUDA tensors of one dtype and shape")
+        if not all(t.device == eps.device for t in ts):
+            raise ValueError("slice arrays must be on one device")
         ptr = lambda t: ctypes.c_void_p(t.data_ptr())
-        return cls(tau, ptr(eps), [ptr(t) for t in u], [ptr(t) for t in pi] if pi is not None else None, keep=ts)
+        return cls(tau, ptr(eps), [ptr(t) for t in u], [ptr(t) for t in pi] if pi is not None else None, keep=ts,
+                   extent=(eps.numel(), eps.device.index, eps.dtype))
 
     @property
     def tau(self):
@@ -288,6 +293,8 @@ class FreezeoutFinder:
         self._lib = load()
         self.grid = grid
         self.device = torch.device(device or "cuda")
+        self.device = torch.device("cuda", self.device.index if self.device.index is not None
+                                   else torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         n = ctypes.c_size_t()
         _raise(self._lib, self._lib.clv_fo_scratch_bytes(ctypes.byref(grid), ctypes.byref(n)))
@@ -301,6 +308,15 @@ class FreezeoutFinder:
 
     def find(self, s0, s1, eps_f):
         V = ctypes.c_void_p
+        g = self.grid
+        need = g.nx * g.ny * (g.eta_pitch or g.neta)
+        dt = self.torch.float64 if g.precision == CLV_FP64 else self.torch.float32
+        for sl in (s0, s1):
+            if sl.extent is not None:     # a slice made from tensors: its arrays must cover the grid
+                numel, dev, dtype = sl.extent
+                if dtype != dt:
+                    raise ClvError(1, f"slice arrays are {dtype}, the grid's precision needs {dt}")
+                check_device_arg(numel, dev, need, self.device.index, "slice array", at_least=True)
         _raise(self._lib, self._lib.clv_fo_find(ctypes.byref(self.grid), ctypes.byref(s0.s), ctypes.byref(s1.s),
                                                 float(eps_f), V(self.rec.data_ptr()), V(self.cube.data_ptr()),
                                                 self.capacity, V(self.count.data_ptr()),
@@ -350,9 +366,17 @@ class CooperFrye:
         t = self.torch
         V = ctypes.c_void_p
         want = t.float64 if self.p.precision == CLV_FP64 else t.float32
-        if rec.dtype != want or not rec.is_contiguous() or (rec.dim() == 2 and rec.shape[1] != FO_NREC):
+        if rec.dtype != want or not rec.is_contiguous() or rec.dim() != 2 or rec.shape[1] != FO_NREC:
             raise ValueError("records must be a contiguous (n, 22) tensor of the precision's type")
+        dev = self.device.index if self.device.index is not None else t.cuda.current_device()
+        check_device_arg(rec.numel(), rec.device.index, rec.numel(), dev, "records")
         cap = rec.shape[0] if nel is None else int(nel)
+        if not 0 <= cap <= rec.shape[0]:
+            raise ClvError(1, f"nel = {cap} outside the {rec.shape[0]} rows of the records")
+        if d_nel is not None:
+            if d_nel.dtype != t.int64 or d_nel.numel() < 1:
+                raise ClvError(1, "d_nel is a device int64 tensor holding the element count")
+            check_device_arg(d_nel.numel(), d_nel.device.index, 1, dev, "d_nel", at_least=True)
         if cap != self._cap:
             n = ctypes.c_size_t()
             _raise(self._lib, self._lib.clv_cf_scratch_bytes(ctypes.byref(self.p), cap, self.nsp, *self.shape[1:],

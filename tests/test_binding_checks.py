@@ -44,3 +44,27 @@ def test_mlp_forward_refuses_feature_shape():
         clv.Hydro.mlp_forward(h, torch.zeros((3, 9)))
     with pytest.raises(clv.ClvError, match="device"):
         clv.Hydro.mlp_forward(h, torch.zeros((3, 10)))           # host memory
+
+
+def test_freezeout_find_refuses_short_or_mistyped_slices():
+    g = clv.fo_grid((5, 4, 3), 0.1, 0.1, 0.1, clv.CLV_FP32)
+    finder = types.SimpleNamespace(grid=g, torch=torch, device=torch.device("cuda", 0))
+    def sl(numel, dtype=torch.float32, dev=0):
+        return clv.FoSlice(1.0, None, [None] * 3, extent=(numel, dev, dtype))
+    with pytest.raises(clv.ClvError, match="values"):
+        clv.FreezeoutFinder.find(finder, sl(59), sl(60), 0.5)                  # 5 x 4 x 3 = 60 needed
+    with pytest.raises(clv.ClvError, match="precision"):
+        clv.FreezeoutFinder.find(finder, sl(60, torch.float64), sl(60), 0.5)
+    with pytest.raises(clv.ClvError, match="device"):
+        clv.FreezeoutFinder.find(finder, sl(60), sl(60, dev=1), 0.5)
+    g.eta_pitch = 4                                                             # rows of 4: 80 values
+    with pytest.raises(clv.ClvError, match="values"):
+        clv.FreezeoutFinder.find(finder, sl(60), sl(80), 0.5)
+
+
+def test_cooper_frye_refuses_records_it_cannot_read():
+    cf = types.SimpleNamespace(torch=torch, device=torch.device("cuda", 0), p=types.SimpleNamespace(precision=clv.CLV_FP32))
+    with pytest.raises(ValueError):
+        clv.CooperFrye.spectra(cf, torch.zeros(22, dtype=torch.float32))       # not (n, 22)
+    with pytest.raises(clv.ClvError, match="device"):
+        clv.CooperFrye.spectra(cf, torch.zeros((4, 22), dtype=torch.float32))  # host memory

@@ -104,6 +104,9 @@ def test_no_elements_gives_zero():
     out = cf.spectra(torch.ones((40, 22), dtype=torch.float32, device="cuda"), d_nel=n)
     torch.cuda.synchronize()
     assert np.all(out.cpu().numpy() == 0)
+    # a count beyond the records' rows is refused before the call
+    with pytest.raises(clv.ClvError):
+        cf.spectra(torch.ones((4, 22), dtype=torch.float32, device="cuda"), nel=5)
 
 
 def test_spectra_of_the_benchmark_surface():
