@@ -836,7 +836,7 @@ def run_reference(args):
                       case.eta_over_s, case.eos, nthreads=ncores)
     o.set_initial(case.eps, case.ux, case.uy, case.ueta)
     steps = max(1, min(args.steps, 20))
-    warm = max(0, min(args.warmup, 2))
+    warm = max(0, min(args.warmup, 3))
     o.step(warm)
     t0 = time.perf_counter()
     o.step(steps)
