@@ -444,11 +444,11 @@ static void kt_interface(const view_t* vw, int axis, double taus, size_t ia, siz
   double L[NR], Rr[NR];
   for (int q = 0; q < NR; ++q) {
     L[q] = Rb[q] + 0.5 * minmod(Rb[q] - Ra[q], Rc[q] - Rb[q]);
-    Rr[q] = Rc[q] - 0.5 * minmod(Rc[q] - Rb[q], Rd[q] - Rc[q]);
+    Rr[q] = Rc[q] - ((PLANT == 24) ? -0.5 : 0.5) * minmod(Rc[q] - Rb[q], Rd[q] - Rc[q]);
   }
   double vl = L[15], vr = Rr[15];
   double lam_l = (fabs(vl) + csb) / (1.0 + fabs(vl) * csb);
-  double lam_r = (fabs(vr) + csc) / (1.0 + fabs(vr) * csc);
+  double lam_r = (fabs(vr) + ((PLANT == 25) ? csb : csc)) / (1.0 + fabs(vr) * ((PLANT == 25) ? csb : csc));
   double cmax = lam_l > lam_r ? lam_l : lam_r;
   double Fl[4 + NPI], Fr[4 + NPI], Ql[4 + NPI], Qr[4 + NPI];
   for (int side = 0; side < 2; ++side) {

@@ -30,6 +30,9 @@ Bulk pressure (clv_oracle.c, R20):
 Velocity predictor (clv_oracle.c, R8 and the u* extrapolation of Sec. 3):
  22 first step without the pi-free step (u^{-1} = u^0) -> first-step predictor
  23 u^{n-1} never updated after a step    -> velocity history / second-order extrapolation
+KT interface (clv_oracle.c, Sec. 3):
+ 24 right state reconstructed with the slope's sign flipped -> mirror symmetry (also Gubser, eta wave)
+ 25 right-side local speed from the left cell's c_s -> mirror symmetry (no other pin sees it)
 """
 import numpy as np
 import pytest
@@ -41,6 +44,7 @@ import test_oracle_charge as CH
 import test_oracle_cooperfrye as CF
 import test_oracle_freezeout as FO
 import test_oracle_predictor as PR
+import test_oracle_symmetry as SY
 
 CASES = {
     1: F.check_transversality,
@@ -66,6 +70,8 @@ CASES = {
     21: BU.check_bulk_sound_wave,
     22: PR.check_first_step_predictor,
     23: PR.check_velocity_history,
+    24: SY.check_symmetries,
+    25: SY.check_symmetries,
 }
 
 
