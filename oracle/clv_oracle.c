@@ -364,7 +364,7 @@ static void source_pi(double g, const double u[4], const double du[16], const do
 #define RHO_MAX 1.0
 #define VISC_EPS_MIN 1e-3
 static double visc_ramp(double e) {
-  double r = e / VISC_EPS_MIN - 1.0;
+  double r = e / VISC_EPS_MIN - ((PLANT == 27) ? 0.0 : 1.0);
   return r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
 }
 static void regulate_pi(const orc_t* h, double e, double* pi) {
@@ -379,7 +379,7 @@ static void regulate_pi(const orc_t* h, double e, double* pi) {
       double v = pi[PI_IDX[m][n]];
       pp += GT[m] * GT[n] * v * v;
     }
-  double bound2 = RHO_MAX * RHO_MAX * (e * e + 3.0 * P * P);
+  double bound2 = RHO_MAX * RHO_MAX * (e * e + ((PLANT == 26) ? 0.0 : 3.0) * P * P);
   double a = fabs(pp);
   if (a > bound2) {
     double f = (bound2 > 0.0) ? sqrt(bound2 / a) : 0.0;

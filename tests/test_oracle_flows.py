@@ -269,6 +269,10 @@ def test_thread_count_does_not_change_bits():
 
 # ------------------------------------------------------- shear regulator
 def test_shear_regulator_caps_oversized_pi():
+    check_regulator_cap()
+
+
+def check_regulator_cap(plant=0):
     """Reading R18: after a stage, |pi_{mu nu} pi^{mu nu}| <= eps^2 + 3 P^2
     (eps, P of the stage input).  Uniform Bjorken cells with an initial
     pi~^{xx} = pi~^{yy} = -pi~^{ee}/2 ten times eps: the first stage scales pi
@@ -279,7 +283,7 @@ def test_shear_regulator_caps_oversized_pi():
     pi = np.zeros((10, n, n, n))
     pi[4] = pi[7] = 10 * e0
     pi[9] = -20 * e0
-    o = oracle.Oracle(n, n, n, 0.3, 0.3, 0.3, 1.0, 0.01, eta_over_s=0.16, periodic=True)
+    o = oracle.Oracle(n, n, n, 0.3, 0.3, 0.3, 1.0, 0.01, eta_over_s=0.16, periodic=True, plant=plant)
     o.set_initial(e, z, z, z, pi)
     o.step(1)
     f = o.fields()
@@ -294,7 +298,38 @@ def test_shear_regulator_caps_oversized_pi():
     assert np.all(np.isfinite(f["eps"])) and np.all(f["eps"] > 0)
 
 
+def test_shear_regulator_cap_is_exact_in_a_static_box():
+    check_regulator_cap_exact()
+
+
+def check_regulator_cap_exact(plant=0):
+    """Reading R18's cap in a static, uniform Cartesian box: no gradient, so
+    T~ and eps stay put (pi~^{tau mu} = 0 at rest) and only the relaxation
+    acts on pi.  With pi~^{xx} = pi~^{yy} = -pi~^{zz}/2 ten times eps, both
+    stages exceed the bound, so after the step |pi_{mu nu} pi^{mu nu}| sits
+    exactly on eps^2 + 3 P^2 of the (unchanged) eps, the conformal P = eps/3."""
+    n, e0 = 2, 10.0
+    e = np.full((n, n, n), e0)
+    z = np.zeros_like(e)
+    pi = np.zeros((10, n, n, n))
+    pi[4] = pi[7] = 10 * e0
+    pi[9] = -20 * e0
+    o = oracle.Oracle(n, n, n, 0.3, 0.3, 0.3, 1.0, 0.01, eta_over_s=0.16, cartesian=True, periodic=True,
+                      plant=plant)
+    o.set_initial(e, z, z, z, pi)
+    o.step(1)
+    f = o.fields()
+    np.testing.assert_allclose(f["eps"], e0, rtol=1e-14)
+    pp = f["pixx"] ** 2 + f["piyy"] ** 2 + f["piee"] ** 2
+    np.testing.assert_allclose(np.sqrt(pp), np.sqrt(e0 ** 2 + 3 * (e0 / 3) ** 2), rtol=1e-12)
+    np.testing.assert_allclose(f["pixx"] / f["piee"], -0.5, rtol=1e-12)     # the cap scales, keeps the shape
+
+
 def test_shear_regulator_ramp_static_box():
+    check_regulator_ramp()
+
+
+def check_regulator_ramp(plant=0):
     """Reading R18's ramp r(eps) = clamp(eps/1e-3 - 1, 0, 1).  In a static,
     uniform Cartesian box every gradient vanishes, T~ and eps stay put, and
     the IS equation reduces to d pi/dt = -pi/tau_pi.  One Heun step with the
@@ -308,7 +343,8 @@ def test_shear_regulator_ramp_static_box():
         z = np.zeros_like(e)
         pi = np.zeros((10, n, n, n))
         pi[5] = a
-        o = oracle.Oracle(n, n, n, 0.3, 0.3, 0.3, 1.0, h, eta_over_s=0.16, cartesian=True, periodic=True)
+        o = oracle.Oracle(n, n, n, 0.3, 0.3, 0.3, 1.0, h, eta_over_s=0.16, cartesian=True, periodic=True,
+                          plant=plant)
         o.set_initial(e, z, z, z, pi)
         o.step(1)
         f = o.fields()

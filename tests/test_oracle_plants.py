@@ -33,6 +33,9 @@ Velocity predictor (clv_oracle.c, R8 and the u* extrapolation of Sec. 3):
 KT interface (clv_oracle.c, Sec. 3):
  24 right state reconstructed with the slope's sign flipped -> mirror symmetry (also Gubser, eta wave)
  25 right-side local speed from the left cell's c_s -> mirror symmetry (no other pin sees it)
+Shear regulator (clv_oracle.c, R18):
+ 26 the cap's bound without its 3 P^2 term -> exact cap in a static box
+ 27 the ramp without its offset (eps/1e-3 instead of eps/1e-3 - 1) -> static-box ramp
 """
 import numpy as np
 import pytest
@@ -72,6 +75,8 @@ CASES = {
     23: PR.check_velocity_history,
     24: SY.check_symmetries,
     25: SY.check_symmetries,
+    26: F.check_regulator_cap_exact,
+    27: F.check_regulator_ramp,
 }
 
 
