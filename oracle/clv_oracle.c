@@ -189,7 +189,8 @@ static void eos_eval(const orc_t* h, double e, double* P, double* T, double* cs2
   if (h->c.eos_kind == 0) {
     *P = e / 3.0;
     *cs2 = 1.0 / 3.0;
-    *T = (e > 0.0) ? pow(30.0 * HBARC * HBARC * HBARC * e / (DOF_CONF * M_PI * M_PI), 0.25) : 0.0;
+    *T = (e > 0.0) ? pow(((PLANT == 29) ? 90.0 : 30.0) * HBARC * HBARC * HBARC * e / (DOF_CONF * M_PI * M_PI), 0.25)
+                   : 0.0;
     return;
   }
   if (!(e > 0.0)) { *P = 0.0; *T = 0.0; *cs2 = h->eosC[0]; return; }
@@ -214,7 +215,7 @@ static void eos_eval(const orc_t* h, double e, double* P, double* T, double* cs2
   int k = (int)floor(x);
   if (k > n - 2) k = n - 2;
   double w = x - (double)k;
-  *P = (1.0 - w) * h->eosP[k] + w * h->eosP[k + 1];
+  *P = (PLANT == 28) ? w * h->eosP[k] + (1.0 - w) * h->eosP[k + 1] : (1.0 - w) * h->eosP[k] + w * h->eosP[k + 1];
   *T = (1.0 - w) * h->eosT[k] + w * h->eosT[k + 1];
   *cs2 = (1.0 - w) * h->eosC[k] + w * h->eosC[k + 1];
 }

@@ -26,11 +26,15 @@ def make(eos=None, **kw):
 
 
 def test_conformal_eos_stefan_boltzmann():
+    check_conformal_eos()
+
+
+def check_conformal_eos(plant=0):
     # Degrees of freedom of a u, d, s quark-gluon gas: 2*8 gluon states and
     # 7/8 * (2 spin * 2 particle/antiparticle * 3 colour * 3 flavour) quark states.
     g = 2 * 8 + 7.0 / 8.0 * (2 * 2 * 3 * 3)
     assert g == 47.5
-    o = make()
+    o = make(plant=plant)
     for T in (0.1, 0.137, 0.3, 0.6):
         P_sb = g * math.pi ** 2 / 90.0 * T ** 4 / HBARC ** 3   # Stefan-Boltzmann pressure
         eps = 3 * P_sb
@@ -42,7 +46,12 @@ def test_conformal_eos_stefan_boltzmann():
 
 
 def test_table_eos_interpolation_against_numpy(eos_table):
-    o = make(eos_table)
+    check_table_eos(eos_table)
+
+
+def check_table_eos(eos_table=None, plant=0):
+    eos_table = eos_table if eos_table is not None else I.crossover_eos_table()
+    o = make(eos_table, plant=plant)
     rng = np.random.default_rng(3)
     lne_nodes = eos_table["lne0"] + eos_table["dlne"] * np.arange(len(eos_table["P"]))
     for lne in rng.uniform(lne_nodes[0], lne_nodes[-1], 400):

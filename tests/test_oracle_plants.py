@@ -36,6 +36,9 @@ KT interface (clv_oracle.c, Sec. 3):
 Shear regulator (clv_oracle.c, R18):
  26 the cap's bound without its 3 P^2 term -> exact cap in a static box
  27 the ramp without its offset (eps/1e-3 instead of eps/1e-3 - 1) -> static-box ramp
+Equation of state (clv_oracle.c, Sec. 3):
+ 28 table interpolation weights swapped for P -> numpy.interp on the nodes
+ 29 conformal T from eps with 90 in place of 30 -> Stefan-Boltzmann law
 """
 import numpy as np
 import pytest
@@ -46,6 +49,7 @@ import test_oracle_bulk as BU
 import test_oracle_charge as CH
 import test_oracle_cooperfrye as CF
 import test_oracle_freezeout as FO
+import test_oracle_eos_prim as EP
 import test_oracle_predictor as PR
 import test_oracle_symmetry as SY
 
@@ -77,6 +81,8 @@ CASES = {
     25: SY.check_symmetries,
     26: F.check_regulator_cap_exact,
     27: F.check_regulator_ramp,
+    28: EP.check_table_eos,
+    29: EP.check_conformal_eos,
 }
 
 
