@@ -851,7 +851,8 @@ int orc_set_initial_T(orc_t* h, const double* T) {
   for (size_t l = 0; l < N; ++l) {
     double e, u[4];
     int resc;
-    if (prim_solve(h, T[l], T[N + l], T[2 * N + l], T[3 * N + l], 0.0, &e, u, &resc) < 0) fail = 1;
+    const double Mx = T[((PLANT == 30) ? 2 : 1) * N + l], My = T[((PLANT == 30) ? 1 : 2) * N + l];
+    if (prim_solve(h, T[l], Mx, My, T[3 * N + l], 0.0, &e, u, &resc) < 0) fail = 1;
     a[l] = e;
     a[N + l] = u[1];
     a[2 * N + l] = u[2];

@@ -9,9 +9,9 @@ import oracle
 from paper_1802_04449_gb300 import inputs as I
 
 
-def _oracle(case, eos):
+def _oracle(case, eos, plant=0):
     return oracle.Oracle(case.nx, case.ny, case.neta, case.dx, case.dy, case.deta, case.tau0, case.dtau,
-                         case.eta_over_s, eos, nthreads=2)
+                         case.eta_over_s, eos, nthreads=2, plant=plant)
 
 
 def _T_of(o, eps, u1, u2, u3):
@@ -25,10 +25,14 @@ def _T_of(o, eps, u1, u2, u3):
 
 @pytest.mark.parametrize("eos", ["crossover", None])
 def test_primitives_reproduce_the_input_T(eos):
+    check_reproduce_T(eos)
+
+
+def check_reproduce_T(eos="crossover", plant=0):
     case = I.hotspot_event(nx=13, ny=11, neta=7, n_spots=25, seed=4, eos=eos)
     rng = np.random.default_rng(8)
     u = [0.6 * rng.uniform(-1, 1, case.eps.shape) for _ in range(3)]
-    o = _oracle(case, case.eos)
+    o = _oracle(case, case.eos, plant)
     T = _T_of(o, case.eps, *u)
     o.set_initial_T(T)
     live = case.eps >= 1e-7

@@ -39,6 +39,8 @@ Shear regulator (clv_oracle.c, R18):
 Equation of state (clv_oracle.c, Sec. 3):
  28 table interpolation weights swapped for P -> numpy.interp on the nodes
  29 conformal T from eps with 90 in place of 30 -> Stefan-Boltzmann law
+Initial state from T^{tau mu} (clv_oracle.c):
+ 30 T^{tau x} and T^{tau y} swapped on the way to the root solve -> perfect-fluid round trip
 """
 import numpy as np
 import pytest
@@ -50,6 +52,7 @@ import test_oracle_charge as CH
 import test_oracle_cooperfrye as CF
 import test_oracle_freezeout as FO
 import test_oracle_eos_prim as EP
+import test_oracle_initial_T as IT
 import test_oracle_predictor as PR
 import test_oracle_symmetry as SY
 
@@ -83,6 +86,7 @@ CASES = {
     27: F.check_regulator_ramp,
     28: EP.check_table_eos,
     29: EP.check_conformal_eos,
+    30: IT.check_reproduce_T,
 }
 
 
